@@ -1,0 +1,128 @@
+/*
+ * libdpd — augmented-parallel-Hammerstein (APH) digital predistortion on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The filter is the joint PA / I/Q-modulator predistorter of Li et al.,
+ * "Parallel Digital Predistortion Design on Mobile GPU and Embedded Multicore
+ * CPU for Mobile Transmitters" (Eq. 1, Algorithm 1):
+ *
+ *   y_n = sum_{p in I_P} sum_{k=0}^{M} h_{p,k}    |x_{n-k}|^{p-1} x_{n-k}
+ *       + sum_{q in I_Q} sum_{k=0}^{M} hbar_{q,k} |x_{n-k}|^{q-1} conj(x_{n-k})
+ *       + c,
+ *
+ * I_P = {1, 3, ..., P}, I_Q = {1, 3, ..., Q}, every branch an FIR of L = M + 1
+ * taps, samples before x_0 taken as zero.  (The paper writes the input x and the
+ * output z; this library calls the output y.)  The paper's orthogonalising
+ * polynomial coefficients u_{m,p} (Sec. 2.1) are the identity here; a caller who
+ * wants them folds them into h, since the filter is linear in h.
+ *
+ * Data layout.  Samples are complex64: interleaved (re, im) float32 pairs, the
+ * layout of C99 `float complex`, `std::complex<float>` and torch.complex64.
+ * Coefficient vectors use the stacking order of Sec. 2.2:
+ *   h = [h_1[0..M], h_3[0..M], ..., h_P[0..M], hbar_1[0..M], ..., hbar_Q[0..M], c]
+ * so K = ((P+1)/2 + (Q+1)/2) * (M+1) + 1 complex values.
+ *
+ * Streams.  Every `stream` argument is a cudaStream_t passed as void* (NULL is
+ * the legacy default stream).  Device work is enqueued on it and the call
+ * returns without synchronising unless stated otherwise.  Call every function
+ * with the CUDA device that was current at dpd_create current.
+ *
+ * Errors.  Every call returns a dpd_status; nothing exits, aborts or traps.
+ * Argument errors are found on the host before any work is enqueued.  Errors
+ * raised by kernels (a bounded wait that ran out) are recorded in a per-handle
+ * device word that dpd_sync_status reads.
+ *
+ * Thread safety.  A handle may be used from one host thread at a time.
+ */
+#ifndef DPD_H
+#define DPD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dpd_status {
+    DPD_OK = 0,
+    DPD_ERR_INVALID_ARGUMENT = 1, /* bad pointer, size, order, overlap or alignment */
+    DPD_ERR_UNSUPPORTED = 2,      /* valid in principle but outside the built range */
+    DPD_ERR_NO_COEFFS = 3,        /* dpd_apply/dpd_grad before dpd_set_coeffs */
+    DPD_ERR_CUDA = 4,             /* a CUDA runtime call or launch failed */
+    DPD_ERR_ALLOC = 5,            /* device or host allocation failed */
+    DPD_ERR_NOT_SPD = 6,          /* least-squares Gram matrix not positive definite */
+    DPD_ERR_TIMEOUT = 7           /* a kernel's bounded wait ran out (device flag) */
+} dpd_status;
+
+/* Where a coefficient buffer lives. */
+enum { DPD_HOST = 0, DPD_DEVICE = 1 };
+
+typedef struct dpd_filter *dpd_handle;
+
+/*
+ * Create a filter for main-branch order P, conjugate-branch order Q and memory
+ * depth M (L = M + 1 taps per branch), on the current CUDA device.
+ *   P, Q : odd, 1..11, or 0 for "no such branch" (not both 0).  The paper uses
+ *          odd orders only (Sec. 2.1); even values give DPD_ERR_INVALID_ARGUMENT.
+ *   M    : 0..7 (1 to 8 taps).
+ * The handle owns its device memory (coefficients, their transformed form, an
+ * error word and the gradient workspace).  *out is set only on success.
+ */
+dpd_status dpd_create(int P, int Q, int M, dpd_handle *out);
+
+/* Release a handle and its device memory.  NULL is accepted.  The caller must
+ * make sure no work that uses the handle is still running. */
+dpd_status dpd_destroy(dpd_handle h);
+
+/* Number of complex coefficients K of the handle's model (Sec. 2.2). */
+dpd_status dpd_num_coeffs(dpd_handle h, int *K);
+
+/*
+ * Install the coefficient vector h (K complex64 values, stacking order of
+ * Sec. 2.2).  `where` is DPD_HOST or DPD_DEVICE.  Host buffers are copied
+ * before the call returns; device buffers are read by a kernel on `stream`, so
+ * they must stay valid until that kernel has run.  The caller keeps ownership.
+ * K must equal dpd_num_coeffs.  Work is ordered on `stream`: later calls on
+ * the same stream see the new coefficients.
+ */
+dpd_status dpd_set_coeffs(dpd_handle h, const void *coeffs, int K, int where, void *stream);
+
+/*
+ * Predistort n samples: y = DPD(x) (Eq. 1), zero history before x[0].
+ *   x, y : device pointers to n complex64 each, 8-byte aligned, owned by the
+ *          caller; the ranges must not overlap (DPD_ERR_INVALID_ARGUMENT).
+ *          16-byte alignment of both selects the bulk-copy (TMA) pipeline.
+ *   n    : >= 0; n == 0 returns DPD_OK and launches nothing.
+ * Allocates nothing and does not synchronise; safe to capture in a CUDA graph.
+ */
+dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stream);
+
+/*
+ * Launch shape of dpd_apply for this handle (used by the autotuner):
+ *   V           samples per thread, 2 or 4
+ *   warps       consumer warps per CTA, 1..16 (tile = warps*32*V samples)
+ *   stages      depth of the shared-memory bulk-copy ring, 2..8
+ *   ctas_per_sm CTAs per SM of the persistent grid, 0 = as many as fit
+ *   use_tma     1 = bulk-copy pipeline, 0 = plain global loads
+ * A shape that does not fit the device makes dpd_apply return DPD_ERR_CUDA.
+ */
+dpd_status dpd_set_fwd_launch(dpd_handle h, int V, int warps, int stages, int ctas_per_sm, int use_tma);
+
+/*
+ * Synchronise `stream`, then read and clear the handle's device error word.
+ * Returns DPD_ERR_TIMEOUT if a kernel recorded that a bounded wait ran out,
+ * DPD_ERR_CUDA if the stream reported an error, else DPD_OK.
+ */
+dpd_status dpd_sync_status(dpd_handle h, void *stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *dpd_status_string(dpd_status s);
+
+/* Number of kernels this library has launched in this process (all handles). */
+uint64_t dpd_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPD_H */

@@ -1,0 +1,129 @@
+"""GB300-native augmented-parallel-Hammerstein (APH) digital predistortion.
+
+Python face of ``libdpd.so`` (C ABI in ``include/dpd.h``).  Every step of the
+filter runs in the library's CUDA kernels; this module only checks tensor
+types and passes pointers, sizes and the current CUDA stream.  PyTorch supplies
+device memory and streams.
+
+    import torch, paper_1612_09001_gb300 as dpd
+    f = dpd.DPD(P=9, Q=9, M=4)
+    f.set_coeffs(h)                 # complex64, K values, stacking order of Sec. 2.2
+    y = f.apply(x)                  # x: complex64 CUDA tensor
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import DPDError, DPD_HOST, DPD_DEVICE  # noqa: F401
+
+__all__ = ["DPD", "DPDError", "num_coeffs", "kernel_launches", "lib"]
+
+
+def lib():
+    return _lib.load()
+
+
+def num_coeffs(P: int, Q: int, M: int) -> int:
+    bp = (P + 1) // 2 if P > 0 else 0
+    bq = (Q + 1) // 2 if Q > 0 else 0
+    return (bp + bq) * (M + 1) + 1
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libdpd in this process so far."""
+    return int(lib().dpd_kernel_launches())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_samples(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.complex64:
+        raise TypeError(f"{name} must be complex64, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class DPD:
+    """One APH predistorter: orders P (main) and Q (conjugate), memory depth M."""
+
+    def __init__(self, P: int, Q: int, M: int):
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        _lib.check("dpd_create", self._lib.dpd_create(P, Q, M, ctypes.byref(h)))
+        self._h = h
+        self.P, self.Q, self.M = P, Q, M
+        k = ctypes.c_int()
+        _lib.check("dpd_num_coeffs", self._lib.dpd_num_coeffs(self._h, ctypes.byref(k)))
+        self.K = k.value
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dpd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- coefficients
+    def set_coeffs(self, h, stream=None):
+        """Install K complex64 coefficients from a CUDA tensor, a CPU tensor or a numpy array."""
+        import numpy as np
+        import torch
+        if isinstance(h, np.ndarray):
+            h = torch.from_numpy(np.ascontiguousarray(h.astype(np.complex64)))
+        if not isinstance(h, torch.Tensor) or h.dtype != torch.complex64 or h.numel() != self.K:
+            raise ValueError(f"coefficients must be {self.K} complex64 values")
+        h = h.contiguous()
+        where = DPD_DEVICE if h.is_cuda else DPD_HOST
+        self._coef_ref = h   # keep a device source alive until the kernel that reads it has run
+        _lib.check("dpd_set_coeffs", self._lib.dpd_set_coeffs(
+            self._h, ctypes.c_void_p(h.data_ptr()), self.K, where, _stream_ptr(stream)))
+
+    # -- forward
+    def apply(self, x, out=None, stream=None):
+        """y = DPD(x) for a complex64 CUDA tensor (1-D or any shape, filtered as one stream)."""
+        import torch
+        _check_samples(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        else:
+            _check_samples(out, "out")
+            if out.numel() != x.numel():
+                raise ValueError("out must have as many elements as x")
+        _lib.check("dpd_apply", self._lib.dpd_apply(
+            self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+            x.numel(), _stream_ptr(stream)))
+        return out
+
+    def set_fwd_launch(self, V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1):
+        _lib.check("dpd_set_fwd_launch", self._lib.dpd_set_fwd_launch(
+            self._h, V, warps, stages, ctas_per_sm, use_tma))
+
+    def sync_status(self, stream=None):
+        """Synchronise the stream and raise if a kernel recorded an error."""
+        _lib.check("dpd_sync_status", self._lib.dpd_sync_status(self._h, _stream_ptr(stream)))

@@ -1,0 +1,211 @@
+// libdpd C ABI: handle management, argument checks and kernel dispatch.
+// Declarations and the contract of every entry point are in include/dpd.h.
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dpd.h"
+#include "dpd_internal.h"
+
+struct dpd_filter {
+    int P, Q, M;
+    int Bp, Bq, B, T, K;
+    int device;
+    int sm_count;
+    float2 *d_h;      // K complex coefficients, stacking order of Sec. 2.2
+    float *d_tab;     // widely-linear table for the forward kernels
+    int *d_status;    // kernel error word
+    bool has_coeffs;
+    dpd::FwdLaunch fwd;
+};
+
+namespace dpd {
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+cudaError_t launch_fwd_any(int B, int T, const FwdArgs &a, const FwdLaunch &L, int sm_count,
+                           cudaStream_t s)
+{
+    switch (B) {
+    case 1: return launch_fwd<1>(T, a, L, sm_count, s);
+    case 2: return launch_fwd<2>(T, a, L, sm_count, s);
+    case 3: return launch_fwd<3>(T, a, L, sm_count, s);
+    case 4: return launch_fwd<4>(T, a, L, sm_count, s);
+    case 5: return launch_fwd<5>(T, a, L, sm_count, s);
+    case 6: return launch_fwd<6>(T, a, L, sm_count, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace dpd
+
+namespace {
+
+int nbranch(int order) { return order > 0 ? (order + 1) / 2 : 0; }
+
+bool valid_order(int o) { return o == 0 || (o > 0 && o <= 11 && (o % 2) == 1); }
+
+bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+bool overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+dpd_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DPD_OK : DPD_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+const char *dpd_status_string(dpd_status s)
+{
+    switch (s) {
+    case DPD_OK: return "DPD_OK";
+    case DPD_ERR_INVALID_ARGUMENT: return "DPD_ERR_INVALID_ARGUMENT";
+    case DPD_ERR_UNSUPPORTED: return "DPD_ERR_UNSUPPORTED";
+    case DPD_ERR_NO_COEFFS: return "DPD_ERR_NO_COEFFS";
+    case DPD_ERR_CUDA: return "DPD_ERR_CUDA";
+    case DPD_ERR_ALLOC: return "DPD_ERR_ALLOC";
+    case DPD_ERR_NOT_SPD: return "DPD_ERR_NOT_SPD";
+    case DPD_ERR_TIMEOUT: return "DPD_ERR_TIMEOUT";
+    }
+    return "DPD_ERR_UNKNOWN";
+}
+
+uint64_t dpd_kernel_launches(void) { return dpd::g_launches.load(std::memory_order_relaxed); }
+
+dpd_status dpd_create(int P, int Q, int M, dpd_handle *out)
+{
+    if (!out) return DPD_ERR_INVALID_ARGUMENT;
+    if (!valid_order(P) || !valid_order(Q) || (P == 0 && Q == 0)) return DPD_ERR_INVALID_ARGUMENT;
+    if (M < 0 || M + 1 > dpd::kMaxT) return DPD_ERR_INVALID_ARGUMENT;
+    dpd_filter *f = new (std::nothrow) dpd_filter();
+    if (!f) return DPD_ERR_ALLOC;
+    f->P = P;
+    f->Q = Q;
+    f->M = M;
+    f->Bp = nbranch(P);
+    f->Bq = nbranch(Q);
+    f->B = f->Bp > f->Bq ? f->Bp : f->Bq;
+    f->T = M + 1;
+    f->K = (f->Bp + f->Bq) * f->T + 1;
+    f->has_coeffs = false;
+    if (cudaGetDevice(&f->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&f->sm_count, cudaDevAttrMultiProcessorCount, f->device) != cudaSuccess) {
+        delete f;
+        return DPD_ERR_CUDA;
+    }
+    if (cudaMalloc(&f->d_h, sizeof(float2) * f->K) != cudaSuccess ||
+        cudaMalloc(&f->d_tab, sizeof(float) * dpd::wl_table_floats(f->B, f->T)) != cudaSuccess ||
+        cudaMalloc(&f->d_status, sizeof(int)) != cudaSuccess) {
+        cudaFree(f->d_h);
+        cudaFree(f->d_tab);
+        cudaFree(f->d_status);
+        delete f;
+        return DPD_ERR_ALLOC;
+    }
+    if (cudaMemset(f->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(f->d_h);
+        cudaFree(f->d_tab);
+        cudaFree(f->d_status);
+        delete f;
+        return DPD_ERR_CUDA;
+    }
+    *out = f;
+    return DPD_OK;
+}
+
+dpd_status dpd_destroy(dpd_handle h)
+{
+    if (!h) return DPD_OK;
+    cudaFree(h->d_h);
+    cudaFree(h->d_tab);
+    cudaFree(h->d_status);
+    delete h;
+    return DPD_OK;
+}
+
+dpd_status dpd_num_coeffs(dpd_handle h, int *K)
+{
+    if (!h || !K) return DPD_ERR_INVALID_ARGUMENT;
+    *K = h->K;
+    return DPD_OK;
+}
+
+dpd_status dpd_set_coeffs(dpd_handle h, const void *coeffs, int K, int where, void *stream)
+{
+    if (!h || !coeffs || K != h->K) return DPD_ERR_INVALID_ARGUMENT;
+    if (where != DPD_HOST && where != DPD_DEVICE) return DPD_ERR_INVALID_ARGUMENT;
+    if (!aligned(coeffs, 4)) return DPD_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float2 *src = static_cast<const float2 *>(coeffs);
+    if (where == DPD_HOST) {
+        cudaError_t e = cudaMemcpyAsync(h->d_h, coeffs, sizeof(float2) * K, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return DPD_ERR_CUDA;
+        src = h->d_h;
+    } else if (!aligned(coeffs, 8)) {
+        return DPD_ERR_INVALID_ARGUMENT;
+    } else if (src != h->d_h) {
+        cudaError_t e = cudaMemcpyAsync(h->d_h, coeffs, sizeof(float2) * K, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return DPD_ERR_CUDA;
+        src = h->d_h;
+    }
+    cudaError_t e = dpd::launch_wl_table(src, h->Bp, h->Bq, h->T, h->d_tab, s);
+    if (e != cudaSuccess) return DPD_ERR_CUDA;
+    h->has_coeffs = true;
+    return DPD_OK;
+}
+
+dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stream)
+{
+    if (!h || n < 0) return DPD_ERR_INVALID_ARGUMENT;
+    if (!h->has_coeffs) return DPD_ERR_NO_COEFFS;
+    if (n == 0) return DPD_OK;
+    if (!x || !y || !aligned(x, 8) || !aligned(y, 8)) return DPD_ERR_INVALID_ARGUMENT;
+    if (n > (int64_t)(INT64_MAX / sizeof(float2))) return DPD_ERR_INVALID_ARGUMENT;
+    const size_t bytes = (size_t)n * sizeof(float2);
+    if (overlap(x, bytes, y, bytes)) return DPD_ERR_INVALID_ARGUMENT;
+    dpd::FwdArgs a;
+    a.x = static_cast<const float2 *>(x);
+    a.y = static_cast<float2 *>(y);
+    a.n = n;
+    a.tab = h->d_tab;
+    a.status = h->d_status;
+    a.vec_store = aligned(y, 16) ? 1 : 0;
+    dpd::FwdLaunch L = h->fwd;
+    if (!aligned(x, 16)) L.use_tma = 0;
+    return cuda_status(dpd::launch_fwd_any(h->B, h->T, a, L, h->sm_count, static_cast<cudaStream_t>(stream)));
+}
+
+dpd_status dpd_set_fwd_launch(dpd_handle h, int V, int warps, int stages, int ctas_per_sm, int use_tma)
+{
+    if (!h) return DPD_ERR_INVALID_ARGUMENT;
+    if ((V != 2 && V != 4) || warps < 1 || warps > 16 || stages < 2 || stages > 8 || ctas_per_sm < 0 ||
+        (use_tma != 0 && use_tma != 1))
+        return DPD_ERR_INVALID_ARGUMENT;
+    h->fwd.V = V;
+    h->fwd.warps = warps;
+    h->fwd.stages = stages;
+    h->fwd.ctas_per_sm = ctas_per_sm;
+    h->fwd.use_tma = use_tma;
+    return DPD_OK;
+}
+
+dpd_status dpd_sync_status(dpd_handle h, void *stream)
+{
+    if (!h) return DPD_ERR_INVALID_ARGUMENT;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return DPD_ERR_CUDA;
+    int flags = 0;
+    if (cudaMemcpy(&flags, h->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DPD_ERR_CUDA;
+    if (flags && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) return DPD_ERR_CUDA;
+    if (flags & dpd::kFlagTimeout) return DPD_ERR_TIMEOUT;
+    if (flags) return DPD_ERR_CUDA;
+    return DPD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,319 @@
+// Forward APH DPD filter kernels (Eq. 1 / Algorithm 1), templated on the
+// branch count B = max((P+1)/2, (Q+1)/2), the tap count T = M + 1 and the
+// number V of consecutive samples each thread produces.
+//
+// Arithmetic.  Per tap k the main and conjugate branches of Algorithm 1 are
+// regrouped into a widely-linear form: with r = |x|^2,
+//   sum_p h_{p,k} |x|^{p-1} x + sum_q hbar_{q,k} |x|^{q-1} conj(x)
+//     = A_k(r) x + C_k(r) conj(x)
+//     = (P0(r) a + P1(r) b) + j (P2(r) a + P3(r) b),   x = a + j b,
+// four real polynomials of degree B-1 evaluated by Horner's rule: 4B fused
+// multiply-adds per (sample, tap) instead of 8B for the complex products.  The
+// polynomial basis is formed from r without a square root, lowest order first
+// (Sec. 3.2.1).
+//
+// Data movement.  The TMA kernel is persistent: each CTA walks tiles of
+// S = warps*32*V samples.  One producer thread streams every tile, together
+// with the kHalo samples in front of it (the filter history, Eq. 2's shifted
+// rows), into a ring of shared-memory slots with one-dimensional bulk copies
+// completed on mbarriers; consumer warps read their window from shared memory,
+// release the slot and write the outputs with 16-byte streaming stores.  No
+// lane is redundant: the history comes from the staged halo instead of the
+// overlapping warps of the paper's Sec. 3.3.2 design.
+#pragma once
+
+#include "dpd_device.cuh"
+#include "dpd_internal.h"
+
+namespace dpd {
+
+template <int B, int T, int V>
+__device__ __forceinline__ void fwd_compute(const float *__restrict__ tab,
+                                            const float (&wr)[V + T - 1],
+                                            const float (&wi)[V + T - 1], float (&yr)[V],
+                                            float (&yi)[V])
+{
+    constexpr int W = V + T - 1;
+    float r[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) r[j] = fmaf(wr[j], wr[j], wi[j] * wi[j]);
+    const float cr = tab[4 * B * T], ci = tab[4 * B * T + 1];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        yr[v] = cr;
+        yi[v] = ci;
+    }
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+        float cf[4 * B];
+        const float4 *t4 = reinterpret_cast<const float4 *>(tab + 4 * B * k);
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const float4 q = t4[i];
+            cf[4 * i + 0] = q.x;
+            cf[4 * i + 1] = q.y;
+            cf[4 * i + 2] = q.z;
+            cf[4 * i + 3] = q.w;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int j = v + (T - 1) - k;   // window index of sample n - k
+            float p0 = cf[0 * B + B - 1], p1 = cf[1 * B + B - 1];
+            float p2 = cf[2 * B + B - 1], p3 = cf[3 * B + B - 1];
+#pragma unroll
+            for (int m = B - 2; m >= 0; --m) {
+                p0 = fmaf(p0, r[j], cf[0 * B + m]);
+                p1 = fmaf(p1, r[j], cf[1 * B + m]);
+                p2 = fmaf(p2, r[j], cf[2 * B + m]);
+                p3 = fmaf(p3, r[j], cf[3 * B + m]);
+            }
+            yr[v] = fmaf(p0, wr[j], yr[v]);
+            yr[v] = fmaf(p1, wi[j], yr[v]);
+            yi[v] = fmaf(p2, wr[j], yi[v]);
+            yi[v] = fmaf(p3, wi[j], yi[v]);
+        }
+    }
+}
+
+template <int B, int T>
+__host__ __device__ constexpr int tab_bytes()
+{
+    return ((wl_table_floats(B, T) * 4 + 127) / 128) * 128;
+}
+
+// Shared-memory bytes of the TMA kernel for a given launch shape.
+template <int B, int T, int V>
+__host__ __device__ constexpr size_t fwd_tma_smem(int warps, int stages)
+{
+    return (size_t)tab_bytes<B, T>() + 128 +
+           (size_t)stages * (size_t)(kHalo + warps * 32 * V) * sizeof(float2);
+}
+
+template <int B, int T, int V>
+__global__ void __launch_bounds__(32 * 17) fwd_tma_kernel(FwdArgs a, int stages, int64_t ntiles)
+{
+    constexpr int W = V + T - 1;
+    constexpr int TABF = wl_table_floats(B, T);
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *tab = reinterpret_cast<float *>(smem);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + tab_bytes<B, T>());   // full[s], empty[s]
+    float2 *ring = reinterpret_cast<float2 *>(smem + tab_bytes<B, T>() + 128);
+
+    const int nwarps = blockDim.x / 32 - 1;   // consumer warps; the last warp produces
+    const int S = nwarps * 32 * V;
+    const int slot_elems = kHalo + S;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int i = tid; i < TABF; i += blockDim.x) tab[i] = a.tab[i];
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(smem_addr(&bars[s]), 1);
+            mbar_init(smem_addr(&bars[stages + s]), nwarps);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == nwarps) {
+        // ---------------------------------------------------------------- producer
+        if (lane != 0) return;
+        const uint64_t pol = policy_evict_first();
+        int64_t it = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int s = (int)(it % stages);
+            const uint32_t ph = (uint32_t)((it / stages) & 1);
+            if (it >= stages && !mbar_wait(smem_addr(&bars[stages + s]), ph ^ 1u, a.status)) {
+                ok = false;
+                break;
+            }
+            const int64_t s0 = tile * S;
+            int64_t lo = s0 - kHalo;
+            int off = 0;
+            if (lo < 0) {
+                off = (int)(-lo);
+                lo = 0;
+            }
+            const int64_t hi = (s0 + S < a.n) ? s0 + S : a.n;
+            const int64_t cnt = (hi - lo) & ~int64_t(1);   // whole 16-byte units
+            const uint32_t bytes = (uint32_t)(cnt * (int64_t)sizeof(float2));
+            const uint32_t fb = smem_addr(&bars[s]);
+            mbar_arrive_expect_tx(fb, bytes);
+            if (bytes)
+                bulk_copy_g2s_stream(smem_addr(ring + (size_t)s * slot_elems + off), a.x + lo, bytes,
+                                     fb, pol);
+        }
+        if (!ok) {
+            // Let the copies already issued land before the CTA exits.
+            const int64_t first = it > stages ? it - stages : 0;
+            for (int64_t j = first; j < it; ++j)
+                mbar_wait(smem_addr(&bars[j % stages]), (uint32_t)((j / stages) & 1), a.status);
+        }
+        return;
+    }
+
+    // -------------------------------------------------------------------- consumers
+    const int t_in_tile = warp * 32 + lane;
+    int64_t it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int s = (int)(it % stages);
+        const uint32_t ph = (uint32_t)((it / stages) & 1);
+        if (!mbar_wait(smem_addr(&bars[s]), ph, a.status)) return;
+        const float2 *slot = ring + (size_t)s * slot_elems;
+        const int64_t s0 = tile * S;
+        const int64_t g0 = s0 + (int64_t)t_in_tile * V;
+        const int64_t lo = (s0 - kHalo > 0) ? s0 - kHalo : 0;
+        const int64_t hi = (s0 + S < a.n) ? s0 + S : a.n;
+        const int64_t vhi = lo + ((hi - lo) & ~int64_t(1));
+        const bool full = (s0 >= kHalo) && (s0 + S <= vhi);
+        float wr[W], wi[W];
+        if (full) {
+            constexpr int MP = ((T - 1) + 1) & ~1;   // history rounded up to a 16-byte unit
+            constexpr int E = V + MP;
+            constexpr int D = MP - (T - 1);
+            const float4 *src = reinterpret_cast<const float4 *>(slot + t_in_tile * V + kHalo - MP);
+            float er[E], ei[E];
+#pragma unroll
+            for (int i = 0; i < E / 2; ++i) {
+                const float4 q = src[i];
+                er[2 * i] = q.x;
+                ei[2 * i] = q.y;
+                er[2 * i + 1] = q.z;
+                ei[2 * i + 1] = q.w;
+            }
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                wr[j] = er[j + D];
+                wi[j] = ei[j + D];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const int64_t g = g0 - (T - 1) + j;
+                float2 v = make_float2(0.f, 0.f);
+                if (g >= lo && g < vhi)
+                    v = slot[g - (s0 - kHalo)];
+                else if (g >= 0 && g < a.n)
+                    v = a.x[g];
+                wr[j] = v.x;
+                wi[j] = v.y;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));
+
+        float yr[V], yi[V];
+        fwd_compute<B, T, V>(tab, wr, wi, yr, yi);
+        if (full && a.vec_store) {
+            float4 *yp = reinterpret_cast<float4 *>(a.y + g0);
+#pragma unroll
+            for (int i = 0; i < V / 2; ++i)
+                st_stream_f4(yp + i, make_float4(yr[2 * i], yi[2 * i], yr[2 * i + 1], yi[2 * i + 1]));
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (g0 + v < a.n) a.y[g0 + v] = make_float2(yr[v], yi[v]);
+        }
+    }
+}
+
+// Plain-load variant: every thread reads its window straight from global
+// memory (through L1).  Used for buffers that are only 8-byte aligned and as
+// the no-TMA baseline.
+template <int B, int T, int V>
+__global__ void __launch_bounds__(256) fwd_ldg_kernel(FwdArgs a)
+{
+    constexpr int W = V + T - 1;
+    constexpr int TABF = wl_table_floats(B, T);
+    __shared__ __align__(16) float tab[((TABF + 3) / 4) * 4];
+    for (int i = threadIdx.x; i < TABF; i += blockDim.x) tab[i] = a.tab[i];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * V;
+    for (int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V; g0 < a.n; g0 += stride) {
+        float wr[W], wi[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int64_t g = g0 - (T - 1) + j;
+            float2 v = make_float2(0.f, 0.f);
+            if (g >= 0 && g < a.n) v = __ldg(a.x + g);
+            wr[j] = v.x;
+            wi[j] = v.y;
+        }
+        float yr[V], yi[V];
+        fwd_compute<B, T, V>(tab, wr, wi, yr, yi);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if (g0 + v < a.n) a.y[g0 + v] = make_float2(yr[v], yi[v]);
+    }
+}
+
+template <int B, int T, int V>
+cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cudaStream_t s)
+{
+    if (L.use_tma) {
+        const int threads = (L.warps + 1) * 32;
+        const int S = L.warps * 32 * V;
+        const int64_t ntiles = (a.n + S - 1) / S;
+        const size_t smem = fwd_tma_smem<B, T, V>(L.warps, L.stages);
+        auto kern = fwd_tma_kernel<B, T, V>;
+        static size_t smem_set = 0;   // per instantiation
+        if (smem > smem_set) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            smem_set = smem;
+        }
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        const int cps = (L.ctas_per_sm > 0 && L.ctas_per_sm < occ) ? L.ctas_per_sm : occ;
+        int64_t grid = (int64_t)sm_count * cps;
+        if (grid > ntiles) grid = ntiles;
+        kern<<<(unsigned)grid, threads, smem, s>>>(a, L.stages, ntiles);
+        count_launch();
+        return cudaGetLastError();
+    }
+    const int threads = 256;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fwd_ldg_kernel<B, T, V>,
+                                                                  threads, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const int64_t need = (a.n + (int64_t)threads * V - 1) / ((int64_t)threads * V);
+    int64_t grid = (int64_t)sm_count * occ;
+    if (grid > need) grid = need;
+    fwd_ldg_kernel<B, T, V><<<(unsigned)grid, threads, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int B, int T>
+cudaError_t launch_fwd_t(const FwdArgs &a, const FwdLaunch &L, int sm_count, cudaStream_t s)
+{
+    switch (L.V) {
+    case 2: return launch_fwd_tv<B, T, 2>(a, L, sm_count, s);
+    case 4: return launch_fwd_tv<B, T, 4>(a, L, sm_count, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+#define DPD_DEFINE_LAUNCH_FWD(BB)                                                                  \
+    template <>                                                                                    \
+    cudaError_t launch_fwd<BB>(int T, const FwdArgs &a, const FwdLaunch &L, int sm_count,         \
+                               cudaStream_t s)                                                     \
+    {                                                                                              \
+        switch (T) {                                                                               \
+        case 1: return launch_fwd_t<BB, 1>(a, L, sm_count, s);                                     \
+        case 2: return launch_fwd_t<BB, 2>(a, L, sm_count, s);                                     \
+        case 3: return launch_fwd_t<BB, 3>(a, L, sm_count, s);                                     \
+        case 4: return launch_fwd_t<BB, 4>(a, L, sm_count, s);                                     \
+        case 5: return launch_fwd_t<BB, 5>(a, L, sm_count, s);                                     \
+        case 6: return launch_fwd_t<BB, 6>(a, L, sm_count, s);                                     \
+        case 7: return launch_fwd_t<BB, 7>(a, L, sm_count, s);                                     \
+        case 8: return launch_fwd_t<BB, 8>(a, L, sm_count, s);                                     \
+        default: return cudaErrorInvalidValue;                                                     \
+        }                                                                                          \
+    }
+
+}  // namespace dpd

@@ -1,0 +1,6 @@
+// Forward-filter instantiations for B = 1 branch pairs (orders up to 1).
+#include "dpd_fwd.cuh"
+
+namespace dpd {
+DPD_DEFINE_LAUNCH_FWD(1)
+}  // namespace dpd

@@ -1,0 +1,6 @@
+// Forward-filter instantiations for B = 2 branch pairs (orders up to 3).
+#include "dpd_fwd.cuh"
+
+namespace dpd {
+DPD_DEFINE_LAUNCH_FWD(2)
+}  // namespace dpd

@@ -1,0 +1,6 @@
+// Forward-filter instantiations for B = 3 branch pairs (orders up to 5).
+#include "dpd_fwd.cuh"
+
+namespace dpd {
+DPD_DEFINE_LAUNCH_FWD(3)
+}  // namespace dpd

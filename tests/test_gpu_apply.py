@@ -1,0 +1,180 @@
+"""GPU parity of dpd_apply (Eq. 1 / Algorithm 1) against the FP64 oracle.
+
+Every case runs the CUDA path through the C ABI (paper_1612_09001_gb300.DPD)
+and the oracle on the same seeded complex64 inputs, and compares element by
+element (normwise relative error and max element error <= 1e-5)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import dpd_synth as synth
+import oracle
+from util import assert_parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1612_09001_gb300 as dpd  # noqa: E402
+from paper_1612_09001_gb300 import _lib  # noqa: E402
+
+
+def run_gpu(x, h, P, Q, M, launch=None, offset=0, out_offset=0):
+    f = dpd.DPD(P, Q, M)
+    if launch:
+        f.set_fwd_launch(**launch)
+    f.set_coeffs(torch.from_numpy(h).cuda())
+    n = len(x)
+    xb = torch.zeros(n + offset + 2, dtype=torch.complex64, device="cuda")
+    xb[offset: offset + n] = torch.from_numpy(x).cuda()
+    yb = torch.full((n + out_offset + 2,), complex(7.0, -7.0), dtype=torch.complex64, device="cuda")
+    xv = xb[offset: offset + n]
+    yv = yb[out_offset: out_offset + n]
+    f.apply(xv, out=yv)
+    f.sync_status()
+    yb = yb.cpu().numpy()
+    # guard elements around the output must be untouched
+    assert np.all(yb[:out_offset] == np.complex64(7 - 7j))
+    assert np.all(yb[out_offset + n:] == np.complex64(7 - 7j))
+    f.close()
+    return yb[out_offset: out_offset + n]
+
+
+def test_config0_clipped_gaussian_p5_m2():
+    x = synth.clipped_gaussian(1 << 16, 0.3, key=(0, 0))
+    h = synth.coeffs(5, 5, 2, key=(0, 1))
+    assert_parity(run_gpu(x, h, 5, 5, 2), oracle.apply(x, h, 5, 5, 2), what="config 0")
+
+
+def test_table2_p5_q3_l5_ragged():
+    x = synth.ofdm2(100003, key=(1, 0))
+    h = synth.coeffs(5, 3, 4, key=(1, 1))
+    assert_parity(run_gpu(x, h, 5, 3, 4), oracle.apply(x, h, 5, 3, 4), what="table 2")
+
+
+def test_config1_full_size_ofdm_p9_m4():
+    """Full 2^24-sample OFDM workload at the benchmark's launch shape."""
+    n = 1 << 24
+    x = synth.ofdm2(n, key=(0, 0))
+    h = synth.coeffs(9, 9, 4, key=(0, 1))
+    y = run_gpu(x, h, 9, 9, 4)
+    assert_parity(y, oracle.apply(x, h, 9, 9, 4), what="config 1")
+
+
+MODELS = [(P, Q, M) for P in (0, 1, 3, 5, 7, 9, 11) for Q in (0, 1, 3, 5, 7, 9, 11)
+          for M in (0, 3, 7) if P + Q > 0]
+
+
+@pytest.mark.parametrize("P,Q,M", MODELS)
+def test_model_sweep(P, Q, M):
+    n = 3001 + 17 * M
+    x = synth.clipped_gaussian(n, 0.5, key=(2, P, Q, M))
+    h = synth.coeffs(P, Q, M, key=(2, P, Q, M, 1), f_std=0.3, g_std=0.3)
+    assert_parity(run_gpu(x, h, P, Q, M), oracle.apply(x, h, P, Q, M), what=f"P={P} Q={Q} M={M}")
+
+
+@pytest.mark.parametrize("M", range(8))
+def test_every_memory_depth(M):
+    x = synth.clipped_gaussian(5000, 0.4, key=(3, M))
+    h = synth.coeffs(7, 5, M, key=(3, M, 1), f_std=0.3, g_std=0.3)
+    assert_parity(run_gpu(x, h, 7, 5, M), oracle.apply(x, h, 7, 5, M), what=f"M={M}")
+
+
+LAUNCHES = [
+    dict(V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1),
+    dict(V=2, warps=8, stages=4, ctas_per_sm=0, use_tma=1),
+    dict(V=4, warps=1, stages=2, ctas_per_sm=1, use_tma=1),
+    dict(V=2, warps=16, stages=8, ctas_per_sm=0, use_tma=1),
+    dict(V=4, warps=4, stages=3, ctas_per_sm=2, use_tma=1),
+    dict(V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=0),
+    dict(V=2, warps=8, stages=4, ctas_per_sm=0, use_tma=0),
+]
+
+
+@pytest.mark.parametrize("launch", LAUNCHES, ids=lambda d: "V{V}w{warps}s{stages}c{ctas_per_sm}t{use_tma}".format(**d))
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 8, 9, 255, 256, 257, 1023, 1024, 1025, 2047, 4100, 70001])
+def test_sizes_and_launch_shapes(launch, n):
+    P, Q, M = 9, 9, 4
+    x = synth.clipped_gaussian(n, 0.5, key=(4, n))
+    h = synth.coeffs(P, Q, M, key=(4, 1), f_std=0.3, g_std=0.3)
+    assert_parity(run_gpu(x, h, P, Q, M, launch=launch), oracle.apply(x, h, P, Q, M), what=f"n={n} {launch}")
+
+
+@pytest.mark.parametrize("offset,out_offset", [(1, 0), (0, 1), (1, 1), (3, 2)])
+def test_eight_byte_aligned_buffers(offset, out_offset):
+    x = synth.clipped_gaussian(9999, 0.4, key=(5, offset))
+    h = synth.coeffs(5, 5, 2, key=(5, 1))
+    y = run_gpu(x, h, 5, 5, 2, offset=offset, out_offset=out_offset)
+    assert_parity(y, oracle.apply(x, h, 5, 5, 2), what=f"offsets {offset},{out_offset}")
+
+
+def test_identity_is_bitwise():
+    x = synth.clipped_gaussian(123457, 0.3, key=(6, 0))
+    for P, Q, M in [(5, 5, 2), (9, 9, 4), (11, 11, 7), (1, 0, 0)]:
+        h = np.zeros(dpd.num_coeffs(P, Q, M), np.complex64)
+        h[0] = 1
+        y = run_gpu(x, h, P, Q, M)
+        assert np.array_equal(y.view(np.uint64), x.view(np.uint64)), (P, Q, M)
+
+
+def test_empty_input_launches_nothing():
+    f = dpd.DPD(5, 5, 2)
+    f.set_coeffs(synth.coeffs(5, 5, 2))
+    torch.cuda.synchronize()
+    before = dpd.kernel_launches()
+    x = torch.empty(0, dtype=torch.complex64, device="cuda")
+    y = f.apply(x)
+    assert y.numel() == 0 and dpd.kernel_launches() == before
+    f.sync_status()
+
+
+def test_host_side_errors_with_device():
+    lib = _lib.load()
+    f = dpd.DPD(5, 5, 2)
+    x = torch.zeros(100, dtype=torch.complex64, device="cuda")
+    y = torch.zeros(100, dtype=torch.complex64, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    # before coefficients are set
+    assert lib.dpd_apply(f.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), 100, s) == 3
+    f.set_coeffs(synth.coeffs(5, 5, 2))
+    # overlapping and in-place ranges
+    assert lib.dpd_apply(f.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 100, s) == 1
+    assert lib.dpd_apply(f.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr() + 8 * 50), 100, s) == 1
+    # misaligned (4-byte) pointer, negative length, wrong coefficient count
+    assert lib.dpd_apply(f.handle, ctypes.c_void_p(x.data_ptr() + 4), ctypes.c_void_p(y.data_ptr()), 10, s) == 1
+    assert lib.dpd_apply(f.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), -1, s) == 1
+    h = torch.zeros(18, dtype=torch.complex64)
+    assert lib.dpd_set_coeffs(f.handle, ctypes.c_void_p(h.data_ptr()), 18, 0, s) == 1
+    assert lib.dpd_set_fwd_launch(f.handle, 3, 8, 4, 0, 1) == 1
+    assert lib.dpd_set_fwd_launch(f.handle, 4, 8, 9, 0, 1) == 1
+    f.sync_status()
+
+
+def test_device_coefficients_and_graph_replay():
+    P, Q, M = 7, 7, 3
+    n = 200000
+    x = synth.clipped_gaussian(n, 0.3, key=(7, 0))
+    h1 = synth.coeffs(P, Q, M, key=(7, 1))
+    h2 = synth.coeffs(P, Q, M, key=(7, 2), f_std=0.1)
+    f = dpd.DPD(P, Q, M)
+    hd = torch.from_numpy(h1).cuda()
+    f.set_coeffs(hd)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        f.apply(xd, out=yd)        # warm up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        f.set_coeffs(hd)
+        f.apply(xd, out=yd)
+    g.replay()
+    torch.cuda.synchronize()
+    assert_parity(yd.cpu().numpy(), oracle.apply(x, h1, P, Q, M), what="graph h1")
+    hd.copy_(torch.from_numpy(h2).cuda())   # the graph re-reads the device coefficients
+    g.replay()
+    torch.cuda.synchronize()
+    assert_parity(yd.cpu().numpy(), oracle.apply(x, h2, P, Q, M), what="graph h2")
+    f.sync_status()
