@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the APH DPD filter on GB300.
+
+One step = one pass of the predistorter (basis, branch FIRs, accumulation with
+the LO-leakage constant) over one batch of 2^24 complex64 samples of a
+synthetic two-carrier OFDM signal, P = Q = 9, M = 4 (K = 51 coefficients).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is device-timed throughput (CUDA
+events on the launching stream, inputs resident in HBM, two alternating buffer
+sets so that no step reads data the previous step left in L2); ``e2e`` is the
+same metric through the library's host-buffer path with the host<->device
+copies inside the timed region.  With N > 1 (torchrun) every rank runs an
+independent replica on its own batch: weak scaling, no collective on the data
+path.  ``--impl reference`` times the FP64 CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DPD Gsamples/s and % of roofline, plain vs batched; adjoint step ms; Gram TFLOP/s"
+P, Q, M = 9, 9, 4
+N_SAMPLES = 1 << 24
+BYTES_PER_SAMPLE = 16            # 8 B complex64 read + 8 B written
+FLOPS_ALG = lambda P, Q, M: 8 * (((P + 1) // 2) + ((Q + 1) // 2)) * (M + 1) + 3 * ((P + 1) // 2) + 2
+FLOPS_WL = lambda P, Q, M: 8 * max((P + 1) // 2, (Q + 1) // 2) * (M + 1) + 3
+SM_COUNT_NOMINAL, FP32_LANES_PER_SM = 152, 128
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = ("APH DPD filter (Eq. 1), 2^24-sample two-carrier OFDM (1024-pt IFFT, 600 QPSK "
+            "subcarriers, 72-sample CP, +-0.3 Nyquist, RMS 0.25), P=Q=9, M=4, K=51, complex64")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--min-warmup-s", type=float, default=1.5,
+                    help="keep warming up for at least this long so clocks settle and get sampled")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("dpd_fwd.cuh", "dpd_device.cuh", "dpd_internal.h"):
+        with open(os.path.join(ROOT, "paper_1612_09001_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not d or d.get("source_hash") != kernel_source_hash():
+        return None
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), util=float(parts[4]),
+                                     hw=parts[6], hwt=parts[7], swt=parts[8], pcap=parts[9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        load = [r for r in rows if r["util"] > 0] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(load)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- reference arm
+def cpu_oracle_throughput(n_sample: int, min_seconds: float, nthreads: int = 0):
+    """Time the FP64 oracle (as it stands) on the first n_sample samples of the workload."""
+    import oracle
+    import dpd_synth as synth
+    x = synth.ofdm2(n_sample, key=(0, 0))
+    h = synth.coeffs(P, Q, M, key=(0, 1))
+    oracle.apply(x[:4096], h, P, Q, M, nthreads=nthreads)    # load + warm
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.apply(x, h, P, Q, M, nthreads=nthreads)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return reps * n_sample / el / 1e9, el, reps, oracle.threads(nthreads)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    import dpd_synth as synth
+    n_sample = 1 << 18
+    x = synth.ofdm2(n_sample, key=(0, 0))
+    h = synth.coeffs(P, Q, M, key=(0, 1))
+    for _ in range(max(args.warmup, 0)):
+        oracle.apply(x, h, P, Q, M)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.apply(x, h, P, Q, M)
+    el = time.perf_counter() - t0
+    v = args.steps * n_sample / el / 1e9
+    cores = oracle.threads()
+    sample = f"first 2^18 samples of the workload per step, FP64 C oracle, {cores} threads"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "Gsamples/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "P": P, "Q": Q, "M": M,
+                                        "n_samples_per_step": n_sample},
+        "cpu_baseline": {"value": v, "unit": "Gsamples/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    import dpd_synth as synth
+    import paper_1612_09001_gb300 as dpd
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if pg is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    n = N_SAMPLES
+    x_host = synth.ofdm2(n, key=(rank, 0))
+    h = synth.coeffs(P, Q, M, key=(0, 1))
+    f = dpd.DPD(P, Q, M)
+    f.set_coeffs(torch.from_numpy(h).to(dev))
+    xs = [torch.from_numpy(x_host).to(dev) for _ in range(2)]
+    ys = [torch.empty_like(xs[0]) for _ in range(2)]
+    stream = torch.cuda.current_stream(dev)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    # warm-up: at least W steps and at least min_warmup_s of the same work
+    t0 = time.perf_counter()
+    i = 0
+    while i < args.warmup or time.perf_counter() - t0 < args.min_warmup_s:
+        f.apply(xs[i % 2], out=ys[i % 2])
+        i += 1
+        if i % 64 == 0:
+            torch.cuda.synchronize(dev)
+    f.sync_status()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = dpd.kernel_launches()
+    w0 = time.perf_counter()
+    for k in range(K):
+        ev[k][0].record(stream)
+        f.apply(xs[k % 2], out=ys[k % 2])
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - w0
+    barrier()
+    launches = dpd.kernel_launches() - launches0
+    clocks = sampler.stop()
+    f.sync_status()
+    per = [a.elapsed_time(b) * 1e-3 for a, b in ev]
+    total = ev[0][0].elapsed_time(ev[-1][1]) * 1e-3
+    total_max = max_over_ranks(total)
+    value = world * K * n / total_max / 1e9
+    mean_launch = sum(per) / len(per)
+
+    # ---- end to end: pinned host buffers, copies inside the timed region
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd, yd = xs[0], ys[0]
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        f.apply(xd, out=yd)
+        yh.copy_(yd, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    K2 = max(3, min(K, 20))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K2):
+        xd.copy_(xh, non_blocking=True)
+        f.apply(xd, out=yd)
+        yh.copy_(yd, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_t = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
+    e2e = {"value": world * K2 * n / e2e_t / 1e9, "unit": "Gsamples/s",
+           "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
+           "path": "pinned host -> cudaMemcpyAsync -> dpd_apply -> cudaMemcpyAsync -> pinned host"}
+
+    if rank != 0:
+        f.close()
+        if pg is not None:
+            pg.destroy_process_group()
+        return 0
+
+    peaks, peak_kind = measured_peaks()
+    achieved = BYTES_PER_SAMPLE * n / mean_launch / 1e9
+    tr = recorded_traffic("fwd_tma_kernel<5,5,4>")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "peak_kind": f"of {peak_kind} (copy bandwidth)",
+                "kernel": "fwd_tma_kernel<B=5,T=5,V=4>", "bytes_per_sample": BYTES_PER_SAMPLE}
+    sm_mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else peaks.get("sm_max_mhz", 2070.0)
+    props = torch.cuda.get_device_properties(dev)
+    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    rate = n / mean_launch
+    alu = {"fp32_peak_tflops": fp32_peak, "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+           "flops_per_sample_alg1": FLOPS_ALG(P, Q, M), "flops_per_sample_executed": FLOPS_WL(P, Q, M),
+           "achieved_tflops_alg1": rate * FLOPS_ALG(P, Q, M) / 1e12,
+           "achieved_tflops_executed": rate * FLOPS_WL(P, Q, M) / 1e12,
+           "frac_executed": rate * FLOPS_WL(P, Q, M) / 1e12 / fp32_peak}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, el, reps, cores = cpu_oracle_throughput(1 << 22, 10.0)
+        cpu = {"value": v, "unit": "Gsamples/s", "cores": cores, "kind": "oracle",
+               "sample": f"first 2^22 samples of the workload, repeated {reps}x ({el:.1f} s), FP64 C oracle"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_max / K * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "P": P, "Q": Q, "M": M, "n_samples_per_step": n,
+                   "l2": "inputs larger than L2: 134 MB in + 134 MB out per step, two alternating buffer sets",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "launch": dict(f.fwd_launch)},
+        "wall_s_timed": wall, "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "alu": alu,
+        "e2e": e2e, "cpu_baseline": cpu,
+        "samples_per_s_per_gpu": K * n / total / 1e9,
+    }
+    print(json.dumps(line), flush=True)
+    f.close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -66,6 +66,7 @@ class DPD:
         k = ctypes.c_int()
         _lib.check("dpd_num_coeffs", self._lib.dpd_num_coeffs(self._h, ctypes.byref(k)))
         self.K = k.value
+        self.fwd_launch = dict(V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1)
 
     # -- lifetime
     def close(self):
@@ -123,6 +124,7 @@ class DPD:
     def set_fwd_launch(self, V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1):
         _lib.check("dpd_set_fwd_launch", self._lib.dpd_set_fwd_launch(
             self._h, V, warps, stages, ctas_per_sm, use_tma))
+        self.fwd_launch = dict(V=V, warps=warps, stages=stages, ctas_per_sm=ctas_per_sm, use_tma=use_tma)
 
     def sync_status(self, stream=None):
         """Synchronise the stream and raise if a kernel recorded an error."""
