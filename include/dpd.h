@@ -79,9 +79,11 @@ dpd_status dpd_num_coeffs(dpd_handle h, int *K);
 
 /*
  * Install the coefficient vector h (K complex64 values, stacking order of
- * Sec. 2.2).  `where` is DPD_HOST or DPD_DEVICE.  Host buffers are copied
- * before the call returns; device buffers are read by a kernel on `stream`, so
- * they must stay valid until that kernel has run.  The caller keeps ownership.
+ * Sec. 2.2).  `where` is DPD_HOST or DPD_DEVICE.  Host buffers are copied and
+ * the call synchronises `stream` (it keeps a host copy of the prepared table,
+ * so it must not be captured in a CUDA graph); device buffers are read by a
+ * kernel on `stream` without synchronising (capturable), so they must stay
+ * valid until that kernel has run.  The caller keeps ownership.
  * K must equal dpd_num_coeffs.  Work is ordered on `stream`: later calls on
  * the same stream see the new coefficients.
  */
@@ -98,15 +100,46 @@ dpd_status dpd_set_coeffs(dpd_handle h, const void *coeffs, int K, int where, vo
 dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stream);
 
 /*
+ * Adjoint of dpd_apply for a real loss L (not in the paper: used for
+ * gradient-based direct learning).  Given gy = dL/dy for y = DPD(x), writes
+ *   gh[j] = sum_n conj(Psi_{n,j}) gy_n            (K values, Psi of Eq. 2)
+ *   gx[i] = sum_k conj(dy_{i+k}/dx_i) gy_{i+k} + (dy_{i+k}/dconj(x_i)) conj(gy_{i+k})
+ * with every gradient in the convention dL/dRe + j dL/dIm (PyTorch's).
+ *   x, gy : device, n complex64 each, 8-byte aligned.
+ *   gh    : device, K complex64, or NULL; overwritten (not accumulated).
+ *   gx    : device, n complex64, or NULL; overwritten; must not overlap x, gy, gh.
+ * At least one of gh, gx non-NULL.  gx needs coefficients (DPD_ERR_NO_COEFFS),
+ * gh does not.  The basis is recomputed from x; nothing from dpd_apply is kept.
+ * gh is reduced through the handle's workspace (one partial row per CTA, summed
+ * in FP64 in a fixed order): results are deterministic, and calls on one handle
+ * must not run concurrently on different streams.  n == 0 zeroes gh.
+ * Allocates nothing; does not synchronise.
+ */
+dpd_status dpd_grad(dpd_handle h, const void *x, const void *gy, int64_t n, void *gh, void *gx,
+                    void *stream);
+
+/*
+ * Launch shape of dpd_grad's coefficient-gradient kernel (used by the
+ * autotuner): gh_blocks CTAs per tap group (1 .. 4 * SM count), tap_group taps
+ * per group (1, 2 or 4).
+ */
+dpd_status dpd_set_adj_launch(dpd_handle h, int gh_blocks, int tap_group);
+
+/*
  * Launch shape of dpd_apply for this handle (used by the autotuner):
- *   V           samples per thread, 2 or 4
+ *   mode        bit 0: coefficients passed by value as kernel parameters (used
+ *               only after dpd_set_coeffs from host memory; otherwise ignored);
+ *               bit 1: packed two-wide FP32 fused multiply-adds
+ *   V           samples per thread, 2, 4 or 8
  *   warps       consumer warps per CTA, 1..16 (tile = warps*32*V samples)
  *   stages      depth of the shared-memory bulk-copy ring, 2..8
  *   ctas_per_sm CTAs per SM of the persistent grid, 0 = as many as fit
  *   use_tma     1 = bulk-copy pipeline, 0 = plain global loads
- * A shape that does not fit the device makes dpd_apply return DPD_ERR_CUDA.
+ * A shape that does not fit the device, or a mode / V not built for the
+ * handle's (P, Q, M), makes dpd_apply return DPD_ERR_CUDA.
  */
-dpd_status dpd_set_fwd_launch(dpd_handle h, int V, int warps, int stages, int ctas_per_sm, int use_tma);
+dpd_status dpd_set_fwd_launch(dpd_handle h, int mode, int V, int warps, int stages, int ctas_per_sm,
+                              int use_tma);
 
 /*
  * Synchronise `stream`, then read and clear the handle's device error word.

@@ -66,7 +66,7 @@ class DPD:
         k = ctypes.c_int()
         _lib.check("dpd_num_coeffs", self._lib.dpd_num_coeffs(self._h, ctypes.byref(k)))
         self.K = k.value
-        self.fwd_launch = dict(V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1)
+        self.fwd_launch = dict(mode=0, V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1)
 
     # -- lifetime
     def close(self):
@@ -121,10 +121,37 @@ class DPD:
             x.numel(), _stream_ptr(stream)))
         return out
 
-    def set_fwd_launch(self, V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1):
+    # -- adjoint
+    def grad(self, x, gy, gh=None, gx=None, stream=None):
+        """Gradients of a real loss through y = DPD(x) given gy = dL/dy (dL/dRe + j dL/dIm).
+
+        Writes into gh (K complex64, CUDA) and/or gx (like x) when given; returns (gh, gx)."""
+        _check_samples(x, "x")
+        _check_samples(gy, "gy")
+        if gy.numel() != x.numel():
+            raise ValueError("gy must have as many elements as x")
+        if gh is not None:
+            _check_samples(gh, "gh")
+            if gh.numel() != self.K:
+                raise ValueError(f"gh must have {self.K} elements")
+        if gx is not None:
+            _check_samples(gx, "gx")
+            if gx.numel() != x.numel():
+                raise ValueError("gx must have as many elements as x")
+        _lib.check("dpd_grad", self._lib.dpd_grad(
+            self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(gy.data_ptr()), x.numel(),
+            ctypes.c_void_p(gh.data_ptr() if gh is not None else None),
+            ctypes.c_void_p(gx.data_ptr() if gx is not None else None), _stream_ptr(stream)))
+        return gh, gx
+
+    def set_adj_launch(self, gh_blocks, tap_group):
+        _lib.check("dpd_set_adj_launch", self._lib.dpd_set_adj_launch(self._h, gh_blocks, tap_group))
+
+    def set_fwd_launch(self, V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1, mode=0):
         _lib.check("dpd_set_fwd_launch", self._lib.dpd_set_fwd_launch(
-            self._h, V, warps, stages, ctas_per_sm, use_tma))
-        self.fwd_launch = dict(V=V, warps=warps, stages=stages, ctas_per_sm=ctas_per_sm, use_tma=use_tma)
+            self._h, mode, V, warps, stages, ctas_per_sm, use_tma))
+        self.fwd_launch = dict(mode=mode, V=V, warps=warps, stages=stages, ctas_per_sm=ctas_per_sm,
+                               use_tma=use_tma)
 
     def sync_status(self, stream=None):
         """Synchronise the stream and raise if a kernel recorded an error."""

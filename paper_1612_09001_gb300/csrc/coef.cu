@@ -1,22 +1,46 @@
-// Coefficient preparation: the stacked vector of Sec. 2.2 -> the widely-linear
-// per-tap polynomial table the forward kernels read (see dpd_internal.h).
+// Coefficient preparation: the stacked vector of Sec. 2.2 -> the per-tap
+// polynomial tables read by the forward kernels (widely-linear form, see
+// dpd_internal.h) and by the adjoint input-gradient kernel (see dpd_adj.cuh).
+// Also the FP64 finalisation of the coefficient gradient.
 #include "dpd_internal.h"
 
 namespace dpd {
 
 __global__ void wl_table_kernel(const float2 *__restrict__ h, int Bp, int Bq, int T, int B,
-                                float *__restrict__ tab)
+                                float *__restrict__ tab, float *__restrict__ adj)
 {
     const int i = threadIdx.x;   // one thread per (tap k, order index m)
     if (i < T * B) {
         const int k = i / B, m = i % B;
         const float2 A = (m < Bp) ? h[m * T + k] : make_float2(0.f, 0.f);          // h_{2m+1,k}
         const float2 C = (m < Bq) ? h[(Bp + m) * T + k] : make_float2(0.f, 0.f);   // hbar_{2m+1,k}
-        float *row = tab + 4 * B * k;
-        row[0 * B + m] = A.x + C.x;      // Re(A+C)
-        row[1 * B + m] = -(A.y - C.y);   // -Im(A-C)
-        row[2 * B + m] = A.y + C.y;      // Im(A+C)
-        row[3 * B + m] = A.x - C.x;      // Re(A-C)
+        tab[wl_index(B, k, m, 0)] = A.x + C.x;      // P0 = Re(A+C)
+        tab[wl_index(B, k, m, 1)] = -(A.y - C.y);   // P1 = -Im(A-C)
+        tab[wl_index(B, k, m, 2)] = A.y + C.y;      // P2 = Im(A+C)
+        tab[wl_index(B, k, m, 3)] = A.x - C.x;      // P3 = Re(A-C)
+        if (adj) {
+            const int per_tap = 4 * B + 4 * (B - 1);
+            float *q = adj + per_tap * k;
+            // E_m = (m+1) h_m, H_m = (m+1) hbar_m  (coefficients of r^m)
+            const float s = (float)(m + 1);
+            const float Er = s * A.x, Ei = s * A.y, Hr = s * C.x, Hi = s * C.y;
+            q[0 * B + m] = Er + Hr;
+            q[1 * B + m] = Ei + Hi;
+            q[2 * B + m] = Hi - Ei;
+            q[3 * B + m] = Er - Hr;
+            if (m < B - 1) {
+                // F_m = (m+1) h_{m+1}, G_m = (m+1) hbar_{m+1}
+                const float2 A1 = (m + 1 < Bp) ? h[(m + 1) * T + k] : make_float2(0.f, 0.f);
+                const float2 C1 = (m + 1 < Bq) ? h[(Bp + m + 1) * T + k] : make_float2(0.f, 0.f);
+                const float Fr = s * A1.x, Fi = s * A1.y, Gr = s * C1.x, Gi = s * C1.y;
+                float *r = q + 4 * B;
+                const int RB = B - 1;
+                r[0 * RB + m] = Gr + Fr;
+                r[1 * RB + m] = Gi + Fi;
+                r[2 * RB + m] = Fi - Gi;
+                r[3 * RB + m] = Gr - Fr;
+            }
+        }
     }
     if (i == 0) {
         const float2 c = h[(Bp + Bq) * T];
@@ -25,10 +49,32 @@ __global__ void wl_table_kernel(const float2 *__restrict__ h, int Bp, int Bq, in
     }
 }
 
-cudaError_t launch_wl_table(const float2 *h, int Bp, int Bq, int T, float *tab, cudaStream_t s)
+cudaError_t launch_wl_table(const float2 *h, int Bp, int Bq, int T, float *tab, float *adj_tab,
+                            cudaStream_t s)
 {
     const int B = Bp > Bq ? Bp : Bq;
-    wl_table_kernel<<<1, 64, 0, s>>>(h, Bp, Bq, T, B, tab);
+    wl_table_kernel<<<1, 64, 0, s>>>(h, Bp, Bq, T, B, tab, adj_tab);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void adj_finalize_kernel(const float2 *__restrict__ partials, int rows, int K,
+                                    float2 *__restrict__ gh)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    double re = 0.0, im = 0.0;
+    for (int r = 0; r < rows; ++r) {
+        const float2 v = partials[(size_t)r * K + i];
+        re += v.x;
+        im += v.y;
+    }
+    gh[i] = make_float2((float)re, (float)im);
+}
+
+cudaError_t launch_adj_finalize(const float2 *partials, int rows, int K, float2 *gh, cudaStream_t s)
+{
+    adj_finalize_kernel<<<(K + 127) / 128, 128, 0, s>>>(partials, rows, K, gh);
     count_launch();
     return cudaGetLastError();
 }

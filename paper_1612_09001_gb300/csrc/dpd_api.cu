@@ -18,13 +18,33 @@ struct dpd_filter {
     float2 *d_h;      // K complex coefficients, stacking order of Sec. 2.2
     float *d_tab;     // widely-linear table for the forward kernels
     int *d_status;    // kernel error word
+    float *d_adj_tab; // adjoint (derivative-polynomial) table
+    float2 *d_partials;  // coefficient-gradient workspace: rows_max x K complex
+    int rows_max;
     bool has_coeffs;
+    bool host_tab_valid;  // h_tab mirrors d_tab (coefficients were set from host memory)
+    dpd::HostTab h_tab;
     dpd::FwdLaunch fwd;
+    dpd::AdjLaunch adj;
 };
 
 namespace dpd {
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+cudaError_t launch_adj_any(int B, const AdjArgs &a, const AdjLaunch &L, int T, int Bp, int Bq, int K,
+                           int sm_count, cudaStream_t s)
+{
+    switch (B) {
+    case 1: return launch_adj<1>(a, L, T, Bp, Bq, K, sm_count, s);
+    case 2: return launch_adj<2>(a, L, T, Bp, Bq, K, sm_count, s);
+    case 3: return launch_adj<3>(a, L, T, Bp, Bq, K, sm_count, s);
+    case 4: return launch_adj<4>(a, L, T, Bp, Bq, K, sm_count, s);
+    case 5: return launch_adj<5>(a, L, T, Bp, Bq, K, sm_count, s);
+    case 6: return launch_adj<6>(a, L, T, Bp, Bq, K, sm_count, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_fwd_any(int B, int T, const FwdArgs &a, const FwdLaunch &L, int sm_count,
                            cudaStream_t s)
@@ -94,25 +114,30 @@ dpd_status dpd_create(int P, int Q, int M, dpd_handle *out)
     f->T = M + 1;
     f->K = (f->Bp + f->Bq) * f->T + 1;
     f->has_coeffs = false;
+    f->host_tab_valid = false;
     if (cudaGetDevice(&f->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&f->sm_count, cudaDevAttrMultiProcessorCount, f->device) != cudaSuccess) {
         delete f;
         return DPD_ERR_CUDA;
     }
+    f->rows_max = 4 * f->sm_count;
+    f->adj.gh_blocks = 2 * f->sm_count;
+    f->adj.tap_group = f->B <= 2 ? 4 : 2;
+    f->d_h = nullptr;
+    f->d_tab = nullptr;
+    f->d_status = nullptr;
+    f->d_adj_tab = nullptr;
+    f->d_partials = nullptr;
     if (cudaMalloc(&f->d_h, sizeof(float2) * f->K) != cudaSuccess ||
         cudaMalloc(&f->d_tab, sizeof(float) * dpd::wl_table_floats(f->B, f->T)) != cudaSuccess ||
+        cudaMalloc(&f->d_adj_tab, sizeof(float) * dpd::adj_table_floats(f->B, f->T)) != cudaSuccess ||
+        cudaMalloc(&f->d_partials, sizeof(float2) * (size_t)f->rows_max * f->K) != cudaSuccess ||
         cudaMalloc(&f->d_status, sizeof(int)) != cudaSuccess) {
-        cudaFree(f->d_h);
-        cudaFree(f->d_tab);
-        cudaFree(f->d_status);
-        delete f;
+        dpd_destroy(f);
         return DPD_ERR_ALLOC;
     }
     if (cudaMemset(f->d_status, 0, sizeof(int)) != cudaSuccess) {
-        cudaFree(f->d_h);
-        cudaFree(f->d_tab);
-        cudaFree(f->d_status);
-        delete f;
+        dpd_destroy(f);
         return DPD_ERR_CUDA;
     }
     *out = f;
@@ -124,6 +149,8 @@ dpd_status dpd_destroy(dpd_handle h)
     if (!h) return DPD_OK;
     cudaFree(h->d_h);
     cudaFree(h->d_tab);
+    cudaFree(h->d_adj_tab);
+    cudaFree(h->d_partials);
     cudaFree(h->d_status);
     delete h;
     return DPD_OK;
@@ -154,8 +181,17 @@ dpd_status dpd_set_coeffs(dpd_handle h, const void *coeffs, int K, int where, vo
         if (e != cudaSuccess) return DPD_ERR_CUDA;
         src = h->d_h;
     }
-    cudaError_t e = dpd::launch_wl_table(src, h->Bp, h->Bq, h->T, h->d_tab, s);
+    h->host_tab_valid = false;
+    cudaError_t e = dpd::launch_wl_table(src, h->Bp, h->Bq, h->T, h->d_tab, h->d_adj_tab, s);
     if (e != cudaSuccess) return DPD_ERR_CUDA;
+    if (where == DPD_HOST) {
+        // Keep a host copy of the table so that dpd_apply can pass it by value.
+        e = cudaMemcpyAsync(h->h_tab.v, h->d_tab, sizeof(float) * dpd::wl_table_floats(h->B, h->T),
+                            cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return DPD_ERR_CUDA;
+        h->host_tab_valid = true;
+    }
     h->has_coeffs = true;
     return DPD_OK;
 }
@@ -176,17 +212,76 @@ dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stre
     a.tab = h->d_tab;
     a.status = h->d_status;
     a.vec_store = aligned(y, 16) ? 1 : 0;
+    a.host_tab = h->host_tab_valid ? &h->h_tab : nullptr;
     dpd::FwdLaunch L = h->fwd;
     if (!aligned(x, 16)) L.use_tma = 0;
+    if (!h->host_tab_valid) L.mode &= ~dpd::kModeParamCoef;
     return cuda_status(dpd::launch_fwd_any(h->B, h->T, a, L, h->sm_count, static_cast<cudaStream_t>(stream)));
 }
 
-dpd_status dpd_set_fwd_launch(dpd_handle h, int V, int warps, int stages, int ctas_per_sm, int use_tma)
+dpd_status dpd_grad(dpd_handle h, const void *x, const void *gy, int64_t n, void *gh, void *gx,
+                    void *stream)
+{
+    if (!h || n < 0) return DPD_ERR_INVALID_ARGUMENT;
+    if (!gh && !gx) return DPD_ERR_INVALID_ARGUMENT;
+    if (gx && !h->has_coeffs) return DPD_ERR_NO_COEFFS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (gh && !aligned(gh, 8)) return DPD_ERR_INVALID_ARGUMENT;
+    if (n > (int64_t)(INT64_MAX / sizeof(float2))) return DPD_ERR_INVALID_ARGUMENT;
+    const size_t bytes = (size_t)n * sizeof(float2), kbytes = sizeof(float2) * h->K;
+    if (n > 0) {
+        if (!x || !gy || !aligned(x, 8) || !aligned(gy, 8)) return DPD_ERR_INVALID_ARGUMENT;
+        if (gx && (!aligned(gx, 8) || overlap(gx, bytes, x, bytes) || overlap(gx, bytes, gy, bytes)))
+            return DPD_ERR_INVALID_ARGUMENT;
+        if (gh && (overlap(gh, kbytes, x, bytes) || overlap(gh, kbytes, gy, bytes) ||
+                   (gx && overlap(gh, kbytes, gx, bytes))))
+            return DPD_ERR_INVALID_ARGUMENT;
+    }
+    if (n == 0) {
+        if (gh && cudaMemsetAsync(gh, 0, kbytes, s) != cudaSuccess) return DPD_ERR_CUDA;
+        return DPD_OK;
+    }
+    dpd::AdjArgs a;
+    a.x = static_cast<const float2 *>(x);
+    a.gy = static_cast<const float2 *>(gy);
+    a.n = n;
+    a.gx = static_cast<float2 *>(gx);
+    a.partials = gh ? h->d_partials : nullptr;
+    a.adj_tab = h->d_adj_tab;
+    a.status = h->d_status;
+    dpd::AdjLaunch L = h->adj;
+    int64_t need = (n + 1023) / 1024;
+    if (L.gh_blocks > need) L.gh_blocks = (int)need;
+    if (L.gh_blocks > h->rows_max) L.gh_blocks = h->rows_max;
+    if (L.gh_blocks < 1) L.gh_blocks = 1;
+    cudaError_t e = dpd::launch_adj_any(h->B, a, L, h->T, h->Bp, h->Bq, h->K, h->sm_count, s);
+    if (e != cudaSuccess) return DPD_ERR_CUDA;
+    if (gh) {
+        e = dpd::launch_adj_finalize(h->d_partials, L.gh_blocks, h->K, static_cast<float2 *>(gh), s);
+        if (e != cudaSuccess) return DPD_ERR_CUDA;
+    }
+    return DPD_OK;
+}
+
+dpd_status dpd_set_adj_launch(dpd_handle h, int gh_blocks, int tap_group)
 {
     if (!h) return DPD_ERR_INVALID_ARGUMENT;
-    if ((V != 2 && V != 4) || warps < 1 || warps > 16 || stages < 2 || stages > 8 || ctas_per_sm < 0 ||
+    if (gh_blocks < 1 || gh_blocks > h->rows_max) return DPD_ERR_INVALID_ARGUMENT;
+    if (tap_group != 1 && tap_group != 2 && tap_group != 4) return DPD_ERR_INVALID_ARGUMENT;
+    h->adj.gh_blocks = gh_blocks;
+    h->adj.tap_group = tap_group;
+    return DPD_OK;
+}
+
+dpd_status dpd_set_fwd_launch(dpd_handle h, int mode, int V, int warps, int stages, int ctas_per_sm,
+                              int use_tma)
+{
+    if (!h) return DPD_ERR_INVALID_ARGUMENT;
+    if (mode < 0 || mode > 3) return DPD_ERR_INVALID_ARGUMENT;
+    if ((V != 2 && V != 4 && V != 8) || warps < 1 || warps > 16 || stages < 2 || stages > 8 || ctas_per_sm < 0 ||
         (use_tma != 0 && use_tma != 1))
         return DPD_ERR_INVALID_ARGUMENT;
+    h->fwd.mode = mode;
     h->fwd.V = V;
     h->fwd.warps = warps;
     h->fwd.stages = stages;

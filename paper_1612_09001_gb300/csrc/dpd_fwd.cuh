@@ -27,51 +27,79 @@
 
 namespace dpd {
 
-template <int B, int T, int V>
-__device__ __forceinline__ void fwd_compute(const float *__restrict__ tab,
+// Coefficient table passed by value (kernel parameter bank).
+template <int B, int T>
+struct ParamTab {
+    float v[wl_table_floats(B, T)];
+};
+
+// V outputs from a window of V + T - 1 inputs (window index j is sample n0 - (T-1) + j).
+// MODE bit kModeParamCoef: coefficients come from the parameter bank and are
+// used directly as FMA operands; otherwise one tap's B float4s are loaded from
+// shared memory.  MODE bit kModePackedFma: the polynomial pairs {P0,P2} and
+// {P1,P3} are evaluated with packed f32x2 FMAs.
+template <int B, int T, int V, int MODE>
+__device__ __forceinline__ void fwd_compute(const float *__restrict__ stab, const ParamTab<B, T> &ptab,
                                             const float (&wr)[V + T - 1],
                                             const float (&wi)[V + T - 1], float (&yr)[V],
                                             float (&yi)[V])
 {
     constexpr int W = V + T - 1;
+    constexpr bool PARAM = (MODE & kModeParamCoef) != 0;
+    constexpr bool PACKED = (MODE & kModePackedFma) != 0;
     float r[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) r[j] = fmaf(wr[j], wr[j], wi[j] * wi[j]);
-    const float cr = tab[4 * B * T], ci = tab[4 * B * T + 1];
+    const float cr = PARAM ? ptab.v[4 * B * T] : stab[4 * B * T];
+    const float ci = PARAM ? ptab.v[4 * B * T + 1] : stab[4 * B * T + 1];
+    float2 acc[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        yr[v] = cr;
-        yi[v] = ci;
-    }
+    for (int v = 0; v < V; ++v) acc[v] = make_float2(cr, ci);
 #pragma unroll
     for (int k = 0; k < T; ++k) {
-        float cf[4 * B];
-        const float4 *t4 = reinterpret_cast<const float4 *>(tab + 4 * B * k);
+        float4 cf[B];   // per order m: {P0, P2, P1, P3}
 #pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const float4 q = t4[i];
-            cf[4 * i + 0] = q.x;
-            cf[4 * i + 1] = q.y;
-            cf[4 * i + 2] = q.z;
-            cf[4 * i + 3] = q.w;
+        for (int m = 0; m < B; ++m) {
+            if constexpr (PARAM)
+                cf[m] = make_float4(ptab.v[(k * B + m) * 4 + 0], ptab.v[(k * B + m) * 4 + 1],
+                                    ptab.v[(k * B + m) * 4 + 2], ptab.v[(k * B + m) * 4 + 3]);
+            else
+                cf[m] = reinterpret_cast<const float4 *>(stab)[k * B + m];
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int j = v + (T - 1) - k;   // window index of sample n - k
-            float p0 = cf[0 * B + B - 1], p1 = cf[1 * B + B - 1];
-            float p2 = cf[2 * B + B - 1], p3 = cf[3 * B + B - 1];
+            if constexpr (PACKED) {
+                const float2 rr = make_float2(r[j], r[j]);
+                float2 pa = make_float2(cf[B - 1].x, cf[B - 1].y);   // {P0, P2}
+                float2 pb = make_float2(cf[B - 1].z, cf[B - 1].w);   // {P1, P3}
 #pragma unroll
-            for (int m = B - 2; m >= 0; --m) {
-                p0 = fmaf(p0, r[j], cf[0 * B + m]);
-                p1 = fmaf(p1, r[j], cf[1 * B + m]);
-                p2 = fmaf(p2, r[j], cf[2 * B + m]);
-                p3 = fmaf(p3, r[j], cf[3 * B + m]);
+                for (int m = B - 2; m >= 0; --m) {
+                    pa = __ffma2_rn(pa, rr, make_float2(cf[m].x, cf[m].y));
+                    pb = __ffma2_rn(pb, rr, make_float2(cf[m].z, cf[m].w));
+                }
+                acc[v] = __ffma2_rn(pa, make_float2(wr[j], wr[j]), acc[v]);
+                acc[v] = __ffma2_rn(pb, make_float2(wi[j], wi[j]), acc[v]);
+            } else {
+                float p0 = cf[B - 1].x, p2 = cf[B - 1].y, p1 = cf[B - 1].z, p3 = cf[B - 1].w;
+#pragma unroll
+                for (int m = B - 2; m >= 0; --m) {
+                    p0 = fmaf(p0, r[j], cf[m].x);
+                    p2 = fmaf(p2, r[j], cf[m].y);
+                    p1 = fmaf(p1, r[j], cf[m].z);
+                    p3 = fmaf(p3, r[j], cf[m].w);
+                }
+                acc[v].x = fmaf(p0, wr[j], acc[v].x);
+                acc[v].x = fmaf(p1, wi[j], acc[v].x);
+                acc[v].y = fmaf(p2, wr[j], acc[v].y);
+                acc[v].y = fmaf(p3, wi[j], acc[v].y);
             }
-            yr[v] = fmaf(p0, wr[j], yr[v]);
-            yr[v] = fmaf(p1, wi[j], yr[v]);
-            yi[v] = fmaf(p2, wr[j], yi[v]);
-            yi[v] = fmaf(p3, wi[j], yi[v]);
         }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        yr[v] = acc[v].x;
+        yi[v] = acc[v].y;
     }
 }
 
@@ -89,8 +117,9 @@ __host__ __device__ constexpr size_t fwd_tma_smem(int warps, int stages)
            (size_t)stages * (size_t)(kHalo + warps * 32 * V) * sizeof(float2);
 }
 
-template <int B, int T, int V>
-__global__ void __launch_bounds__(32 * 17) fwd_tma_kernel(FwdArgs a, int stages, int64_t ntiles)
+template <int B, int T, int V, int MODE>
+__global__ void __launch_bounds__(32 * 17)
+    fwd_tma_kernel(FwdArgs a, int stages, int64_t ntiles, const __grid_constant__ ParamTab<B, T> ptab)
 {
     constexpr int W = V + T - 1;
     constexpr int TABF = wl_table_floats(B, T);
@@ -203,7 +232,7 @@ __global__ void __launch_bounds__(32 * 17) fwd_tma_kernel(FwdArgs a, int stages,
         if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));
 
         float yr[V], yi[V];
-        fwd_compute<B, T, V>(tab, wr, wi, yr, yi);
+        fwd_compute<B, T, V, MODE>(tab, ptab, wr, wi, yr, yi);
         if (full && a.vec_store) {
             float4 *yp = reinterpret_cast<float4 *>(a.y + g0);
 #pragma unroll
@@ -220,8 +249,9 @@ __global__ void __launch_bounds__(32 * 17) fwd_tma_kernel(FwdArgs a, int stages,
 // Plain-load variant: every thread reads its window straight from global
 // memory (through L1).  Used for buffers that are only 8-byte aligned and as
 // the no-TMA baseline.
-template <int B, int T, int V>
-__global__ void __launch_bounds__(256) fwd_ldg_kernel(FwdArgs a)
+template <int B, int T, int V, int MODE>
+__global__ void __launch_bounds__(256)
+    fwd_ldg_kernel(FwdArgs a, const __grid_constant__ ParamTab<B, T> ptab)
 {
     constexpr int W = V + T - 1;
     constexpr int TABF = wl_table_floats(B, T);
@@ -240,22 +270,27 @@ __global__ void __launch_bounds__(256) fwd_ldg_kernel(FwdArgs a)
             wi[j] = v.y;
         }
         float yr[V], yi[V];
-        fwd_compute<B, T, V>(tab, wr, wi, yr, yi);
+        fwd_compute<B, T, V, MODE>(tab, ptab, wr, wi, yr, yi);
 #pragma unroll
         for (int v = 0; v < V; ++v)
             if (g0 + v < a.n) a.y[g0 + v] = make_float2(yr[v], yi[v]);
     }
 }
 
-template <int B, int T, int V>
+template <int B, int T, int V, int MODE>
 cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cudaStream_t s)
 {
+    ParamTab<B, T> ptab{};
+    if constexpr ((MODE & kModeParamCoef) != 0) {
+        if (!a.host_tab) return cudaErrorInvalidValue;
+        for (int i = 0; i < wl_table_floats(B, T); ++i) ptab.v[i] = a.host_tab->v[i];
+    }
     if (L.use_tma) {
         const int threads = (L.warps + 1) * 32;
         const int S = L.warps * 32 * V;
         const int64_t ntiles = (a.n + S - 1) / S;
         const size_t smem = fwd_tma_smem<B, T, V>(L.warps, L.stages);
-        auto kern = fwd_tma_kernel<B, T, V>;
+        auto kern = fwd_tma_kernel<B, T, V, MODE>;
         static size_t smem_set = 0;   // per instantiation
         if (smem > smem_set) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -270,30 +305,59 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
         const int cps = (L.ctas_per_sm > 0 && L.ctas_per_sm < occ) ? L.ctas_per_sm : occ;
         int64_t grid = (int64_t)sm_count * cps;
         if (grid > ntiles) grid = ntiles;
-        kern<<<(unsigned)grid, threads, smem, s>>>(a, L.stages, ntiles);
+        kern<<<(unsigned)grid, threads, smem, s>>>(a, L.stages, ntiles, ptab);
         count_launch();
         return cudaGetLastError();
     }
     const int threads = 256;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fwd_ldg_kernel<B, T, V>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fwd_ldg_kernel<B, T, V, MODE>,
                                                                   threads, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const int64_t need = (a.n + (int64_t)threads * V - 1) / ((int64_t)threads * V);
     int64_t grid = (int64_t)sm_count * occ;
     if (grid > need) grid = need;
-    fwd_ldg_kernel<B, T, V><<<(unsigned)grid, threads, 0, s>>>(a);
+    fwd_ldg_kernel<B, T, V, MODE><<<(unsigned)grid, threads, 0, s>>>(a, ptab);
     count_launch();
     return cudaGetLastError();
+}
+
+// Launch shapes instantiated for every (B, T); the other modes and V = 8 are
+// built for the (B, T) pairs of the benchmarked workloads only.
+template <int B, int T>
+constexpr bool fwd_all_modes()
+{
+    return (B == 5 && T == 5) || (B == 3 && T == 3) || (B == 4 && T == 4) || (B == 6 && T == 8);
+}
+
+template <int B, int T, int MODE>
+cudaError_t launch_fwd_mode(const FwdArgs &a, const FwdLaunch &L, int sm_count, cudaStream_t s)
+{
+    switch (L.V) {
+    case 2: return launch_fwd_tv<B, T, 2, MODE>(a, L, sm_count, s);
+    case 4: return launch_fwd_tv<B, T, 4, MODE>(a, L, sm_count, s);
+    case 8:
+        if constexpr (fwd_all_modes<B, T>()) return launch_fwd_tv<B, T, 8, MODE>(a, L, sm_count, s);
+        return cudaErrorNotSupported;
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int B, int T>
 cudaError_t launch_fwd_t(const FwdArgs &a, const FwdLaunch &L, int sm_count, cudaStream_t s)
 {
-    switch (L.V) {
-    case 2: return launch_fwd_tv<B, T, 2>(a, L, sm_count, s);
-    case 4: return launch_fwd_tv<B, T, 4>(a, L, sm_count, s);
+    switch (L.mode) {
+    case 0: return launch_fwd_mode<B, T, 0>(a, L, sm_count, s);
+    case 1:
+    case 2:
+    case 3:
+        if constexpr (fwd_all_modes<B, T>()) {
+            if (L.mode == 1) return launch_fwd_mode<B, T, 1>(a, L, sm_count, s);
+            if (L.mode == 2) return launch_fwd_mode<B, T, 2>(a, L, sm_count, s);
+            return launch_fwd_mode<B, T, 3>(a, L, sm_count, s);
+        }
+        return cudaErrorNotSupported;
     default: return cudaErrorInvalidValue;
     }
 }

@@ -18,16 +18,32 @@ constexpr int kMaxT = 8;       // M + 1 <= 8
 constexpr int kHalo = 8;       // samples of history staged in front of a tile (>= kMaxT - 1, 16-byte multiple)
 
 // Size in floats of the widely-linear coefficient table consumed by the
-// forward kernels: for each tap k, four real polynomials in r = |x|^2
-// (B coefficients each, lowest order first), then Re c, Im c.
-//   P0 = Re(A+C), P1 = -Im(A-C), P2 = Im(A+C), P3 = Re(A-C)
+// forward kernels.  Four real polynomials in r = |x|^2 per tap k,
+//   P0 = Re(A+C), P1 = -Im(A-C), P2 = Im(A+C), P3 = Re(A-C),
 // where A_k(r) = sum_b h_{2b+1,k} r^b and C_k(r) = sum_b hbar_{2b+1,k} r^b, so that
 // A_k(r) x + C_k(r) conj(x) = (P0 a + P1 b) + j (P2 a + P3 b) for x = a + j b.
+// Layout: tab[(k*B + m)*4 + {0,1,2,3}] = {P0, P2, P1, P3} coefficient of r^m
+// (so {P0,P2} and {P1,P3} are adjacent pairs), then Re c, Im c at 4*B*T.
 __host__ __device__ constexpr int wl_table_floats(int B, int T) { return 4 * B * T + 2; }
+__host__ __device__ constexpr int wl_index(int B, int k, int m, int poly)
+{
+    return (k * B + m) * 4 + (poly == 0 ? 0 : poly == 2 ? 1 : poly == 1 ? 2 : 3);
+}
+
+// Largest table that is passed by value as a kernel parameter (B = 6, T = 8).
+constexpr int kMaxTabFloats = 4 * 6 * 8 + 2;
+struct HostTab {
+    float v[kMaxTabFloats];
+};
+
+// Forward compute modes (template bits): coefficients read from the kernel
+// parameter bank instead of shared memory; packed f32x2 fused multiply-adds.
+enum : int { kModeParamCoef = 1, kModePackedFma = 2 };
 
 // Forward launch shape.
 struct FwdLaunch {
-    int V = 4;            // samples per consumer thread (2 or 4)
+    int mode = 0;         // compute mode bits (kModeParamCoef | kModePackedFma)
+    int V = 4;            // samples per consumer thread (2, 4 or 8)
     int warps = 8;        // consumer warps per CTA (tile = warps * 32 * V samples)
     int stages = 4;       // shared-memory ring depth (bulk-copy pipeline)
     int ctas_per_sm = 0;  // 0: as many as fit
@@ -41,7 +57,36 @@ struct FwdArgs {
     const float *tab;     // device widely-linear table, wl_table_floats(B, T) floats
     int *status;          // device error word
     int vec_store;        // y is 16-byte aligned
+    const HostTab *host_tab;   // host copy of the table (param-bank modes), or null
 };
+
+// Floats of the adjoint table: per tap, four polynomials of B coefficients
+// (Q0..Q3 for conj(E) g + H conj(g)) and four of B-1 (R0..R3 for
+// conj(G) g + F conj(g)); see dpd_adj.cuh.
+__host__ __device__ constexpr int adj_table_floats(int B, int T) { return (4 * B + 4 * (B - 1)) * T; }
+
+struct AdjArgs {
+    const float2 *x;
+    const float2 *gy;
+    int64_t n;
+    float2 *gx;             // nullable: input gradient (n)
+    float2 *partials;       // nullable: per-CTA coefficient-gradient rows (rows x K)
+    const float *adj_tab;   // device adjoint table
+    int *status;
+};
+
+struct AdjLaunch {
+    int gh_blocks = 0;      // CTAs per tap group for the coefficient gradient (rows of partials)
+    int tap_group = 2;      // taps per group: 1, 2 or 4
+};
+
+template <int B>
+cudaError_t launch_adj(const AdjArgs &a, const AdjLaunch &L, int T, int Bp, int Bq, int K, int sm_count,
+                       cudaStream_t s);
+cudaError_t launch_adj_any(int B, const AdjArgs &a, const AdjLaunch &L, int T, int Bp, int Bq, int K,
+                           int sm_count, cudaStream_t s);
+// gh[i] = sum over `rows` rows of partials[row * K + i], accumulated in FP64 in row order.
+cudaError_t launch_adj_finalize(const float2 *partials, int rows, int K, float2 *gh, cudaStream_t s);
 
 // Launch the forward filter for max branch count B and T taps (host side;
 // defined per B in fwd_b<B>.cu).  Returns the launch error.
@@ -51,8 +96,10 @@ cudaError_t launch_fwd(int T, const FwdArgs &a, const FwdLaunch &L, int sm_count
 cudaError_t launch_fwd_any(int B, int T, const FwdArgs &a, const FwdLaunch &L, int sm_count,
                            cudaStream_t s);
 
-// Build the widely-linear table from the stacked coefficient vector h (K complex).
-cudaError_t launch_wl_table(const float2 *h, int Bp, int Bq, int T, float *tab, cudaStream_t s);
+// Build the forward widely-linear table and the adjoint table from the stacked
+// coefficient vector h (K complex); adj_tab may be null.
+cudaError_t launch_wl_table(const float2 *h, int Bp, int Bq, int T, float *tab, float *adj_tab,
+                            cudaStream_t s);
 
 void count_launch(int n = 1);
 

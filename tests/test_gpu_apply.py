@@ -19,11 +19,11 @@ import paper_1612_09001_gb300 as dpd  # noqa: E402
 from paper_1612_09001_gb300 import _lib  # noqa: E402
 
 
-def run_gpu(x, h, P, Q, M, launch=None, offset=0, out_offset=0):
+def run_gpu(x, h, P, Q, M, launch=None, offset=0, out_offset=0, host_coeffs=False):
     f = dpd.DPD(P, Q, M)
     if launch:
         f.set_fwd_launch(**launch)
-    f.set_coeffs(torch.from_numpy(h).cuda())
+    f.set_coeffs(h if host_coeffs else torch.from_numpy(h).cuda())
     n = len(x)
     xb = torch.zeros(n + offset + 2, dtype=torch.complex64, device="cuda")
     xb[offset: offset + n] = torch.from_numpy(x).cuda()
@@ -100,6 +100,21 @@ def test_sizes_and_launch_shapes(launch, n):
     assert_parity(run_gpu(x, h, P, Q, M, launch=launch), oracle.apply(x, h, P, Q, M), what=f"n={n} {launch}")
 
 
+@pytest.mark.parametrize("P,Q,M", [(9, 9, 4), (5, 5, 2), (7, 7, 3), (11, 11, 7), (9, 3, 4)])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("V", [4, 8])
+@pytest.mark.parametrize("use_tma", [1, 0])
+@pytest.mark.parametrize("host_coeffs", [True, False])
+def test_compute_modes(P, Q, M, mode, V, use_tma, host_coeffs):
+    """Parameter-bank / shared-memory coefficients and scalar / packed FMAs."""
+    for n in (1, 1000, 65537):
+        x = synth.clipped_gaussian(n, 0.5, key=(8, n, M))
+        h = synth.coeffs(P, Q, M, key=(8, 1), f_std=0.3, g_std=0.3)
+        launch = dict(mode=mode, V=V, warps=8, stages=4, ctas_per_sm=0, use_tma=use_tma)
+        y = run_gpu(x, h, P, Q, M, launch=launch, host_coeffs=host_coeffs)
+        assert_parity(y, oracle.apply(x, h, P, Q, M), what=f"n={n} {launch}")
+
+
 @pytest.mark.parametrize("offset,out_offset", [(1, 0), (0, 1), (1, 1), (3, 2)])
 def test_eight_byte_aligned_buffers(offset, out_offset):
     x = synth.clipped_gaussian(9999, 0.4, key=(5, offset))
@@ -145,8 +160,9 @@ def test_host_side_errors_with_device():
     assert lib.dpd_apply(f.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), -1, s) == 1
     h = torch.zeros(18, dtype=torch.complex64)
     assert lib.dpd_set_coeffs(f.handle, ctypes.c_void_p(h.data_ptr()), 18, 0, s) == 1
-    assert lib.dpd_set_fwd_launch(f.handle, 3, 8, 4, 0, 1) == 1
-    assert lib.dpd_set_fwd_launch(f.handle, 4, 8, 9, 0, 1) == 1
+    assert lib.dpd_set_fwd_launch(f.handle, 0, 3, 8, 4, 0, 1) == 1
+    assert lib.dpd_set_fwd_launch(f.handle, 0, 4, 8, 9, 0, 1) == 1
+    assert lib.dpd_set_fwd_launch(f.handle, 4, 4, 8, 4, 0, 1) == 1
     f.sync_status()
 
 
