@@ -135,8 +135,11 @@ dpd_status dpd_set_adj_launch(dpd_handle h, int gh_blocks, int tap_group);
  *   stages      depth of the shared-memory bulk-copy ring, 2..8
  *   ctas_per_sm CTAs per SM of the persistent grid, 0 = as many as fit
  *   use_tma     1 = bulk-copy pipeline, 0 = plain global loads
- * A shape that does not fit the device, or a mode / V not built for the
- * handle's (P, Q, M), makes dpd_apply return DPD_ERR_CUDA.
+ * Default: mode 3, V 8, 8 warps, 4 stages, as many CTAs as fit, TMA.  Every
+ * (P, Q, M) has modes 2 and 3 at V 4 and 8 and mode 0 at V 4; other
+ * combinations exist only for the benchmarked orders.  A shape that does not
+ * fit the device, or one not built for the handle's (P, Q, M), makes
+ * dpd_apply return DPD_ERR_CUDA.
  */
 dpd_status dpd_set_fwd_launch(dpd_handle h, int mode, int V, int warps, int stages, int ctas_per_sm,
                               int use_tma);

@@ -66,7 +66,7 @@ class DPD:
         k = ctypes.c_int()
         _lib.check("dpd_num_coeffs", self._lib.dpd_num_coeffs(self._h, ctypes.byref(k)))
         self.K = k.value
-        self.fwd_launch = dict(mode=0, V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1)
+        self.fwd_launch = dict(mode=3, V=8, warps=8, stages=4, ctas_per_sm=0, use_tma=1)
 
     # -- lifetime
     def close(self):

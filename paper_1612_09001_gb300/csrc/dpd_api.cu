@@ -214,8 +214,13 @@ dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stre
     a.vec_store = aligned(y, 16) ? 1 : 0;
     a.host_tab = h->host_tab_valid ? &h->h_tab : nullptr;
     dpd::FwdLaunch L = h->fwd;
-    if (!aligned(x, 16)) L.use_tma = 0;
     if (!h->host_tab_valid) L.mode &= ~dpd::kModeParamCoef;
+    if (!aligned(x, 16)) {
+        // 8-byte aligned input: plain-load kernel (built with shared-memory coefficients, V = 4)
+        L.use_tma = 0;
+        L.V = 4;
+        L.mode &= dpd::kModePackedFma;
+    }
     return cuda_status(dpd::launch_fwd_any(h->B, h->T, a, L, h->sm_count, static_cast<cudaStream_t>(stream)));
 }
 

@@ -277,6 +277,25 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Instantiated launch shapes.  Every (B, T) gets the default packed modes
+// (2: shared-memory coefficients, 3: parameter-bank coefficients) at V = 4 and
+// 8 plus the scalar mode 0 at V = 4; the plain-load kernel gets V = 4 with
+// shared-memory coefficients.  The (B, T) pairs of the benchmarked workloads
+// get every combination, for tuning and ablation.
+template <int B, int T>
+constexpr bool fwd_all_modes()
+{
+    return (B == 5 && T == 5) || (B == 3 && T == 3) || (B == 4 && T == 4) || (B == 6 && T == 8);
+}
+
+template <int B, int T, int V, int MODE, bool TMA>
+constexpr bool fwd_built()
+{
+    if (fwd_all_modes<B, T>()) return true;
+    if (!TMA) return V == 4 && (MODE == 0 || MODE == 2);
+    return (V == 4 && MODE == 0) || ((V == 4 || V == 8) && (MODE == 2 || MODE == 3));
+}
+
 template <int B, int T, int V, int MODE>
 cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cudaStream_t s)
 {
@@ -286,49 +305,47 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
         for (int i = 0; i < wl_table_floats(B, T); ++i) ptab.v[i] = a.host_tab->v[i];
     }
     if (L.use_tma) {
-        const int threads = (L.warps + 1) * 32;
-        const int S = L.warps * 32 * V;
-        const int64_t ntiles = (a.n + S - 1) / S;
-        const size_t smem = fwd_tma_smem<B, T, V>(L.warps, L.stages);
-        auto kern = fwd_tma_kernel<B, T, V, MODE>;
-        static size_t smem_set = 0;   // per instantiation
-        if (smem > smem_set) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
+        if constexpr (fwd_built<B, T, V, MODE, true>()) {
+            const int threads = (L.warps + 1) * 32;
+            const int S = L.warps * 32 * V;
+            const int64_t ntiles = (a.n + S - 1) / S;
+            const size_t smem = fwd_tma_smem<B, T, V>(L.warps, L.stages);
+            auto kern = fwd_tma_kernel<B, T, V, MODE>;
+            static size_t smem_set = 0;   // per instantiation
+            if (smem > smem_set) {
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem);
+                if (e != cudaSuccess) return e;
+                smem_set = smem;
+            }
+            int occ = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
             if (e != cudaSuccess) return e;
-            smem_set = smem;
+            if (occ < 1) return cudaErrorInvalidConfiguration;
+            const int cps = (L.ctas_per_sm > 0 && L.ctas_per_sm < occ) ? L.ctas_per_sm : occ;
+            int64_t grid = (int64_t)sm_count * cps;
+            if (grid > ntiles) grid = ntiles;
+            kern<<<(unsigned)grid, threads, smem, s>>>(a, L.stages, ntiles, ptab);
+            count_launch();
+            return cudaGetLastError();
         }
+        return cudaErrorNotSupported;
+    }
+    if constexpr (fwd_built<B, T, V, MODE, false>()) {
+        const int threads = 256;
         int occ = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, fwd_ldg_kernel<B, T, V, MODE>, threads, 0);
         if (e != cudaSuccess) return e;
-        if (occ < 1) return cudaErrorInvalidConfiguration;
-        const int cps = (L.ctas_per_sm > 0 && L.ctas_per_sm < occ) ? L.ctas_per_sm : occ;
-        int64_t grid = (int64_t)sm_count * cps;
-        if (grid > ntiles) grid = ntiles;
-        kern<<<(unsigned)grid, threads, smem, s>>>(a, L.stages, ntiles, ptab);
+        if (occ < 1) occ = 1;
+        const int64_t need = (a.n + (int64_t)threads * V - 1) / ((int64_t)threads * V);
+        int64_t grid = (int64_t)sm_count * occ;
+        if (grid > need) grid = need;
+        fwd_ldg_kernel<B, T, V, MODE><<<(unsigned)grid, threads, 0, s>>>(a, ptab);
         count_launch();
         return cudaGetLastError();
     }
-    const int threads = 256;
-    int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fwd_ldg_kernel<B, T, V, MODE>,
-                                                                  threads, 0);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) occ = 1;
-    const int64_t need = (a.n + (int64_t)threads * V - 1) / ((int64_t)threads * V);
-    int64_t grid = (int64_t)sm_count * occ;
-    if (grid > need) grid = need;
-    fwd_ldg_kernel<B, T, V, MODE><<<(unsigned)grid, threads, 0, s>>>(a, ptab);
-    count_launch();
-    return cudaGetLastError();
-}
-
-// Launch shapes instantiated for every (B, T); the other modes and V = 8 are
-// built for the (B, T) pairs of the benchmarked workloads only.
-template <int B, int T>
-constexpr bool fwd_all_modes()
-{
-    return (B == 5 && T == 5) || (B == 3 && T == 3) || (B == 4 && T == 4) || (B == 6 && T == 8);
+    return cudaErrorNotSupported;
 }
 
 template <int B, int T, int MODE>
@@ -337,9 +354,7 @@ cudaError_t launch_fwd_mode(const FwdArgs &a, const FwdLaunch &L, int sm_count, 
     switch (L.V) {
     case 2: return launch_fwd_tv<B, T, 2, MODE>(a, L, sm_count, s);
     case 4: return launch_fwd_tv<B, T, 4, MODE>(a, L, sm_count, s);
-    case 8:
-        if constexpr (fwd_all_modes<B, T>()) return launch_fwd_tv<B, T, 8, MODE>(a, L, sm_count, s);
-        return cudaErrorNotSupported;
+    case 8: return launch_fwd_tv<B, T, 8, MODE>(a, L, sm_count, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -349,15 +364,9 @@ cudaError_t launch_fwd_t(const FwdArgs &a, const FwdLaunch &L, int sm_count, cud
 {
     switch (L.mode) {
     case 0: return launch_fwd_mode<B, T, 0>(a, L, sm_count, s);
-    case 1:
-    case 2:
-    case 3:
-        if constexpr (fwd_all_modes<B, T>()) {
-            if (L.mode == 1) return launch_fwd_mode<B, T, 1>(a, L, sm_count, s);
-            if (L.mode == 2) return launch_fwd_mode<B, T, 2>(a, L, sm_count, s);
-            return launch_fwd_mode<B, T, 3>(a, L, sm_count, s);
-        }
-        return cudaErrorNotSupported;
+    case 1: return launch_fwd_mode<B, T, 1>(a, L, sm_count, s);
+    case 2: return launch_fwd_mode<B, T, 2>(a, L, sm_count, s);
+    case 3: return launch_fwd_mode<B, T, 3>(a, L, sm_count, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -42,8 +42,8 @@ enum : int { kModeParamCoef = 1, kModePackedFma = 2 };
 
 // Forward launch shape.
 struct FwdLaunch {
-    int mode = 0;         // compute mode bits (kModeParamCoef | kModePackedFma)
-    int V = 4;            // samples per consumer thread (2, 4 or 8)
+    int mode = kModeParamCoef | kModePackedFma;   // compute mode bits
+    int V = 8;            // samples per consumer thread (2, 4 or 8)
     int warps = 8;        // consumer warps per CTA (tile = warps * 32 * V samples)
     int stages = 4;       // shared-memory ring depth (bulk-copy pipeline)
     int ctas_per_sm = 0;  // 0: as many as fit
