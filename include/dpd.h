@@ -100,6 +100,31 @@ dpd_status dpd_set_coeffs(dpd_handle h, const void *coeffs, int K, int where, vo
 dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stream);
 
 /*
+ * Coefficient gradient without any device allocation.  (Not in the paper; a
+ * library convenience.)  Some callers may not allocate device memory at all:
+ * a transmit chain that forbids cudaMalloc once it is streaming (an allocation
+ * can synchronise the device and take unbounded time), or a host framework
+ * that owns every byte of device memory.  Such a caller cannot create a
+ * handle, because dpd_create allocates the handle's workspace.  This entry
+ * point needs no handle and allocates nothing: its scratch is a fixed array of
+ * 512 x 97 complex64 values (397,312 bytes) compiled into the library, which
+ * every device that loads the library keeps until the process exits.
+ *
+ * Computes the same gh as dpd_grad (K values for the model P, Q, M; no
+ * coefficients are needed).  x, gy: device, n complex64, 8-byte aligned; gh:
+ * device, K complex64, overwritten, must not overlap x or gy.  n == 0 zeroes
+ * gh.  Models beyond the scratch (K > 97) give DPD_ERR_UNSUPPORTED, as does a
+ * device ordinal >= 64.  The first call on a device looks up the scratch's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls on a device share the scratch and each call
+ * rewrites the rows it reads, so nothing carries over between calls, but calls
+ * whose kernels overlap on the GPU (different streams, or different host
+ * threads) race on it and must be serialised by the caller.
+ */
+dpd_status dpd_grad_coeffs_noalloc(int P, int Q, int M, const void *x, const void *gy, int64_t n,
+                                   void *gh, void *stream);
+
+/*
  * Adjoint of dpd_apply for a real loss L (not in the paper: used for
  * gradient-based direct learning).  Given gy = dL/dy for y = DPD(x), writes
  *   gh[j] = sum_n conj(Psi_{n,j}) gy_n            (K values, Psi of Eq. 2)

@@ -50,6 +50,7 @@ SIGNATURES = {
     "dpd_set_fwd_launch": [_vp, _i, _i, _i, _i, _i, _i],
     "dpd_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "dpd_set_adj_launch": [_vp, _i, _i],
+    "dpd_grad_coeffs_noalloc": [_i, _i, _i, _vp, _vp, _i64, _vp, _vp],
     "dpd_sync_status": [_vp, _vp],
     "dpd_status_string": [_i],
     "dpd_kernel_launches": [],
