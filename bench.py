@@ -228,7 +228,7 @@ def run_ours(args, world, rank, local):
     x_host = synth.ofdm2(n, key=(rank, 0))
     h = synth.coeffs(P, Q, M, key=(0, 1))
     f = dpd.DPD(P, Q, M)
-    f.set_coeffs(torch.from_numpy(h).to(dev))
+    f.set_coeffs(h)   # estimated offline, installed from host memory (the paper's use)
     xs = [torch.from_numpy(x_host).to(dev) for _ in range(2)]
     ys = [torch.empty_like(xs[0]) for _ in range(2)]
     stream = torch.cuda.current_stream(dev)
@@ -267,30 +267,43 @@ def run_ours(args, world, rank, local):
     value = world * K * n / total_max / 1e9
     mean_launch = sum(per) / len(per)
 
-    # ---- end to end: pinned host buffers, copies inside the timed region
+    # ---- end to end through the library's host path: the kernel reads the
+    # pinned host input and writes the pinned host output in place (zero copy)
     xh = torch.from_numpy(x_host).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
-    xd, yd = xs[0], ys[0]
-    for _ in range(2):
-        xd.copy_(xh, non_blocking=True)
-        f.apply(xd, out=yd)
-        yh.copy_(yd, non_blocking=True)
-    torch.cuda.synchronize(dev)
     K2 = max(3, min(K, 20))
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(K2):
+
+    def timed_host(step):
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K2):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(e0.elapsed_time(e1) * 1e-3)
+
+    l0 = dpd.kernel_launches()
+    t_zc = timed_host(lambda: f.apply_host(xh, out=yh))
+    e2e_launches = (dpd.kernel_launches() - l0) // (K2 + 2)
+    xd, yd = xs[0], ys[0]
+
+    def explicit():
         xd.copy_(xh, non_blocking=True)
         f.apply(xd, out=yd)
         yh.copy_(yd, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_t = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
-    e2e = {"value": world * K2 * n / e2e_t / 1e9, "unit": "Gsamples/s",
+
+    t_cp = timed_host(explicit)
+    e2e = {"value": world * K2 * n / t_zc / 1e9, "unit": "Gsamples/s",
            "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
-           "path": "pinned host -> cudaMemcpyAsync -> dpd_apply -> cudaMemcpyAsync -> pinned host"}
+           "path": "dpd_apply_host: kernel reads pinned host input and writes pinned host output over NVLink-C2C",
+           "gpu_launches_per_step": e2e_launches,
+           "explicit_copy_value": world * K2 * n / t_cp / 1e9,
+           "explicit_copy_path": "cudaMemcpyAsync H2D -> dpd_apply -> cudaMemcpyAsync D2H"}
 
     if rank != 0:
         f.close()
@@ -300,11 +313,13 @@ def run_ours(args, world, rank, local):
 
     peaks, peak_kind = measured_peaks()
     achieved = BYTES_PER_SAMPLE * n / mean_launch / 1e9
-    tr = recorded_traffic("fwd_tma_kernel<5,5,4>")
+    fl = f.fwd_launch
+    kname = f"fwd_tma_kernel<B=5,T=5,V={fl['V']},MODE={fl['mode']}>"
+    tr = recorded_traffic(kname)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "peak_kind": f"of {peak_kind} (copy bandwidth)",
-                "kernel": "fwd_tma_kernel<B=5,T=5,V=4>", "bytes_per_sample": BYTES_PER_SAMPLE}
+                "kernel": kname, "bytes_per_sample": BYTES_PER_SAMPLE}
     sm_mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else peaks.get("sm_max_mhz", 2070.0)
     props = torch.cuda.get_device_properties(dev)
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12

@@ -100,6 +100,18 @@ dpd_status dpd_set_coeffs(dpd_handle h, const void *coeffs, int K, int where, vo
 dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stream);
 
 /*
+ * dpd_apply on buffers in host memory, read and written by the kernel in place
+ * over the CPU-GPU link (zero copy, the technique of Sec. 3.3.1: no staging
+ * copies, no device buffers).  x and y may be pinned or registered host memory
+ * (cudaHostAlloc / cudaHostRegister), managed memory, or -- on systems whose
+ * GPU can access pageable memory, such as Grace-Blackwell -- ordinary
+ * malloc'd memory.  Device memory is rejected (use dpd_apply).  8-byte
+ * alignment, no overlap, n >= 0.  Asynchronous on `stream`: the buffers must
+ * stay valid, and y must not be read, until the stream has reached this work.
+ */
+dpd_status dpd_apply_host(dpd_handle h, const void *x, void *y, int64_t n, void *stream);
+
+/*
  * Coefficient gradient without any device allocation.  (Not in the paper; a
  * library convenience.)  Some callers may not allocate device memory at all:
  * a transmit chain that forbids cudaMalloc once it is streaming (an allocation

@@ -147,6 +147,21 @@ class DPD:
     def set_adj_launch(self, gh_blocks, tap_group):
         _lib.check("dpd_set_adj_launch", self._lib.dpd_set_adj_launch(self._h, gh_blocks, tap_group))
 
+    def apply_host(self, x, out=None, stream=None):
+        """y = DPD(x) for complex64 tensors in (pinned) host memory, read and written in place
+        by the kernel (zero copy).  Asynchronous: synchronise the stream before reading out."""
+        import torch
+        if not isinstance(x, torch.Tensor) or x.dtype != torch.complex64 or x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous complex64 host tensor")
+        if out is None:
+            out = torch.empty_like(x, pin_memory=x.is_pinned())
+        elif out.dtype != torch.complex64 or out.is_cuda or not out.is_contiguous() or out.numel() != x.numel():
+            raise ValueError("out must be a contiguous complex64 host tensor like x")
+        _lib.check("dpd_apply_host", self._lib.dpd_apply_host(
+            self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.numel(),
+            _stream_ptr(stream)))
+        return out
+
     def set_fwd_launch(self, V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1, mode=0):
         _lib.check("dpd_set_fwd_launch", self._lib.dpd_set_fwd_launch(
             self._h, mode, V, warps, stages, ctas_per_sm, use_tma))

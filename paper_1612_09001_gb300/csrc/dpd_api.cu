@@ -216,10 +216,9 @@ dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stre
     dpd::FwdLaunch L = h->fwd;
     if (!h->host_tab_valid) L.mode &= ~dpd::kModeParamCoef;
     if (!aligned(x, 16)) {
-        // 8-byte aligned input: plain-load kernel (built with shared-memory coefficients, V = 4)
+        // 8-byte aligned input: plain-load kernel (built for V = 4)
         L.use_tma = 0;
         L.V = 4;
-        L.mode &= dpd::kModePackedFma;
     }
     return cuda_status(dpd::launch_fwd_any(h->B, h->T, a, L, h->sm_count, static_cast<cudaStream_t>(stream)));
 }
@@ -266,6 +265,51 @@ dpd_status dpd_grad(dpd_handle h, const void *x, const void *gy, int64_t n, void
         if (e != cudaSuccess) return DPD_ERR_CUDA;
     }
     return DPD_OK;
+}
+
+dpd_status dpd_apply_host(dpd_handle h, const void *x, void *y, int64_t n, void *stream)
+{
+    if (!h || n < 0) return DPD_ERR_INVALID_ARGUMENT;
+    if (!h->has_coeffs) return DPD_ERR_NO_COEFFS;
+    if (n == 0) return DPD_OK;
+    if (!x || !y || !aligned(x, 8) || !aligned(y, 8)) return DPD_ERR_INVALID_ARGUMENT;
+    if (n > (int64_t)(INT64_MAX / sizeof(float2))) return DPD_ERR_INVALID_ARGUMENT;
+    const size_t bytes = (size_t)n * sizeof(float2);
+    if (overlap(x, bytes, y, bytes)) return DPD_ERR_INVALID_ARGUMENT;
+    // Resolve each buffer to an address the kernel can dereference.
+    const void *ptrs[2] = {x, y};
+    void *dev[2] = {nullptr, nullptr};
+    int pageable_ok = 0;
+    if (cudaDeviceGetAttribute(&pageable_ok, cudaDevAttrPageableMemoryAccess, h->device) != cudaSuccess)
+        return DPD_ERR_CUDA;
+    for (int i = 0; i < 2; ++i) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, ptrs[i]) != cudaSuccess) {
+            cudaGetLastError();
+            return DPD_ERR_INVALID_ARGUMENT;
+        }
+        if (at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeManaged) {
+            if (!at.devicePointer) return DPD_ERR_INVALID_ARGUMENT;
+            dev[i] = at.devicePointer;
+        } else if (at.type == cudaMemoryTypeUnregistered && pageable_ok) {
+            dev[i] = const_cast<void *>(ptrs[i]);
+        } else {
+            return DPD_ERR_INVALID_ARGUMENT;   // device memory: use dpd_apply
+        }
+    }
+    dpd::FwdArgs a;
+    a.x = static_cast<const float2 *>(dev[0]);
+    a.y = static_cast<float2 *>(dev[1]);
+    a.n = n;
+    a.tab = h->d_tab;
+    a.status = h->d_status;
+    a.vec_store = 0;
+    a.host_tab = h->host_tab_valid ? &h->h_tab : nullptr;
+    dpd::FwdLaunch L = h->fwd;
+    L.use_tma = 0;   // plain loads and stores straight to host memory
+    L.V = 4;
+    L.mode &= dpd::kModePackedFma | (h->host_tab_valid ? dpd::kModeParamCoef : 0);
+    return cuda_status(dpd::launch_fwd_any(h->B, h->T, a, L, h->sm_count, static_cast<cudaStream_t>(stream)));
 }
 
 dpd_status dpd_set_adj_launch(dpd_handle h, int gh_blocks, int tap_group)

@@ -25,6 +25,10 @@
 #include "dpd_device.cuh"
 #include "dpd_internal.h"
 
+#ifndef DPD_FWD_LOCKSTEP
+#define DPD_FWD_LOCKSTEP 0
+#endif
+
 namespace dpd {
 
 // Coefficient table passed by value (kernel parameter bank).
@@ -67,6 +71,32 @@ __device__ __forceinline__ void fwd_compute(const float *__restrict__ stab, cons
                 cf[m] = reinterpret_cast<const float4 *>(stab)[k * B + m];
         }
 #pragma unroll
+        if constexpr (PACKED && DPD_FWD_LOCKSTEP) {
+            // All V samples advance one Horner step together: 2V independent chains.
+            float2 pa[V], pb[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                pa[v] = make_float2(cf[B - 1].x, cf[B - 1].y);
+                pb[v] = make_float2(cf[B - 1].z, cf[B - 1].w);
+            }
+#pragma unroll
+            for (int m = B - 2; m >= 0; --m) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int j = v + (T - 1) - k;
+                    const float2 rr = make_float2(r[j], r[j]);
+                    pa[v] = __ffma2_rn(pa[v], rr, make_float2(cf[m].x, cf[m].y));
+                    pb[v] = __ffma2_rn(pb[v], rr, make_float2(cf[m].z, cf[m].w));
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int j = v + (T - 1) - k;
+                acc[v] = __ffma2_rn(pa[v], make_float2(wr[j], wr[j]), acc[v]);
+                acc[v] = __ffma2_rn(pb[v], make_float2(wi[j], wi[j]), acc[v]);
+            }
+            continue;
+        }
         for (int v = 0; v < V; ++v) {
             const int j = v + (T - 1) - k;   // window index of sample n - k
             if constexpr (PACKED) {
@@ -117,8 +147,15 @@ __host__ __device__ constexpr size_t fwd_tma_smem(int warps, int stages)
            (size_t)stages * (size_t)(kHalo + warps * 32 * V) * sizeof(float2);
 }
 
+#ifndef DPD_FWD_MAX_THREADS
+#define DPD_FWD_MAX_THREADS (32 * 17)
+#endif
+#ifndef DPD_FWD_MIN_BLOCKS
+#define DPD_FWD_MIN_BLOCKS 1
+#endif
+
 template <int B, int T, int V, int MODE>
-__global__ void __launch_bounds__(32 * 17)
+__global__ void __launch_bounds__(DPD_FWD_MAX_THREADS, DPD_FWD_MIN_BLOCKS)
     fwd_tma_kernel(FwdArgs a, int stages, int64_t ntiles, const __grid_constant__ ParamTab<B, T> ptab)
 {
     constexpr int W = V + T - 1;
@@ -279,8 +316,8 @@ __global__ void __launch_bounds__(256)
 
 // Instantiated launch shapes.  Every (B, T) gets the default packed modes
 // (2: shared-memory coefficients, 3: parameter-bank coefficients) at V = 4 and
-// 8 plus the scalar mode 0 at V = 4; the plain-load kernel gets V = 4 with
-// shared-memory coefficients.  The (B, T) pairs of the benchmarked workloads
+// 8 plus the scalar mode 0 at V = 4; the plain-load kernel gets V = 4 in
+// modes 0, 2 and 3.  The (B, T) pairs of the benchmarked workloads
 // get every combination, for tuning and ablation.
 template <int B, int T>
 constexpr bool fwd_all_modes()
@@ -292,7 +329,7 @@ template <int B, int T, int V, int MODE, bool TMA>
 constexpr bool fwd_built()
 {
     if (fwd_all_modes<B, T>()) return true;
-    if (!TMA) return V == 4 && (MODE == 0 || MODE == 2);
+    if (!TMA) return V == 4 && (MODE == 0 || MODE == 2 || MODE == 3);
     return (V == 4 && MODE == 0) || ((V == 4 || V == 8) && (MODE == 2 || MODE == 3));
 }
 

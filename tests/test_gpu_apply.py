@@ -194,3 +194,35 @@ def test_device_coefficients_and_graph_replay():
     torch.cuda.synchronize()
     assert_parity(yd.cpu().numpy(), oracle.apply(x, h2, P, Q, M), what="graph h2")
     f.sync_status()
+
+
+@pytest.mark.parametrize("P,Q,M", [(9, 9, 4), (5, 3, 4), (11, 11, 7)])
+def test_apply_host_zero_copy(P, Q, M):
+    """The kernel reads and writes pinned host buffers in place (Sec. 3.3.1 zero copy)."""
+    n = 300007
+    x = synth.ofdm2(n, key=(9, P))
+    h = synth.coeffs(P, Q, M, key=(9, 1))
+    f = dpd.DPD(P, Q, M)
+    f.set_coeffs(h)
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.full((n,), complex(7, 7), dtype=torch.complex64).pin_memory()
+    f.apply_host(xh, out=yh)
+    f.sync_status()
+    ref = oracle.apply(x, h, P, Q, M)
+    assert_parity(yh.numpy(), ref, what="zero copy pinned")
+    # device memory is refused by the host entry point
+    lib = _lib.load()
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.dpd_apply_host(f.handle, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()), n, s) == 1
+    # ordinary pageable memory works where the GPU can access it, else it is refused
+    xp = torch.from_numpy(x.copy())
+    yp = torch.empty_like(xp)
+    try:
+        f.apply_host(xp, out=yp)
+        f.sync_status()
+        assert_parity(yp.numpy(), ref, what="zero copy pageable")
+    except dpd.DPDError as e:
+        assert e.code == 1
+    f.close()
