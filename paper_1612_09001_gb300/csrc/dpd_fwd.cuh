@@ -25,10 +25,6 @@
 #include "dpd_device.cuh"
 #include "dpd_internal.h"
 
-#ifndef DPD_FWD_LOCKSTEP
-#define DPD_FWD_LOCKSTEP 0
-#endif
-
 namespace dpd {
 
 // Coefficient table passed by value (kernel parameter bank).
@@ -70,9 +66,9 @@ __device__ __forceinline__ void fwd_compute(const float *__restrict__ stab, cons
             else
                 cf[m] = reinterpret_cast<const float4 *>(stab)[k * B + m];
         }
-#pragma unroll
-        if constexpr (PACKED && DPD_FWD_LOCKSTEP) {
-            // All V samples advance one Horner step together: 2V independent chains.
+        if constexpr (PACKED) {
+            // All V samples advance one Horner step together: 2V independent
+            // chains of packed {P0,P2} and {P1,P3} evaluations.
             float2 pa[V], pb[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
@@ -83,7 +79,7 @@ __device__ __forceinline__ void fwd_compute(const float *__restrict__ stab, cons
             for (int m = B - 2; m >= 0; --m) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    const int j = v + (T - 1) - k;
+                    const int j = v + (T - 1) - k;   // window index of sample n - k
                     const float2 rr = make_float2(r[j], r[j]);
                     pa[v] = __ffma2_rn(pa[v], rr, make_float2(cf[m].x, cf[m].y));
                     pb[v] = __ffma2_rn(pb[v], rr, make_float2(cf[m].z, cf[m].w));
@@ -92,25 +88,13 @@ __device__ __forceinline__ void fwd_compute(const float *__restrict__ stab, cons
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const int j = v + (T - 1) - k;
-                acc[v] = __ffma2_rn(pa[v], make_float2(wr[j], wr[j]), acc[v]);
-                acc[v] = __ffma2_rn(pb[v], make_float2(wi[j], wi[j]), acc[v]);
+                acc[v] = __ffma2_rn(pa[v], make_float2(wr[j], wr[j]), acc[v]);   // {P0 a, P2 a}
+                acc[v] = __ffma2_rn(pb[v], make_float2(wi[j], wi[j]), acc[v]);   // {P1 b, P3 b}
             }
-            continue;
-        }
-        for (int v = 0; v < V; ++v) {
-            const int j = v + (T - 1) - k;   // window index of sample n - k
-            if constexpr (PACKED) {
-                const float2 rr = make_float2(r[j], r[j]);
-                float2 pa = make_float2(cf[B - 1].x, cf[B - 1].y);   // {P0, P2}
-                float2 pb = make_float2(cf[B - 1].z, cf[B - 1].w);   // {P1, P3}
+        } else {
 #pragma unroll
-                for (int m = B - 2; m >= 0; --m) {
-                    pa = __ffma2_rn(pa, rr, make_float2(cf[m].x, cf[m].y));
-                    pb = __ffma2_rn(pb, rr, make_float2(cf[m].z, cf[m].w));
-                }
-                acc[v] = __ffma2_rn(pa, make_float2(wr[j], wr[j]), acc[v]);
-                acc[v] = __ffma2_rn(pb, make_float2(wi[j], wi[j]), acc[v]);
-            } else {
+            for (int v = 0; v < V; ++v) {
+                const int j = v + (T - 1) - k;   // window index of sample n - k
                 float p0 = cf[B - 1].x, p2 = cf[B - 1].y, p1 = cf[B - 1].z, p3 = cf[B - 1].w;
 #pragma unroll
                 for (int m = B - 2; m >= 0; --m) {
@@ -147,15 +131,8 @@ __host__ __device__ constexpr size_t fwd_tma_smem(int warps, int stages)
            (size_t)stages * (size_t)(kHalo + warps * 32 * V) * sizeof(float2);
 }
 
-#ifndef DPD_FWD_MAX_THREADS
-#define DPD_FWD_MAX_THREADS (32 * 17)
-#endif
-#ifndef DPD_FWD_MIN_BLOCKS
-#define DPD_FWD_MIN_BLOCKS 1
-#endif
-
 template <int B, int T, int V, int MODE>
-__global__ void __launch_bounds__(DPD_FWD_MAX_THREADS, DPD_FWD_MIN_BLOCKS)
+__global__ void __launch_bounds__(32 * 17)
     fwd_tma_kernel(FwdArgs a, int stages, int64_t ntiles, const __grid_constant__ ParamTab<B, T> ptab)
 {
     constexpr int W = V + T - 1;
@@ -355,9 +332,16 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
                 if (e != cudaSuccess) return e;
                 smem_set = smem;
             }
-            int occ = 0;
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
-            if (e != cudaSuccess) return e;
+            // Occupancy of the last shape launched from this host thread.
+            thread_local int occ_threads = -1;
+            thread_local size_t occ_smem = 0;
+            thread_local int occ = 0;
+            if (threads != occ_threads || smem != occ_smem) {
+                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+                if (e != cudaSuccess) return e;
+                occ_threads = threads;
+                occ_smem = smem;
+            }
             if (occ < 1) return cudaErrorInvalidConfiguration;
             const int cps = (L.ctas_per_sm > 0 && L.ctas_per_sm < occ) ? L.ctas_per_sm : occ;
             int64_t grid = (int64_t)sm_count * cps;
@@ -370,11 +354,13 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
     }
     if constexpr (fwd_built<B, T, V, MODE, false>()) {
         const int threads = 256;
-        int occ = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, fwd_ldg_kernel<B, T, V, MODE>, threads, 0);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
+        thread_local int occ = 0;
+        if (occ == 0) {
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ, fwd_ldg_kernel<B, T, V, MODE>, threads, 0);
+            if (e != cudaSuccess) return e;
+            if (occ < 1) occ = 1;
+        }
         const int64_t need = (a.n + (int64_t)threads * V - 1) / ((int64_t)threads * V);
         int64_t grid = (int64_t)sm_count * occ;
         if (grid > need) grid = need;
