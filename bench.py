@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-patterns", action="store_true",
+                    help="skip the batched / adjoint / Gram side measurements")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up for at least this long so clocks settle and get sampled")
     return ap.parse_args()
@@ -199,6 +201,80 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------------------- our arm
+def _time_graph(fn, reps, dev):
+    """Capture fn() in a CUDA graph, replay it reps times, return seconds per replay."""
+    import torch
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        fn()
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        fn()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream(dev)
+    e0.record(cur)
+    for _ in range(reps):
+        g.replay()
+    e1.record(cur)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) * 1e-3 / reps
+
+
+def measure_batched(dev, reps=20):
+    """64 antenna streams, lengths U[2^12, 2^20], P in {5,7,9}, M in {2..6}:
+    one persistent launch (CUDA graph) against 64 plain launches."""
+    import torch
+    import dpd_synth as synth
+    import paper_1612_09001_gb300 as dpd
+    specs = synth.batch_streams(64, seed=0)
+    streams, handles = [], []
+    for sp in specs:
+        x = torch.from_numpy(sp["x"]).to(dev)
+        streams.append(dict(x=x, y=torch.empty_like(x), P=sp["P"], Q=sp["Q"], M=sp["M"], h=sp["h"]))
+        f = dpd.DPD(sp["P"], sp["Q"], sp["M"])
+        f.set_coeffs(sp["h"])
+        handles.append(f)
+    total = sum(len(sp["x"]) for sp in specs)
+    plan = dpd.BatchedPlan(streams)
+    l0 = dpd.kernel_launches()
+    t_plan = _time_graph(lambda: plan.execute(), reps, dev)
+    launches_plan = (dpd.kernel_launches() - l0) // 2   # captured twice (warm-up + capture)
+
+    def plain():
+        for f, st in zip(handles, streams):
+            f.apply(st["x"], out=st["y"])
+
+    t_graph64 = _time_graph(plain, reps, dev)
+    for _ in range(3):
+        plain()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plain()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_plain = e0.elapsed_time(e1) * 1e-3 / reps
+    plan.sync_status()
+    for f in handles:
+        f.sync_status()
+        f.close()
+    plan.close()
+    return {"workload": "64 streams, n ~ U[2^12, 2^20], P=Q in {5,7,9}, M in {2..6}, clipped Gaussian RMS 0.3",
+            "total_samples": total, "unit": "Gsamples/s",
+            "persistent_graph": total / t_plan / 1e9, "persistent_launches_per_step": launches_plan,
+            "plain_64_launches": total / t_plain / 1e9, "plain_64_in_one_graph": total / t_graph64 / 1e9,
+            "persistent_us": t_plan * 1e6, "plain_64_us": t_plain * 1e6, "plain_64_graph_us": t_graph64 * 1e6,
+            "hbm_frac_persistent": 16 * total / t_plan / 1e9}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -330,6 +406,12 @@ def run_ours(args, world, rank, local):
            "achieved_tflops_executed": rate * FLOPS_WL(P, Q, M) / 1e12,
            "frac_executed": rate * FLOPS_WL(P, Q, M) / 1e12 / fp32_peak}
 
+    patterns = {}
+    if not args.no_patterns:
+        b = measure_batched(dev)
+        b["hbm_frac_persistent"] = b["hbm_frac_persistent"] / peaks["hbm_gbs"]
+        patterns["batched"] = b
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, el, reps, cores = cpu_oracle_throughput(1 << 22, 10.0)
@@ -345,7 +427,7 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "launch": dict(f.fwd_launch)},
         "wall_s_timed": wall, "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "alu": alu,
-        "e2e": e2e, "cpu_baseline": cpu,
+        "e2e": e2e, "cpu_baseline": cpu, "patterns": patterns,
         "samples_per_s_per_gpu": K * n / total / 1e9,
     }
     print(json.dumps(line), flush=True)

@@ -181,6 +181,60 @@ dpd_status dpd_set_adj_launch(dpd_handle h, int gh_blocks, int tap_group);
 dpd_status dpd_set_fwd_launch(dpd_handle h, int mode, int V, int warps, int stages, int ctas_per_sm,
                               int use_tma);
 
+/* ------------------------------------------------------------------ batched */
+
+/*
+ * One antenna stream of a batched plan (not in the paper; the batched form
+ * filters many independent transmit chains in one launch).  Each stream is an
+ * independent instance of Eq. 1 with its own model, coefficients and zero
+ * history.
+ *   x : device, n complex64, 16-byte aligned (bulk copies)
+ *   y : device, n complex64, 8-byte aligned; must not overlap any stream's x
+ *       or another stream's y
+ *   n : >= 0;  P, Q, M : as for dpd_create
+ *   h : K complex64 coefficients, stacking order of Sec. 2.2, in host or
+ *       device memory as given by the `where` argument of dpd_plan_batched
+ */
+typedef struct dpd_stream_desc {
+    const void *x;
+    void *y;
+    int64_t n;
+    int P, Q, M;
+    const void *h;
+} dpd_stream_desc;
+
+typedef struct dpd_plan_s *dpd_plan;
+
+/*
+ * Build a plan for `count` streams: copies the coefficients and prepares their
+ * tables, cuts the streams into tiles and uploads the work list (ordered by
+ * per-sample cost).  The x / y pointers are recorded in the plan; a plan is
+ * executed on those buffers.  Allocates the plan's device memory and
+ * synchronises the device; the caller keeps ownership of descs and h.
+ */
+dpd_status dpd_plan_batched(const dpd_stream_desc *descs, int count, int where, dpd_plan *out);
+
+/*
+ * Filter every stream of the plan with ONE persistent kernel launch on
+ * `stream`.  Allocates nothing and does not synchronise: capture it in a CUDA
+ * graph and replay.  Concurrent executions of one plan must not overlap.
+ */
+dpd_status dpd_exec_batched(dpd_plan plan, void *stream);
+
+/*
+ * Launch shape of dpd_exec_batched (autotuner): V in {4, 8} samples per thread,
+ * warps 1..16 consumer warps (tile = warps*32*V samples; changing the tile
+ * rebuilds the work list, synchronously), stages 2..8, ctas_per_sm >= 0 (0 = as
+ * many as fit).  Default 8, 8, 4, 0.
+ */
+dpd_status dpd_plan_set_launch(dpd_plan plan, int V, int warps, int stages, int ctas_per_sm);
+
+/* Synchronise `stream`, read and clear the plan's device error word (as dpd_sync_status). */
+dpd_status dpd_plan_sync_status(dpd_plan plan, void *stream);
+
+/* Free a plan (NULL accepted).  No execution of it may still be running. */
+dpd_status dpd_plan_destroy(dpd_plan plan);
+
 /*
  * Synchronise `stream`, then read and clear the handle's device error word.
  * Returns DPD_ERR_TIMEOUT if a kernel recorded that a bounded wait ran out,

@@ -17,7 +17,7 @@ import ctypes
 from . import _lib
 from ._lib import DPDError, DPD_HOST, DPD_DEVICE  # noqa: F401
 
-__all__ = ["DPD", "DPDError", "num_coeffs", "kernel_launches", "lib"]
+__all__ = ["DPD", "BatchedPlan", "DPDError", "num_coeffs", "kernel_launches", "lib"]
 
 
 def lib():
@@ -171,3 +171,66 @@ class DPD:
     def sync_status(self, stream=None):
         """Synchronise the stream and raise if a kernel recorded an error."""
         _lib.check("dpd_sync_status", self._lib.dpd_sync_status(self._h, _stream_ptr(stream)))
+
+
+class BatchedPlan:
+    """Many independent streams filtered by one persistent launch.
+
+    ``streams`` is a list of dicts with keys x, y (complex64 CUDA tensors), P, Q,
+    M and h (K complex64 coefficients: numpy array, CPU or CUDA tensor; all on
+    the same side).  The plan records the buffers; ``execute`` launches one
+    kernel on the current (or given) stream and can be captured in a CUDA graph."""
+
+    def __init__(self, streams):
+        import numpy as np
+        import torch
+        self._lib = lib()
+        n = len(streams)
+        descs = (_lib.StreamDesc * max(n, 1))()
+        keep = []
+        where = None
+        for i, st in enumerate(streams):
+            x, y = st["x"], st["y"]
+            _check_samples(x, "x")
+            _check_samples(y, "y")
+            if y.numel() != x.numel():
+                raise ValueError("x and y of a stream must have the same length")
+            h = st["h"]
+            if isinstance(h, np.ndarray):
+                h = torch.from_numpy(np.ascontiguousarray(h.astype(np.complex64)))
+            if h.dtype != torch.complex64 or h.numel() != num_coeffs(st["P"], st["Q"], st["M"]):
+                raise ValueError(f"stream {i}: coefficients must be K complex64 values")
+            h = h.contiguous()
+            w = DPD_DEVICE if h.is_cuda else DPD_HOST
+            if where is None:
+                where = w
+            elif w != where:
+                raise ValueError("all coefficient vectors must be on the same side (host or device)")
+            keep.append(h)
+            descs[i] = _lib.StreamDesc(x.data_ptr(), y.data_ptr(), x.numel(), st["P"], st["Q"], st["M"],
+                                       h.data_ptr())
+        p = ctypes.c_void_p()
+        _lib.check("dpd_plan_batched", self._lib.dpd_plan_batched(
+            ctypes.cast(descs, ctypes.c_void_p), n, DPD_HOST if where is None else where, ctypes.byref(p)))
+        self._p = p
+        self._streams = streams   # keep the recorded buffers alive
+
+    def execute(self, stream=None):
+        _lib.check("dpd_exec_batched", self._lib.dpd_exec_batched(self._p, _stream_ptr(stream)))
+
+    def set_launch(self, V=8, warps=8, stages=4, ctas_per_sm=0):
+        _lib.check("dpd_plan_set_launch", self._lib.dpd_plan_set_launch(self._p, V, warps, stages, ctas_per_sm))
+
+    def sync_status(self, stream=None):
+        _lib.check("dpd_plan_sync_status", self._lib.dpd_plan_sync_status(self._p, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self._lib.dpd_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

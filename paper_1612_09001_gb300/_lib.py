@@ -53,9 +53,19 @@ SIGNATURES = {
     "dpd_set_adj_launch": [_vp, _i, _i],
     "dpd_grad_coeffs_noalloc": [_i, _i, _i, _vp, _vp, _i64, _vp, _vp],
     "dpd_sync_status": [_vp, _vp],
+    "dpd_plan_batched": [_vp, _i, _i, ctypes.POINTER(_vp)],
+    "dpd_exec_batched": [_vp, _vp],
+    "dpd_plan_set_launch": [_vp, _i, _i, _i, _i],
+    "dpd_plan_sync_status": [_vp, _vp],
+    "dpd_plan_destroy": [_vp],
     "dpd_status_string": [_i],
     "dpd_kernel_launches": [],
 }
+class StreamDesc(ctypes.Structure):
+    """dpd_stream_desc of include/dpd.h."""
+    _fields_ = [("x", _vp), ("y", _vp), ("n", _i64), ("P", _i), ("Q", _i), ("M", _i), ("h", _vp)]
+
+
 _RESTYPE = {"dpd_status_string": ctypes.c_char_p, "dpd_kernel_launches": ctypes.c_uint64}
 
 

@@ -1,0 +1,221 @@
+// libdpd C ABI, batched part: plans of many independent streams executed by
+// one persistent launch (see dpd_batched.cuh and include/dpd.h).
+#include <algorithm>
+#include <cstdint>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dpd.h"
+#include "dpd_batched.cuh"
+
+namespace dpd {
+cudaError_t launch_batched_57(const BatchArgs &a, int V, int warps, int stages, int cps, int sm_count,
+                              cudaStream_t s);
+cudaError_t launch_batched_68(const BatchArgs &a, int V, int warps, int stages, int cps, int sm_count,
+                              cudaStream_t s);
+}  // namespace dpd
+
+struct dpd_plan_s {
+    int device = 0, sm_count = 0;
+    std::vector<dpd::BatchStream> streams;   // host copy (device pointers, sizes, table offsets)
+    dpd::BatchStream *d_streams = nullptr;
+    dpd::BatchItem *d_items = nullptr;
+    float *d_tabs = nullptr;
+    float2 *d_h = nullptr;
+    int *d_status = nullptr;
+    int nitems = 0, items_cap = 0;
+    int small = 1;            // every stream has B <= 5 and T <= 7
+    int V = 8, warps = 8, stages = 4, ctas_per_sm = 0;
+};
+
+namespace {
+
+int nbranch(int order) { return order > 0 ? (order + 1) / 2 : 0; }
+bool valid_order(int o) { return o == 0 || (o > 0 && o <= 11 && (o % 2) == 1); }
+bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+bool overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return na && nb && x < y + nb && y < x + na;
+}
+
+void free_plan(dpd_plan p)
+{
+    cudaFree(p->d_streams);
+    cudaFree(p->d_items);
+    cudaFree(p->d_tabs);
+    cudaFree(p->d_h);
+    cudaFree(p->d_status);
+    delete p;
+}
+
+// Work list for tile size S: streams by decreasing per-sample cost (B * T),
+// every tile of a stream in order.  Launched CTAs take items round-robin.
+dpd_status build_items(dpd_plan p)
+{
+    const int S = p->warps * 32 * p->V;
+    std::vector<int> order(p->streams.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return p->streams[a].B * p->streams[a].T > p->streams[b].B * p->streams[b].T;
+    });
+    std::vector<dpd::BatchItem> items;
+    for (int si : order) {
+        const int64_t nt = (p->streams[si].n + S - 1) / S;
+        if (nt > INT32_MAX) return DPD_ERR_UNSUPPORTED;
+        for (int64_t t = 0; t < nt; ++t) items.push_back({si, (int)t});
+    }
+    if (items.size() > (size_t)INT32_MAX) return DPD_ERR_UNSUPPORTED;
+    if ((int)items.size() > p->items_cap) {
+        cudaFree(p->d_items);
+        p->d_items = nullptr;
+        const size_t cap = std::max<size_t>(items.size(), 1);
+        if (cudaMalloc(&p->d_items, cap * sizeof(dpd::BatchItem)) != cudaSuccess) return DPD_ERR_ALLOC;
+        p->items_cap = (int)cap;
+    }
+    if (!items.empty() &&
+        cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(dpd::BatchItem), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return DPD_ERR_CUDA;
+    p->nitems = (int)items.size();
+    return DPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dpd_status dpd_plan_batched(const dpd_stream_desc *descs, int count, int where, dpd_plan *out)
+{
+    if (!out || count < 0 || (count > 0 && !descs)) return DPD_ERR_INVALID_ARGUMENT;
+    if (where != DPD_HOST && where != DPD_DEVICE) return DPD_ERR_INVALID_ARGUMENT;
+    // validate every stream before touching the device
+    size_t hfloats = 0, tfloats = 0;
+    for (int i = 0; i < count; ++i) {
+        const dpd_stream_desc &d = descs[i];
+        if (!valid_order(d.P) || !valid_order(d.Q) || (d.P == 0 && d.Q == 0)) return DPD_ERR_INVALID_ARGUMENT;
+        if (d.M < 0 || d.M + 1 > dpd::kMaxT || d.n < 0 || !d.h) return DPD_ERR_INVALID_ARGUMENT;
+        if (d.n > (int64_t)(INT64_MAX / sizeof(float2))) return DPD_ERR_INVALID_ARGUMENT;
+        if (d.n > 0 && (!d.x || !d.y || !aligned(d.x, 16) || !aligned(d.y, 8))) return DPD_ERR_INVALID_ARGUMENT;
+        if (!aligned(d.h, where == DPD_HOST ? 4 : 8)) return DPD_ERR_INVALID_ARGUMENT;
+        const int Bp = nbranch(d.P), Bq = nbranch(d.Q), B = std::max(Bp, Bq), T = d.M + 1;
+        hfloats += 2 * (size_t)((Bp + Bq) * T + 1);
+        tfloats += (size_t)((dpd::wl_table_floats(B, T) * 4 + 15) / 16) * 4;
+    }
+    for (int i = 0; i < count; ++i) {   // outputs overlap no input and no other output
+        const size_t bi = (size_t)descs[i].n * sizeof(float2);
+        for (int j = 0; j < count; ++j) {
+            const size_t bj = (size_t)descs[j].n * sizeof(float2);
+            if (overlap(descs[i].y, bi, descs[j].x, bj)) return DPD_ERR_INVALID_ARGUMENT;
+            if (j != i && overlap(descs[i].y, bi, descs[j].y, bj)) return DPD_ERR_INVALID_ARGUMENT;
+        }
+    }
+    dpd_plan p = new (std::nothrow) dpd_plan_s();
+    if (!p) return DPD_ERR_ALLOC;
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+        delete p;
+        return DPD_ERR_CUDA;
+    }
+    if (cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&p->d_h, std::max<size_t>(hfloats, 2) * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&p->d_tabs, std::max<size_t>(tfloats, 4) * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&p->d_streams, std::max(count, 1) * sizeof(dpd::BatchStream)) != cudaSuccess) {
+        free_plan(p);
+        return DPD_ERR_ALLOC;
+    }
+    if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) {
+        free_plan(p);
+        return DPD_ERR_CUDA;
+    }
+    size_t hoff = 0, toff = 0;
+    for (int i = 0; i < count; ++i) {
+        const dpd_stream_desc &d = descs[i];
+        const int Bp = nbranch(d.P), Bq = nbranch(d.Q), B = std::max(Bp, Bq), T = d.M + 1;
+        const int K = (Bp + Bq) * T + 1;
+        float2 *hdst = reinterpret_cast<float2 *>(p->d_h + hoff);
+        const cudaMemcpyKind kind = where == DPD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        if (cudaMemcpy(hdst, d.h, sizeof(float2) * K, kind) != cudaSuccess ||
+            dpd::launch_wl_table(hdst, Bp, Bq, T, p->d_tabs + toff, nullptr, 0) != cudaSuccess) {
+            free_plan(p);
+            return DPD_ERR_CUDA;
+        }
+        dpd::BatchStream st;
+        st.x = static_cast<const float2 *>(d.x);
+        st.y = static_cast<float2 *>(d.y);
+        st.n = d.n;
+        st.B = B;
+        st.T = T;
+        st.tab_off = (int)toff;
+        st.tab_bytes = ((dpd::wl_table_floats(B, T) * 4 + 15) / 16) * 16;
+        p->streams.push_back(st);
+        if (B > 5 || T > 7) p->small = 0;
+        hoff += 2 * (size_t)K;
+        toff += (size_t)st.tab_bytes / 4;
+    }
+    if (count > 0 &&
+        cudaMemcpy(p->d_streams, p->streams.data(), count * sizeof(dpd::BatchStream), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        free_plan(p);
+        return DPD_ERR_CUDA;
+    }
+    dpd_status st = build_items(p);
+    if (st == DPD_OK && cudaDeviceSynchronize() != cudaSuccess) st = DPD_ERR_CUDA;
+    if (st != DPD_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return DPD_OK;
+}
+
+dpd_status dpd_plan_set_launch(dpd_plan p, int V, int warps, int stages, int ctas_per_sm)
+{
+    if (!p) return DPD_ERR_INVALID_ARGUMENT;
+    if ((V != 4 && V != 8) || warps < 1 || warps > 16 || stages < 2 || stages > 8 || ctas_per_sm < 0)
+        return DPD_ERR_INVALID_ARGUMENT;
+    const bool retile = (V != p->V || warps != p->warps);
+    p->V = V;
+    p->warps = warps;
+    p->stages = stages;
+    p->ctas_per_sm = ctas_per_sm;
+    return retile ? build_items(p) : DPD_OK;
+}
+
+dpd_status dpd_exec_batched(dpd_plan p, void *stream)
+{
+    if (!p) return DPD_ERR_INVALID_ARGUMENT;
+    if (p->nitems == 0) return DPD_OK;
+    dpd::BatchArgs a;
+    a.streams = p->d_streams;
+    a.items = p->d_items;
+    a.nitems = p->nitems;
+    a.tabs = p->d_tabs;
+    a.status = p->d_status;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = p->small ? dpd::launch_batched_57(a, p->V, p->warps, p->stages, p->ctas_per_sm, p->sm_count, s)
+                             : dpd::launch_batched_68(a, p->V, p->warps, p->stages, p->ctas_per_sm, p->sm_count, s);
+    return e == cudaSuccess ? DPD_OK : DPD_ERR_CUDA;
+}
+
+dpd_status dpd_plan_sync_status(dpd_plan p, void *stream)
+{
+    if (!p) return DPD_ERR_INVALID_ARGUMENT;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return DPD_ERR_CUDA;
+    int flags = 0;
+    if (cudaMemcpy(&flags, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DPD_ERR_CUDA;
+    if (flags && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return DPD_ERR_CUDA;
+    if (flags & dpd::kFlagTimeout) return DPD_ERR_TIMEOUT;
+    if (flags) return DPD_ERR_CUDA;
+    return DPD_OK;
+}
+
+dpd_status dpd_plan_destroy(dpd_plan p)
+{
+    if (p) free_plan(p);
+    return DPD_OK;
+}
+
+}  // extern "C"

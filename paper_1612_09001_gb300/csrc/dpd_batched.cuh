@@ -1,0 +1,189 @@
+// Batched APH DPD: many independent antenna streams of uneven length and
+// model order (P, Q, M) filtered by ONE persistent launch.
+//
+// The host plan cuts every stream into tiles of S samples and orders the
+// (stream, tile) work items by cost; CTA b takes items b, b + grid, ...  One
+// producer thread per CTA streams each item into a shared-memory ring slot
+// with two bulk copies completed on the slot's mbarrier: the stream's
+// widely-linear coefficient table (see dpd_internal.h) and the tile with its
+// kHalo samples of history (zero before the stream's first sample, Eq. 2).
+// Consumer warps dispatch on the item's (B, T) to the same per-sample compute
+// as the single-stream kernel, with coefficients read from the slot.
+#pragma once
+
+#include "dpd_fwd.cuh"
+
+namespace dpd {
+
+struct BatchStream {
+    const float2 *x;
+    float2 *y;
+    int64_t n;
+    int B, T;          // branch pairs, taps
+    int tab_off;       // offset of the stream's table in the table pool (floats, 16-byte aligned)
+    int tab_bytes;     // bytes copied per item (multiple of 16)
+};
+
+struct BatchItem {
+    int stream;
+    int tile;
+};
+
+struct BatchArgs {
+    const BatchStream *streams;
+    const BatchItem *items;
+    int nitems;
+    const float *tabs;
+    int *status;
+};
+
+constexpr int kBatchTabBytes = ((kMaxTabFloats * 4 + 15) / 16) * 16;   // table area of a slot
+
+__host__ __device__ constexpr size_t batch_slot_bytes(int S)
+{
+    return (size_t)kBatchTabBytes + (size_t)(kHalo + S) * sizeof(float2);
+}
+
+template <int B, int T, int V>
+__device__ __forceinline__ void batched_item(const unsigned char *slot, const BatchStream &st, int64_t s0,
+                                             int S, int t_in_tile)
+{
+    constexpr int W = V + T - 1;
+    const float *tab = reinterpret_cast<const float *>(slot);
+    const float2 *xs = reinterpret_cast<const float2 *>(slot + kBatchTabBytes);
+    float wr[W], wi[W];
+    const bool full = load_window<T, V>(xs, s0, S, st.n, st.x, t_in_tile, wr, wi);
+    float yr[V], yi[V];
+    // Coefficients come from the slot (shared memory); the parameter-bank
+    // table argument is not read in this mode.
+    fwd_compute<B, T, V, kModePackedFma>(tab, *reinterpret_cast<const ParamTab<B, T> *>(tab), wr, wi, yr,
+                                         yi);
+    const bool vec = full && ((reinterpret_cast<uintptr_t>(st.y) & 15u) == 0);
+    store_outputs<V>(st.y, s0 + (int64_t)t_in_tile * V, st.n, vec, yr, yi);
+}
+
+#define DPD_BCASE(b, t)                                                                            \
+    case (b) * 16 + (t):                                                                           \
+        if constexpr ((b) <= BMAX && (t) <= TMAX) {                                                \
+            batched_item<(b), (t), V>(slot, st, s0, S, t_in_tile);                                 \
+            break;                                                                                 \
+        }                                                                                          \
+        bad = true;                                                                                \
+        break;
+#define DPD_BCASES(b)                                                                              \
+    DPD_BCASE(b, 1) DPD_BCASE(b, 2) DPD_BCASE(b, 3) DPD_BCASE(b, 4) DPD_BCASE(b, 5)               \
+    DPD_BCASE(b, 6) DPD_BCASE(b, 7) DPD_BCASE(b, 8)
+
+template <int BMAX, int TMAX, int V>
+__global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int stages)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);   // full[s], empty[s]
+    unsigned char *ring = smem + 128;
+    const int nwarps = blockDim.x / 32 - 1;
+    const int S = nwarps * 32 * V;
+    const size_t slot_bytes = batch_slot_bytes(S);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(smem_addr(&bars[s]), 1);
+            mbar_init(smem_addr(&bars[stages + s]), nwarps);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == nwarps) {
+        // ---------------------------------------------------------------- producer
+        if (lane != 0) return;
+        const uint64_t pol = policy_evict_first();
+        int it = 0;
+        bool ok = true;
+        for (int i = blockIdx.x; i < a.nitems; i += gridDim.x, ++it) {
+            const int s = it % stages;
+            const uint32_t ph = (uint32_t)((it / stages) & 1);
+            if (it >= stages && !mbar_wait(smem_addr(&bars[stages + s]), ph ^ 1u, a.status)) {
+                ok = false;
+                break;
+            }
+            const BatchItem w = a.items[i];
+            const BatchStream st = a.streams[w.stream];
+            int64_t lo, cnt;
+            int off;
+            tile_copy_range((int64_t)w.tile * S, S, st.n, lo, cnt, off);
+            const uint32_t xbytes = (uint32_t)(cnt * (int64_t)sizeof(float2));
+            const uint32_t fb = smem_addr(&bars[s]);
+            unsigned char *slot = ring + (size_t)s * slot_bytes;
+            mbar_arrive_expect_tx(fb, xbytes + (uint32_t)st.tab_bytes);
+            bulk_copy_g2s(smem_addr(slot), a.tabs + st.tab_off, (uint32_t)st.tab_bytes, fb);
+            if (xbytes)
+                bulk_copy_g2s_stream(smem_addr(slot + kBatchTabBytes + (size_t)off * sizeof(float2)),
+                                     st.x + lo, xbytes, fb, pol);
+        }
+        if (!ok) {
+            const int first = it > stages ? it - stages : 0;
+            for (int j = first; j < it; ++j)
+                mbar_wait(smem_addr(&bars[j % stages]), (uint32_t)((j / stages) & 1), a.status);
+        }
+        return;
+    }
+
+    // -------------------------------------------------------------------- consumers
+    const int t_in_tile = warp * 32 + lane;
+    int it = 0;
+    for (int i = blockIdx.x; i < a.nitems; i += gridDim.x, ++it) {
+        const int s = it % stages;
+        const uint32_t ph = (uint32_t)((it / stages) & 1);
+        if (!mbar_wait(smem_addr(&bars[s]), ph, a.status)) return;
+        const unsigned char *slot = ring + (size_t)s * slot_bytes;
+        const BatchItem w = a.items[i];
+        const BatchStream st = a.streams[w.stream];
+        const int64_t s0 = (int64_t)w.tile * S;
+        bool bad = false;
+        switch (st.B * 16 + st.T) {
+            DPD_BCASES(1)
+            DPD_BCASES(2)
+            DPD_BCASES(3)
+            DPD_BCASES(4)
+            DPD_BCASES(5)
+            DPD_BCASES(6)
+        default: bad = true;
+        }
+        if (bad && lane == 0) atomicOr(a.status, kFlagBadWork);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));   // slot (table + tile) no longer read
+    }
+}
+
+#undef DPD_BCASES
+#undef DPD_BCASE
+
+template <int BMAX, int TMAX, int V>
+cudaError_t launch_batched_impl(const BatchArgs &a, int warps, int stages, int ctas_per_sm, int sm_count,
+                                cudaStream_t s)
+{
+    const int threads = (warps + 1) * 32;
+    const int S = warps * 32 * V;
+    const size_t smem = 128 + (size_t)stages * batch_slot_bytes(S);
+    auto kern = fwd_batched_kernel<BMAX, TMAX, V>;
+    static size_t smem_set = 0;
+    if (smem > smem_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int cps = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
+    int grid = sm_count * cps;
+    if (grid > a.nitems) grid = a.nitems;
+    if (grid < 1) return cudaSuccess;
+    kern<<<grid, threads, smem, s>>>(a, stages);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace dpd

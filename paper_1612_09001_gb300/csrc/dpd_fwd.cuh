@@ -131,6 +131,88 @@ __host__ __device__ constexpr size_t fwd_tma_smem(int warps, int stages)
            (size_t)stages * (size_t)(kHalo + warps * 32 * V) * sizeof(float2);
 }
 
+// Read the window of thread t_in_tile of a tile that starts at sample s0 from a
+// shared-memory slot holding global samples [s0 - kHalo, ...).  Samples in
+// [lo, vhi) are in the slot; the sample just past vhi (odd tail) comes from
+// global memory; samples outside [0, n) are zero.  Returns true when the whole
+// tile and its history are in the slot (the vectorised fast path).
+template <int T, int V>
+__device__ __forceinline__ bool load_window(const float2 *slot, int64_t s0, int S, int64_t n,
+                                            const float2 *__restrict__ x, int t_in_tile,
+                                            float (&wr)[V + T - 1], float (&wi)[V + T - 1])
+{
+    constexpr int W = V + T - 1;
+    const int64_t g0 = s0 + (int64_t)t_in_tile * V;
+    const int64_t lo = (s0 - kHalo > 0) ? s0 - kHalo : 0;
+    const int64_t hi = (s0 + S < n) ? s0 + S : n;
+    const int64_t vhi = lo + ((hi - lo) & ~int64_t(1));
+    const bool full = (s0 >= kHalo) && (s0 + S <= vhi);
+    if (full) {
+        constexpr int MP = ((T - 1) + 1) & ~1;   // history rounded up to a 16-byte unit
+        constexpr int E = V + MP;
+        constexpr int D = MP - (T - 1);
+        const float4 *src = reinterpret_cast<const float4 *>(slot + t_in_tile * V + kHalo - MP);
+        float er[E], ei[E];
+#pragma unroll
+        for (int i = 0; i < E / 2; ++i) {
+            const float4 q = src[i];
+            er[2 * i] = q.x;
+            ei[2 * i] = q.y;
+            er[2 * i + 1] = q.z;
+            ei[2 * i + 1] = q.w;
+        }
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            wr[j] = er[j + D];
+            wi[j] = ei[j + D];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int64_t g = g0 - (T - 1) + j;
+            float2 v = make_float2(0.f, 0.f);
+            if (g >= lo && g < vhi)
+                v = slot[g - (s0 - kHalo)];
+            else if (g >= 0 && g < n)
+                v = x[g];
+            wr[j] = v.x;
+            wi[j] = v.y;
+        }
+    }
+    return full;
+}
+
+// Bulk-copy geometry of a tile: global sample range [lo, lo + cnt) (cnt even)
+// lands at slot element `off`.
+__device__ __forceinline__ void tile_copy_range(int64_t s0, int S, int64_t n, int64_t &lo, int64_t &cnt,
+                                                int &off)
+{
+    lo = s0 - kHalo;
+    off = 0;
+    if (lo < 0) {
+        off = (int)(-lo);
+        lo = 0;
+    }
+    const int64_t hi = (s0 + S < n) ? s0 + S : n;
+    cnt = (hi - lo) & ~int64_t(1);
+}
+
+template <int V>
+__device__ __forceinline__ void store_outputs(float2 *__restrict__ y, int64_t g0, int64_t n, bool full_vec,
+                                              const float (&yr)[V], const float (&yi)[V])
+{
+    if (full_vec) {
+        float4 *yp = reinterpret_cast<float4 *>(y + g0);
+#pragma unroll
+        for (int i = 0; i < V / 2; ++i)
+            st_stream_f4(yp + i, make_float4(yr[2 * i], yi[2 * i], yr[2 * i + 1], yi[2 * i + 1]));
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if (g0 + v < n) y[g0 + v] = make_float2(yr[v], yi[v]);
+    }
+}
+
 template <int B, int T, int V, int MODE>
 __global__ void __launch_bounds__(32 * 17)
     fwd_tma_kernel(FwdArgs a, int stages, int64_t ntiles, const __grid_constant__ ParamTab<B, T> ptab)
@@ -171,14 +253,9 @@ __global__ void __launch_bounds__(32 * 17)
                 break;
             }
             const int64_t s0 = tile * S;
-            int64_t lo = s0 - kHalo;
-            int off = 0;
-            if (lo < 0) {
-                off = (int)(-lo);
-                lo = 0;
-            }
-            const int64_t hi = (s0 + S < a.n) ? s0 + S : a.n;
-            const int64_t cnt = (hi - lo) & ~int64_t(1);   // whole 16-byte units
+            int64_t lo, cnt;
+            int off;
+            tile_copy_range(s0, S, a.n, lo, cnt, off);
             const uint32_t bytes = (uint32_t)(cnt * (int64_t)sizeof(float2));
             const uint32_t fb = smem_addr(&bars[s]);
             mbar_arrive_expect_tx(fb, bytes);
@@ -204,59 +281,14 @@ __global__ void __launch_bounds__(32 * 17)
         if (!mbar_wait(smem_addr(&bars[s]), ph, a.status)) return;
         const float2 *slot = ring + (size_t)s * slot_elems;
         const int64_t s0 = tile * S;
-        const int64_t g0 = s0 + (int64_t)t_in_tile * V;
-        const int64_t lo = (s0 - kHalo > 0) ? s0 - kHalo : 0;
-        const int64_t hi = (s0 + S < a.n) ? s0 + S : a.n;
-        const int64_t vhi = lo + ((hi - lo) & ~int64_t(1));
-        const bool full = (s0 >= kHalo) && (s0 + S <= vhi);
         float wr[W], wi[W];
-        if (full) {
-            constexpr int MP = ((T - 1) + 1) & ~1;   // history rounded up to a 16-byte unit
-            constexpr int E = V + MP;
-            constexpr int D = MP - (T - 1);
-            const float4 *src = reinterpret_cast<const float4 *>(slot + t_in_tile * V + kHalo - MP);
-            float er[E], ei[E];
-#pragma unroll
-            for (int i = 0; i < E / 2; ++i) {
-                const float4 q = src[i];
-                er[2 * i] = q.x;
-                ei[2 * i] = q.y;
-                er[2 * i + 1] = q.z;
-                ei[2 * i + 1] = q.w;
-            }
-#pragma unroll
-            for (int j = 0; j < W; ++j) {
-                wr[j] = er[j + D];
-                wi[j] = ei[j + D];
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < W; ++j) {
-                const int64_t g = g0 - (T - 1) + j;
-                float2 v = make_float2(0.f, 0.f);
-                if (g >= lo && g < vhi)
-                    v = slot[g - (s0 - kHalo)];
-                else if (g >= 0 && g < a.n)
-                    v = a.x[g];
-                wr[j] = v.x;
-                wi[j] = v.y;
-            }
-        }
+        const bool full = load_window<T, V>(slot, s0, S, a.n, a.x, t_in_tile, wr, wi);
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));
 
         float yr[V], yi[V];
         fwd_compute<B, T, V, MODE>(tab, ptab, wr, wi, yr, yi);
-        if (full && a.vec_store) {
-            float4 *yp = reinterpret_cast<float4 *>(a.y + g0);
-#pragma unroll
-            for (int i = 0; i < V / 2; ++i)
-                st_stream_f4(yp + i, make_float4(yr[2 * i], yi[2 * i], yr[2 * i + 1], yi[2 * i + 1]));
-        } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                if (g0 + v < a.n) a.y[g0 + v] = make_float2(yr[v], yi[v]);
-        }
+        store_outputs<V>(a.y, s0 + (int64_t)t_in_tile * V, a.n, full && a.vec_store, yr, yi);
     }
 }
 
