@@ -23,9 +23,10 @@ struct dpd_plan_s {
     dpd::BatchStream *d_streams = nullptr;
     dpd::BatchItem *d_items = nullptr;
     float *d_tabs = nullptr;
-    float2 *d_h = nullptr;
+    float *d_h = nullptr;          // raw coefficients, 2*K floats per stream
     int *d_status = nullptr;
     int nitems = 0, items_cap = 0;
+    int64_t tab_floats = 0;
     int small = 1;            // every stream has B <= 5 and T <= 7
     int V = 8, warps = 8, stages = 4, ctas_per_sm = 0;
 };
@@ -155,6 +156,7 @@ dpd_status dpd_plan_batched(const dpd_stream_desc *descs, int count, int where, 
         hoff += 2 * (size_t)K;
         toff += (size_t)st.tab_bytes / 4;
     }
+    p->tab_floats = (int64_t)toff;
     if (count > 0 &&
         cudaMemcpy(p->d_streams, p->streams.data(), count * sizeof(dpd::BatchStream), cudaMemcpyHostToDevice) !=
             cudaSuccess) {
@@ -192,7 +194,9 @@ dpd_status dpd_exec_batched(dpd_plan p, void *stream)
     a.streams = p->d_streams;
     a.items = p->d_items;
     a.nitems = p->nitems;
+    a.nstreams = (int)p->streams.size();
     a.tabs = p->d_tabs;
+    a.tab_floats = p->tab_floats;
     a.status = p->d_status;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = p->small ? dpd::launch_batched_57(a, p->V, p->warps, p->stages, p->ctas_per_sm, p->sm_count, s)

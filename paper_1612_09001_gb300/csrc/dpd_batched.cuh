@@ -33,7 +33,9 @@ struct BatchArgs {
     const BatchStream *streams;
     const BatchItem *items;
     int nitems;
+    int nstreams;
     const float *tabs;
+    int64_t tab_floats;   // size of the table pool
     int *status;
 };
 
@@ -42,6 +44,18 @@ constexpr int kBatchTabBytes = ((kMaxTabFloats * 4 + 15) / 16) * 16;   // table 
 __host__ __device__ constexpr size_t batch_slot_bytes(int S)
 {
     return (size_t)kBatchTabBytes + (size_t)(kHalo + S) * sizeof(float2);
+}
+
+// Range checks of a work item against the plan (stream index, table inside
+// the pool and the slot, tile inside the stream, 16-byte aligned input).  The
+// producer and the consumers evaluate the same predicate on the same item, so
+// a bad item is skipped by both sides and no wait is left unmatched.
+__device__ __forceinline__ bool item_ok(const BatchArgs &a, const BatchItem &w, const BatchStream &st, int S)
+{
+    return w.stream >= 0 && w.stream < a.nstreams && st.tab_off >= 0 && st.tab_bytes > 0 &&
+           st.tab_bytes <= kBatchTabBytes && (st.tab_bytes & 15) == 0 && (st.tab_off & 3) == 0 &&
+           (int64_t)st.tab_off + st.tab_bytes / 4 <= a.tab_floats && w.tile >= 0 &&
+           (int64_t)w.tile * S < st.n && ((reinterpret_cast<uintptr_t>(st.x) & 15u) == 0);
 }
 
 template <int B, int T, int V>
@@ -108,12 +122,17 @@ __global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int s
                 break;
             }
             const BatchItem w = a.items[i];
-            const BatchStream st = a.streams[w.stream];
+            const BatchStream st = a.streams[(w.stream >= 0 && w.stream < a.nstreams) ? w.stream : 0];
+            const uint32_t fb = smem_addr(&bars[s]);
+            if (!item_ok(a, w, st, S)) {
+                atomicOr(a.status, kFlagBadWork);
+                mbar_arrive_expect_tx(fb, 0);   // complete the phase with no copies
+                continue;
+            }
             int64_t lo, cnt;
             int off;
             tile_copy_range((int64_t)w.tile * S, S, st.n, lo, cnt, off);
             const uint32_t xbytes = (uint32_t)(cnt * (int64_t)sizeof(float2));
-            const uint32_t fb = smem_addr(&bars[s]);
             unsigned char *slot = ring + (size_t)s * slot_bytes;
             mbar_arrive_expect_tx(fb, xbytes + (uint32_t)st.tab_bytes);
             bulk_copy_g2s(smem_addr(slot), a.tabs + st.tab_off, (uint32_t)st.tab_bytes, fb);
@@ -138,10 +157,10 @@ __global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int s
         if (!mbar_wait(smem_addr(&bars[s]), ph, a.status)) return;
         const unsigned char *slot = ring + (size_t)s * slot_bytes;
         const BatchItem w = a.items[i];
-        const BatchStream st = a.streams[w.stream];
+        const BatchStream st = a.streams[(w.stream >= 0 && w.stream < a.nstreams) ? w.stream : 0];
         const int64_t s0 = (int64_t)w.tile * S;
-        bool bad = false;
-        switch (st.B * 16 + st.T) {
+        bool bad = !item_ok(a, w, st, S);
+        if (!bad) switch (st.B * 16 + st.T) {
             DPD_BCASES(1)
             DPD_BCASES(2)
             DPD_BCASES(3)
