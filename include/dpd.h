@@ -181,6 +181,60 @@ dpd_status dpd_set_adj_launch(dpd_handle h, int gh_blocks, int tap_group);
 dpd_status dpd_set_fwd_launch(dpd_handle h, int mode, int V, int warps, int stages, int ctas_per_sm,
                               int use_tma);
 
+/* ------------------------------------------------------------ least squares */
+
+/* Precision of the Gram contraction Psi^H Psi (accumulation is FP32, the
+ * K x K solve FP64 in every mode):
+ *   DPD_PREC_FP32    plain FP32 fused multiply-adds on the CUDA cores
+ *   DPD_PREC_TF32X3  tensor cores, operands split a = hi + lo in TF32,
+ *                    hi*hi + hi*lo + lo*hi (about FP32 accuracy)
+ *   DPD_PREC_BF16X3  tensor cores, the same split in BF16 (about 16 bits) */
+enum { DPD_PREC_FP32 = 0, DPD_PREC_TF32X3 = 1, DPD_PREC_BF16X3 = 2 };
+
+/*
+ * Normal equations of the least-squares estimate of Sec. 2.2 for the
+ * handle's model: G = Psi^H Psi (K x K) and g = Psi^H t, Psi the basis matrix
+ * of Eq. 2 built from u (zero history, n rows).
+ *   u  : device, n complex64, 8-byte aligned (n >= 1)
+ *   t  : device, n complex64, or NULL (then g and tt are not formed)
+ *   G  : device, K*K complex128 (row-major, full Hermitian), written
+ *   g  : device, K complex128, or NULL;  tt : host double (t^H t) or NULL
+ * Uses and may grow the handle's estimation workspace (growing allocates and
+ * synchronises the device); tt != NULL synchronises `stream`.
+ */
+dpd_status dpd_gram(dpd_handle h, const void *u, const void *t, int64_t n, int precision, void *G, void *g,
+                    double *tt, void *stream);
+
+/*
+ * Least-squares coefficients (Sec. 2.2): h = argmin ||Psi(u) h - t||_2, i.e.
+ * (Psi^H Psi) h = Psi^H t.  The Gram matrix is formed in `precision`, the
+ * system is equilibrated (D = diag(G)^{-1/2}) and solved by an FP64 Cholesky
+ * factorisation, then refined `refine_iters` times (0..100) with
+ * h += G^{-1} Psi^H (t - Psi h), the residual computed by the FP32 filter
+ * and adjoint kernels.  In the indirect learning architecture u is the PA
+ * output divided by its gain and t the predistorter output.
+ *   h_out : device, K complex64, written (the handle's own coefficients are
+ *           left unchanged; install the result with dpd_set_coeffs)
+ *   stats : host double[2] or NULL: [0] condition estimate of D G D (squared
+ *           ratio of the extreme Cholesky pivots), [1] ||t - Psi h||^2 / ||t||^2
+ *           from G, g and t^H t in FP64
+ * Synchronises `stream`.  DPD_ERR_NOT_SPD if G is not positive definite
+ * (e.g. u all zero).  Uses and may grow the handle's workspace.
+ */
+dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, int precision, int refine_iters,
+                        void *h_out, double *stats, void *stream);
+
+/*
+ * `count` independent estimates for the handle's model (e.g. one per antenna):
+ * u[i], t[i] device pointers to n[i] complex64.  One Gram launch covers every
+ * problem; h_out receives count*K complex64 (problem-major).  info_out (host,
+ * count ints, nullable) gets 0 or the failing Cholesky pivot + 1 per problem;
+ * any failure returns DPD_ERR_NOT_SPD after the others are solved.
+ */
+dpd_status dpd_estimate_batched(dpd_handle h, const void *const *u, const void *const *t, const int64_t *n,
+                                int count, int precision, int refine_iters, void *h_out, int *info_out,
+                                void *stream);
+
 /* ------------------------------------------------------------------ batched */
 
 /*

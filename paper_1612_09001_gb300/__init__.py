@@ -15,7 +15,9 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib
-from ._lib import DPDError, DPD_HOST, DPD_DEVICE  # noqa: F401
+from ._lib import DPDError, DPD_HOST, DPD_DEVICE, DPD_PREC_FP32, DPD_PREC_TF32X3, DPD_PREC_BF16X3  # noqa: F401
+
+PRECISIONS = {"fp32": DPD_PREC_FP32, "tf32x3": DPD_PREC_TF32X3, "bf16x3": DPD_PREC_BF16X3}
 
 __all__ = ["DPD", "BatchedPlan", "DPDError", "num_coeffs", "kernel_launches", "lib"]
 
@@ -143,6 +145,57 @@ class DPD:
             ctypes.c_void_p(gh.data_ptr() if gh is not None else None),
             ctypes.c_void_p(gx.data_ptr() if gx is not None else None), _stream_ptr(stream)))
         return gh, gx
+
+    # -- least squares (Sec. 2.2)
+    def gram(self, u, t=None, precision="tf32x3", stream=None):
+        """(G, g, tt): G = Psi^H Psi (K x K complex128 CUDA tensor), g = Psi^H t, tt = t^H t."""
+        import torch
+        _check_samples(u, "u")
+        if t is not None:
+            _check_samples(t, "t")
+        G = torch.empty((self.K, self.K), dtype=torch.complex128, device=u.device)
+        g = torch.empty(self.K, dtype=torch.complex128, device=u.device) if t is not None else None
+        tt = ctypes.c_double(0.0)
+        _lib.check("dpd_gram", self._lib.dpd_gram(
+            self._h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(t.data_ptr() if t is not None else None),
+            u.numel(), PRECISIONS[precision], ctypes.c_void_p(G.data_ptr()),
+            ctypes.c_void_p(g.data_ptr() if g is not None else None),
+            ctypes.byref(tt) if t is not None else None, _stream_ptr(stream)))
+        return G, g, (tt.value if t is not None else None)
+
+    def estimate(self, u, t, precision="tf32x3", refine_iters=2, stream=None):
+        """Least-squares coefficients (complex64 CUDA tensor of K) and stats
+        (condition estimate of the equilibrated Gram matrix, relative residual)."""
+        import torch
+        _check_samples(u, "u")
+        _check_samples(t, "t")
+        h = torch.empty(self.K, dtype=torch.complex64, device=u.device)
+        stats = (ctypes.c_double * 2)()
+        _lib.check("dpd_estimate", self._lib.dpd_estimate(
+            self._h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(t.data_ptr()), u.numel(),
+            PRECISIONS[precision], refine_iters, ctypes.c_void_p(h.data_ptr()), stats, _stream_ptr(stream)))
+        return h, {"cond_est": stats[0], "rel_residual": stats[1]}
+
+    def estimate_batched(self, us, ts, precision="tf32x3", refine_iters=2, stream=None):
+        """Independent estimates for lists of (u, t); returns (count x K complex64 tensor, info list)."""
+        import torch
+        if len(us) != len(ts) or not us:
+            raise ValueError("us and ts must be non-empty lists of the same length")
+        for u, t in zip(us, ts):
+            _check_samples(u, "u")
+            _check_samples(t, "t")
+        cnt = len(us)
+        up = (ctypes.c_void_p * cnt)(*[u.data_ptr() for u in us])
+        tp = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in ts])
+        ns = (ctypes.c_int64 * cnt)(*[u.numel() for u in us])
+        info = (ctypes.c_int * cnt)()
+        h = torch.empty((cnt, self.K), dtype=torch.complex64, device=us[0].device)
+        rc = self._lib.dpd_estimate_batched(self._h, ctypes.cast(up, ctypes.c_void_p), ctypes.cast(tp, ctypes.c_void_p),
+                                            ctypes.cast(ns, ctypes.c_void_p), cnt, PRECISIONS[precision],
+                                            refine_iters, ctypes.c_void_p(h.data_ptr()), info, _stream_ptr(stream))
+        if rc not in (0, 6):
+            _lib.check("dpd_estimate_batched", rc)
+        return h, list(info)
 
     def set_adj_launch(self, gh_blocks, tap_group):
         _lib.check("dpd_set_adj_launch", self._lib.dpd_set_adj_launch(self._h, gh_blocks, tap_group))

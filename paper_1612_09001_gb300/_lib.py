@@ -24,6 +24,7 @@ STATUS = {
     7: "DPD_ERR_TIMEOUT",
 }
 DPD_HOST, DPD_DEVICE = 0, 1
+DPD_PREC_FP32, DPD_PREC_TF32X3, DPD_PREC_BF16X3 = 0, 1, 2
 
 
 class DPDError(RuntimeError):
@@ -53,6 +54,9 @@ SIGNATURES = {
     "dpd_set_adj_launch": [_vp, _i, _i],
     "dpd_grad_coeffs_noalloc": [_i, _i, _i, _vp, _vp, _i64, _vp, _vp],
     "dpd_sync_status": [_vp, _vp],
+    "dpd_gram": [_vp, _vp, _vp, _i64, _i, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp],
+    "dpd_estimate": [_vp, _vp, _vp, _i64, _i, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp],
+    "dpd_estimate_batched": [_vp, _vp, _vp, _vp, _i, _i, _i, _vp, _pi, _vp],
     "dpd_plan_batched": [_vp, _i, _i, ctypes.POINTER(_vp)],
     "dpd_exec_batched": [_vp, _vp],
     "dpd_plan_set_launch": [_vp, _i, _i, _i, _i],

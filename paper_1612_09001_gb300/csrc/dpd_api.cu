@@ -10,23 +10,7 @@
 #include "../../include/dpd.h"
 #include "dpd_internal.h"
 
-struct dpd_filter {
-    int P, Q, M;
-    int Bp, Bq, B, T, K;
-    int device;
-    int sm_count;
-    float2 *d_h;      // K complex coefficients, stacking order of Sec. 2.2
-    float *d_tab;     // widely-linear table for the forward kernels
-    int *d_status;    // kernel error word
-    float *d_adj_tab; // adjoint (derivative-polynomial) table
-    float2 *d_partials;  // coefficient-gradient workspace: rows_max x K complex
-    int rows_max;
-    bool has_coeffs;
-    bool host_tab_valid;  // h_tab mirrors d_tab (coefficients were set from host memory)
-    dpd::HostTab h_tab;
-    dpd::FwdLaunch fwd;
-    dpd::AdjLaunch adj;
-};
+#include "dpd_handle.h"
 
 namespace dpd {
 static std::atomic<uint64_t> g_launches{0};
@@ -152,6 +136,7 @@ dpd_status dpd_destroy(dpd_handle h)
     cudaFree(h->d_adj_tab);
     cudaFree(h->d_partials);
     cudaFree(h->d_status);
+    free_estimate_workspace(h->est);
     delete h;
     return DPD_OK;
 }

@@ -1,0 +1,47 @@
+// The handle behind dpd_handle (include/dpd.h), shared by the libdpd API
+// translation units.  Not part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "dpd_internal.h"
+
+// Device workspace of dpd_estimate, grown on demand.
+struct EstimateWorkspace {
+    int cpp = 0;                  // Gram CTAs per problem the partials were sized for
+    int nprob = 0;                // problems the per-problem arrays were sized for
+    int64_t nsamp = 0;            // samples the y / e buffers hold
+    void *probs = nullptr;        // GramProblem[nprob]
+    float *partials = nullptr;    // [nprob * cpp][kGramRows][kGramCols]
+    double *S = nullptr;          // [nprob][kGramRows][kGramCols]
+    double2 *G = nullptr, *g = nullptr, *L = nullptr, *h64 = nullptr, *delta = nullptr;
+    double *d = nullptr, *tt = nullptr;
+    int *info = nullptr;
+    float2 *hf = nullptr;         // coefficients of the refinement pass (complex64)
+    float *tab = nullptr;         // their forward table
+    float2 *y = nullptr, *e = nullptr;
+};
+
+struct dpd_filter {
+    int P, Q, M;
+    int Bp, Bq, B, T, K;
+    int device;
+    int sm_count;
+    float2 *d_h;      // K complex coefficients, stacking order of Sec. 2.2
+    float *d_tab;     // widely-linear table for the forward kernels
+    int *d_status;    // kernel error word
+    float *d_adj_tab; // adjoint (derivative-polynomial) table
+    float2 *d_partials;  // coefficient-gradient workspace: rows_max x K complex
+    int rows_max;
+    bool has_coeffs;
+    bool host_tab_valid;  // h_tab mirrors d_tab (coefficients were set from host memory)
+    dpd::HostTab h_tab;
+    dpd::FwdLaunch fwd;
+    dpd::AdjLaunch adj;
+    EstimateWorkspace est;
+};
+
+void free_estimate_workspace(EstimateWorkspace &w);
+

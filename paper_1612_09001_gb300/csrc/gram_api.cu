@@ -1,0 +1,291 @@
+// libdpd C ABI, least-squares part: dpd_gram, dpd_estimate and
+// dpd_estimate_batched (contracts in include/dpd.h, method in dpd_gram.cuh).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dpd.h"
+#include "dpd_gram.cuh"
+#include "dpd_handle.h"
+
+namespace {
+
+bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+template <class T>
+bool grow(T *&p, size_t have, size_t need)
+{
+    if (need <= have && p) return true;
+    cudaFree(p);
+    p = nullptr;
+    return cudaMalloc(&p, std::max<size_t>(need, 1) * sizeof(T)) == cudaSuccess;
+}
+
+// Make sure the workspace holds nprob problems with cpp Gram CTAs each and
+// nsamp samples of refinement buffers.  Synchronises the device when it grows.
+dpd_status reserve(dpd_handle h, int nprob, int cpp, int64_t nsamp)
+{
+    EstimateWorkspace &w = h->est;
+    const int K = h->K;
+    bool ok = true;
+    if (nprob > w.nprob || cpp * nprob > w.cpp * w.nprob) {
+        cudaDeviceSynchronize();
+        const size_t np = (size_t)nprob, parts = (size_t)nprob * cpp;
+        ok = ok && grow(reinterpret_cast<dpd::GramProblem *&>(w.probs), 0, np);
+        ok = ok && grow(w.partials, 0, parts * dpd::kGramRows * dpd::kGramCols);
+        ok = ok && grow(w.S, 0, np * dpd::kGramRows * dpd::kGramCols);
+        ok = ok && grow(w.G, 0, np * K * K) && grow(w.L, 0, np * K * K);
+        ok = ok && grow(w.g, 0, np * K) && grow(w.h64, 0, np * K) && grow(w.delta, 0, np * K);
+        ok = ok && grow(w.d, 0, np * K) && grow(w.tt, 0, np) && grow(w.info, 0, np);
+        ok = ok && grow(w.hf, 0, (size_t)K) && grow(w.tab, 0, (size_t)dpd::wl_table_floats(h->B, h->T));
+        if (!ok) return DPD_ERR_ALLOC;
+        w.nprob = nprob;
+        w.cpp = cpp;
+    }
+    if (nsamp > w.nsamp) {
+        cudaDeviceSynchronize();
+        ok = grow(w.y, 0, (size_t)nsamp) && grow(w.e, 0, (size_t)nsamp);
+        if (!ok) return DPD_ERR_ALLOC;
+        w.nsamp = nsamp;
+    }
+    return DPD_OK;
+}
+
+bool valid_precision(int p) { return p == DPD_PREC_FP32 || p == DPD_PREC_TF32X3 || p == DPD_PREC_BF16X3; }
+
+int gram_cpp(dpd_handle h, int nprob, int64_t n)
+{
+    // one CTA per SM in total, at least one per problem, no more than row blocks
+    int cpp = std::max(1, h->sm_count / std::max(nprob, 1));
+    const int64_t blocks = (n + 31) / 32;
+    if (cpp > blocks) cpp = (int)std::max<int64_t>(blocks, 1);
+    return cpp;
+}
+
+// Gram (+ reduction + assembly) of nprob problems already described in w.probs.
+dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_t s)
+{
+    EstimateWorkspace &w = h->est;
+    dpd::GramArgs a;
+    a.probs = static_cast<const dpd::GramProblem *>(w.probs);
+    a.nprob = nprob;
+    a.cpp = cpp;
+    a.Bp = h->Bp;
+    a.Bq = h->Bq;
+    a.T = h->T;
+    a.K = h->K;
+    a.partials = w.partials;
+    a.status = h->d_status;
+    if (dpd::launch_gram(precision, a, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dpd::launch_gram_reduce(w.partials, nprob, cpp, h->K, w.S, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dpd::launch_gram_assemble(w.S, nprob, h->K, w.G, w.g, w.tt, s) != cudaSuccess) return DPD_ERR_CUDA;
+    return DPD_OK;
+}
+
+// One refinement step of problem p:  h64[p] += G^{-1} Psi^H (t - Psi h).
+dpd_status refine_once(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, cudaStream_t s)
+{
+    EstimateWorkspace &w = h->est;
+    const int K = h->K;
+    if (dpd::launch_h_to_f32(w.h64 + (size_t)p * K, K, w.hf, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dpd::launch_wl_table(w.hf, h->Bp, h->Bq, h->T, w.tab, nullptr, s) != cudaSuccess) return DPD_ERR_CUDA;
+    dpd::FwdArgs fa;
+    fa.x = u;
+    fa.y = w.y;
+    fa.n = n;
+    fa.tab = w.tab;
+    fa.status = h->d_status;
+    fa.vec_store = 1;
+    fa.host_tab = nullptr;
+    dpd::FwdLaunch L = h->fwd;
+    L.mode = dpd::kModePackedFma;   // coefficients live on the device
+    if ((reinterpret_cast<uintptr_t>(u) & 15u) != 0) {
+        L.use_tma = 0;
+        L.V = 4;
+    }
+    if (dpd::launch_fwd_any(h->B, h->T, fa, L, h->sm_count, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dpd::launch_residual(t, w.y, n, w.e, s) != cudaSuccess) return DPD_ERR_CUDA;
+    dpd::AdjArgs aa;
+    aa.x = u;
+    aa.gy = w.e;
+    aa.n = n;
+    aa.gx = nullptr;
+    aa.partials = h->d_partials;
+    aa.adj_tab = h->d_adj_tab;
+    aa.status = h->d_status;
+    dpd::AdjLaunch al = h->adj;
+    const int64_t need = (n + 1023) / 1024;
+    if (al.gh_blocks > need) al.gh_blocks = (int)need;
+    if (al.gh_blocks > h->rows_max) al.gh_blocks = h->rows_max;
+    if (al.gh_blocks < 1) al.gh_blocks = 1;
+    if (dpd::launch_adj_any(h->B, aa, al, h->T, h->Bp, h->Bq, K, h->sm_count, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dpd::launch_adj_finalize64(h->d_partials, al.gh_blocks, K, w.delta, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dpd::launch_chol_solve(w.L + (size_t)p * K * K, w.d + (size_t)p * K, w.info + p, w.delta, 1, K,
+                               w.h64 + (size_t)p * K, 1, s) != cudaSuccess)
+        return DPD_ERR_CUDA;
+    return DPD_OK;
+}
+
+// Statistics of problem p on the host: condition estimate of the equilibrated
+// Gram matrix from the Cholesky diagonal, and ||t - Psi h||^2 / ||t||^2 from
+// G, g, t^H t and h (FP64).
+dpd_status host_stats(dpd_handle h, int p, double *stats)
+{
+    EstimateWorkspace &w = h->est;
+    const int K = h->K;
+    std::vector<double2> L((size_t)K * K), G((size_t)K * K), g(K), x(K);
+    double tt = 0;
+    if (cudaMemcpy(L.data(), w.L + (size_t)p * K * K, sizeof(double2) * K * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(G.data(), w.G + (size_t)p * K * K, sizeof(double2) * K * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(g.data(), w.g + (size_t)p * K, sizeof(double2) * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(x.data(), w.h64 + (size_t)p * K, sizeof(double2) * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&tt, w.tt + p, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return DPD_ERR_CUDA;
+    double lmin = INFINITY, lmax = 0;
+    for (int i = 0; i < K; ++i) {
+        lmin = std::min(lmin, L[(size_t)i * K + i].x);
+        lmax = std::max(lmax, L[(size_t)i * K + i].x);
+    }
+    // r^2 = t^H t - 2 Re(h^H g) + h^H G h
+    double hg = 0, hGh = 0;
+    for (int a = 0; a < K; ++a) {
+        hg += x[a].x * g[a].x + x[a].y * g[a].y;
+        double re = 0, im = 0;
+        for (int b = 0; b < K; ++b) {
+            const double2 gab = G[(size_t)a * K + b];
+            re += gab.x * x[b].x - gab.y * x[b].y;
+            im += gab.x * x[b].y + gab.y * x[b].x;
+        }
+        hGh += x[a].x * re + x[a].y * im;
+    }
+    stats[0] = (lmax / lmin) * (lmax / lmin);
+    stats[1] = tt > 0 ? std::max(0.0, tt - 2 * hg + hGh) / tt : 0.0;
+    return DPD_OK;
+}
+
+dpd_status check_inputs(dpd_handle h, const void *u, const void *t, int64_t n, int precision)
+{
+    if (!h || n < 1 || !u || !aligned8(u) || (t && !aligned8(t))) return DPD_ERR_INVALID_ARGUMENT;
+    if (!valid_precision(precision)) return DPD_ERR_INVALID_ARGUMENT;
+    if (n > ((int64_t)1 << 40)) return DPD_ERR_UNSUPPORTED;
+    if (2 * h->K + 2 > dpd::kGramCols) return DPD_ERR_UNSUPPORTED;
+    return DPD_OK;
+}
+
+}  // namespace
+
+void free_estimate_workspace(EstimateWorkspace &w)
+{
+    cudaFree(w.probs);
+    cudaFree(w.partials);
+    cudaFree(w.S);
+    cudaFree(w.G);
+    cudaFree(w.g);
+    cudaFree(w.L);
+    cudaFree(w.h64);
+    cudaFree(w.delta);
+    cudaFree(w.d);
+    cudaFree(w.tt);
+    cudaFree(w.info);
+    cudaFree(w.hf);
+    cudaFree(w.tab);
+    cudaFree(w.y);
+    cudaFree(w.e);
+    w = EstimateWorkspace();
+}
+
+extern "C" {
+
+dpd_status dpd_gram(dpd_handle h, const void *u, const void *t, int64_t n, int precision, void *G, void *g,
+                    double *tt, void *stream)
+{
+    dpd_status st = check_inputs(h, u, t, n, precision);
+    if (st != DPD_OK) return st;
+    if (!G || !aligned8(G) || (g && (!t || !aligned8(g)))) return DPD_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int cpp = gram_cpp(h, 1, n);
+    if ((st = reserve(h, 1, cpp, 0)) != DPD_OK) return st;
+    const dpd::GramProblem pr{static_cast<const float2 *>(u), static_cast<const float2 *>(t), n};
+    if (cudaMemcpyAsync(h->est.probs, &pr, sizeof(pr), cudaMemcpyHostToDevice, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if ((st = run_gram(h, 1, cpp, precision, s)) != DPD_OK) return st;
+    const size_t KK = (size_t)h->K * h->K;
+    if (cudaMemcpyAsync(G, h->est.G, sizeof(double2) * KK, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return DPD_ERR_CUDA;
+    if (g && cudaMemcpyAsync(g, h->est.g, sizeof(double2) * h->K, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return DPD_ERR_CUDA;
+    if (tt && t && (cudaMemcpyAsync(tt, h->est.tt, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess))
+        return DPD_ERR_CUDA;
+    return DPD_OK;
+}
+
+dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, int precision, int refine_iters,
+                        void *h_out, double *stats, void *stream)
+{
+    dpd_status st = check_inputs(h, u, t, n, precision);
+    if (st != DPD_OK) return st;
+    if (!t || !h_out || !aligned8(h_out) || refine_iters < 0 || refine_iters > 100) return DPD_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int cpp = gram_cpp(h, 1, n);
+    if ((st = reserve(h, 1, cpp, refine_iters > 0 ? n : 0)) != DPD_OK) return st;
+    EstimateWorkspace &w = h->est;
+    const dpd::GramProblem pr{static_cast<const float2 *>(u), static_cast<const float2 *>(t), n};
+    if (cudaMemcpyAsync(w.probs, &pr, sizeof(pr), cudaMemcpyHostToDevice, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if ((st = run_gram(h, 1, cpp, precision, s)) != DPD_OK) return st;
+    if (dpd::launch_chol(w.G, 1, h->K, w.L, w.d, w.info, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dpd::launch_chol_solve(w.L, w.d, w.info, w.g, 1, h->K, w.h64, 0, s) != cudaSuccess) return DPD_ERR_CUDA;
+    int info = 0;
+    if (cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return DPD_ERR_CUDA;
+    if (info != 0) return DPD_ERR_NOT_SPD;
+    for (int i = 0; i < refine_iters; ++i)
+        if ((st = refine_once(h, 0, pr.u, pr.t, n, s)) != DPD_OK) return st;
+    if (dpd::launch_h_to_f32(w.h64, h->K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (stats) return host_stats(h, 0, stats);
+    return DPD_OK;
+}
+
+dpd_status dpd_estimate_batched(dpd_handle h, const void *const *u, const void *const *t, const int64_t *n,
+                                int count, int precision, int refine_iters, void *h_out, int *info_out, void *stream)
+{
+    if (!h || count < 1 || !u || !t || !n || !h_out || !aligned8(h_out)) return DPD_ERR_INVALID_ARGUMENT;
+    if (refine_iters < 0 || refine_iters > 100 || !valid_precision(precision)) return DPD_ERR_INVALID_ARGUMENT;
+    if (2 * h->K + 2 > dpd::kGramCols) return DPD_ERR_UNSUPPORTED;
+    std::vector<dpd::GramProblem> probs((size_t)count);
+    int64_t nmax = 1;
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 1 || !u[i] || !t[i] || !aligned8(u[i]) || !aligned8(t[i])) return DPD_ERR_INVALID_ARGUMENT;
+        probs[i] = {static_cast<const float2 *>(u[i]), static_cast<const float2 *>(t[i]), n[i]};
+        nmax = std::max(nmax, n[i]);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int cpp = gram_cpp(h, count, nmax);
+    dpd_status st = reserve(h, count, cpp, refine_iters > 0 ? nmax : 0);
+    if (st != DPD_OK) return st;
+    EstimateWorkspace &w = h->est;
+    if (cudaMemcpy(w.probs, probs.data(), sizeof(dpd::GramProblem) * count, cudaMemcpyHostToDevice) != cudaSuccess)
+        return DPD_ERR_CUDA;
+    if ((st = run_gram(h, count, cpp, precision, s)) != DPD_OK) return st;
+    if (dpd::launch_chol(w.G, count, h->K, w.L, w.d, w.info, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dpd::launch_chol_solve(w.L, w.d, w.info, w.g, count, h->K, w.h64, 0, s) != cudaSuccess) return DPD_ERR_CUDA;
+    std::vector<int> info((size_t)count);
+    if (cudaMemcpyAsync(info.data(), w.info, sizeof(int) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return DPD_ERR_CUDA;
+    bool any_bad = false;
+    for (int i = 0; i < count; ++i) any_bad |= info[i] != 0;
+    for (int it = 0; it < refine_iters; ++it)
+        for (int p = 0; p < count; ++p)
+            if (info[p] == 0 && (st = refine_once(h, p, probs[p].u, probs[p].t, probs[p].n, s)) != DPD_OK) return st;
+    if (dpd::launch_h_to_f32(w.h64, count * h->K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (info_out) std::copy(info.begin(), info.end(), info_out);
+    return any_bad ? DPD_ERR_NOT_SPD : DPD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,262 @@
+// FP64 side of the least-squares estimate (see dpd_gram.cuh): fixed-order
+// reduction of the Gram partials, assembly of G = Psi^H Psi and g = Psi^H t,
+// equilibrated Cholesky factorisation and triangular solves, and the small
+// kernels of the iterative refinement.
+#include "dpd_gram.cuh"
+
+namespace dpd {
+
+__global__ void gram_reduce_kernel(const float *__restrict__ partials, int cpp, int C, double *__restrict__ S)
+{
+    const int p = blockIdx.y;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // i * kGramCols + j
+    if (idx >= kGramRows * kGramCols) return;
+    const int i = idx / kGramCols, j = idx % kGramCols;
+    double s = 0.0;
+    if (i < C && j < C && i <= j) {
+        const float *base = partials + (size_t)p * cpp * kGramRows * kGramCols + idx;
+        for (int c = 0; c < cpp; ++c) s += (double)base[(size_t)c * kGramRows * kGramCols];
+    }
+    S[(size_t)p * kGramRows * kGramCols + idx] = s;
+}
+
+cudaError_t launch_gram_reduce(const float *partials, int nprob, int cpp, int K, double *S, cudaStream_t s)
+{
+    dim3 grid((kGramRows * kGramCols + 255) / 256, nprob);
+    gram_reduce_kernel<<<grid, 256, 0, s>>>(partials, cpp, 2 * K + 2, S);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ double sym(const double *S, int i, int j)
+{
+    return i <= j ? S[(size_t)i * kGramCols + j] : S[(size_t)j * kGramCols + i];
+}
+
+__global__ void gram_assemble_kernel(const double *__restrict__ Sall, int K, double2 *__restrict__ G,
+                                     double2 *__restrict__ g, double *__restrict__ tt)
+{
+    const int p = blockIdx.y;
+    const double *S = Sall + (size_t)p * kGramRows * kGramCols;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int o = K + 1;   // offset of the imaginary block
+    if (idx < K * K) {
+        const int a = idx / K, b = idx % K;
+        G[(size_t)p * K * K + idx] = make_double2(sym(S, a, b) + sym(S, o + a, o + b),
+                                                  sym(S, a, o + b) - sym(S, o + a, b));
+    } else if (idx < K * K + K) {
+        const int a = idx - K * K;
+        if (g) g[(size_t)p * K + a] = make_double2(sym(S, a, K) + sym(S, o + a, 2 * K + 1),
+                                                   sym(S, a, 2 * K + 1) - sym(S, o + a, K));
+    } else if (idx == K * K + K) {
+        if (tt) tt[p] = sym(S, K, K) + sym(S, 2 * K + 1, 2 * K + 1);
+    }
+}
+
+cudaError_t launch_gram_assemble(const double *S, int nprob, int K, double2 *G, double2 *g, double *tt,
+                                 cudaStream_t s)
+{
+    dim3 grid((K * K + K + 1 + 255) / 256, nprob);
+    gram_assemble_kernel<<<grid, 256, 0, s>>>(S, K, G, g, tt);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b)   // a * conj(b)
+{
+    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// One CTA per problem: A = D G D in shared memory, factored in place (right
+// looking, lower triangle), written to L; d = diag(G)^{-1/2}.
+__global__ void chol_kernel(const double2 *__restrict__ Gall, int K, double2 *__restrict__ Lall,
+                            double *__restrict__ dall, int *__restrict__ info)
+{
+    extern __shared__ double2 A[];   // K x K
+    __shared__ double dsh[kMaxT * 12 + 1];
+    __shared__ int bad;
+    const int p = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const double2 *G = Gall + (size_t)p * K * K;
+    if (tid == 0) bad = 0;
+    for (int i = tid; i < K; i += nt) {
+        const double gii = G[(size_t)i * K + i].x;
+        dsh[i] = gii > 0.0 ? 1.0 / sqrt(gii) : 0.0;
+        if (!(gii > 0.0)) atomicMax(&bad, i + 1);
+    }
+    __syncthreads();
+    for (int e = tid; e < K * K; e += nt) {
+        const int i = e / K, j = e % K;
+        const double2 v = G[e];
+        A[e] = make_double2(v.x * dsh[i] * dsh[j], v.y * dsh[i] * dsh[j]);
+    }
+    __syncthreads();
+    for (int j = 0; j < K && !bad; ++j) {
+        if (tid == 0) {
+            const double piv = A[(size_t)j * K + j].x;
+            if (!(piv > 0.0) || !isfinite(piv))
+                bad = j + 1;
+            else
+                A[(size_t)j * K + j] = make_double2(sqrt(piv), 0.0);
+        }
+        __syncthreads();
+        if (bad) break;
+        const double ljj = A[(size_t)j * K + j].x;
+        for (int i = j + 1 + tid; i < K; i += nt) {
+            const double2 v = A[(size_t)i * K + j];
+            A[(size_t)i * K + j] = make_double2(v.x / ljj, v.y / ljj);
+        }
+        __syncthreads();
+        const int m = K - j - 1;   // trailing update of the lower triangle
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = j + 1 + e / m, k = j + 1 + e % m;
+            if (k <= i) {
+                const double2 u = cmulc(A[(size_t)i * K + j], A[(size_t)k * K + j]);
+                A[(size_t)i * K + k].x -= u.x;
+                A[(size_t)i * K + k].y -= u.y;
+            }
+        }
+        __syncthreads();
+    }
+    double2 *L = Lall + (size_t)p * K * K;
+    for (int e = tid; e < K * K; e += nt) {
+        const int i = e / K, k = e % K;
+        L[e] = k <= i ? A[e] : make_double2(0.0, 0.0);
+    }
+    for (int i = tid; i < K; i += nt) dall[(size_t)p * K + i] = dsh[i];
+    if (tid == 0) info[p] = bad;
+}
+
+cudaError_t launch_chol(const double2 *G, int nprob, int K, double2 *L, double *d, int *info, cudaStream_t s)
+{
+    const size_t smem = sizeof(double2) * K * K;
+    static size_t set = 0;
+    if (smem > set) {
+        cudaError_t e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set = smem;
+    }
+    chol_kernel<<<nprob, 256, smem, s>>>(G, K, L, d, info);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// One warp per problem: G x = rhs with G = D^{-1} L L^H D^{-1}:  x = D (L^H)^{-1} L^{-1} D rhs.
+__global__ void chol_solve_kernel(const double2 *__restrict__ Lall, const double *__restrict__ dall,
+                                  const int *__restrict__ info, const double2 *__restrict__ rhs, int K,
+                                  double2 *__restrict__ h, int accumulate)
+{
+    __shared__ double2 w[12 * kMaxT + 1];
+    const int p = blockIdx.x, lane = threadIdx.x;
+    if (info[p] != 0) return;
+    const double2 *L = Lall + (size_t)p * K * K;
+    const double *d = dall + (size_t)p * K;
+    const double2 *b = rhs + (size_t)p * K;
+    for (int i = lane; i < K; i += 32) w[i] = make_double2(b[i].x * d[i], b[i].y * d[i]);
+    __syncwarp();
+    for (int i = 0; i < K; ++i) {   // forward: L w = D b
+        double2 s = make_double2(0.0, 0.0);
+        for (int k = lane; k < i; k += 32) {
+            const double2 u = cmul(L[(size_t)i * K + k], w[k]);
+            s.x += u.x;
+            s.y += u.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        }
+        if (lane == 0) {
+            const double lii = L[(size_t)i * K + i].x;
+            w[i] = make_double2((w[i].x - s.x) / lii, (w[i].y - s.y) / lii);
+        }
+        __syncwarp();
+    }
+    for (int i = K - 1; i >= 0; --i) {   // backward: L^H v = w
+        double2 s = make_double2(0.0, 0.0);
+        for (int k = i + 1 + lane; k < K; k += 32) {
+            const double2 l = L[(size_t)k * K + i];
+            const double2 u = make_double2(l.x * w[k].x + l.y * w[k].y, l.x * w[k].y - l.y * w[k].x);   // conj(l) w
+            s.x += u.x;
+            s.y += u.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        }
+        if (lane == 0) {
+            const double lii = L[(size_t)i * K + i].x;
+            w[i] = make_double2((w[i].x - s.x) / lii, (w[i].y - s.y) / lii);
+        }
+        __syncwarp();
+    }
+    double2 *out = h + (size_t)p * K;
+    for (int i = lane; i < K; i += 32) {
+        const double2 x = make_double2(w[i].x * d[i], w[i].y * d[i]);
+        if (accumulate)
+            out[i] = make_double2(out[i].x + x.x, out[i].y + x.y);
+        else
+            out[i] = x;
+    }
+}
+
+cudaError_t launch_chol_solve(const double2 *L, const double *d, const int *info, const double2 *rhs, int nprob,
+                              int K, double2 *h, int accumulate, cudaStream_t s)
+{
+    chol_solve_kernel<<<nprob, 32, 0, s>>>(L, d, info, rhs, K, h, accumulate);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void h_to_f32_kernel(const double2 *__restrict__ h, int n, float2 *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)h[i].x, (float)h[i].y);
+}
+
+cudaError_t launch_h_to_f32(const double2 *h, int n, float2 *out, cudaStream_t s)
+{
+    h_to_f32_kernel<<<(n + 127) / 128, 128, 0, s>>>(h, n, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void residual_kernel(const float2 *__restrict__ t, const float2 *__restrict__ y, int64_t n,
+                                float2 *__restrict__ e)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 a = t[i], b = y[i];
+        e[i] = make_float2(a.x - b.x, a.y - b.y);
+    }
+}
+
+cudaError_t launch_residual(const float2 *t, const float2 *y, int64_t n, float2 *e, cudaStream_t s)
+{
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) return cudaSuccess;
+    residual_kernel<<<(unsigned)blocks, 256, 0, s>>>(t, y, n, e);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void adj_finalize64_kernel(const float2 *__restrict__ partials, int rows, int K, double2 *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    double re = 0.0, im = 0.0;
+    for (int r = 0; r < rows; ++r) {
+        const float2 v = partials[(size_t)r * K + i];
+        re += v.x;
+        im += v.y;
+    }
+    out[i] = make_double2(re, im);
+}
+
+cudaError_t launch_adj_finalize64(const float2 *partials, int rows, int K, double2 *out, cudaStream_t s)
+{
+    adj_finalize64_kernel<<<(K + 127) / 128, 128, 0, s>>>(partials, rows, K, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace dpd

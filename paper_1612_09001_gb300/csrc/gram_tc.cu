@@ -1,0 +1,368 @@
+// Gram contraction S = A^T A of the real-form basis (see dpd_gram.cuh):
+// tcgen05 tensor-core kernel with split BF16 / TF32 operands, and the plain
+// FP32 CUDA-core form it is compared against.
+#include <cuda_bf16.h>
+
+#include "dpd_gram.cuh"
+#include "dpd_tc.cuh"
+
+namespace dpd {
+
+namespace {
+
+constexpr int kGramThreads = 256;
+constexpr int kTile = 16384;          // 128 operand rows x 128 bytes
+constexpr int kBuf = 2 * kTile;       // 256 operand rows
+constexpr int kStageBytes = 2 * kBuf; // hi + lo
+constexpr int kStages = 2;
+constexpr int kPsiStride = 64 + kMaxT - 1;
+
+// Value of real-form column c at stage row rr (sample n0 + rr).
+struct ColumnDecode {
+    bool is_t, imag, conj, one;
+    int b, k;
+};
+
+__device__ __forceinline__ ColumnDecode decode_column(int c, int K, int Bp, int T)
+{
+    ColumnDecode d{};
+    int j;
+    if (c < K) {
+        j = c;
+    } else if (c == K) {
+        d.is_t = true;
+        return d;
+    } else if (c < 2 * K + 1) {
+        d.imag = true;
+        j = c - K - 1;
+    } else {
+        d.is_t = true;
+        d.imag = true;
+        return d;
+    }
+    if (j == K - 1) {
+        d.one = true;
+        return d;
+    }
+    if (j < Bp * T) {
+        d.b = j / T;
+        d.k = j % T;
+    } else {
+        d.conj = true;
+        d.b = (j - Bp * T) / T;
+        d.k = (j - Bp * T) % T;
+    }
+    return d;
+}
+
+__device__ __forceinline__ float column_value(const ColumnDecode &d, const float2 *psi, const float2 *tv, int rr,
+                                              int T, bool valid)
+{
+    if (!valid) return 0.f;
+    if (d.is_t) return d.imag ? tv[rr].y : tv[rr].x;
+    if (d.one) return d.imag ? 0.f : 1.f;
+    const float2 p = psi[d.b * kPsiStride + rr + (T - 1) - d.k];
+    return d.imag ? (d.conj ? -p.y : p.y) : p.x;
+}
+
+// Fill psi[b][w] = |u|^{2b} u for samples n0 - (T-1) + w (zero outside [0, n)) and tv[rr] = t.
+template <int R>
+__device__ __forceinline__ void stage_basis(const GramProblem &pr, int64_t n0, int T, int B, float2 *psi, float2 *tv)
+{
+    const int W = R + T - 1;
+    for (int i = threadIdx.x; i < W * B; i += blockDim.x) {
+        const int bb = i / W, w = i % W;
+        const int64_t j = n0 - (T - 1) + w;
+        float2 v = make_float2(0.f, 0.f);
+        if (j >= 0 && j < pr.n) {
+            const float2 x = pr.u[j];
+            const float r = fmaf(x.x, x.x, x.y * x.y);
+            float p = 1.f;
+            for (int e = 0; e < bb; ++e) p *= r;
+            v = make_float2(p * x.x, p * x.y);
+        }
+        psi[bb * kPsiStride + w] = v;
+    }
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        float2 v = make_float2(0.f, 0.f);
+        if (pr.t && n0 + i < pr.n) v = pr.t[n0 + i];
+        tv[i] = v;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ tensor cores
+template <int FMT>
+__global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
+{
+    constexpr int R = (FMT == kFmtBF16) ? 64 : 32;    // rows per stage: 128 bytes per operand row
+    constexpr int EPC = (FMT == kFmtBF16) ? 8 : 4;    // elements per 16-byte chunk
+    constexpr int NK = 4;                             // MMAs along K per stage (K = 16 bf16 / 8 tf32)
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *stages = smem;
+    float2 *psi = reinterpret_cast<float2 *>(smem + kStages * kStageBytes);
+    float2 *tv = psi + kMaxB * kPsiStride;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tv + 64);   // mma_done[kStages], final
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kStages + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int prob = blockIdx.x / a.cpp, chunk = blockIdx.x % a.cpp;
+    const GramProblem pr = a.probs[prob];
+    const int K = a.K, C = 2 * K + 2, T = a.T, B = a.Bp > a.Bq ? a.Bp : a.Bq;
+    const bool two = C > 128;
+    const int N0 = ((C + 15) / 16) * 16;
+    const int N1 = two ? N0 - 128 : 0;
+    const int64_t nblk = (pr.n + R - 1) / R;
+    const int64_t b0 = nblk * chunk / a.cpp, b1 = nblk * (chunk + 1) / a.cpp;
+
+    for (int i = tid; i < kStages * kStageBytes / 16; i += kGramThreads)
+        reinterpret_cast<uint4 *>(stages)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int s = 0; s <= kStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_addr(tmem_slot), 512);
+        tmem_relinquish();
+    }
+    fence_async_shared();
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc0 = umma_idesc(FMT, 128, N0);
+    const uint32_t idesc1 = two ? umma_idesc(FMT, 128, N1) : 0u;
+
+    uint32_t accumulate = 0;   // issuing thread only
+    int it = 0;
+    bool failed = false;
+    for (int64_t blk = b0; blk < b1; ++blk, ++it) {
+        const int s = it % kStages;
+        bool ok = true;
+        if (it >= kStages) ok = mbar_wait(smem_addr(&bars[s]), (uint32_t)(((it / kStages) - 1) & 1), a.status);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        unsigned char *hi = stages + s * kStageBytes;
+        unsigned char *lo = hi + kBuf;
+        const int64_t n0 = blk * R;
+        stage_basis<R>(pr, n0, T, B, psi, tv);
+        __syncthreads();
+        for (int task = tid; task < C * 8; task += kGramThreads) {
+            const int c = task >> 3, ch = task & 7;
+            const ColumnDecode d = decode_column(c, K, a.Bp, T);
+            uint32_t hw[4], lw[4];
+            if constexpr (FMT == kFmtBF16) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r0 = ch * EPC + 2 * q;
+                    const float v0 = column_value(d, psi, tv, r0, T, n0 + r0 < pr.n);
+                    const float v1 = column_value(d, psi, tv, r0 + 1, T, n0 + r0 + 1 < pr.n);
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                    const float2 hf = __bfloat1622float2(h2);
+                    const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+                    hw[q] = *reinterpret_cast<const uint32_t *>(&h2);
+                    lw[q] = *reinterpret_cast<const uint32_t *>(&l2);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r0 = ch * EPC + q;
+                    const float v = column_value(d, psi, tv, r0, T, n0 + r0 < pr.n);
+                    const float h = to_tf32(v);
+                    hw[q] = __float_as_uint(h);
+                    lw[q] = __float_as_uint(to_tf32(v - h));
+                }
+            }
+            const uint32_t off = sw128_offset(c, ch);
+            *reinterpret_cast<uint4 *>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        fence_async_shared();
+        tc_fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after_sync();
+            const uint32_t hb = smem_addr(hi), lb = smem_addr(lo);
+            const uint32_t pa[3] = {hb, hb, lb}, pb[3] = {hb, lb, hb};   // hi*hi + hi*lo + lo*hi
+#pragma unroll
+            for (int kk = 0; kk < NK; ++kk) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const uint32_t ka = pa[q] + kk * 32, kb = pb[q] + kk * 32;
+                    if constexpr (FMT == kFmtBF16) {
+                        umma_bf16(tmem, umma_desc_sw128(ka), umma_desc_sw128(kb), idesc0, accumulate);
+                        if (two)
+                            umma_bf16(tmem + (uint32_t)N0, umma_desc_sw128(ka + kTile), umma_desc_sw128(kb + kTile),
+                                      idesc1, accumulate);
+                    } else {
+                        umma_tf32(tmem, umma_desc_sw128(ka), umma_desc_sw128(kb), idesc0, accumulate);
+                        if (two)
+                            umma_tf32(tmem + (uint32_t)N0, umma_desc_sw128(ka + kTile), umma_desc_sw128(kb + kTile),
+                                      idesc1, accumulate);
+                    }
+                    accumulate = 1;
+                }
+            }
+            umma_commit(smem_addr(&bars[s]));
+        }
+    }
+    // every MMA issued by this CTA has completed once the final commit arrives
+    if (tid == 0) umma_commit(smem_addr(&bars[kStages]));
+    const bool done = mbar_wait(smem_addr(&bars[kStages]), 0u, a.status);
+    tc_fence_after_sync();
+    float *part = a.partials + (size_t)blockIdx.x * kGramRows * kGramCols;
+    const bool any = (it > 0) && !failed && done;
+    if (warp < 4) {
+        const int row = 32 * warp + lane;
+        for (int cc = 0; cc < N0 / 16; ++cc) {
+            float v[16];
+            if (any) {
+                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(cc * 16), v);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = 0.f;
+            }
+            float4 *dst = reinterpret_cast<float4 *>(part + (size_t)row * kGramCols + cc * 16);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+    } else if (two) {
+        const int w4 = warp - 4;
+        const int row = 128 + 32 * w4 + lane;
+        for (int cc = 0; cc < N1 / 16; ++cc) {
+            float v[16];
+            if (any) {
+                tmem_ld16(tmem + ((uint32_t)(32 * w4) << 16) + (uint32_t)(N0 + cc * 16), v);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = 0.f;
+            }
+            float4 *dst = reinterpret_cast<float4 *>(part + (size_t)row * kGramCols + 128 + cc * 16);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after_sync();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+size_t gram_tc_smem() { return 1024 + (size_t)kStages * kStageBytes + (kMaxB * kPsiStride + 64) * 8 + 64; }
+
+// ------------------------------------------------------------------ FP32 CUDA cores
+// Each CTA stages 64 rows of A (row-major, 256 padded columns, FP32) in shared
+// memory; thread t owns one 8 x 8 block (I, J), I <= J, of the upper triangle
+// of S and accumulates it over the rows.
+constexpr int kF32Rows = 64;
+constexpr int kF32Threads = 352;   // >= 25 * 26 / 2 = 325 diagonal-and-upper 8 x 8 blocks
+
+__global__ void __launch_bounds__(kF32Threads, 1) gram_fp32_kernel(GramArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_f[];
+    float *Atile = reinterpret_cast<float *>(smem_f);                    // [kF32Rows][256]
+    float2 *psi = reinterpret_cast<float2 *>(Atile + kF32Rows * 256);  // [kMaxB][kPsiStride]
+    float2 *tv = psi + kMaxB * kPsiStride;
+
+    const int tid = threadIdx.x;
+    const int prob = blockIdx.x / a.cpp, chunk = blockIdx.x % a.cpp;
+    const GramProblem pr = a.probs[prob];
+    const int K = a.K, C = 2 * K + 2, T = a.T, B = a.Bp > a.Bq ? a.Bp : a.Bq;
+    const int nb8 = (C + 7) / 8;
+    // block (I, J) of this thread: enumerate the upper triangle row by row
+    int I = -1, J = -1;
+    {
+        int idx = tid;
+        for (int i = 0; i < nb8 && I < 0; ++i) {
+            const int cnt = nb8 - i;
+            if (idx < cnt) {
+                I = i;
+                J = i + idx;
+            } else {
+                idx -= cnt;
+            }
+        }
+    }
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    const int64_t nblk = (pr.n + kF32Rows - 1) / kF32Rows;
+    const int64_t b0 = nblk * chunk / a.cpp, b1 = nblk * (chunk + 1) / a.cpp;
+    for (int64_t blk = b0; blk < b1; ++blk) {
+        const int64_t n0 = blk * kF32Rows;
+        __syncthreads();
+        stage_basis<kF32Rows>(pr, n0, T, B, psi, tv);
+        __syncthreads();
+        for (int e = tid; e < kF32Rows * 256; e += kF32Threads) {
+            const int rr = e >> 8, c = e & 255;
+            float v = 0.f;
+            if (c < C) v = column_value(decode_column(c, K, a.Bp, T), psi, tv, rr, T, n0 + rr < pr.n);
+            Atile[e] = v;
+        }
+        __syncthreads();
+        if (I >= 0) {
+            for (int rr = 0; rr < kF32Rows; ++rr) {
+                const float4 *row = reinterpret_cast<const float4 *>(Atile + rr * 256);
+                const float4 a0 = row[2 * I], a1 = row[2 * I + 1], b0v = row[2 * J], b1v = row[2 * J + 1];
+                const float ai[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bj[8] = {b0v.x, b0v.y, b0v.z, b0v.w, b1v.x, b1v.y, b1v.z, b1v.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(ai[i], bj[j], acc[i][j]);
+            }
+        }
+    }
+    float *part = a.partials + (size_t)blockIdx.x * kGramRows * kGramCols;
+    if (I >= 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int r = 8 * I + i, c = 8 * J + j;
+                if (r < kGramRows && c < kGramCols) part[(size_t)r * kGramCols + c] = acc[i][j];
+            }
+    }
+}
+
+size_t gram_fp32_smem() { return (size_t)kF32Rows * 256 * 4 + (kMaxB * kPsiStride + 64) * 8; }
+
+cudaError_t launch_gram(int precision, const GramArgs &a, cudaStream_t s)
+{
+    const int grid = a.nprob * a.cpp;
+    if (grid <= 0) return cudaSuccess;
+    if (precision == kPrecFP32) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(gram_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)gram_fp32_smem());
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        gram_fp32_kernel<<<grid, kF32Threads, gram_fp32_smem(), s>>>(a);
+        count_launch();
+        return cudaGetLastError();
+    }
+    auto kern = precision == kPrecBF16x3 ? gram_tc_kernel<kFmtBF16> : gram_tc_kernel<kFmtTF32>;
+    static bool attr_set[2] = {false, false};
+    const int ai = precision == kPrecBF16x3 ? 0 : 1;
+    if (!attr_set[ai]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem());
+        if (e != cudaSuccess) return e;
+        attr_set[ai] = true;
+    }
+    kern<<<grid, kGramThreads, gram_tc_smem(), s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace dpd

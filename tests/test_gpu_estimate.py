@@ -1,0 +1,137 @@
+"""Least-squares estimation on the GPU (Sec. 2.2): the Gram matrix Psi^H Psi
+and Psi^H t in every precision mode against the FP64 oracle, and the solved
+coefficients against the FP64 oracle's solution and against the coefficients
+that generated the data."""
+import numpy as np
+import pytest
+
+import dpd_synth as synth
+import oracle
+from oracle import basis
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1612_09001_gb300 as dpd  # noqa: E402
+
+# Element-wise bound of the Gram, relative to sqrt(G_aa G_bb) (Cauchy-Schwarz):
+# FP32 accumulation for every mode; BF16 hi+lo keeps about 16 mantissa bits.
+GRAM_TOL = {"fp32": 2e-6, "tf32x3": 2e-6, "bf16x3": 5e-5}
+
+
+def _gram_check(P, Q, M, n, precision, seed):
+    u = synth.clipped_gaussian(n, 0.4, key=(60, seed, 0))
+    t = synth.ofdm2(n, key=(60, seed, 1))
+    f = dpd.DPD(P, Q, M)
+    G, g, tt = f.gram(torch.from_numpy(u).cuda(), torch.from_numpy(t).cuda(), precision=precision)
+    f.sync_status()
+    Gr, gr = oracle.gram(u, t, P, Q, M)
+    G = G.cpu().numpy()
+    g = g.cpu().numpy()
+    d = np.sqrt(np.abs(np.diag(Gr)))
+    scale = np.outer(d, d)
+    err = np.abs(G - Gr) / scale
+    tol = GRAM_TOL[precision]
+    assert err.max() <= tol, (P, Q, M, n, precision, err.max(), np.unravel_index(err.argmax(), err.shape))
+    tts = float(np.sum(np.abs(t.astype(np.complex128)) ** 2))
+    gerr = np.abs(g - gr) / (d * np.sqrt(tts))
+    assert gerr.max() <= tol, (precision, gerr.max())
+    assert abs(tt - tts) <= tol * tts
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("P,Q,M,n", [(5, 3, 4, 5003), (1, 0, 0, 100), (9, 9, 4, 20011), (9, 9, 6, 3001),
+                                     (11, 11, 7, 4099), (3, 1, 2, 63), (7, 7, 3, 1)])
+def test_gram_against_oracle(P, Q, M, n, precision):
+    _gram_check(P, Q, M, n, precision, seed=P * 100 + M * 10 + n % 7)
+
+
+def _ls_problem(P, Q, M, n, seed):
+    u, theta = synth.ls_problem(n, P, Q, M, seed=seed)
+    t = oracle.apply(u, theta, P, Q, M).astype(np.complex64)   # noise-free target from the model
+    return u, t, theta
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("tf32x3", 1e-4), ("bf16x3", 1e-3)])
+def test_estimate_recovers_model_coefficients(precision, tol):
+    P, Q, M, n = 5, 3, 4, 50000
+    u, t, theta = _ls_problem(P, Q, M, n, 1)
+    f = dpd.DPD(P, Q, M)
+    h, st = f.estimate(torch.from_numpy(u).cuda(), torch.from_numpy(t).cuda(), precision=precision, refine_iters=3)
+    h = h.cpu().numpy().astype(np.complex128)
+    ref = oracle.ls(u, t, P, Q, M)
+    e_ref = np.linalg.norm(h - ref) / np.linalg.norm(ref)
+    e_true = np.linalg.norm(h - theta) / np.linalg.norm(theta)
+    assert e_ref <= tol and e_true <= tol, (precision, e_ref, e_true, st)
+    assert st["rel_residual"] < 1e-8 and st["cond_est"] >= 1.0
+
+
+def test_estimate_full_size_p11_m7():
+    """2^22 rows x 97 columns: recovery of the generating coefficients and
+    sampled Gram entries (each an O(n) sum) against FP64 numpy."""
+    P, Q, M, n = 11, 11, 7, 1 << 22
+    u, theta = synth.ls_problem(n, P, Q, M, seed=0)
+    ud = torch.from_numpy(u).cuda()
+    f = dpd.DPD(P, Q, M)
+    f.set_coeffs(theta)
+    td = f.apply(ud)                      # t = Psi(u) theta, FP32
+    t = td.cpu().numpy()
+    G, g, _ = f.gram(ud, td, precision="tf32x3")
+    G = G.cpu().numpy()
+    rng = np.random.default_rng(61)
+    u64 = u.astype(np.complex128)
+    K = f.K
+    for a, b in list(rng.integers(0, K, size=(12, 2))) + [(0, 0), (K - 1, K - 1), (K - 2, 3)]:
+        ca = basis.basis_matrix(u64[:0], P, Q, M)  # shape check only
+        colA = _column(u64, P, Q, M, int(a))
+        colB = _column(u64, P, Q, M, int(b))
+        ref = np.vdot(colA, colB)
+        scale = np.sqrt(np.vdot(colA, colA).real * np.vdot(colB, colB).real)
+        assert abs(G[a, b] - ref) <= 2e-6 * scale, (a, b, G[a, b], ref)
+    for precision, tol in (("tf32x3", 1e-2), ("bf16x3", 1e-1), ("fp32", 1e-2)):
+        h, st = f.estimate(ud, td, precision=precision, refine_iters=3)
+        e = np.linalg.norm(h.cpu().numpy() - theta) / np.linalg.norm(theta)
+        print(f"P=11 M=7 n=2^22 {precision}: coefficient error {e:.3e}, cond(DGD) ~ {st['cond_est']:.3e}, "
+              f"rel residual {st['rel_residual']:.3e}")
+        assert e <= tol, (precision, e, st)
+
+
+def _column(u, P, Q, M, j):
+    """Column j of the basis matrix (Eq. 2) without forming the rest."""
+    L = M + 1
+    bp = (P + 1) // 2 if P else 0
+    bq = (Q + 1) // 2 if Q else 0
+    n = len(u)
+    if j == (bp + bq) * L:
+        return np.ones(n, np.complex128)
+    conj = j >= bp * L
+    jj = j - bp * L if conj else j
+    b, k = jj // L, jj % L
+    v = np.abs(u) ** (2 * b) * (np.conj(u) if conj else u)
+    out = np.zeros(n, np.complex128)
+    out[k:] = v[: n - k]
+    return out
+
+
+def test_estimate_rejects_singular_gram():
+    f = dpd.DPD(5, 5, 2)
+    u = torch.zeros(4096, dtype=torch.complex64, device="cuda")
+    t = torch.ones(4096, dtype=torch.complex64, device="cuda")
+    with pytest.raises(dpd.DPDError) as e:
+        f.estimate(u, t, precision="tf32x3")
+    assert e.value.code == 6
+
+
+def test_estimate_batched_matches_single():
+    P, Q, M = 7, 7, 3
+    probs = [_ls_problem(P, Q, M, 20000 + 17 * i, 70 + i) for i in range(6)]
+    f = dpd.DPD(P, Q, M)
+    us = [torch.from_numpy(u).cuda() for u, _, _ in probs]
+    ts = [torch.from_numpy(t).cuda() for _, t, _ in probs]
+    hb, info = f.estimate_batched(us, ts, precision="tf32x3", refine_iters=2)
+    assert info == [0] * len(probs)
+    for i, (u, t, theta) in enumerate(probs):
+        hs, _ = f.estimate(us[i], ts[i], precision="tf32x3", refine_iters=2)
+        np.testing.assert_allclose(hb[i].cpu().numpy(), hs.cpu().numpy(), rtol=0, atol=1e-5)
+        e = np.linalg.norm(hb[i].cpu().numpy() - theta) / np.linalg.norm(theta)
+        assert e < 1e-4, (i, e)
