@@ -217,7 +217,7 @@ dpd_status dpd_gram(dpd_handle h, const void *u, const void *t, int64_t n, int p
  *           left unchanged; install the result with dpd_set_coeffs)
  *   stats : host double[2] or NULL: [0] condition estimate of D G D (squared
  *           ratio of the extreme Cholesky pivots), [1] ||t - Psi h||^2 / ||t||^2
- *           from G, g and t^H t in FP64
+ *           of the returned h (FP32 residual, FP64 sums)
  * Synchronises `stream`.  DPD_ERR_NOT_SPD if G is not positive definite
  * (e.g. u all zero).  Uses and may grow the handle's workspace.
  */

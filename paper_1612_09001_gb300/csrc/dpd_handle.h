@@ -22,6 +22,7 @@ struct EstimateWorkspace {
     float2 *hf = nullptr;         // coefficients of the refinement pass (complex64)
     float *tab = nullptr;         // their forward table
     float2 *y = nullptr, *e = nullptr;
+    double *norm_part = nullptr;  // 2 * 1024 partial sums + 2 results
 };
 
 struct dpd_filter {

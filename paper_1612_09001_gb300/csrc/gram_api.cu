@@ -41,6 +41,7 @@ dpd_status reserve(dpd_handle h, int nprob, int cpp, int64_t nsamp)
         ok = ok && grow(w.g, 0, np * K) && grow(w.h64, 0, np * K) && grow(w.delta, 0, np * K);
         ok = ok && grow(w.d, 0, np * K) && grow(w.tt, 0, np) && grow(w.info, 0, np);
         ok = ok && grow(w.hf, 0, (size_t)K) && grow(w.tab, 0, (size_t)dpd::wl_table_floats(h->B, h->T));
+        ok = ok && grow(w.norm_part, 0, (size_t)2 * 1024 + 2);
         if (!ok) return DPD_ERR_ALLOC;
         w.nprob = nprob;
         w.cpp = cpp;
@@ -85,8 +86,8 @@ dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_
     return DPD_OK;
 }
 
-// One refinement step of problem p:  h64[p] += G^{-1} Psi^H (t - Psi h).
-dpd_status refine_once(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, cudaStream_t s)
+// e = t - Psi(u) h for the current FP64 coefficients of problem p (FP32 filter).
+dpd_status residual_of(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, cudaStream_t s)
 {
     EstimateWorkspace &w = h->est;
     const int K = h->K;
@@ -108,6 +109,16 @@ dpd_status refine_once(dpd_handle h, int p, const float2 *u, const float2 *t, in
     }
     if (dpd::launch_fwd_any(h->B, h->T, fa, L, h->sm_count, s) != cudaSuccess) return DPD_ERR_CUDA;
     if (dpd::launch_residual(t, w.y, n, w.e, s) != cudaSuccess) return DPD_ERR_CUDA;
+    return DPD_OK;
+}
+
+// One refinement step of problem p:  h64[p] += G^{-1} Psi^H (t - Psi h).
+dpd_status refine_once(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, cudaStream_t s)
+{
+    EstimateWorkspace &w = h->est;
+    const int K = h->K;
+    dpd_status st = residual_of(h, p, u, t, n, s);
+    if (st != DPD_OK) return st;
     dpd::AdjArgs aa;
     aa.x = u;
     aa.gy = w.e;
@@ -129,40 +140,30 @@ dpd_status refine_once(dpd_handle h, int p, const float2 *u, const float2 *t, in
     return DPD_OK;
 }
 
-// Statistics of problem p on the host: condition estimate of the equilibrated
-// Gram matrix from the Cholesky diagonal, and ||t - Psi h||^2 / ||t||^2 from
-// G, g, t^H t and h (FP64).
-dpd_status host_stats(dpd_handle h, int p, double *stats)
+// Statistics of problem p: condition estimate of the equilibrated Gram matrix
+// from the Cholesky diagonal (squared ratio of the extreme pivots), and
+// ||t - Psi h||^2 / ||t||^2 with the FP32 residual of the final coefficients
+// summed in FP64 on the device.
+dpd_status stats_of(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, double *stats, cudaStream_t s)
 {
     EstimateWorkspace &w = h->est;
     const int K = h->K;
-    std::vector<double2> L((size_t)K * K), G((size_t)K * K), g(K), x(K);
-    double tt = 0;
-    if (cudaMemcpy(L.data(), w.L + (size_t)p * K * K, sizeof(double2) * K * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(G.data(), w.G + (size_t)p * K * K, sizeof(double2) * K * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(g.data(), w.g + (size_t)p * K, sizeof(double2) * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(x.data(), w.h64 + (size_t)p * K, sizeof(double2) * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(&tt, w.tt + p, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    dpd_status st = residual_of(h, p, u, t, n, s);
+    if (st != DPD_OK) return st;
+    if (dpd::launch_sqnorm2(w.e, t, n, w.norm_part, w.norm_part + 2 * 1024, s) != cudaSuccess) return DPD_ERR_CUDA;
+    std::vector<double2> L((size_t)K * K);
+    double nrm[2] = {0, 0};
+    if (cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaMemcpy(L.data(), w.L + (size_t)p * K * K, sizeof(double2) * K * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(nrm, w.norm_part + 2 * 1024, sizeof(nrm), cudaMemcpyDeviceToHost) != cudaSuccess)
         return DPD_ERR_CUDA;
     double lmin = INFINITY, lmax = 0;
     for (int i = 0; i < K; ++i) {
         lmin = std::min(lmin, L[(size_t)i * K + i].x);
         lmax = std::max(lmax, L[(size_t)i * K + i].x);
     }
-    // r^2 = t^H t - 2 Re(h^H g) + h^H G h
-    double hg = 0, hGh = 0;
-    for (int a = 0; a < K; ++a) {
-        hg += x[a].x * g[a].x + x[a].y * g[a].y;
-        double re = 0, im = 0;
-        for (int b = 0; b < K; ++b) {
-            const double2 gab = G[(size_t)a * K + b];
-            re += gab.x * x[b].x - gab.y * x[b].y;
-            im += gab.x * x[b].y + gab.y * x[b].x;
-        }
-        hGh += x[a].x * re + x[a].y * im;
-    }
     stats[0] = (lmax / lmin) * (lmax / lmin);
-    stats[1] = tt > 0 ? std::max(0.0, tt - 2 * hg + hGh) / tt : 0.0;
+    stats[1] = nrm[1] > 0 ? nrm[0] / nrm[1] : 0.0;
     return DPD_OK;
 }
 
@@ -194,6 +195,7 @@ void free_estimate_workspace(EstimateWorkspace &w)
     cudaFree(w.tab);
     cudaFree(w.y);
     cudaFree(w.e);
+    cudaFree(w.norm_part);
     w = EstimateWorkspace();
 }
 
@@ -230,7 +232,7 @@ dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, i
     if (!t || !h_out || !aligned8(h_out) || refine_iters < 0 || refine_iters > 100) return DPD_ERR_INVALID_ARGUMENT;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int cpp = gram_cpp(h, 1, n);
-    if ((st = reserve(h, 1, cpp, refine_iters > 0 ? n : 0)) != DPD_OK) return st;
+    if ((st = reserve(h, 1, cpp, (refine_iters > 0 || stats) ? n : 0)) != DPD_OK) return st;
     EstimateWorkspace &w = h->est;
     const dpd::GramProblem pr{static_cast<const float2 *>(u), static_cast<const float2 *>(t), n};
     if (cudaMemcpyAsync(w.probs, &pr, sizeof(pr), cudaMemcpyHostToDevice, s) != cudaSuccess) return DPD_ERR_CUDA;
@@ -246,7 +248,7 @@ dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, i
         if ((st = refine_once(h, 0, pr.u, pr.t, n, s)) != DPD_OK) return st;
     if (dpd::launch_h_to_f32(w.h64, h->K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return DPD_ERR_CUDA;
-    if (stats) return host_stats(h, 0, stats);
+    if (stats) return stats_of(h, 0, pr.u, pr.t, n, stats, s);
     return DPD_OK;
 }
 

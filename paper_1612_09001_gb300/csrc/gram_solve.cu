@@ -239,6 +239,55 @@ cudaError_t launch_residual(const float2 *t, const float2 *y, int64_t n, float2 
     return cudaGetLastError();
 }
 
+// Per-block FP64 sums of |e|^2 and |t|^2, then one fixed-order final sum.
+constexpr int kNormBlocks = 1024;
+
+__global__ void sqnorm2_kernel(const float2 *__restrict__ e, const float2 *__restrict__ t, int64_t n,
+                               double *__restrict__ part)
+{
+    __shared__ double se[256], st[256];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 x = e[i], y = t[i];
+        a += (double)x.x * x.x + (double)x.y * x.y;
+        b += (double)y.x * y.x + (double)y.y * y.y;
+    }
+    se[threadIdx.x] = a;
+    st[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            se[threadIdx.x] += se[threadIdx.x + o];
+            st[threadIdx.x] += st[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = se[0];
+        part[2 * blockIdx.x + 1] = st[0];
+    }
+}
+
+__global__ void sum_pairs_kernel(const double *__restrict__ part, int nb, double *__restrict__ out)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    out[0] = a;
+    out[1] = b;
+}
+
+cudaError_t launch_sqnorm2(const float2 *e, const float2 *t, int64_t n, double *part, double *out, cudaStream_t s)
+{
+    sqnorm2_kernel<<<kNormBlocks, 256, 0, s>>>(e, t, n, part);
+    count_launch();
+    sum_pairs_kernel<<<1, 1, 0, s>>>(part, kNormBlocks, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
 __global__ void adj_finalize64_kernel(const float2 *__restrict__ partials, int rows, int K, double2 *__restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;

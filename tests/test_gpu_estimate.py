@@ -30,11 +30,15 @@ def _gram_check(P, Q, M, n, precision, seed):
     g = g.cpu().numpy()
     d = np.sqrt(np.abs(np.diag(Gr)))
     scale = np.outer(d, d)
-    err = np.abs(G - Gr) / scale
+    zero = scale == 0          # columns that are identically zero (taps beyond a short input)
+    assert np.all(G[zero] == 0), "entries of all-zero columns must be exactly zero"
+    err = np.abs(G - Gr)[~zero] / scale[~zero]
     tol = GRAM_TOL[precision]
-    assert err.max() <= tol, (P, Q, M, n, precision, err.max(), np.unravel_index(err.argmax(), err.shape))
+    assert err.max() <= tol, (P, Q, M, n, precision, err.max())
     tts = float(np.sum(np.abs(t.astype(np.complex128)) ** 2))
-    gerr = np.abs(g - gr) / (d * np.sqrt(tts))
+    nz = d > 0
+    assert np.all(g[~nz] == 0)
+    gerr = np.abs(g - gr)[nz] / (d[nz] * np.sqrt(tts))
     assert gerr.max() <= tol, (precision, gerr.max())
     assert abs(tt - tts) <= tol * tts
 
@@ -63,7 +67,7 @@ def test_estimate_recovers_model_coefficients(precision, tol):
     e_ref = np.linalg.norm(h - ref) / np.linalg.norm(ref)
     e_true = np.linalg.norm(h - theta) / np.linalg.norm(theta)
     assert e_ref <= tol and e_true <= tol, (precision, e_ref, e_true, st)
-    assert st["rel_residual"] < 1e-8 and st["cond_est"] >= 1.0
+    assert st["rel_residual"] < 1e-10 and st["cond_est"] >= 1.0
 
 
 def test_estimate_full_size_p11_m7():
@@ -82,7 +86,6 @@ def test_estimate_full_size_p11_m7():
     u64 = u.astype(np.complex128)
     K = f.K
     for a, b in list(rng.integers(0, K, size=(12, 2))) + [(0, 0), (K - 1, K - 1), (K - 2, 3)]:
-        ca = basis.basis_matrix(u64[:0], P, Q, M)  # shape check only
         colA = _column(u64, P, Q, M, int(a))
         colB = _column(u64, P, Q, M, int(b))
         ref = np.vdot(colA, colB)
