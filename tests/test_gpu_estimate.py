@@ -90,7 +90,9 @@ def test_estimate_full_size_p11_m7():
         colB = _column(u64, P, Q, M, int(b))
         ref = np.vdot(colA, colB)
         scale = np.sqrt(np.vdot(colA, colA).real * np.vdot(colB, colB).real)
-        assert abs(G[a, b] - ref) <= 2e-6 * scale, (a, b, G[a, b], ref)
+        # FP32 accumulation of ~n / 152 = 2.8e4 rows per CTA: random-walk error
+        # about sqrt(2.8e4) * 2^-24 = 1e-5 of the Cauchy-Schwarz scale
+        assert abs(G[a, b] - ref) <= 1e-5 * scale, (a, b, G[a, b], ref)
     for precision, tol in (("tf32x3", 1e-2), ("bf16x3", 1e-1), ("fp32", 1e-2)):
         h, st = f.estimate(ud, td, precision=precision, refine_iters=3)
         e = np.linalg.norm(h.cpu().numpy() - theta) / np.linalg.norm(theta)
