@@ -93,6 +93,16 @@ __device__ __forceinline__ void stage_basis(const GramProblem &pr, int64_t n0, i
 }  // namespace
 
 // ------------------------------------------------------------------ tensor cores
+// The tensor core's FP32 accumulator drops low-order bits on every MMA step, a
+// bias that grows with the number of steps summed into one accumulator.  So
+// each accumulation covers a chunk of kChunk stages only: after a chunk, every
+// thread adds its share of the tensor-memory accumulators (one lane quarter,
+// 144 of the 288 columns) into FP32 registers with round-to-nearest, and the
+// next chunk starts from zero.  The next stage's basis is generated while the
+// tensor core finishes the chunk.
+constexpr int kChunk = 4;
+constexpr int kAccCols = 144;   // per thread: half of the 288 accumulator columns of a lane
+
 template <int FMT>
 __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
 {
@@ -104,18 +114,21 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
     unsigned char *stages = smem;
     float2 *psi = reinterpret_cast<float2 *>(smem + kStages * kStageBytes);
     float2 *tv = psi + kMaxB * kPsiStride;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tv + 64);   // mma_done[kStages], final
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tv + 64);   // stage_done[kStages], chunk_done
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kStages + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
     const int prob = blockIdx.x / a.cpp, chunk = blockIdx.x % a.cpp;
     const GramProblem pr = a.probs[prob];
     const int K = a.K, C = 2 * K + 2, T = a.T, B = a.Bp > a.Bq ? a.Bp : a.Bq;
     const bool two = C > 128;
     const int N0 = ((C + 15) / 16) * 16;
     const int N1 = two ? N0 - 128 : 0;
+    const int used_cols = N0 + N1;   // tensor-memory columns holding D0 then D1
     const int64_t nblk = (pr.n + R - 1) / R;
     const int64_t b0 = nblk * chunk / a.cpp, b1 = nblk * (chunk + 1) / a.cpp;
+    const int nits = (int)(b1 - b0);
 
     for (int i = tid; i < kStages * kStageBytes / 16; i += kGramThreads)
         reinterpret_cast<uint4 *>(stages)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -134,11 +147,34 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc0 = umma_idesc(FMT, 128, N0);
     const uint32_t idesc1 = two ? umma_idesc(FMT, 128, N1) : 0u;
+    const uint32_t my_taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(half * kAccCols);
 
-    uint32_t accumulate = 0;   // issuing thread only
-    int it = 0;
+    float acc[kAccCols];
+#pragma unroll
+    for (int i = 0; i < kAccCols; ++i) acc[i] = 0.f;
+
+    // Add the finished chunk's accumulators (this thread's lane and columns) into acc.
+    auto drain = [&](int c) -> bool {
+        const bool ok = mbar_wait(smem_addr(&bars[kStages]), (uint32_t)(c & 1), a.status);
+        tc_fence_after_sync();
+        if (ok) {
+#pragma unroll
+            for (int cc = 0; cc < kAccCols / 16; ++cc) {
+                if (half * kAccCols + cc * 16 < used_cols) {
+                    float v[16];
+                    tmem_ld16(my_taddr + (uint32_t)(cc * 16), v);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) acc[cc * 16 + q] += v[q];
+                }
+            }
+        }
+        tc_fence_before_sync();
+        return ok;
+    };
+
     bool failed = false;
-    for (int64_t blk = b0; blk < b1; ++blk, ++it) {
+    int chunk_commits = 0;   // issuing thread only
+    for (int it = 0; it < nits; ++it) {
         const int s = it % kStages;
         bool ok = true;
         if (it >= kStages) ok = mbar_wait(smem_addr(&bars[s]), (uint32_t)(((it / kStages) - 1) & 1), a.status);
@@ -148,7 +184,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
         }
         unsigned char *hi = stages + s * kStageBytes;
         unsigned char *lo = hi + kBuf;
-        const int64_t n0 = blk * R;
+        const int64_t n0 = (b0 + it) * R;
         stage_basis<R>(pr, n0, T, B, psi, tv);
         __syncthreads();
         for (int task = tid; task < C * 8; task += kGramThreads) {
@@ -184,10 +220,18 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
         fence_async_shared();
         tc_fence_before_sync();
         __syncthreads();
+        if (it > 0 && it % kChunk == 0) {   // previous chunk: drain before it is overwritten
+            const bool okd = drain(it / kChunk - 1);
+            if (__syncthreads_or(!okd)) {
+                failed = true;
+                break;
+            }
+        }
         if (tid == 0) {
             tc_fence_after_sync();
             const uint32_t hb = smem_addr(hi), lb = smem_addr(lo);
             const uint32_t pa[3] = {hb, hb, lb}, pb[3] = {hb, lb, hb};   // hi*hi + hi*lo + lo*hi
+            uint32_t accumulate = (it % kChunk == 0) ? 0u : 1u;
 #pragma unroll
             for (int kk = 0; kk < NK; ++kk) {
 #pragma unroll
@@ -208,43 +252,36 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
                 }
             }
             umma_commit(smem_addr(&bars[s]));
+            if ((it + 1) % kChunk == 0 || it + 1 == nits) {
+                umma_commit(smem_addr(&bars[kStages]));
+                ++chunk_commits;
+            }
         }
     }
-    // every MMA issued by this CTA has completed once the final commit arrives
-    if (tid == 0) umma_commit(smem_addr(&bars[kStages]));
-    const bool done = mbar_wait(smem_addr(&bars[kStages]), 0u, a.status);
-    tc_fence_after_sync();
+    if (!failed && nits > 0) {   // the last chunk
+        const bool okd = drain((nits - 1) / kChunk);
+        failed = __syncthreads_or(!okd);
+    } else {
+        __syncthreads();
+    }
+    if (failed) {
+        // let every MMA this CTA issued finish before tensor memory is released
+        if (tid == 0) {
+            umma_commit(smem_addr(&bars[kStages]));
+            mbar_wait(smem_addr(&bars[kStages]), (uint32_t)(chunk_commits & 1), a.status);
+        }
+        __syncthreads();
+    }
     float *part = a.partials + (size_t)blockIdx.x * kGramRows * kGramCols;
-    const bool any = (it > 0) && !failed && done;
-    if (warp < 4) {
-        const int row = 32 * warp + lane;
-        for (int cc = 0; cc < N0 / 16; ++cc) {
-            float v[16];
-            if (any) {
-                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(cc * 16), v);
-            } else {
+    const int row = 32 * quarter + lane;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) v[q] = 0.f;
-            }
-            float4 *dst = reinterpret_cast<float4 *>(part + (size_t)row * kGramCols + cc * 16);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        }
-    } else if (two) {
-        const int w4 = warp - 4;
-        const int row = 128 + 32 * w4 + lane;
-        for (int cc = 0; cc < N1 / 16; ++cc) {
-            float v[16];
-            if (any) {
-                tmem_ld16(tmem + ((uint32_t)(32 * w4) << 16) + (uint32_t)(N0 + cc * 16), v);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 16; ++q) v[q] = 0.f;
-            }
-            float4 *dst = reinterpret_cast<float4 *>(part + (size_t)row * kGramCols + 128 + cc * 16);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        }
+    for (int i = 0; i < kAccCols; ++i) {
+        const int c = half * kAccCols + i;   // tensor-memory column
+        const float v = failed ? 0.f : acc[i];
+        if (c < N0)
+            part[(size_t)row * kGramCols + c] = v;
+        else if (c < used_cols)
+            part[(size_t)(128 + row) * kGramCols + 128 + (c - N0)] = v;
     }
     tc_fence_before_sync();
     __syncthreads();
