@@ -275,6 +275,98 @@ def measure_batched(dev, reps=20):
             "hbm_frac_persistent": 16 * total / t_plan / 1e9}
 
 
+def measure_direct(dev, steps=300):
+    """Direct learning, 2^20 OFDM samples, DPD P=Q=7, M=3 through the synthetic
+    I/Q + PA transmitter: one graph-replayed Adam step, and the NMSE reached
+    against indirect learning (3 LS iterations)."""
+    import torch
+    import dpd_synth as synth
+    from paper_1612_09001_gb300.direct import DirectLearner, Transmitter, indirect_learning, nmse_db
+    import paper_1612_09001_gb300 as dpd
+    t = synth.synthetic_pa(seed=1)
+    tx = Transmitter([t["iq"], t["pa"]], device=dev)
+    x = torch.from_numpy(synth.ofdm2(1 << 20, key=(0, 0))).to(dev)
+    base = nmse_db(tx.apply(x), x)
+    learner = DirectLearner(x, tx, 7, 7, 3, lr=2e-3).capture()
+    l0 = dpd.kernel_launches()
+    learner.step()
+    torch.cuda.synchronize(dev)
+    ms = learner.time_step(50)
+    learner.train(steps)
+    with torch.no_grad():
+        direct = nmse_db(tx.apply(learner.filt.apply(x)), x)
+    h_ila = indirect_learning(x, tx, 7, 7, 3, iterations=3)
+    f = dpd.DPD(7, 7, 3)
+    f.set_coeffs(h_ila)
+    ila = nmse_db(tx.apply(f.apply(x)), x)
+    return {"workload": "2^20 OFDM samples, DPD P=Q=7 M=3 (K=33), transmitter: I/Q (g=1.02, 2 deg, LO 0.005) + PA P=7 M=3",
+            "adjoint_step_ms": ms, "step": "graph replay: DPD -> I/Q -> PA -> loss -> adjoint PA, I/Q, DPD -> Adam",
+            "nmse_db_no_dpd": base, "nmse_db_direct": direct, "direct_steps": steps + 54,
+            "nmse_db_ila_3_iterations": ila}
+
+
+def measure_gram(dev, reps=5):
+    """LS Gram of 2^22 rows x K=97 (P=Q=11, M=7) in every precision, and the
+    batch of 256 estimations of 2^16 rows."""
+    import numpy as np
+    import torch
+    import dpd_synth as synth
+    import paper_1612_09001_gb300 as dpd
+    P, Q, M, n = 11, 11, 7, 1 << 22
+    u, theta = synth.ls_problem(n, P, Q, M, seed=0)
+    f = dpd.DPD(P, Q, M)
+    K = f.K
+    ud = torch.from_numpy(u).to(dev)
+    g = dpd.DPD(P, Q, M)
+    g.set_coeffs(theta)
+    td = g.apply(ud)
+    useful = 8.0 * n * K * K
+    out = {"workload": "Psi 2^22 rows x 97 complex columns (P=Q=11, M=7), clipped Gaussian RMS 0.3, t = Psi theta",
+           "flops_convention": "useful = 8 n K^2 (complex Gram); the tensor path executes 3 split products on 256 x 208 padded tiles",
+           "single": {}, "batch": {}}
+    for prec in ("fp32", "tf32x3", "bf16x3"):
+        f.gram(ud, td, precision=prec)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            f.gram(ud, td, precision=prec)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        t_gram = e0.elapsed_time(e1) * 1e-3 / reps
+        t0 = time.perf_counter()
+        h, st = f.estimate(ud, td, precision=prec, refine_iters=3)
+        t_est = time.perf_counter() - t0
+        err = float(np.linalg.norm(h.cpu().numpy() - theta) / np.linalg.norm(theta))
+        out["single"][prec] = {"gram_ms": t_gram * 1e3, "gram_tflops_useful": useful / t_gram / 1e12,
+                               "estimate_ms_3_refinements": t_est * 1e3, "coef_rel_error_vs_true": err,
+                               "cond_est_DGD": st["cond_est"], "rel_residual": st["rel_residual"]}
+    # batch: 256 antennas x 2^16 rows
+    nb, nr = 256, 1 << 16
+    us, ts, thetas = [], [], []
+    for b in range(nb):
+        ub, thb = synth.ls_problem(nr, P, Q, M, seed=b)
+        ubd = torch.from_numpy(ub).to(dev)
+        g.set_coeffs(thb)
+        us.append(ubd)
+        ts.append(g.apply(ubd))
+        thetas.append(thb)
+    useful_b = 8.0 * nb * nr * K * K
+    for prec in ("tf32x3", "bf16x3"):
+        f.estimate_batched(us, ts, precision=prec, refine_iters=0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        hb, info = f.estimate_batched(us, ts, precision=prec, refine_iters=0)
+        t_b = time.perf_counter() - t0
+        hb = hb.cpu().numpy()
+        errs = [float(np.linalg.norm(hb[i] - thetas[i]) / np.linalg.norm(thetas[i])) for i in range(nb)]
+        out["batch"][prec] = {"problems": nb, "rows_each": nr, "gram_and_solve_ms": t_b * 1e3,
+                              "tflops_useful": useful_b / t_b / 1e12, "coef_rel_error_median": float(np.median(errs)),
+                              "coef_rel_error_max": float(np.max(errs)), "not_spd": int(sum(1 for i in info if i))}
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -411,6 +503,8 @@ def run_ours(args, world, rank, local):
         b = measure_batched(dev)
         b["hbm_frac_persistent"] = b["hbm_frac_persistent"] / peaks["hbm_gbs"]
         patterns["batched"] = b
+        patterns["adjoint"] = measure_direct(dev)
+        patterns["gram"] = measure_gram(dev)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:

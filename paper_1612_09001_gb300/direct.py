@@ -1,0 +1,134 @@
+"""Direct-learning predistortion through a transmitter model, and the indirect
+learning architecture of Sec. 2.2 for comparison.
+
+Direct learning: the predistorter coefficients h are trained by gradient
+descent (Adam) on
+    L(h) = ||TX(DPD_h(x)) - G x||^2 / ||x||^2,
+where TX is a fixed transmitter model made of APH filters (an I/Q modulator
+stage followed by a PA stage with memory).  Every stage is a DPDFunction, so
+the gradients flow through the library's adjoint kernels: the PA and I/Q stages
+contribute input gradients, the predistorter its coefficient gradient.  The
+polynomial basis is recomputed from the saved stage inputs in the backward
+pass (nothing else is kept).  One training step (forward through three
+filters, loss, adjoint back through three filters, Adam) can be captured in a
+CUDA graph and replayed.
+
+Indirect learning (Sec. 2.2): iterate z = DPD_h(x), s = TX(z) / G,
+h = argmin ||Psi(s) h - z|| (dpd_estimate), 1-3 times.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import torch
+
+from . import DPD
+from .autograd import DPDFunction
+
+
+class Transmitter:
+    """A chain of fixed APH filter stages, each given as dict(P, Q, M, h)."""
+
+    def __init__(self, stages, device="cuda"):
+        self.stages = []
+        for st in stages:
+            f = DPD(st["P"], st["Q"], st["M"])
+            h = torch.as_tensor(st["h"]).to(device=device, dtype=torch.complex64).contiguous()
+            self.stages.append((f, h))
+
+    def __call__(self, v):
+        for f, h in self.stages:
+            v = DPDFunction.apply(v, h, f)
+        return v
+
+    def apply(self, v):
+        with torch.no_grad():
+            return self(v)
+
+
+def nmse_db(y, ref):
+    e = (y - ref).abs().pow(2).sum()
+    return 10.0 * math.log10(float(e) / float(ref.abs().pow(2).sum()))
+
+
+class DirectLearner:
+    """Adam on the predistorter coefficients through the transmitter model."""
+
+    def __init__(self, x, tx, P, Q, M, gain=1.0, lr=1e-3, h0=None):
+        self.x = x
+        self.tx = tx
+        self.filt = DPD(P, Q, M)
+        if h0 is None:
+            h0 = torch.zeros(self.filt.K, dtype=torch.complex64, device=x.device)
+            h0[0] = 1.0   # start from the identity predistorter
+        self.h = torch.nn.Parameter(h0.clone().contiguous())
+        self.gain = gain
+        self.scale = 1.0 / float(x.abs().pow(2).sum())
+        self.opt = torch.optim.Adam([self.h], lr=lr, capturable=True)
+        self.graph = None
+        self.static_loss = None
+
+    def loss(self):
+        y = self.tx(DPDFunction.apply(self.x, self.h, self.filt))
+        return torch.view_as_real(y - self.gain * self.x).pow(2).sum() * self.scale
+
+    def _step(self):
+        self.opt.zero_grad(set_to_none=False)
+        loss = self.loss()
+        loss.backward()
+        self.opt.step()
+        return loss
+
+    def capture(self, warmup=3):
+        """Capture one training step in a CUDA graph (after a few eager steps)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self._step()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.static_loss = self._step()
+        return self
+
+    def step(self):
+        if self.graph is not None:
+            self.graph.replay()
+            return self.static_loss
+        return self._step()
+
+    def train(self, steps):
+        hist = []
+        for i in range(steps):
+            loss = self.step()
+            if i % max(1, steps // 20) == 0 or i == steps - 1:
+                hist.append((i, float(loss)))
+        return hist
+
+    def time_step(self, reps=50):
+        """Milliseconds per graph-replayed training step."""
+        if self.graph is None:
+            self.capture()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            self.graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+
+def indirect_learning(x, tx, P, Q, M, gain=1.0, iterations=3, precision="tf32x3", refine_iters=2):
+    """ILA (Sec. 2.2): returns the coefficient vector after `iterations` LS fits."""
+    est = DPD(P, Q, M)
+    h = None
+    for _ in range(iterations):
+        z = x if h is None else est.apply(x)
+        s = tx.apply(z) / gain
+        h, _ = est.estimate(s.contiguous(), z.contiguous(), precision=precision, refine_iters=refine_iters)
+        est.set_coeffs(h)
+    return h
