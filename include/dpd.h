@@ -215,8 +215,8 @@ dpd_status dpd_gram(dpd_handle h, const void *u, const void *t, int64_t n, int p
  * output divided by its gain and t the predistorter output.
  *   h_out : device, K complex64, written (the handle's own coefficients are
  *           left unchanged; install the result with dpd_set_coeffs)
- *   stats : host double[2] or NULL: [0] condition estimate of D G D (squared
- *           ratio of the extreme Cholesky pivots), [1] ||t - Psi h||^2 / ||t||^2
+ *   stats : host double[2] or NULL: [0] 2-norm condition number of D G D
+ *           (power iterations with the FP64 Cholesky factor), [1] ||t - Psi h||^2 / ||t||^2
  *           of the returned h (FP32 residual, FP64 sums)
  * Synchronises `stream`.  DPD_ERR_NOT_SPD if G is not positive definite
  * (e.g. u all zero).  Uses and may grow the handle's workspace.

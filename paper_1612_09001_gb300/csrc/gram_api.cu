@@ -140,8 +140,75 @@ dpd_status refine_once(dpd_handle h, int p, const float2 *u, const float2 *t, in
     return DPD_OK;
 }
 
-// Statistics of problem p: condition estimate of the equilibrated Gram matrix
-// from the Cholesky diagonal (squared ratio of the extreme pivots), and
+// 2-norm condition number of A = L L^H (the equilibrated Gram matrix) by power
+// iterations on A and on A^{-1} (two triangular solves per step), FP64 on the host.
+double cond_estimate(const std::vector<double2> &L, int K)
+{
+    auto mulL = [&](const std::vector<double2> &x, bool herm) {   // L x or L^H x
+        std::vector<double2> y((size_t)K, make_double2(0, 0));
+        for (int i = 0; i < K; ++i)
+            for (int k = 0; k <= i; ++k) {
+                const double2 l = L[(size_t)i * K + k];
+                if (!herm) {
+                    y[i].x += l.x * x[k].x - l.y * x[k].y;
+                    y[i].y += l.x * x[k].y + l.y * x[k].x;
+                } else {
+                    y[k].x += l.x * x[i].x + l.y * x[i].y;
+                    y[k].y += l.x * x[i].y - l.y * x[i].x;
+                }
+            }
+        return y;
+    };
+    auto solveL = [&](std::vector<double2> b, bool herm) {   // L^{-1} b or L^{-H} b
+        if (!herm) {
+            for (int i = 0; i < K; ++i) {
+                double2 s = b[i];
+                for (int k = 0; k < i; ++k) {
+                    const double2 l = L[(size_t)i * K + k];
+                    s.x -= l.x * b[k].x - l.y * b[k].y;
+                    s.y -= l.x * b[k].y + l.y * b[k].x;
+                }
+                const double d = L[(size_t)i * K + i].x;
+                b[i] = make_double2(s.x / d, s.y / d);
+            }
+        } else {
+            for (int i = K - 1; i >= 0; --i) {
+                double2 s = b[i];
+                for (int k = i + 1; k < K; ++k) {
+                    const double2 l = L[(size_t)k * K + i];
+                    s.x -= l.x * b[k].x + l.y * b[k].y;
+                    s.y -= l.x * b[k].y - l.y * b[k].x;
+                }
+                const double d = L[(size_t)i * K + i].x;
+                b[i] = make_double2(s.x / d, s.y / d);
+            }
+        }
+        return b;
+    };
+    auto norm = [&](const std::vector<double2> &x) {
+        double s = 0;
+        for (const auto &v : x) s += v.x * v.x + v.y * v.y;
+        return std::sqrt(s);
+    };
+    auto power = [&](bool inverse) {
+        std::vector<double2> x((size_t)K);
+        for (int i = 0; i < K; ++i) x[i] = make_double2(1.0 + 0.01 * i, 0.003 * i);
+        double lam = 0;
+        for (int it = 0; it < 100; ++it) {
+            const double nx = norm(x);
+            for (auto &v : x) v = make_double2(v.x / nx, v.y / nx);
+            std::vector<double2> y = inverse ? solveL(solveL(x, false), true) : mulL(mulL(x, true), false);
+            lam = norm(y);
+            x = y;
+        }
+        return lam;
+    };
+    const double lmax = power(false), linv = power(true);
+    return lmax * linv;
+}
+
+// Statistics of problem p: 2-norm condition number of the equilibrated Gram
+// matrix (power iterations on its Cholesky factor), and
 // ||t - Psi h||^2 / ||t||^2 with the FP32 residual of the final coefficients
 // summed in FP64 on the device.
 dpd_status stats_of(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, double *stats, cudaStream_t s)
@@ -157,12 +224,7 @@ dpd_status stats_of(dpd_handle h, int p, const float2 *u, const float2 *t, int64
         cudaMemcpy(L.data(), w.L + (size_t)p * K * K, sizeof(double2) * K * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(nrm, w.norm_part + 2 * 1024, sizeof(nrm), cudaMemcpyDeviceToHost) != cudaSuccess)
         return DPD_ERR_CUDA;
-    double lmin = INFINITY, lmax = 0;
-    for (int i = 0; i < K; ++i) {
-        lmin = std::min(lmin, L[(size_t)i * K + i].x);
-        lmax = std::max(lmax, L[(size_t)i * K + i].x);
-    }
-    stats[0] = (lmax / lmin) * (lmax / lmin);
+    stats[0] = cond_estimate(L, K);
     stats[1] = nrm[1] > 0 ? nrm[0] / nrm[1] : 0.0;
     return DPD_OK;
 }

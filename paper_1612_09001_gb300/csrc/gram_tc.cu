@@ -93,28 +93,196 @@ __device__ __forceinline__ void stage_basis(const GramProblem &pr, int64_t n0, i
 }  // namespace
 
 // ------------------------------------------------------------------ tensor cores
-// The tensor core's FP32 accumulator drops low-order bits on every MMA step, a
-// bias that grows with the number of steps summed into one accumulator.  So
-// each accumulation covers a chunk of kChunk stages only: after a chunk, every
-// thread adds its share of the tensor-memory accumulators (one lane quarter,
-// 144 of the 288 columns) into FP32 registers with round-to-nearest, and the
-// next chunk starts from zero.  The next stage's basis is generated while the
-// tensor core finishes the chunk.
+// Operand generation.  Every real-form column of A is one of 15 "series" --
+// Re / Im of psi_b(u_j) for b < 6, Re / Im of t, or the constant 1 -- read at
+// row rr from element w = rr + off, off = T-1-k for the tap-k column and T-1
+// for the unshifted ones (element w of a stage is sample n0 - (T-1) + w).  So
+// each stage converts every basis value to its hi / lo pair once, into a
+// series array in shared memory, and an operand chunk (8 BF16 or 4 TF32 rows
+// of one column) is a few 32-bit shared loads and two 16-byte stores.  BF16
+// series are kept twice, as 16-bit arrays starting at element 0 and at
+// element 1, so a chunk at any offset reads whole aligned words.  The global
+// loads of the next stage are issued before the current stage is generated.
+//
+// Accumulation.  The tensor core's FP32 accumulator drops low-order bits on
+// every MMA step, a bias that grows with the number of steps summed into one
+// accumulator.  So each accumulation covers a chunk of kChunk stages only:
+// after a chunk, every thread adds its share of the tensor-memory
+// accumulators (one lane quarter, 144 of the 288 columns) into FP32
+// registers with round-to-nearest, and the next chunk starts from zero.
 constexpr int kChunk = 4;
 constexpr int kAccCols = 144;   // per thread: half of the 288 accumulator columns of a lane
+constexpr int kSeries = 15;     // 2 per basis order (6), 2 for t, 1 constant
+constexpr int kSerLen = 72;     // elements per series (>= 64 + kMaxT - 1, even)
+// Per series: BF16: hi, hi shifted by one, lo, lo shifted by one (16-bit each);
+// TF32: hi, lo (32-bit each).  Both 4 * kSerLen * 2 bytes.
+constexpr int kSerBytes = 4 * kSerLen * 2;
+constexpr int kStagingBytes = kSeries * kSerBytes;
+
+// Column map entry: series | off << 8 | flags << 16 (bit 0 negate, bit 1 zero column).
+__device__ __forceinline__ int column_map(int c, int K, int Bp, int T)
+{
+    const ColumnDecode d = decode_column(c, K, Bp, T);
+    int series, off = T - 1, flags = 0;
+    if (d.is_t) {
+        series = d.imag ? 13 : 12;
+    } else if (d.one) {
+        series = 14;
+        if (d.imag) flags |= 2;
+    } else {
+        series = 2 * d.b + (d.imag ? 1 : 0);
+        off = T - 1 - d.k;
+        if (d.imag && d.conj) flags |= 1;
+    }
+    return series | (off << 8) | (flags << 16);
+}
+
+struct Prefetch {
+    float2 u;     // basis sample, element w = tid (threads 0 .. kSerLen-1)
+    float2 t;     // target of row tid - 128 (threads 128 .. 128 + R - 1)
+    bool urow, trow;
+};
+
+template <int R>
+__device__ __forceinline__ Prefetch prefetch_stage(const GramProblem &pr, int64_t n0, int T)
+{
+    Prefetch f{};
+    const int tid = threadIdx.x;
+    if (tid < kSerLen) {
+        const int64_t j = n0 - (T - 1) + tid;
+        f.urow = tid < R + T - 1 && j >= 0 && j < pr.n;
+        if (f.urow) f.u = pr.u[j];
+    }
+    if (tid >= 128 && tid < 128 + R) {
+        const int64_t j = n0 + (tid - 128);
+        f.trow = j < pr.n;
+        if (f.trow && pr.t) f.t = pr.t[j];
+    }
+    return f;
+}
+
+template <int FMT>
+__device__ __forceinline__ void put_series(unsigned char *stg, int series, int w, float v)
+{
+    unsigned char *base = stg + series * kSerBytes;
+    if constexpr (FMT == kFmtBF16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        uint16_t *hi0 = reinterpret_cast<uint16_t *>(base);   // element i at i
+        uint16_t *hi1 = hi0 + kSerLen;                         // element i at i - 1
+        uint16_t *lo0 = hi0 + 2 * kSerLen;
+        uint16_t *lo1 = hi0 + 3 * kSerLen;
+        const uint16_t hb = *reinterpret_cast<const uint16_t *>(&h), lb = *reinterpret_cast<const uint16_t *>(&l);
+        hi0[w] = hb;
+        lo0[w] = lb;
+        if (w >= 1) {
+            hi1[w - 1] = hb;
+            lo1[w - 1] = lb;
+        }
+    } else {
+        uint32_t *hi = reinterpret_cast<uint32_t *>(base);
+        uint32_t *lo = hi + kSerLen;
+        const float h = to_tf32(v);
+        hi[w] = __float_as_uint(h);
+        lo[w] = __float_as_uint(to_tf32(v - h));
+    }
+}
+
+// Convert the prefetched samples of a stage into the series arrays.
+template <int FMT, int R>
+__device__ __forceinline__ void stage_series(unsigned char *stg, const Prefetch &f, int T, int B)
+{
+    const int tid = threadIdx.x;
+    if (tid < kSerLen) {
+        const float r = fmaf(f.u.x, f.u.x, f.u.y * f.u.y);
+        float p = 1.f;
+        for (int b = 0; b < B; ++b) {   // psi_b = |u|^{2b} u, low order first
+            put_series<FMT>(stg, 2 * b, tid, f.urow ? p * f.u.x : 0.f);
+            put_series<FMT>(stg, 2 * b + 1, tid, f.urow ? p * f.u.y : 0.f);
+            p *= r;
+        }
+    }
+    if (tid >= 128 && tid < 128 + R) {
+        const int w = tid - 128 + (T - 1);
+        put_series<FMT>(stg, 12, w, f.trow ? f.t.x : 0.f);
+        put_series<FMT>(stg, 13, w, f.trow ? f.t.y : 0.f);
+        put_series<FMT>(stg, 14, w, f.trow ? 1.f : 0.f);
+    }
+}
+
+// One 16-byte chunk (rows ch*EPC .. +EPC) of real-form column c, hi and lo.
+template <int FMT>
+__device__ __forceinline__ void make_chunk(const unsigned char *stg, int cm, int ch, int nvalid, uint4 &H, uint4 &L)
+{
+    const int series = cm & 0xFF, off = (cm >> 8) & 0xFF, flags = cm >> 16;
+    const unsigned char *base = stg + series * kSerBytes;
+    uint32_t h[4], l[4];
+    if constexpr (FMT == kFmtBF16) {
+        const int o = ch * 8 + off;
+        const uint32_t *hw = reinterpret_cast<const uint32_t *>(base) + ((o & 1) ? kSerLen / 2 + (o - 1) / 2 : o / 2);
+        const uint32_t *lw = hw + kSerLen;   // lo arrays follow the two hi arrays
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h[q] = hw[q];
+            l[q] = lw[q];
+        }
+        if (flags & 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                h[q] ^= 0x80008000u;
+                l[q] ^= 0x80008000u;
+            }
+        }
+        if (nvalid < 64) {   // last stage of the problem: rows past the end are zero
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r0 = ch * 8 + 2 * q;
+                const uint32_t m = (r0 < nvalid ? 0x0000FFFFu : 0u) | (r0 + 1 < nvalid ? 0xFFFF0000u : 0u);
+                h[q] &= m;
+                l[q] &= m;
+            }
+        }
+    } else {
+        const int o = ch * 4 + off;
+        const uint32_t *hw = reinterpret_cast<const uint32_t *>(base) + o;
+        const uint32_t *lw = hw + kSerLen;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h[q] = hw[q];
+            l[q] = lw[q];
+        }
+        if (flags & 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                h[q] ^= 0x80000000u;
+                l[q] ^= 0x80000000u;
+            }
+        }
+        if (nvalid < 32) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (ch * 4 + q >= nvalid) h[q] = l[q] = 0u;
+        }
+    }
+    if (flags & 2) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h[q] = l[q] = 0u;
+    }
+    H = make_uint4(h[0], h[1], h[2], h[3]);
+    L = make_uint4(l[0], l[1], l[2], l[3]);
+}
 
 template <int FMT>
 __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
 {
     constexpr int R = (FMT == kFmtBF16) ? 64 : 32;    // rows per stage: 128 bytes per operand row
-    constexpr int EPC = (FMT == kFmtBF16) ? 8 : 4;    // elements per 16-byte chunk
     constexpr int NK = 4;                             // MMAs along K per stage (K = 16 bf16 / 8 tf32)
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *stages = smem;
-    float2 *psi = reinterpret_cast<float2 *>(smem + kStages * kStageBytes);
-    float2 *tv = psi + kMaxB * kPsiStride;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tv + 64);   // stage_done[kStages], chunk_done
+    unsigned char *staging = smem + kStages * kStageBytes;              // 2 x kStagingBytes
+    int *colmap = reinterpret_cast<int *>(staging + 2 * kStagingBytes);  // [256]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(colmap + 256);         // stage_done[kStages], chunk_done
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kStages + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -132,6 +300,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
 
     for (int i = tid; i < kStages * kStageBytes / 16; i += kGramThreads)
         reinterpret_cast<uint4 *>(stages)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int c = tid; c < 256; c += kGramThreads) colmap[c] = c < C ? column_map(c, K, a.Bp, T) : 0;
     if (tid == 0) {
         for (int s = 0; s <= kStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
         fence_barrier_init();
@@ -140,6 +309,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
         tmem_alloc(smem_addr(tmem_slot), 512);
         tmem_relinquish();
     }
+    if (nits > 0) stage_series<FMT, R>(staging, prefetch_stage<R>(pr, b0 * R, T), T, B);
     fence_async_shared();
     tc_fence_before_sync();
     __syncthreads();
@@ -182,41 +352,23 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
             failed = true;
             break;
         }
+        const int64_t n0 = (b0 + it) * R;
+        Prefetch nxt{};
+        if (it + 1 < nits) nxt = prefetch_stage<R>(pr, n0 + R, T);   // in flight during generation
+        const unsigned char *stg = staging + (it & 1) * kStagingBytes;
         unsigned char *hi = stages + s * kStageBytes;
         unsigned char *lo = hi + kBuf;
-        const int64_t n0 = (b0 + it) * R;
-        stage_basis<R>(pr, n0, T, B, psi, tv);
-        __syncthreads();
+        const int64_t rem = pr.n - n0;
+        const int nvalid = rem < R ? (int)rem : R;
         for (int task = tid; task < C * 8; task += kGramThreads) {
             const int c = task >> 3, ch = task & 7;
-            const ColumnDecode d = decode_column(c, K, a.Bp, T);
-            uint32_t hw[4], lw[4];
-            if constexpr (FMT == kFmtBF16) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int r0 = ch * EPC + 2 * q;
-                    const float v0 = column_value(d, psi, tv, r0, T, n0 + r0 < pr.n);
-                    const float v1 = column_value(d, psi, tv, r0 + 1, T, n0 + r0 + 1 < pr.n);
-                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-                    const float2 hf = __bfloat1622float2(h2);
-                    const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-                    hw[q] = *reinterpret_cast<const uint32_t *>(&h2);
-                    lw[q] = *reinterpret_cast<const uint32_t *>(&l2);
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int r0 = ch * EPC + q;
-                    const float v = column_value(d, psi, tv, r0, T, n0 + r0 < pr.n);
-                    const float h = to_tf32(v);
-                    hw[q] = __float_as_uint(h);
-                    lw[q] = __float_as_uint(to_tf32(v - h));
-                }
-            }
+            uint4 H, L;
+            make_chunk<FMT>(stg, colmap[c], ch, nvalid, H, L);
             const uint32_t off = sw128_offset(c, ch);
-            *reinterpret_cast<uint4 *>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4 *>(lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            *reinterpret_cast<uint4 *>(hi + off) = H;
+            *reinterpret_cast<uint4 *>(lo + off) = L;
         }
+        if (it + 1 < nits) stage_series<FMT, R>(staging + ((it + 1) & 1) * kStagingBytes, nxt, T, B);
         fence_async_shared();
         tc_fence_before_sync();
         __syncthreads();
@@ -291,7 +443,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
     }
 }
 
-size_t gram_tc_smem() { return 1024 + (size_t)kStages * kStageBytes + (kMaxB * kPsiStride + 64) * 8 + 64; }
+size_t gram_tc_smem() { return 1024 + (size_t)kStages * kStageBytes + 2 * (size_t)kStagingBytes + 256 * 4 + 64; }
 
 // ------------------------------------------------------------------ FP32 CUDA cores
 // Each CTA stages 64 rows of A (row-major, 256 padded columns, FP32) in shared
