@@ -99,17 +99,28 @@ dpd_status dpd_set_coeffs(dpd_handle h, const void *coeffs, int K, int where, vo
  */
 dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stream);
 
+/* Modes of dpd_apply_host. */
+enum { DPD_HOST_PIPELINED = 0, DPD_HOST_ZERO_COPY = 1 };
+
 /*
- * dpd_apply on buffers in host memory, read and written by the kernel in place
- * over the CPU-GPU link (zero copy, the technique of Sec. 3.3.1: no staging
- * copies, no device buffers).  x and y may be pinned or registered host memory
- * (cudaHostAlloc / cudaHostRegister), managed memory, or -- on systems whose
- * GPU can access pageable memory, such as Grace-Blackwell -- ordinary
- * malloc'd memory.  Device memory is rejected (use dpd_apply).  8-byte
- * alignment, no overlap, n >= 0.  Asynchronous on `stream`: the buffers must
- * stay valid, and y must not be read, until the stream has reached this work.
+ * dpd_apply on buffers in host memory (x, y: n complex64 each, 8-byte aligned,
+ * not overlapping; pinned / registered, managed, or -- where the GPU can access
+ * it, as on Grace-Blackwell -- ordinary pageable memory; device memory is
+ * rejected, use dpd_apply).
+ *   DPD_HOST_PIPELINED : the input is cut into chunks of 2^21 samples; each
+ *       chunk (with 8 samples of history in front) is copied to the device,
+ *       filtered and copied back on one of three internal streams in turn, so
+ *       copies in both directions overlap the kernels (the multi-stream
+ *       alternative of Sec. 3.4).  The first call allocates the staging buffers
+ *       (3 x 2 x 16 MB) and streams; pinned buffers make the copies
+ *       asynchronous.
+ *   DPD_HOST_ZERO_COPY : the kernel reads and writes the host buffers in place
+ *       over the CPU-GPU link, without staging (Sec. 3.3.1).
+ * Ordered after earlier work on `stream`; returns without synchronising, and
+ * `stream` is ordered after the last chunk: synchronise it before reading y.
+ * Not capturable in a CUDA graph.
  */
-dpd_status dpd_apply_host(dpd_handle h, const void *x, void *y, int64_t n, void *stream);
+dpd_status dpd_apply_host(dpd_handle h, const void *x, void *y, int64_t n, int mode, void *stream);
 
 /*
  * Coefficient gradient without any device allocation.  (Not in the paper; a

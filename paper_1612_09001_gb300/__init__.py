@@ -200,9 +200,10 @@ class DPD:
     def set_adj_launch(self, gh_blocks, tap_group):
         _lib.check("dpd_set_adj_launch", self._lib.dpd_set_adj_launch(self._h, gh_blocks, tap_group))
 
-    def apply_host(self, x, out=None, stream=None):
-        """y = DPD(x) for complex64 tensors in (pinned) host memory, read and written in place
-        by the kernel (zero copy).  Asynchronous: synchronise the stream before reading out."""
+    def apply_host(self, x, out=None, stream=None, zero_copy=False):
+        """y = DPD(x) for complex64 tensors in (pinned) host memory: chunked copy / compute
+        pipeline, or zero copy (the kernel reads and writes the host buffers in place).
+        Asynchronous: synchronise the stream before reading out."""
         import torch
         if not isinstance(x, torch.Tensor) or x.dtype != torch.complex64 or x.is_cuda or not x.is_contiguous():
             raise ValueError("x must be a contiguous complex64 host tensor")
@@ -212,7 +213,7 @@ class DPD:
             raise ValueError("out must be a contiguous complex64 host tensor like x")
         _lib.check("dpd_apply_host", self._lib.dpd_apply_host(
             self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.numel(),
-            _stream_ptr(stream)))
+            _lib.DPD_HOST_ZERO_COPY if zero_copy else _lib.DPD_HOST_PIPELINED, _stream_ptr(stream)))
         return out
 
     def set_fwd_launch(self, V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1, mode=0):

@@ -1,5 +1,6 @@
 // libdpd C ABI: handle management, argument checks and kernel dispatch.
 // Declarations and the contract of every entry point are in include/dpd.h.
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cstring>
@@ -137,6 +138,7 @@ dpd_status dpd_destroy(dpd_handle h)
     cudaFree(h->d_partials);
     cudaFree(h->d_status);
     free_estimate_workspace(h->est);
+    free_host_pipeline(h->host);
     delete h;
     return DPD_OK;
 }
@@ -252,15 +254,54 @@ dpd_status dpd_grad(dpd_handle h, const void *x, const void *gy, int64_t n, void
     return DPD_OK;
 }
 
-dpd_status dpd_apply_host(dpd_handle h, const void *x, void *y, int64_t n, void *stream)
+namespace {
+
+// Host pointer kinds: 0 pinned / registered / managed (device-accessible), 1 pageable, -1 device or error.
+int host_kind(const void *p, void **dev)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeManaged) {
+        *dev = at.devicePointer;
+        return at.devicePointer ? 0 : -1;
+    }
+    if (at.type == cudaMemoryTypeUnregistered) {
+        *dev = const_cast<void *>(p);
+        return 1;
+    }
+    return -1;
+}
+
+dpd_status apply_zero_copy(dpd_handle h, const void *x, void *y, int64_t n, cudaStream_t stream);
+dpd_status apply_pipelined(dpd_handle h, const void *x, void *y, int64_t n, cudaStream_t stream);
+
+}  // namespace
+
+dpd_status dpd_apply_host(dpd_handle h, const void *x, void *y, int64_t n, int mode, void *stream)
 {
     if (!h || n < 0) return DPD_ERR_INVALID_ARGUMENT;
+    if (mode != DPD_HOST_PIPELINED && mode != DPD_HOST_ZERO_COPY) return DPD_ERR_INVALID_ARGUMENT;
     if (!h->has_coeffs) return DPD_ERR_NO_COEFFS;
     if (n == 0) return DPD_OK;
     if (!x || !y || !aligned(x, 8) || !aligned(y, 8)) return DPD_ERR_INVALID_ARGUMENT;
     if (n > (int64_t)(INT64_MAX / sizeof(float2))) return DPD_ERR_INVALID_ARGUMENT;
     const size_t bytes = (size_t)n * sizeof(float2);
     if (overlap(x, bytes, y, bytes)) return DPD_ERR_INVALID_ARGUMENT;
+    void *dx = nullptr, *dy = nullptr;
+    const int kx = host_kind(x, &dx), ky = host_kind(y, &dy);
+    if (kx < 0 || ky < 0) return DPD_ERR_INVALID_ARGUMENT;   // device memory: use dpd_apply
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (mode == DPD_HOST_ZERO_COPY) return apply_zero_copy(h, x, y, n, s);
+    return apply_pipelined(h, x, y, n, s);
+}
+
+namespace {
+
+dpd_status apply_zero_copy(dpd_handle h, const void *x, void *y, int64_t n, cudaStream_t stream)
+{
     // Resolve each buffer to an address the kernel can dereference.
     const void *ptrs[2] = {x, y};
     void *dev[2] = {nullptr, nullptr};
@@ -294,7 +335,90 @@ dpd_status dpd_apply_host(dpd_handle h, const void *x, void *y, int64_t n, void 
     L.use_tma = 0;   // plain loads and stores straight to host memory
     L.V = 4;
     L.mode &= dpd::kModePackedFma | (h->host_tab_valid ? dpd::kModeParamCoef : 0);
-    return cuda_status(dpd::launch_fwd_any(h->B, h->T, a, L, h->sm_count, static_cast<cudaStream_t>(stream)));
+    return cuda_status(dpd::launch_fwd_any(h->B, h->T, a, L, h->sm_count, stream));
+}
+
+constexpr int64_t kHostChunk = (int64_t)1 << 21;
+
+dpd_status ensure_pipeline(dpd_handle h)
+{
+    HostPipeline &P = h->host;
+    if (P.chunk) return DPD_OK;
+    for (int i = 0; i < kHostSlots; ++i) {
+        if (cudaMalloc(&P.in[i], sizeof(float2) * (kHostChunk + dpd::kHalo)) != cudaSuccess ||
+            cudaMalloc(&P.out[i], sizeof(float2) * (kHostChunk + dpd::kHalo)) != cudaSuccess) {
+            free_host_pipeline(P);
+            return DPD_ERR_ALLOC;
+        }
+        if (cudaStreamCreateWithFlags(&P.streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P.done[i], cudaEventDisableTiming) != cudaSuccess) {
+            free_host_pipeline(P);
+            return DPD_ERR_CUDA;
+        }
+    }
+    if (cudaEventCreateWithFlags(&P.start, cudaEventDisableTiming) != cudaSuccess) {
+        free_host_pipeline(P);
+        return DPD_ERR_CUDA;
+    }
+    P.chunk = kHostChunk;
+    return DPD_OK;
+}
+
+// Chunks of the input are copied in (with kHalo samples of history), filtered
+// and copied out on kHostSlots streams in turn, so host-to-device copies,
+// kernels and device-to-host copies of different chunks overlap.  Ordered
+// after `stream`'s earlier work; `stream` waits for every chunk at the end.
+dpd_status apply_pipelined(dpd_handle h, const void *x, void *y, int64_t n, cudaStream_t stream)
+{
+    dpd_status st = ensure_pipeline(h);
+    if (st != DPD_OK) return st;
+    HostPipeline &P = h->host;
+    if (cudaEventRecord(P.start, stream) != cudaSuccess) return DPD_ERR_CUDA;
+    for (int i = 0; i < kHostSlots; ++i)
+        if (cudaStreamWaitEvent(P.streams[i], P.start, 0) != cudaSuccess) return DPD_ERR_CUDA;
+    const float2 *xs = static_cast<const float2 *>(x);
+    float2 *ys = static_cast<float2 *>(y);
+    const int64_t nchunks = (n + P.chunk - 1) / P.chunk;
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int slot = (int)(c % kHostSlots);
+        cudaStream_t s = P.streams[slot];
+        const int64_t c0 = c * P.chunk, len = std::min(P.chunk, n - c0);
+        const int64_t hs = std::min<int64_t>(c0, dpd::kHalo);   // history samples copied in front
+        if (cudaMemcpyAsync(P.in[slot], xs + c0 - hs, sizeof(float2) * (hs + len), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return DPD_ERR_CUDA;
+        dpd::FwdArgs a;
+        a.x = P.in[slot];
+        a.y = P.out[slot];
+        a.n = hs + len;
+        a.tab = h->d_tab;
+        a.status = h->d_status;
+        a.vec_store = 1;
+        a.host_tab = h->host_tab_valid ? &h->h_tab : nullptr;
+        dpd::FwdLaunch L = h->fwd;
+        if (!h->host_tab_valid) L.mode &= ~dpd::kModeParamCoef;
+        if (dpd::launch_fwd_any(h->B, h->T, a, L, h->sm_count, s) != cudaSuccess) return DPD_ERR_CUDA;
+        if (cudaMemcpyAsync(ys + c0, P.out[slot] + hs, sizeof(float2) * len, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return DPD_ERR_CUDA;
+    }
+    for (int i = 0; i < kHostSlots; ++i)
+        if (cudaEventRecord(P.done[i], P.streams[i]) != cudaSuccess || cudaStreamWaitEvent(stream, P.done[i], 0) != cudaSuccess)
+            return DPD_ERR_CUDA;
+    return DPD_OK;
+}
+
+}  // namespace
+
+extern "C++" void free_host_pipeline(HostPipeline &P)
+{
+    for (int i = 0; i < kHostSlots; ++i) {
+        cudaFree(P.in[i]);
+        cudaFree(P.out[i]);
+        if (P.streams[i]) cudaStreamDestroy(P.streams[i]);
+        if (P.done[i]) cudaEventDestroy(P.done[i]);
+    }
+    if (P.start) cudaEventDestroy(P.start);
+    P = HostPipeline();
 }
 
 dpd_status dpd_set_adj_launch(dpd_handle h, int gh_blocks, int tap_group)

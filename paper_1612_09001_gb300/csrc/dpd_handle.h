@@ -25,6 +25,17 @@ struct EstimateWorkspace {
     double *norm_part = nullptr;  // 2 * 1024 partial sums + 2 results
 };
 
+// Device staging of dpd_apply_host's copy / compute pipeline, created on first use.
+constexpr int kHostSlots = 3;
+struct HostPipeline {
+    int64_t chunk = 0;                         // samples per chunk (capacity excludes the history)
+    float2 *in[kHostSlots] = {};
+    float2 *out[kHostSlots] = {};
+    cudaStream_t streams[kHostSlots] = {};
+    cudaEvent_t done[kHostSlots] = {};
+    cudaEvent_t start = nullptr;
+};
+
 struct dpd_filter {
     int P, Q, M;
     int Bp, Bq, B, T, K;
@@ -42,7 +53,9 @@ struct dpd_filter {
     dpd::FwdLaunch fwd;
     dpd::AdjLaunch adj;
     EstimateWorkspace est;
+    HostPipeline host;
 };
 
 void free_estimate_workspace(EstimateWorkspace &w);
+void free_host_pipeline(HostPipeline &p);
 

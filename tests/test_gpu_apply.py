@@ -196,33 +196,37 @@ def test_device_coefficients_and_graph_replay():
     f.sync_status()
 
 
-@pytest.mark.parametrize("P,Q,M", [(9, 9, 4), (5, 3, 4), (11, 11, 7)])
-def test_apply_host_zero_copy(P, Q, M):
-    """The kernel reads and writes pinned host buffers in place (Sec. 3.3.1 zero copy)."""
-    n = 300007
-    x = synth.ofdm2(n, key=(9, P))
+@pytest.mark.parametrize("zero_copy", [False, True])
+@pytest.mark.parametrize("P,Q,M,n", [(9, 9, 4, 300007), (5, 3, 4, 2 * (1 << 21) + 12345), (11, 11, 7, (1 << 21) + 1),
+                                     (7, 0, 3, 5)])
+def test_apply_host(P, Q, M, n, zero_copy):
+    """Host buffers: chunked copy / compute pipeline (chunks of 2^21 samples with
+    history), or zero copy (the kernel reads and writes pinned host memory)."""
+    x = synth.ofdm2(n, key=(9, P, n % 97))
     h = synth.coeffs(P, Q, M, key=(9, 1))
     f = dpd.DPD(P, Q, M)
     f.set_coeffs(h)
     xh = torch.from_numpy(x).pin_memory()
     yh = torch.full((n,), complex(7, 7), dtype=torch.complex64).pin_memory()
-    f.apply_host(xh, out=yh)
+    f.apply_host(xh, out=yh, zero_copy=zero_copy)
     f.sync_status()
     ref = oracle.apply(x, h, P, Q, M)
-    assert_parity(yh.numpy(), ref, what="zero copy pinned")
+    assert_parity(yh.numpy(), ref, what=f"host path zero_copy={zero_copy}")
     # device memory is refused by the host entry point
     lib = _lib.load()
     xd = torch.from_numpy(x).cuda()
     yd = torch.empty_like(xd)
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    assert lib.dpd_apply_host(f.handle, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()), n, s) == 1
-    # ordinary pageable memory works where the GPU can access it, else it is refused
+    assert lib.dpd_apply_host(f.handle, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()), n,
+                              int(zero_copy), s) == 1
+    assert lib.dpd_apply_host(f.handle, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(yh.data_ptr()), n, 7, s) == 1
+    # ordinary pageable memory: copies work anywhere; zero copy where the GPU can access it, else refused
     xp = torch.from_numpy(x.copy())
     yp = torch.empty_like(xp)
     try:
-        f.apply_host(xp, out=yp)
+        f.apply_host(xp, out=yp, zero_copy=zero_copy)
         f.sync_status()
-        assert_parity(yp.numpy(), ref, what="zero copy pageable")
+        assert_parity(yp.numpy(), ref, what="host path pageable")
     except dpd.DPDError as e:
-        assert e.code == 1
+        assert zero_copy and e.code == 1
     f.close()
