@@ -242,6 +242,8 @@ def measure_batched(dev, reps=20):
         handles.append(f)
     total = sum(len(sp["x"]) for sp in specs)
     plan = dpd.BatchedPlan(streams)
+    from paper_1612_09001_gb300 import tune
+    best, _ = tune.tune_batched(plan)          # tile / stage / grid picked by timing, before the timed region
     l0 = dpd.kernel_launches()
     t_plan = _time_graph(lambda: plan.execute(), reps, dev)
     launches_plan = (dpd.kernel_launches() - l0) // 2   # captured twice (warm-up + capture)
@@ -270,6 +272,7 @@ def measure_batched(dev, reps=20):
     return {"workload": "64 streams, n ~ U[2^12, 2^20], P=Q in {5,7,9}, M in {2..6}, clipped Gaussian RMS 0.3",
             "total_samples": total, "unit": "Gsamples/s",
             "persistent_graph": total / t_plan / 1e9, "persistent_launches_per_step": launches_plan,
+            "persistent_launch_shape": {"V": best[0], "warps": best[1], "stages": best[2], "ctas_per_sm": best[3]},
             "plain_64_launches": total / t_plain / 1e9, "plain_64_in_one_graph": total / t_graph64 / 1e9,
             "persistent_us": t_plan * 1e6, "plain_64_us": t_plain * 1e6, "plain_64_graph_us": t_graph64 * 1e6,
             "hbm_frac_persistent": 16 * total / t_plan / 1e9}
