@@ -109,9 +109,12 @@ __device__ __forceinline__ void stage_basis(const GramProblem &pr, int64_t n0, i
 // accumulator.  So each accumulation covers a chunk of kChunk stages only:
 // after a chunk, every thread adds its share of the tensor-memory
 // accumulators (one lane quarter, 144 of the 288 columns) into FP32
-// registers with round-to-nearest, and the next chunk starts from zero.
+// sums with round-to-nearest (D0 in registers, D1 in shared memory), and the
+// next chunk starts from zero.
 constexpr int kChunk = 4;
-constexpr int kAccCols = 144;   // per thread: half of the 288 accumulator columns of a lane
+constexpr int kAccCols = 104;   // per generator thread: half of D0's 208 columns of its lane
+constexpr int kD1Cols = 80;     // D1 running sums in shared memory: 128 lanes x 80 columns
+constexpr int kD1Half = 40;
 constexpr int kSeries = 15;     // 2 per basis order (6), 2 for t, 1 constant
 constexpr int kSerLen = 72;     // elements per series (>= 64 + kMaxT - 1, even)
 // Per series: BF16: hi, hi shifted by one, lo, lo shifted by one (16-bit each);
@@ -272,8 +275,26 @@ __device__ __forceinline__ void make_chunk(const unsigned char *stg, int cm, int
     L = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// Named barrier 1 over the eight generator warps, with an OR vote of `pred`.
+__device__ __forceinline__ bool gen_sync_or(bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred)
+        : "memory");
+    return r != 0;
+}
+
+// Warp roles: warps 0-7 generate operands and own the FP32 running sums;
+// warp 8 (lane 0) issues the MMAs.  Barriers: full[s] (8 generator arrivals:
+// stage s written), empty[s] (MMA commit: stage s consumed), chunk_done (MMA
+// commit after a chunk's last stage), tmem_free (8 generator arrivals: the
+// chunk has been drained from tensor memory).
 template <int FMT>
-__global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
+__global__ void __launch_bounds__(kGramThreads + 32, 1) gram_tc_kernel(GramArgs a)
 {
     constexpr int R = (FMT == kFmtBF16) ? 64 : 32;    // rows per stage: 128 bytes per operand row
     constexpr int NK = 4;                             // MMAs along K per stage (K = 16 bf16 / 8 tf32)
@@ -282,168 +303,212 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(GramArgs a)
     unsigned char *stages = smem;
     unsigned char *staging = smem + kStages * kStageBytes;              // 2 x kStagingBytes
     int *colmap = reinterpret_cast<int *>(staging + 2 * kStagingBytes);  // [256]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(colmap + 256);         // stage_done[kStages], chunk_done
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kStages + 1);
+    float *d1sum = reinterpret_cast<float *>(colmap + 256);               // [128][kD1Cols]
+    uint64_t *full = reinterpret_cast<uint64_t *>(d1sum + 128 * kD1Cols);
+    uint64_t *empty = full + kStages;
+    uint64_t *chunk_done = empty + kStages;
+    uint64_t *tmem_free = chunk_done + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_free + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;
     const int prob = blockIdx.x / a.cpp, chunk = blockIdx.x % a.cpp;
     const GramProblem pr = a.probs[prob];
     const int K = a.K, C = 2 * K + 2, T = a.T, B = a.Bp > a.Bq ? a.Bp : a.Bq;
     const bool two = C > 128;
     const int N0 = ((C + 15) / 16) * 16;
     const int N1 = two ? N0 - 128 : 0;
-    const int used_cols = N0 + N1;   // tensor-memory columns holding D0 then D1
     const int64_t nblk = (pr.n + R - 1) / R;
     const int64_t b0 = nblk * chunk / a.cpp, b1 = nblk * (chunk + 1) / a.cpp;
     const int nits = (int)(b1 - b0);
+    const int nchunks = (nits + kChunk - 1) / kChunk;
 
-    for (int i = tid; i < kStages * kStageBytes / 16; i += kGramThreads)
+    for (int i = tid; i < kStages * kStageBytes / 16; i += blockDim.x)
         reinterpret_cast<uint4 *>(stages)[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int c = tid; c < 256; c += kGramThreads) colmap[c] = c < C ? column_map(c, K, a.Bp, T) : 0;
+    for (int c = tid; c < 256; c += blockDim.x) colmap[c] = c < C ? column_map(c, K, a.Bp, T) : 0;
+    for (int i = tid; i < 128 * kD1Cols; i += blockDim.x) d1sum[i] = 0.f;
     if (tid == 0) {
-        for (int s = 0; s <= kStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_addr(&full[s]), 8);
+            mbar_init(smem_addr(&empty[s]), 1);
+        }
+        mbar_init(smem_addr(chunk_done), 1);
+        mbar_init(smem_addr(tmem_free), 8);
         fence_barrier_init();
     }
-    if (warp == 0) {
+    if (warp == 8) {
         tmem_alloc(smem_addr(tmem_slot), 512);
         tmem_relinquish();
     }
-    if (nits > 0) stage_series<FMT, R>(staging, prefetch_stage<R>(pr, b0 * R, T), T, B);
+    if (nits > 0 && warp < 8) stage_series<FMT, R>(staging, prefetch_stage<R>(pr, b0 * R, T), T, B);
     fence_async_shared();
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc0 = umma_idesc(FMT, 128, N0);
-    const uint32_t idesc1 = two ? umma_idesc(FMT, 128, N1) : 0u;
-    const uint32_t my_taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(half * kAccCols);
-
-    float acc[kAccCols];
-#pragma unroll
-    for (int i = 0; i < kAccCols; ++i) acc[i] = 0.f;
-
-    // Add the finished chunk's accumulators (this thread's lane and columns) into acc.
-    auto drain = [&](int c) -> bool {
-        const bool ok = mbar_wait(smem_addr(&bars[kStages]), (uint32_t)(c & 1), a.status);
-        tc_fence_after_sync();
-        if (ok) {
-#pragma unroll
-            for (int cc = 0; cc < kAccCols / 16; ++cc) {
-                if (half * kAccCols + cc * 16 < used_cols) {
-                    float v[16];
-                    tmem_ld16(my_taddr + (uint32_t)(cc * 16), v);
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) acc[cc * 16 + q] += v[q];
-                }
-            }
-        }
-        tc_fence_before_sync();
-        return ok;
-    };
 
     bool failed = false;
-    int chunk_commits = 0;   // issuing thread only
-    for (int it = 0; it < nits; ++it) {
-        const int s = it % kStages;
-        bool ok = true;
-        if (it >= kStages) ok = mbar_wait(smem_addr(&bars[s]), (uint32_t)(((it / kStages) - 1) & 1), a.status);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
+    if (warp == 8) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc0 = umma_idesc(FMT, 128, N0);
+            const uint32_t idesc1 = two ? umma_idesc(FMT, 128, N1) : 0u;
+            int commits = 0;
+            bool issued_all = true;
+            for (int it = 0; it < nits; ++it) {
+                const int s = it % kStages;
+                if (!mbar_wait(smem_addr(&full[s]), (uint32_t)((it / kStages) & 1), a.status)) {
+                    issued_all = false;
+                    break;
+                }
+                if (it > 0 && it % kChunk == 0 &&
+                    !mbar_wait(smem_addr(tmem_free), (uint32_t)((it / kChunk - 1) & 1), a.status)) {
+                    issued_all = false;
+                    break;
+                }
+                tc_fence_after_sync();
+                const uint32_t hb = smem_addr(stages + s * kStageBytes), lb = hb + kBuf;
+                const uint32_t pa[3] = {hb, hb, lb}, pb[3] = {hb, lb, hb};   // hi*hi + hi*lo + lo*hi
+                uint32_t accumulate = (it % kChunk == 0) ? 0u : 1u;
+#pragma unroll
+                for (int kk = 0; kk < NK; ++kk) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const uint32_t ka = pa[q] + kk * 32, kb = pb[q] + kk * 32;
+                        if constexpr (FMT == kFmtBF16) {
+                            umma_bf16(tmem, umma_desc_sw128(ka), umma_desc_sw128(kb), idesc0, accumulate);
+                            if (two)
+                                umma_bf16(tmem + (uint32_t)N0, umma_desc_sw128(ka + kTile),
+                                          umma_desc_sw128(kb + kTile), idesc1, accumulate);
+                        } else {
+                            umma_tf32(tmem, umma_desc_sw128(ka), umma_desc_sw128(kb), idesc0, accumulate);
+                            if (two)
+                                umma_tf32(tmem + (uint32_t)N0, umma_desc_sw128(ka + kTile),
+                                          umma_desc_sw128(kb + kTile), idesc1, accumulate);
+                        }
+                        accumulate = 1;
+                    }
+                }
+                umma_commit(smem_addr(&empty[s]));
+                if ((it + 1) % kChunk == 0 || it + 1 == nits) {
+                    umma_commit(smem_addr(chunk_done));
+                    ++commits;
+                }
+            }
+            // Every MMA issued must be complete before tensor memory is released.
+            // Normally the last chunk's commit covers them all (the generators
+            // wait on that same phase).  After a failure, commit once more and
+            // wait for that phase.
+            if (issued_all) {
+                if (nits > 0) mbar_wait(smem_addr(chunk_done), (uint32_t)((commits - 1) & 1), a.status);
+            } else {
+                umma_commit(smem_addr(chunk_done));
+                mbar_wait(smem_addr(chunk_done), (uint32_t)(commits & 1), a.status);
+            }
         }
-        const int64_t n0 = (b0 + it) * R;
-        Prefetch nxt{};
-        if (it + 1 < nits) nxt = prefetch_stage<R>(pr, n0 + R, T);   // in flight during generation
-        const unsigned char *stg = staging + (it & 1) * kStagingBytes;
-        unsigned char *hi = stages + s * kStageBytes;
-        unsigned char *lo = hi + kBuf;
-        const int64_t rem = pr.n - n0;
-        const int nvalid = rem < R ? (int)rem : R;
-        for (int task = tid; task < C * 8; task += kGramThreads) {
-            const int c = task >> 3, ch = task & 7;
-            uint4 H, L;
-            make_chunk<FMT>(stg, colmap[c], ch, nvalid, H, L);
-            const uint32_t off = sw128_offset(c, ch);
-            *reinterpret_cast<uint4 *>(hi + off) = H;
-            *reinterpret_cast<uint4 *>(lo + off) = L;
-        }
-        if (it + 1 < nits) stage_series<FMT, R>(staging + ((it + 1) & 1) * kStagingBytes, nxt, T, B);
-        fence_async_shared();
-        tc_fence_before_sync();
-        __syncthreads();
-        if (it > 0 && it % kChunk == 0) {   // previous chunk: drain before it is overwritten
-            const bool okd = drain(it / kChunk - 1);
-            if (__syncthreads_or(!okd)) {
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ generators
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = 32 * quarter + lane;   // tensor-memory lane
+        const uint32_t lane_taddr = tmem + ((uint32_t)(32 * quarter) << 16);
+        float acc[kAccCols];
+#pragma unroll
+        for (int i = 0; i < kAccCols; ++i) acc[i] = 0.f;
+
+        auto drain = [&](int c) -> bool {
+            const bool ok = mbar_wait(smem_addr(chunk_done), (uint32_t)(c & 1), a.status);
+            tc_fence_after_sync();
+            if (ok) {
+#pragma unroll
+                for (int cc = 0; cc < kAccCols / 8; ++cc) {
+                    if (half * kAccCols + cc * 8 < N0) {
+                        float v[8];
+                        tmem_ld8(lane_taddr + (uint32_t)(half * kAccCols + cc * 8), v);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) acc[cc * 8 + q] += v[q];
+                    }
+                }
+                if (two) {
+                    float *d1row = d1sum + row * kD1Cols + half * kD1Half;
+#pragma unroll
+                    for (int cc = 0; cc < kD1Half / 8; ++cc) {
+                        if (half * kD1Half + cc * 8 < N1) {
+                            float v[8];
+                            tmem_ld8(lane_taddr + (uint32_t)(N0 + half * kD1Half + cc * 8), v);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) d1row[cc * 8 + q] += v[q];
+                        }
+                    }
+                }
+            }
+            tc_fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(tmem_free));
+            return ok;
+        };
+
+        for (int it = 0; it < nits; ++it) {
+            const int s = it % kStages;
+            bool ok = true;
+            if (it >= kStages) ok = mbar_wait(smem_addr(&empty[s]), (uint32_t)(((it / kStages) - 1) & 1), a.status);
+            if (gen_sync_or(!ok)) {   // also: every generator finished the previous stage
                 failed = true;
                 break;
             }
-        }
-        if (tid == 0) {
-            tc_fence_after_sync();
-            const uint32_t hb = smem_addr(hi), lb = smem_addr(lo);
-            const uint32_t pa[3] = {hb, hb, lb}, pb[3] = {hb, lb, hb};   // hi*hi + hi*lo + lo*hi
-            uint32_t accumulate = (it % kChunk == 0) ? 0u : 1u;
-#pragma unroll
-            for (int kk = 0; kk < NK; ++kk) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const uint32_t ka = pa[q] + kk * 32, kb = pb[q] + kk * 32;
-                    if constexpr (FMT == kFmtBF16) {
-                        umma_bf16(tmem, umma_desc_sw128(ka), umma_desc_sw128(kb), idesc0, accumulate);
-                        if (two)
-                            umma_bf16(tmem + (uint32_t)N0, umma_desc_sw128(ka + kTile), umma_desc_sw128(kb + kTile),
-                                      idesc1, accumulate);
-                    } else {
-                        umma_tf32(tmem, umma_desc_sw128(ka), umma_desc_sw128(kb), idesc0, accumulate);
-                        if (two)
-                            umma_tf32(tmem + (uint32_t)N0, umma_desc_sw128(ka + kTile), umma_desc_sw128(kb + kTile),
-                                      idesc1, accumulate);
-                    }
-                    accumulate = 1;
+            const int64_t n0 = (b0 + it) * R;
+            Prefetch nxt{};
+            if (it + 1 < nits) nxt = prefetch_stage<R>(pr, n0 + R, T);   // in flight during generation
+            const unsigned char *stg = staging + (it & 1) * kStagingBytes;
+            unsigned char *hi = stages + s * kStageBytes;
+            unsigned char *lo = hi + kBuf;
+            const int64_t rem = pr.n - n0;
+            const int nvalid = rem < R ? (int)rem : R;
+            for (int task = tid; task < C * 8; task += kGramThreads) {
+                const int c = task >> 3, ch = task & 7;
+                uint4 H, L;
+                make_chunk<FMT>(stg, colmap[c], ch, nvalid, H, L);
+                const uint32_t off = sw128_offset(c, ch);
+                *reinterpret_cast<uint4 *>(hi + off) = H;
+                *reinterpret_cast<uint4 *>(lo + off) = L;
+            }
+            if (it + 1 < nits) stage_series<FMT, R>(staging + ((it + 1) & 1) * kStagingBytes, nxt, T, B);
+            fence_async_shared();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&full[s]));
+            if (it > 0 && it % kChunk == 0) {   // drain the previous chunk while this stage is queued
+                const bool okd = drain(it / kChunk - 1);
+                if (gen_sync_or(!okd)) {
+                    failed = true;
+                    break;
                 }
             }
-            umma_commit(smem_addr(&bars[s]));
-            if ((it + 1) % kChunk == 0 || it + 1 == nits) {
-                umma_commit(smem_addr(&bars[kStages]));
-                ++chunk_commits;
-            }
         }
-    }
-    if (!failed && nits > 0) {   // the last chunk
-        const bool okd = drain((nits - 1) / kChunk);
-        failed = __syncthreads_or(!okd);
-    } else {
-        __syncthreads();
-    }
-    if (failed) {
-        // let every MMA this CTA issued finish before tensor memory is released
-        if (tid == 0) {
-            umma_commit(smem_addr(&bars[kStages]));
-            mbar_wait(smem_addr(&bars[kStages]), (uint32_t)(chunk_commits & 1), a.status);
-        }
-        __syncthreads();
-    }
-    float *part = a.partials + (size_t)blockIdx.x * kGramRows * kGramCols;
-    const int row = 32 * quarter + lane;
+        if (!failed && nits > 0) failed = gen_sync_or(!drain(nchunks - 1));
+
+        float *part = a.partials + (size_t)blockIdx.x * kGramRows * kGramCols;
+        const bool zero = failed || nits == 0;
 #pragma unroll
-    for (int i = 0; i < kAccCols; ++i) {
-        const int c = half * kAccCols + i;   // tensor-memory column
-        const float v = failed ? 0.f : acc[i];
-        if (c < N0)
-            part[(size_t)row * kGramCols + c] = v;
-        else if (c < used_cols)
-            part[(size_t)(128 + row) * kGramCols + 128 + (c - N0)] = v;
+        for (int i = 0; i < kAccCols; ++i) {
+            const int c = half * kAccCols + i;   // column of D0
+            if (c < N0) part[(size_t)row * kGramCols + c] = zero ? 0.f : acc[i];
+        }
+        for (int i = 0; i < kD1Half; ++i) {
+            const int c = half * kD1Half + i;   // column of D1 (real-form column 128 + c)
+            if (c < N1) part[(size_t)(128 + row) * kGramCols + 128 + c] = zero ? 0.f : d1sum[row * kD1Cols + c];
+        }
     }
     tc_fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 8) {
         tc_fence_after_sync();
         tmem_dealloc(tmem, 512);
     }
 }
 
-size_t gram_tc_smem() { return 1024 + (size_t)kStages * kStageBytes + 2 * (size_t)kStagingBytes + 256 * 4 + 64; }
+size_t gram_tc_smem()
+{
+    return 1024 + (size_t)kStages * kStageBytes + 2 * (size_t)kStagingBytes + 256 * 4 + 128 * kD1Cols * 4 + 128;
+}
 
 // ------------------------------------------------------------------ FP32 CUDA cores
 // Each CTA stages 64 rows of A (row-major, 256 padded columns, FP32) in shared
@@ -549,7 +614,7 @@ cudaError_t launch_gram(int precision, const GramArgs &a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set[ai] = true;
     }
-    kern<<<grid, kGramThreads, gram_tc_smem(), s>>>(a);
+    kern<<<grid, kGramThreads + 32, gram_tc_smem(), s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
