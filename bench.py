@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-patterns", action="store_true",
                     help="skip the batched / adjoint / Gram side measurements")
+    ap.add_argument("--e2e-zero-copy", action="store_true",
+                    help="also time the zero-copy host path (slow on this link; off by default)")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up for at least this long so clocks settle and get sampled")
     return ap.parse_args()
@@ -342,7 +344,11 @@ def measure_gram(dev, reps=5):
         h, st = f.estimate(ud, td, precision=prec, refine_iters=3)
         t_est = time.perf_counter() - t0
         err = float(np.linalg.norm(h.cpu().numpy() - theta) / np.linalg.norm(theta))
+        executed = None
+        if prec != "fp32":   # three split products on 128 x 208 and 128 x 80 accumulator tiles
+            executed = 3 * 2.0 * n * (128 * 208 + 128 * 80)
         out["single"][prec] = {"gram_ms": t_gram * 1e3, "gram_tflops_useful": useful / t_gram / 1e12,
+                               "tensor_tflops_executed": (executed / t_gram / 1e12) if executed else None,
                                "estimate_ms_3_refinements": t_est * 1e3, "coef_rel_error_vs_true": err,
                                "cond_est_DGD": st["cond_est"], "rel_residual": st["rel_residual"]}
     # batch: 256 antennas x 2^16 rows
@@ -370,6 +376,10 @@ def measure_gram(dev, reps=5):
                               "coef_rel_error_median_2_refinements": float(np.median(errs)),
                               "coef_rel_error_max_2_refinements": float(np.max(errs)),
                               "not_spd": int(sum(1 for i in info if i))}
+    peaks, kind = measured_peaks()
+    bf = out["single"]["bf16x3"]
+    bf["tensor_frac_of_bf16_peak"] = bf["tensor_tflops_executed"] / peaks.get("bf16_tflops", 1900.0)
+    bf["peak_kind"] = f"of {kind} BF16 burst (dense cuBLAS)"
     return out
 
 
@@ -420,26 +430,26 @@ def run_ours(args, world, rank, local):
     f.sync_status()
 
     K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize(dev)
     launches0 = dpd.kernel_launches()
     w0 = time.perf_counter()
+    e_start.record(stream)
     for k in range(K):
-        ev[k][0].record(stream)
         f.apply(xs[k % 2], out=ys[k % 2])
-        ev[k][1].record(stream)
+    e_end.record(stream)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - w0
     barrier()
     launches = dpd.kernel_launches() - launches0
     clocks = sampler.stop()
     f.sync_status()
-    per = [a.elapsed_time(b) * 1e-3 for a, b in ev]
-    total = ev[0][0].elapsed_time(ev[-1][1]) * 1e-3
+    total = e_start.elapsed_time(e_end) * 1e-3
     total_max = max_over_ranks(total)
     value = world * K * n / total_max / 1e9
-    mean_launch = sum(per) / len(per)
+    mean_launch = total / K   # one kernel launch per step
 
     # ---- end to end through the library's host path: the kernel reads the
     # pinned host input and writes the pinned host output in place (zero copy)
@@ -464,7 +474,7 @@ def run_ours(args, world, rank, local):
     l0 = dpd.kernel_launches()
     t_pipe = timed_host(lambda: f.apply_host(xh, out=yh))
     e2e_launches = (dpd.kernel_launches() - l0) // (K2 + 2)
-    t_zc = timed_host(lambda: f.apply_host(xh, out=yh, zero_copy=True))
+    t_zc = timed_host(lambda: f.apply_host(xh, out=yh, zero_copy=True)) if args.e2e_zero_copy else None
     xd, yd = xs[0], ys[0]
 
     def explicit():
@@ -478,7 +488,7 @@ def run_ours(args, world, rank, local):
            "path": "dpd_apply_host (pipelined): pinned host -> 2^21-sample chunks copied in, filtered and copied out "
                    "on three streams, overlapping both copy directions with the kernels",
            "gpu_launches_per_step": e2e_launches,
-           "zero_copy_value": world * K2 * n / t_zc / 1e9,
+           "zero_copy_value": (world * K2 * n / t_zc / 1e9) if t_zc else None,
            "zero_copy_path": "dpd_apply_host (zero copy): the kernel reads and writes the pinned host buffers in place",
            "explicit_copy_value": world * K2 * n / t_cp / 1e9,
            "explicit_copy_path": "cudaMemcpyAsync H2D -> dpd_apply -> cudaMemcpyAsync D2H, one after the other"}
