@@ -52,8 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-patterns", action="store_true",
                     help="skip the batched / adjoint / Gram side measurements")
-    ap.add_argument("--e2e-zero-copy", action="store_true",
-                    help="also time the zero-copy host path (slow on this link; off by default)")
+    ap.add_argument("--pattern", choices=["batched", "adjoint", "gram"], default=None,
+                    help="run only this side measurement (1 GPU) and print its JSON; for profiling")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up for at least this long so clocks settle and get sampled")
     return ap.parse_args()
@@ -451,8 +451,8 @@ def run_ours(args, world, rank, local):
     value = world * K * n / total_max / 1e9
     mean_launch = total / K   # one kernel launch per step
 
-    # ---- end to end through the library's host path: the kernel reads the
-    # pinned host input and writes the pinned host output in place (zero copy)
+    # ---- end to end through the library's host path (dpd_apply_host): pinned
+    # host input in, pinned host output back, copies inside the timed region
     xh = torch.from_numpy(x_host).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     K2 = max(3, min(K, 20))
@@ -472,9 +472,9 @@ def run_ours(args, world, rank, local):
         return max_over_ranks(e0.elapsed_time(e1) * 1e-3)
 
     l0 = dpd.kernel_launches()
-    t_pipe = timed_host(lambda: f.apply_host(xh, out=yh))
+    t_zc = timed_host(lambda: f.apply_host(xh, out=yh, zero_copy=True))
     e2e_launches = (dpd.kernel_launches() - l0) // (K2 + 2)
-    t_zc = timed_host(lambda: f.apply_host(xh, out=yh, zero_copy=True)) if args.e2e_zero_copy else None
+    t_pipe = timed_host(lambda: f.apply_host(xh, out=yh))
     xd, yd = xs[0], ys[0]
 
     def explicit():
@@ -483,13 +483,32 @@ def run_ours(args, world, rank, local):
         yh.copy_(yd, non_blocking=True)
 
     t_cp = timed_host(explicit)
-    e2e = {"value": world * K2 * n / t_pipe / 1e9, "unit": "Gsamples/s",
+
+    # host-link ceiling: both copy directions at once on two streams (copy engines)
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def link_copies():
+        s_in.wait_stream(stream)
+        s_out.wait_stream(stream)
+        with torch.cuda.stream(s_in):
+            xd.copy_(xh, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            yh.copy_(ys[1], non_blocking=True)
+        stream.wait_stream(s_in)
+        stream.wait_stream(s_out)
+
+    t_link = timed_host(link_copies)
+    link_gbs = 2 * n * 8 / (t_link / K2) / 1e9
+    e2e = {"value": world * K2 * n / t_zc / 1e9, "unit": "Gsamples/s",
            "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
-           "path": "dpd_apply_host (pipelined): pinned host -> 2^21-sample chunks copied in, filtered and copied out "
-                   "on three streams, overlapping both copy directions with the kernels",
+           "path": "dpd_apply_host (zero copy): one kernel reads the pinned host input and writes the pinned "
+                   "host output in place over the CPU-GPU link, staged through shared memory in whole lines",
            "gpu_launches_per_step": e2e_launches,
-           "zero_copy_value": (world * K2 * n / t_zc / 1e9) if t_zc else None,
-           "zero_copy_path": "dpd_apply_host (zero copy): the kernel reads and writes the pinned host buffers in place",
+           "link": {"h2d_plus_d2h_gbs": link_gbs, "frac": (2 * n * 8 / (t_zc / K2) / 1e9) / link_gbs,
+                    "how": "cudaMemcpyAsync H2D and D2H of the same buffers concurrently on two streams"},
+           "pipelined_value": world * K2 * n / t_pipe / 1e9,
+           "pipelined_path": "dpd_apply_host (pipelined): 2^21-sample chunks copied in, filtered and copied out "
+                             "on three streams, overlapping both copy directions with the kernels",
            "explicit_copy_value": world * K2 * n / t_cp / 1e9,
            "explicit_copy_path": "cudaMemcpyAsync H2D -> dpd_apply -> cudaMemcpyAsync D2H, one after the other"}
 
@@ -556,6 +575,13 @@ def main():
     world, rank, local = dist_init()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.pattern:
+        import torch
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        fn = {"batched": measure_batched, "adjoint": measure_direct, "gram": measure_gram}[args.pattern]
+        print(json.dumps({"pattern": args.pattern, "result": fn(dev)}, default=float))
+        return 0
     return run_ours(args, world, rank, local)
 
 

@@ -115,7 +115,11 @@ enum { DPD_HOST_PIPELINED = 0, DPD_HOST_ZERO_COPY = 1 };
  *       (3 x 2 x 16 MB) and streams; pinned buffers make the copies
  *       asynchronous.
  *   DPD_HOST_ZERO_COPY : the kernel reads and writes the host buffers in place
- *       over the CPU-GPU link, without staging (Sec. 3.3.1).
+ *       over the CPU-GPU link, without staging copies (Sec. 3.3.1).  With both
+ *       buffers 16-byte aligned, each CTA moves a 2048-sample tile (plus 8
+ *       history samples) with coalesced 16-byte accesses through shared
+ *       memory, so every byte crosses the link once; otherwise every thread
+ *       loads its own window with 8-byte loads (slower).
  * Ordered after earlier work on `stream`; returns without synchronising, and
  * `stream` is ordered after the last chunk: synchronise it before reading y.
  * Not capturable in a CUDA graph.
@@ -172,6 +176,24 @@ dpd_status dpd_grad(dpd_handle h, const void *x, const void *gy, int64_t n, void
  * per group (1, 2 or 4).
  */
 dpd_status dpd_set_adj_launch(dpd_handle h, int gh_blocks, int tap_group);
+
+/*
+ * Streaming predistortion: consecutive calls filter consecutive blocks of one
+ * continuous sample stream (the predistortion stage filters a continuous
+ * stream of transmit samples, Sec. 2 and Sec. 4).  The history before x[0] is the last M input
+ * samples of the previous dpd_apply_stream call on this handle (zero after
+ * dpd_create or dpd_reset_stream), so the outputs equal one dpd_apply over the
+ * concatenated input.  Two launches on `stream`: the forward filter (zero
+ * history), then one warp that recomputes y[0 .. min(M, n)) with the saved
+ * history and saves the last 8 input samples into the handle.  Calls on one
+ * handle must therefore be ordered on one stream (or synchronised), and x must
+ * stay valid until the second launch has run.  Same buffer rules and errors as
+ * dpd_apply; n == 0 changes nothing.  Allocation-free and capturable.
+ */
+dpd_status dpd_apply_stream(dpd_handle h, const void *x, void *y, int64_t n, void *stream);
+
+/* Zero the streaming history (asynchronously on `stream`). */
+dpd_status dpd_reset_stream(dpd_handle h, void *stream);
 
 /*
  * Launch shape of dpd_apply for this handle (used by the autotuner):

@@ -200,6 +200,24 @@ class DPD:
     def set_adj_launch(self, gh_blocks, tap_group):
         _lib.check("dpd_set_adj_launch", self._lib.dpd_set_adj_launch(self._h, gh_blocks, tap_group))
 
+    def apply_stream(self, x, out=None, stream=None):
+        """Filter the next block of a continuous stream (history carried across calls)."""
+        import torch
+        _check_samples(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        else:
+            _check_samples(out, "out")
+            if out.numel() != x.numel():
+                raise ValueError("out must have as many elements as x")
+        _lib.check("dpd_apply_stream", self._lib.dpd_apply_stream(
+            self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.numel(),
+            _stream_ptr(stream)))
+        return out
+
+    def reset_stream(self, stream=None):
+        _lib.check("dpd_reset_stream", self._lib.dpd_reset_stream(self._h, _stream_ptr(stream)))
+
     def apply_host(self, x, out=None, stream=None, zero_copy=False):
         """y = DPD(x) for complex64 tensors in (pinned) host memory: chunked copy / compute
         pipeline, or zero copy (the kernel reads and writes the host buffers in place).

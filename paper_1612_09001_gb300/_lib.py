@@ -50,6 +50,8 @@ SIGNATURES = {
     "dpd_set_coeffs": [_vp, _vp, _i, _i, _vp],
     "dpd_apply": [_vp, _vp, _vp, _i64, _vp],
     "dpd_apply_host": [_vp, _vp, _vp, _i64, _i, _vp],
+    "dpd_apply_stream": [_vp, _vp, _vp, _i64, _vp],
+    "dpd_reset_stream": [_vp, _vp],
     "dpd_set_fwd_launch": [_vp, _i, _i, _i, _i, _i, _i],
     "dpd_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "dpd_set_adj_launch": [_vp, _i, _i],

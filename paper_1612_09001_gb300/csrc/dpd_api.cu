@@ -12,6 +12,7 @@
 #include "dpd_internal.h"
 
 #include "dpd_handle.h"
+#include "dpd_zc.h"
 
 namespace dpd {
 static std::atomic<uint64_t> g_launches{0};
@@ -27,6 +28,19 @@ cudaError_t launch_adj_any(int B, const AdjArgs &a, const AdjLaunch &L, int T, i
     case 4: return launch_adj<4>(a, L, T, Bp, Bq, K, sm_count, s);
     case 5: return launch_adj<5>(a, L, T, Bp, Bq, K, sm_count, s);
     case 6: return launch_adj<6>(a, L, T, Bp, Bq, K, sm_count, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_zc_any(int B, int T, const FwdArgs &a, bool param_coef, cudaStream_t s)
+{
+    switch (B) {
+    case 1: return launch_zc<1>(T, a, param_coef, s);
+    case 2: return launch_zc<2>(T, a, param_coef, s);
+    case 3: return launch_zc<3>(T, a, param_coef, s);
+    case 4: return launch_zc<4>(T, a, param_coef, s);
+    case 5: return launch_zc<5>(T, a, param_coef, s);
+    case 6: return launch_zc<6>(T, a, param_coef, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -113,15 +127,18 @@ dpd_status dpd_create(int P, int Q, int M, dpd_handle *out)
     f->d_status = nullptr;
     f->d_adj_tab = nullptr;
     f->d_partials = nullptr;
+    f->d_hist = nullptr;
     if (cudaMalloc(&f->d_h, sizeof(float2) * f->K) != cudaSuccess ||
         cudaMalloc(&f->d_tab, sizeof(float) * dpd::wl_table_floats(f->B, f->T)) != cudaSuccess ||
         cudaMalloc(&f->d_adj_tab, sizeof(float) * dpd::adj_table_floats(f->B, f->T)) != cudaSuccess ||
         cudaMalloc(&f->d_partials, sizeof(float2) * (size_t)f->rows_max * f->K) != cudaSuccess ||
-        cudaMalloc(&f->d_status, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&f->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&f->d_hist, sizeof(float2) * dpd::kHalo) != cudaSuccess) {
         dpd_destroy(f);
         return DPD_ERR_ALLOC;
     }
-    if (cudaMemset(f->d_status, 0, sizeof(int)) != cudaSuccess) {
+    if (cudaMemset(f->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(f->d_hist, 0, sizeof(float2) * dpd::kHalo) != cudaSuccess) {
         dpd_destroy(f);
         return DPD_ERR_CUDA;
     }
@@ -137,6 +154,7 @@ dpd_status dpd_destroy(dpd_handle h)
     cudaFree(h->d_adj_tab);
     cudaFree(h->d_partials);
     cudaFree(h->d_status);
+    cudaFree(h->d_hist);
     free_estimate_workspace(h->est);
     free_host_pipeline(h->host);
     delete h;
@@ -331,8 +349,10 @@ dpd_status apply_zero_copy(dpd_handle h, const void *x, void *y, int64_t n, cuda
     a.status = h->d_status;
     a.vec_store = 0;
     a.host_tab = h->host_tab_valid ? &h->h_tab : nullptr;
+    if (aligned(a.x, 16) && aligned(a.y, 16))   // staged, coalesced 16-byte accesses
+        return cuda_status(dpd::launch_zc_any(h->B, h->T, a, h->host_tab_valid, stream));
     dpd::FwdLaunch L = h->fwd;
-    L.use_tma = 0;   // plain loads and stores straight to host memory
+    L.use_tma = 0;   // 8-byte aligned buffers: plain loads and stores straight to host memory
     L.V = 4;
     L.mode &= dpd::kModePackedFma | (h->host_tab_valid ? dpd::kModeParamCoef : 0);
     return cuda_status(dpd::launch_fwd_any(h->B, h->T, a, L, h->sm_count, stream));
@@ -429,6 +449,23 @@ dpd_status dpd_set_adj_launch(dpd_handle h, int gh_blocks, int tap_group)
     h->adj.gh_blocks = gh_blocks;
     h->adj.tap_group = tap_group;
     return DPD_OK;
+}
+
+dpd_status dpd_apply_stream(dpd_handle h, const void *x, void *y, int64_t n, void *stream)
+{
+    if (!h || n < 0) return DPD_ERR_INVALID_ARGUMENT;
+    if (!h->has_coeffs) return DPD_ERR_NO_COEFFS;
+    if (n == 0) return DPD_OK;
+    const dpd_status st = dpd_apply(h, x, y, n, stream);   // zero history; checks the buffers
+    if (st != DPD_OK) return st;
+    return cuda_status(dpd::launch_stream_head(h->d_tab, h->B, h->T, static_cast<const float2 *>(x), n, h->d_hist,
+                                               static_cast<float2 *>(y), static_cast<cudaStream_t>(stream)));
+}
+
+dpd_status dpd_reset_stream(dpd_handle h, void *stream)
+{
+    if (!h) return DPD_ERR_INVALID_ARGUMENT;
+    return cuda_status(cudaMemsetAsync(h->d_hist, 0, sizeof(float2) * dpd::kHalo, static_cast<cudaStream_t>(stream)));
 }
 
 dpd_status dpd_set_fwd_launch(dpd_handle h, int mode, int V, int warps, int stages, int ctas_per_sm,

@@ -44,6 +44,7 @@ struct dpd_filter {
     float2 *d_h;      // K complex coefficients, stacking order of Sec. 2.2
     float *d_tab;     // widely-linear table for the forward kernels
     int *d_status;    // kernel error word
+    float2 *d_hist;   // streaming history: the kHalo input samples before the next dpd_apply_stream
     float *d_adj_tab; // adjoint (derivative-polynomial) table
     float2 *d_partials;  // coefficient-gradient workspace: rows_max x K complex
     int rows_max;
@@ -59,3 +60,12 @@ struct dpd_filter {
 void free_estimate_workspace(EstimateWorkspace &w);
 void free_host_pipeline(HostPipeline &p);
 
+
+namespace dpd {
+// Streaming head: recompute y[0 .. min(T-1, n)) with the kHalo samples in hist
+// as the history before x[0] (the forward kernels assume zero history), then
+// hist <- the last kHalo samples of (hist ++ x).  One warp; runs after the
+// forward launch on the same stream.
+cudaError_t launch_stream_head(const float *tab, int B, int T, const float2 *x, int64_t n, float2 *hist,
+                               float2 *y, cudaStream_t s);
+}  // namespace dpd

@@ -230,3 +230,41 @@ def test_apply_host(P, Q, M, n, zero_copy):
     except dpd.DPDError as e:
         assert zero_copy and e.code == 1
     f.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 8, 9, 2047, 2048, 2049, 2056, 4095, 4097, 100003])
+@pytest.mark.parametrize("P,Q,M,device_coeffs", [(9, 9, 4, False), (9, 9, 4, True), (11, 11, 7, False),
+                                                 (3, 1, 0, True), (5, 5, 2, False)])
+def test_zero_copy_tiles_and_tails(n, P, Q, M, device_coeffs):
+    """Zero copy on 16-byte aligned pinned buffers (the staged kernel): ragged
+    tile tails, odd lengths, tiles shorter than the history, both coefficient
+    sources."""
+    x = synth.ofdm2(n, key=(31, P, n % 89))
+    h = synth.coeffs(P, Q, M, key=(31, 2))
+    f = dpd.DPD(P, Q, M)
+    f.set_coeffs(torch.from_numpy(h).cuda() if device_coeffs else h)
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.full((n + 2,), complex(7, -7), dtype=torch.complex64).pin_memory()
+    f.apply_host(xh, out=yh[:n], zero_copy=True)
+    f.sync_status()
+    f.close()
+    y = yh.numpy()
+    assert np.all(y[n:] == np.complex64(7 - 7j))   # nothing written past the end
+    assert_parity(y[:n], oracle.apply(x, h, P, Q, M), what=f"zero copy n={n}")
+
+
+@pytest.mark.parametrize("xo,yo", [(1, 0), (0, 1), (1, 1)])
+def test_zero_copy_eight_byte_aligned(xo, yo):
+    """8-byte aligned host buffers take the plain-load path."""
+    n = 50001
+    x = synth.ofdm2(n, key=(32, xo, yo))
+    h = synth.coeffs(7, 7, 3, key=(32, 1))
+    f = dpd.DPD(7, 7, 3)
+    f.set_coeffs(h)
+    xb = torch.zeros(n + 1, dtype=torch.complex64).pin_memory()
+    xb[xo: xo + n] = torch.from_numpy(x)
+    yb = torch.zeros(n + 1, dtype=torch.complex64).pin_memory()
+    f.apply_host(xb[xo: xo + n], out=yb[yo: yo + n], zero_copy=True)
+    f.sync_status()
+    f.close()
+    assert_parity(yb[yo: yo + n].numpy(), oracle.apply(x, h, 7, 7, 3), what="zero copy 8-byte aligned")
