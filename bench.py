@@ -416,6 +416,8 @@ def run_ours(args, world, rank, local):
     xs = [torch.from_numpy(x_host).to(dev) for _ in range(2)]
     ys = [torch.empty_like(xs[0]) for _ in range(2)]
     stream = torch.cuda.current_stream(dev)
+    from paper_1612_09001_gb300 import tune
+    tune.tune_forward(f, xs[0], ys[0])   # launch shape picked by timing, before the timed region
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -558,7 +560,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": WORKLOAD, "P": P, "Q": Q, "M": M, "n_samples_per_step": n,
                    "l2": "inputs larger than L2: 134 MB in + 134 MB out per step, two alternating buffer sets",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "launch": dict(f.fwd_launch)},
+                   "launch": dict(f.fwd_launch), "launch_picked_by": "autotuner (tune.tune_forward)"},
         "wall_s_timed": wall, "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "alu": alu,
         "e2e": e2e, "cpu_baseline": cpu, "patterns": patterns,
         "samples_per_s_per_gpu": K * n / total / 1e9,

@@ -105,6 +105,14 @@ __device__ __forceinline__ uint64_t policy_evict_first()
     return p;
 }
 
+// Programmatic dependent launch.  grid_dep_wait: block until the grids this one
+// depends on (earlier work in the stream) have completed and their memory
+// operations are visible; returns at once when there are none.
+// grid_dep_launch_dependents: allow the next grid in the stream to start
+// launching (its CTAs still wait in their own grid_dep_wait).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 // Streaming (evict-first) 16-byte global store.
 __device__ __forceinline__ void st_stream_f4(float4 *p, float4 v)
 {

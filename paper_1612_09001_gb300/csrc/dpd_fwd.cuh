@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(32 * 17)
     const int slot_elems = kHalo + S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    for (int i = tid; i < TABF; i += blockDim.x) tab[i] = a.tab[i];
+    // Prologue that touches no global memory (overlaps the previous grid's tail
+    // under programmatic dependent launch), then wait for that grid.
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(smem_addr(&bars[s]), 1);
@@ -237,6 +238,10 @@ __global__ void __launch_bounds__(32 * 17)
         }
         fence_barrier_init();
     }
+    grid_dep_launch_dependents();
+    grid_dep_wait();
+    if constexpr ((MODE & kModeParamCoef) == 0)
+        for (int i = tid; i < TABF; i += blockDim.x) tab[i] = a.tab[i];
     __syncthreads();
 
     if (warp == nwarps) {
@@ -378,9 +383,22 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
             const int cps = (L.ctas_per_sm > 0 && L.ctas_per_sm < occ) ? L.ctas_per_sm : occ;
             int64_t grid = (int64_t)sm_count * cps;
             if (grid > ntiles) grid = ntiles;
-            kern<<<(unsigned)grid, threads, smem, s>>>(a, L.stages, ntiles, ptab);
+            // Programmatic dependent launch: this grid may begin launching while
+            // the previous one in the stream drains (the kernel waits for it
+            // before touching global memory).
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)grid);
+            cfg.blockDim = dim3((unsigned)threads);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, L.stages, ntiles, ptab);
             count_launch();
-            return cudaGetLastError();
+            return e != cudaSuccess ? e : cudaGetLastError();
         }
         return cudaErrorNotSupported;
     }

@@ -104,7 +104,7 @@ class DirectLearner:
         for i in range(steps):
             loss = self.step()
             if i % max(1, steps // 20) == 0 or i == steps - 1:
-                hist.append((i, float(loss)))
+                hist.append((i, float(loss.detach())))
         return hist
 
     def time_step(self, reps=50):
