@@ -327,16 +327,17 @@ def measure_gram(dev, reps=5):
     td = g.apply(ud)
     useful = 8.0 * n * K * K
     out = {"workload": "Psi 2^22 rows x 97 complex columns (P=Q=11, M=7), clipped Gaussian RMS 0.3, t = Psi theta",
-           "flops_convention": "useful = 8 n K^2 (complex Gram); the tensor path executes 3 split products on 256 x 208 padded tiles",
+           "flops_convention": "useful = 8 n K^2 (complex Gram); the tensor path executes one 128 x 256 MMA per K step "
+                               "(A = hi, B = [hi; lo] of the 2BT+3 = 99 distinct real columns, padded to 128): 2 n 128 256 flops",
            "single": {}, "batch": {}}
     for prec in ("fp32", "tf32x3", "bf16x3"):
-        f.gram(ud, td, precision=prec)
+        f.gram(ud, td, precision=prec, want_tt=False)
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(reps):
-            f.gram(ud, td, precision=prec)
+            f.gram(ud, td, precision=prec, want_tt=False)   # Gram + FP64 reduction + assembly, no host sync
         e1.record()
         torch.cuda.synchronize(dev)
         t_gram = e0.elapsed_time(e1) * 1e-3 / reps
@@ -345,8 +346,8 @@ def measure_gram(dev, reps=5):
         t_est = time.perf_counter() - t0
         err = float(np.linalg.norm(h.cpu().numpy() - theta) / np.linalg.norm(theta))
         executed = None
-        if prec != "fp32":   # three split products on 128 x 208 and 128 x 80 accumulator tiles
-            executed = 3 * 2.0 * n * (128 * 208 + 128 * 80)
+        if prec != "fp32":   # one 128 x 256 MMA per K step
+            executed = 2.0 * n * 128 * 256
         out["single"][prec] = {"gram_ms": t_gram * 1e3, "gram_tflops_useful": useful / t_gram / 1e12,
                                "tensor_tflops_executed": (executed / t_gram / 1e12) if executed else None,
                                "estimate_ms_3_refinements": t_est * 1e3, "coef_rel_error_vs_true": err,

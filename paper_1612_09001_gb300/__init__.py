@@ -147,8 +147,11 @@ class DPD:
         return gh, gx
 
     # -- least squares (Sec. 2.2)
-    def gram(self, u, t=None, precision="tf32x3", stream=None):
-        """(G, g, tt): G = Psi^H Psi (K x K complex128 CUDA tensor), g = Psi^H t, tt = t^H t."""
+    def gram(self, u, t=None, precision="tf32x3", stream=None, want_tt=True):
+        """(G, g, tt): G = Psi^H Psi (K x K complex128 CUDA tensor), g = Psi^H t, tt = t^H t.
+
+        tt is read back to the host (the call synchronises the stream) unless
+        want_tt is False, in which case it is None and the call is asynchronous."""
         import torch
         _check_samples(u, "u")
         if t is not None:
@@ -160,8 +163,8 @@ class DPD:
             self._h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(t.data_ptr() if t is not None else None),
             u.numel(), PRECISIONS[precision], ctypes.c_void_p(G.data_ptr()),
             ctypes.c_void_p(g.data_ptr() if g is not None else None),
-            ctypes.byref(tt) if t is not None else None, _stream_ptr(stream)))
-        return G, g, (tt.value if t is not None else None)
+            ctypes.byref(tt) if (t is not None and want_tt) else None, _stream_ptr(stream)))
+        return G, g, (tt.value if (t is not None and want_tt) else None)
 
     def estimate(self, u, t, precision="tf32x3", refine_iters=2, stream=None):
         """Least-squares coefficients (complex64 CUDA tensor of K) and stats

@@ -1,22 +1,31 @@
 // Least-squares estimation of the APH coefficients (Sec. 2.2):
 //   h = (Psi^H Psi)^{-1} Psi^H t,  Psi = basis matrix of Eq. 2 built from u.
 //
-// Real form.  With A = [Re Psi | Re t | Im Psi | Im t] (n x C, C = 2K + 2),
-// every quantity needed is a block of S = A^T A:
-//   Re G_ab = S[a][b] + S[K+1+a][K+1+b],   Im G_ab = S[a][K+1+b] - S[K+1+a][b]
-//   Re g_a  = S[a][K] + S[K+1+a][2K+1],    Im g_a  = S[a][2K+1] - S[K+1+a][K]
-//   t^H t   = S[K][K] + S[2K+1][2K+1]
-// (G = Psi^H Psi, g = Psi^H t).  S is a dense contraction over the n rows, so
-// it runs on the tensor cores: each CTA generates R rows of A at a time (the
-// basis, recomputed from u, never stored in global memory) into shared memory
-// as operand rows (one per column of A, K-major, 128-byte swizzle), split into
-// a high and a low part (BF16 or TF32), and issues
-//   S += hi^T hi + hi^T lo + lo^T hi
-// as tcgen05 MMAs accumulating in tensor memory (FP32), in two 128-row tiles
-// that cover the upper triangle of S only.  Each CTA writes its partial S;
-// the partials are summed in FP64 in a fixed order.  The K x K system is then
-// equilibrated and factored in FP64 (Cholesky), and refined against the FP32
-// residual t - Psi h computed by the filter and adjoint kernels.
+// Real form.  With A = [Re Psi | Re t | Im Psi | Im t] (n x (2K + 2)), every
+// quantity needed is a block of A^T A:
+//   Re G_ab = <Re a, Re b> + <Im a, Im b>,   Im G_ab = <Re a, Im b> - <Im a, Re b>
+//   Re g_a  = <Re a, Re t> + <Im a, Im t>,   Im g_a  = <Re a, Im t> - <Im a, Re t>
+//   t^H t   = <Re t, Re t> + <Im t, Im t>
+// (G = Psi^H Psi, g = Psi^H t).  The conjugate branch's basis is the conjugate
+// of the main branch's (Eq. 2), so Re conj(z) = Re z and Im conj(z) = -Im z:
+// every real column of A is +-1 times one of D = 2 B T + 3 distinct columns
+// X (B = max(Bp, Bq)), or zero (Im of the constant column):
+//   d = b T + k          Re psi_b(u_{n-k})    (b < B, k < T)
+//   d = B T + b T + k    Im psi_b(u_{n-k})
+//   d = 2 B T            1
+//   d = 2 B T + 1, + 2   Re t, Im t
+// and S = X^T X (D x D, D <= 99) holds all of A^T A up to signs.  S is a dense
+// contraction over the n rows, so it runs on the tensor cores: each CTA
+// generates R rows of X at a time (the basis, recomputed from u, never stored
+// in global memory) into shared memory as operand rows (one per distinct
+// column, K-major, 128-byte swizzle), split into a high and a low part (BF16
+// or TF32), X = hi + lo.  The split product hi^T hi + hi^T lo + lo^T hi is
+// P + Q + Q^T with P = hi^T hi and Q = hi^T lo, and one MMA with A = hi
+// (128 rows) and B = [hi; lo] (256 rows) yields [P | Q]: one 128 x 256 tcgen05
+// MMA per K step, accumulating in tensor memory (FP32).  Each CTA writes its
+// partial P and Q; S = P + Q + Q^T is summed in FP64 in a fixed order.  The K x K system is then equilibrated and factored in FP64
+// (Cholesky), and refined against the FP32 residual t - Psi h computed by the
+// filter and adjoint kernels.
 #pragma once
 
 #include "dpd_internal.h"
@@ -29,15 +38,37 @@ struct GramProblem {
     int64_t n;
 };
 
-constexpr int kGramRows = 256;   // real-form columns, padded (two 128-row MMA tiles)
-constexpr int kGramCols = 208;   // widest accumulator tile (N <= 208 covers C <= 196)
+constexpr int kGramS = 112;             // distinct columns, padded (D <= 99); row stride of S
+constexpr int kGramRows = 128;          // rows of a partial (the MMA's M)
+constexpr int kGramPartCols = 2 * kGramS;   // a partial: P in columns [0, 112), Q in [112, 224)
+
+__host__ __device__ constexpr int gram_distinct(int B, int T) { return 2 * B * T + 3; }
+
+// Distinct column and sign of the real and imaginary parts of complex column j
+// of Psi (stacking order of Sec. 2.2); sign 0 marks a zero column.
+struct ColRef {
+    int d, sign;
+};
+__host__ __device__ inline void psi_column_refs(int j, int K, int Bp, int B, int T, ColRef &re, ColRef &im)
+{
+    if (j == K - 1) {   // the constant column (LO leakage term c)
+        re = ColRef{2 * B * T, 1};
+        im = ColRef{0, 0};
+        return;
+    }
+    const bool conj = j >= Bp * T;
+    const int jj = conj ? j - Bp * T : j;
+    const int b = jj / T, k = jj % T;
+    re = ColRef{b * T + k, 1};
+    im = ColRef{B * T + b * T + k, conj ? -1 : 1};
+}
 
 struct GramArgs {
     const GramProblem *probs;
     int nprob;
     int cpp;               // CTAs per problem (row chunks)
     int Bp, Bq, T, K;
-    float *partials;       // [nprob * cpp][kGramRows][kGramCols]
+    float *partials;       // [nprob * cpp][kGramRows][kGramPartCols]
     int *status;
 };
 
@@ -45,11 +76,14 @@ struct GramArgs {
 enum : int { kPrecFP32 = 0, kPrecTF32x3 = 1, kPrecBF16x3 = 2 };
 
 cudaError_t launch_gram(int precision, const GramArgs &a, cudaStream_t s);
-// S[p][i][j] (i <= j < 2K+2) = sum over the problem's CTAs of the partials, in FP64.
-cudaError_t launch_gram_reduce(const float *partials, int nprob, int cpp, int K, double *S, cudaStream_t s);
+// S[p][i][c] (i < D, c < 2 kGramS) = sum over the problem's CTAs of the partial P and Q
+// blocks, in FP64 and a fixed order (S = P + Q + Q^T is formed by the assembly).
+cudaError_t launch_gram_reduce(const float *partials, int nprob, int cpp, int D, double *S, cudaStream_t s);
 // G (K x K, row-major), g (K) and t^H t per problem from S.
-cudaError_t launch_gram_assemble(const double *S, int nprob, int K, double2 *G, double2 *g, double *tt,
-                                 cudaStream_t s);
+cudaError_t launch_gram_assemble(const double *S, int nprob, int K, int Bp, int B, int T, double2 *G, double2 *g,
+                                 double *tt, cudaStream_t s);
+// CTAs per row chunk the launch wants for nprob problems of up to n rows.
+int gram_ctas_per_problem(int precision, int sm_count, int nprob, int64_t n);
 // Equilibrated Cholesky factorisation of every G: D G D = L L^H, D = diag(G)^{-1/2}.
 // L (lower, row-major K x K) and d (K) per problem; info[p] = 0 or the failing pivot + 1.
 cudaError_t launch_chol(const double2 *G, int nprob, int K, double2 *L, double *d, int *info, cudaStream_t s);

@@ -14,8 +14,8 @@ struct EstimateWorkspace {
     int nprob = 0;                // problems the per-problem arrays were sized for
     int64_t nsamp = 0;            // samples the y / e buffers hold
     void *probs = nullptr;        // GramProblem[nprob]
-    float *partials = nullptr;    // [nprob * cpp][kGramRows][kGramCols]
-    double *S = nullptr;          // [nprob][kGramRows][kGramCols]
+    float *partials = nullptr;    // [nprob * cpp][kGramRows][kGramPartCols]
+    double *S = nullptr;          // [nprob][kGramS][kGramPartCols]: summed P and Q blocks
     double2 *G = nullptr, *g = nullptr, *L = nullptr, *h64 = nullptr, *delta = nullptr;
     double *d = nullptr, *tt = nullptr;
     int *info = nullptr;

@@ -35,8 +35,8 @@ dpd_status reserve(dpd_handle h, int nprob, int cpp, int64_t nsamp)
         cudaDeviceSynchronize();
         const size_t np = (size_t)nprob, parts = (size_t)nprob * cpp;
         ok = ok && grow(reinterpret_cast<dpd::GramProblem *&>(w.probs), 0, np);
-        ok = ok && grow(w.partials, 0, parts * dpd::kGramRows * dpd::kGramCols);
-        ok = ok && grow(w.S, 0, np * dpd::kGramRows * dpd::kGramCols);
+        ok = ok && grow(w.partials, 0, parts * dpd::kGramRows * dpd::kGramPartCols);
+        ok = ok && grow(w.S, 0, np * dpd::kGramS * dpd::kGramPartCols);
         ok = ok && grow(w.G, 0, np * K * K) && grow(w.L, 0, np * K * K);
         ok = ok && grow(w.g, 0, np * K) && grow(w.h64, 0, np * K) && grow(w.delta, 0, np * K);
         ok = ok && grow(w.d, 0, np * K) && grow(w.tt, 0, np) && grow(w.info, 0, np);
@@ -57,13 +57,9 @@ dpd_status reserve(dpd_handle h, int nprob, int cpp, int64_t nsamp)
 
 bool valid_precision(int p) { return p == DPD_PREC_FP32 || p == DPD_PREC_TF32X3 || p == DPD_PREC_BF16X3; }
 
-int gram_cpp(dpd_handle h, int nprob, int64_t n)
+int gram_cpp(dpd_handle h, int nprob, int64_t n, int precision)
 {
-    // one CTA per SM in total, at least one per problem, no more than row blocks
-    int cpp = std::max(1, h->sm_count / std::max(nprob, 1));
-    const int64_t blocks = (n + 31) / 32;
-    if (cpp > blocks) cpp = (int)std::max<int64_t>(blocks, 1);
-    return cpp;
+    return dpd::gram_ctas_per_problem(precision, h->sm_count, nprob, n);
 }
 
 // Gram (+ reduction + assembly) of nprob problems already described in w.probs.
@@ -81,8 +77,10 @@ dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_
     a.partials = w.partials;
     a.status = h->d_status;
     if (dpd::launch_gram(precision, a, s) != cudaSuccess) return DPD_ERR_CUDA;
-    if (dpd::launch_gram_reduce(w.partials, nprob, cpp, h->K, w.S, s) != cudaSuccess) return DPD_ERR_CUDA;
-    if (dpd::launch_gram_assemble(w.S, nprob, h->K, w.G, w.g, w.tt, s) != cudaSuccess) return DPD_ERR_CUDA;
+    const int D = dpd::gram_distinct(h->B, h->T);
+    if (dpd::launch_gram_reduce(w.partials, nprob, cpp, D, w.S, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dpd::launch_gram_assemble(w.S, nprob, h->K, h->Bp, h->B, h->T, w.G, w.g, w.tt, s) != cudaSuccess)
+        return DPD_ERR_CUDA;
     return DPD_OK;
 }
 
@@ -234,7 +232,7 @@ dpd_status check_inputs(dpd_handle h, const void *u, const void *t, int64_t n, i
     if (!h || n < 1 || !u || !aligned8(u) || (t && !aligned8(t))) return DPD_ERR_INVALID_ARGUMENT;
     if (!valid_precision(precision)) return DPD_ERR_INVALID_ARGUMENT;
     if (n > ((int64_t)1 << 40)) return DPD_ERR_UNSUPPORTED;
-    if (2 * h->K + 2 > dpd::kGramCols) return DPD_ERR_UNSUPPORTED;
+    if (dpd::gram_distinct(h->B, h->T) > dpd::kGramS) return DPD_ERR_UNSUPPORTED;
     return DPD_OK;
 }
 
@@ -270,7 +268,7 @@ dpd_status dpd_gram(dpd_handle h, const void *u, const void *t, int64_t n, int p
     if (st != DPD_OK) return st;
     if (!G || !aligned8(G) || (g && (!t || !aligned8(g)))) return DPD_ERR_INVALID_ARGUMENT;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int cpp = gram_cpp(h, 1, n);
+    const int cpp = gram_cpp(h, 1, n, precision);
     if ((st = reserve(h, 1, cpp, 0)) != DPD_OK) return st;
     const dpd::GramProblem pr{static_cast<const float2 *>(u), static_cast<const float2 *>(t), n};
     if (cudaMemcpyAsync(h->est.probs, &pr, sizeof(pr), cudaMemcpyHostToDevice, s) != cudaSuccess) return DPD_ERR_CUDA;
@@ -293,7 +291,7 @@ dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, i
     if (st != DPD_OK) return st;
     if (!t || !h_out || !aligned8(h_out) || refine_iters < 0 || refine_iters > 100) return DPD_ERR_INVALID_ARGUMENT;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int cpp = gram_cpp(h, 1, n);
+    const int cpp = gram_cpp(h, 1, n, precision);
     if ((st = reserve(h, 1, cpp, (refine_iters > 0 || stats) ? n : 0)) != DPD_OK) return st;
     EstimateWorkspace &w = h->est;
     const dpd::GramProblem pr{static_cast<const float2 *>(u), static_cast<const float2 *>(t), n};
@@ -319,7 +317,7 @@ dpd_status dpd_estimate_batched(dpd_handle h, const void *const *u, const void *
 {
     if (!h || count < 1 || !u || !t || !n || !h_out || !aligned8(h_out)) return DPD_ERR_INVALID_ARGUMENT;
     if (refine_iters < 0 || refine_iters > 100 || !valid_precision(precision)) return DPD_ERR_INVALID_ARGUMENT;
-    if (2 * h->K + 2 > dpd::kGramCols) return DPD_ERR_UNSUPPORTED;
+    if (dpd::gram_distinct(h->B, h->T) > dpd::kGramS) return DPD_ERR_UNSUPPORTED;
     std::vector<dpd::GramProblem> probs((size_t)count);
     int64_t nmax = 1;
     for (int i = 0; i < count; ++i) {
@@ -328,7 +326,7 @@ dpd_status dpd_estimate_batched(dpd_handle h, const void *const *u, const void *
         nmax = std::max(nmax, n[i]);
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int cpp = gram_cpp(h, count, nmax);
+    int cpp = gram_cpp(h, count, nmax, precision);
     dpd_status st = reserve(h, count, cpp, refine_iters > 0 ? nmax : 0);
     if (st != DPD_OK) return st;
     EstimateWorkspace &w = h->est;

@@ -6,58 +6,77 @@
 
 namespace dpd {
 
-__global__ void gram_reduce_kernel(const float *__restrict__ partials, int cpp, int C, double *__restrict__ S)
+// Column sums over the problem's CTAs of the partial P and Q blocks (rows and
+// columns < D), in FP64 and a fixed order: SPQ[i][c] for c < 2 kGramS.
+__global__ void gram_reduce_kernel(const float *__restrict__ partials, int cpp, int D, double *__restrict__ SPQ)
 {
     const int p = blockIdx.y;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // i * kGramCols + j
-    if (idx >= kGramRows * kGramCols) return;
-    const int i = idx / kGramCols, j = idx % kGramCols;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // i * kGramPartCols + c
+    if (idx >= kGramS * kGramPartCols) return;
+    const int i = idx / kGramPartCols, c = idx % kGramPartCols, j = c % kGramS;
     double s = 0.0;
-    if (i < C && j < C && i <= j) {
-        const float *base = partials + (size_t)p * cpp * kGramRows * kGramCols + idx;
-        for (int c = 0; c < cpp; ++c) s += (double)base[(size_t)c * kGramRows * kGramCols];
+    if (i < D && j < D) {
+        const size_t part = (size_t)kGramRows * kGramPartCols;
+        const float *base = partials + (size_t)p * cpp * part + (size_t)i * kGramPartCols + c;
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        int k = 0;
+        for (; k + 4 <= cpp; k += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s4[q] += (double)base[(size_t)(k + q) * part];
+        }
+        for (; k < cpp; ++k) s4[0] += (double)base[(size_t)k * part];
+        s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
-    S[(size_t)p * kGramRows * kGramCols + idx] = s;
+    SPQ[(size_t)p * kGramS * kGramPartCols + idx] = s;
 }
 
-cudaError_t launch_gram_reduce(const float *partials, int nprob, int cpp, int K, double *S, cudaStream_t s)
+cudaError_t launch_gram_reduce(const float *partials, int nprob, int cpp, int D, double *S, cudaStream_t s)
 {
-    dim3 grid((kGramRows * kGramCols + 255) / 256, nprob);
-    gram_reduce_kernel<<<grid, 256, 0, s>>>(partials, cpp, 2 * K + 2, S);
+    dim3 grid((kGramS * kGramPartCols + 255) / 256, nprob);
+    gram_reduce_kernel<<<grid, 256, 0, s>>>(partials, cpp, D, S);
     count_launch();
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ double sym(const double *S, int i, int j)
+// <x, y> for two signed distinct-column references: S = P + Q + Q^T from the
+// summed blocks (P upper triangle in columns [0, kGramS), Q in [kGramS, 2 kGramS)).
+__device__ __forceinline__ double dot(const double *SPQ, ColRef x, ColRef y)
 {
-    return i <= j ? S[(size_t)i * kGramCols + j] : S[(size_t)j * kGramCols + i];
+    if (x.sign == 0 || y.sign == 0) return 0.0;
+    const int i = x.d < y.d ? x.d : y.d, j = x.d < y.d ? y.d : x.d;
+    const double v = SPQ[(size_t)i * kGramPartCols + j] + SPQ[(size_t)i * kGramPartCols + kGramS + j] +
+                     SPQ[(size_t)j * kGramPartCols + kGramS + i];
+    return x.sign * y.sign > 0 ? v : -v;
 }
 
-__global__ void gram_assemble_kernel(const double *__restrict__ Sall, int K, double2 *__restrict__ G,
-                                     double2 *__restrict__ g, double *__restrict__ tt)
+__global__ void gram_assemble_kernel(const double *__restrict__ Sall, int K, int Bp, int B, int T,
+                                     double2 *__restrict__ G, double2 *__restrict__ g, double *__restrict__ tt)
 {
     const int p = blockIdx.y;
-    const double *S = Sall + (size_t)p * kGramRows * kGramCols;
+    const double *S = Sall + (size_t)p * kGramS * kGramPartCols;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int o = K + 1;   // offset of the imaginary block
+    const ColRef tre{2 * B * T + 1, 1}, tim{2 * B * T + 2, 1};
     if (idx < K * K) {
         const int a = idx / K, b = idx % K;
-        G[(size_t)p * K * K + idx] = make_double2(sym(S, a, b) + sym(S, o + a, o + b),
-                                                  sym(S, a, o + b) - sym(S, o + a, b));
+        ColRef ar, ai, br, bi;
+        psi_column_refs(a, K, Bp, B, T, ar, ai);
+        psi_column_refs(b, K, Bp, B, T, br, bi);
+        G[(size_t)p * K * K + idx] = make_double2(dot(S, ar, br) + dot(S, ai, bi), dot(S, ar, bi) - dot(S, ai, br));
     } else if (idx < K * K + K) {
         const int a = idx - K * K;
-        if (g) g[(size_t)p * K + a] = make_double2(sym(S, a, K) + sym(S, o + a, 2 * K + 1),
-                                                   sym(S, a, 2 * K + 1) - sym(S, o + a, K));
+        ColRef ar, ai;
+        psi_column_refs(a, K, Bp, B, T, ar, ai);
+        if (g) g[(size_t)p * K + a] = make_double2(dot(S, ar, tre) + dot(S, ai, tim), dot(S, ar, tim) - dot(S, ai, tre));
     } else if (idx == K * K + K) {
-        if (tt) tt[p] = sym(S, K, K) + sym(S, 2 * K + 1, 2 * K + 1);
+        if (tt) tt[p] = dot(S, tre, tre) + dot(S, tim, tim);
     }
 }
 
-cudaError_t launch_gram_assemble(const double *S, int nprob, int K, double2 *G, double2 *g, double *tt,
-                                 cudaStream_t s)
+cudaError_t launch_gram_assemble(const double *S, int nprob, int K, int Bp, int B, int T, double2 *G, double2 *g,
+                                 double *tt, cudaStream_t s)
 {
     dim3 grid((K * K + K + 1 + 255) / 256, nprob);
-    gram_assemble_kernel<<<grid, 256, 0, s>>>(S, K, G, g, tt);
+    gram_assemble_kernel<<<grid, 256, 0, s>>>(S, K, Bp, B, T, G, g, tt);
     count_launch();
     return cudaGetLastError();
 }

@@ -1,6 +1,6 @@
-// Gram contraction S = A^T A of the real-form basis (see dpd_gram.cuh):
-// tcgen05 tensor-core kernel with split BF16 / TF32 operands, and the plain
-// FP32 CUDA-core form it is compared against.
+// Gram contraction S = X^T X of the distinct real columns of the basis (see
+// dpd_gram.cuh): tcgen05 tensor-core kernel with split BF16 / TF32 operands,
+// and the plain FP32 CUDA-core form it is compared against.
 #include <cuda_bf16.h>
 
 #include "dpd_gram.cuh"
@@ -10,158 +10,76 @@ namespace dpd {
 
 namespace {
 
-constexpr int kGramThreads = 256;
-constexpr int kTile = 16384;          // 128 operand rows x 128 bytes
-constexpr int kBuf = 2 * kTile;       // 256 operand rows
-constexpr int kStageBytes = 2 * kBuf; // hi + lo
-constexpr int kStages = 2;
-constexpr int kPsiStride = 64 + kMaxT - 1;
-
-// Value of real-form column c at stage row rr (sample n0 + rr).
-struct ColumnDecode {
-    bool is_t, imag, conj, one;
-    int b, k;
-};
-
-__device__ __forceinline__ ColumnDecode decode_column(int c, int K, int Bp, int T)
-{
-    ColumnDecode d{};
-    int j;
-    if (c < K) {
-        j = c;
-    } else if (c == K) {
-        d.is_t = true;
-        return d;
-    } else if (c < 2 * K + 1) {
-        d.imag = true;
-        j = c - K - 1;
-    } else {
-        d.is_t = true;
-        d.imag = true;
-        return d;
-    }
-    if (j == K - 1) {
-        d.one = true;
-        return d;
-    }
-    if (j < Bp * T) {
-        d.b = j / T;
-        d.k = j % T;
-    } else {
-        d.conj = true;
-        d.b = (j - Bp * T) / T;
-        d.k = (j - Bp * T) % T;
-    }
-    return d;
-}
-
-__device__ __forceinline__ float column_value(const ColumnDecode &d, const float2 *psi, const float2 *tv, int rr,
-                                              int T, bool valid)
-{
-    if (!valid) return 0.f;
-    if (d.is_t) return d.imag ? tv[rr].y : tv[rr].x;
-    if (d.one) return d.imag ? 0.f : 1.f;
-    const float2 p = psi[d.b * kPsiStride + rr + (T - 1) - d.k];
-    return d.imag ? (d.conj ? -p.y : p.y) : p.x;
-}
-
-// Fill psi[b][w] = |u|^{2b} u for samples n0 - (T-1) + w (zero outside [0, n)) and tv[rr] = t.
-template <int R>
-__device__ __forceinline__ void stage_basis(const GramProblem &pr, int64_t n0, int T, int B, float2 *psi, float2 *tv)
-{
-    const int W = R + T - 1;
-    for (int i = threadIdx.x; i < W * B; i += blockDim.x) {
-        const int bb = i / W, w = i % W;
-        const int64_t j = n0 - (T - 1) + w;
-        float2 v = make_float2(0.f, 0.f);
-        if (j >= 0 && j < pr.n) {
-            const float2 x = pr.u[j];
-            const float r = fmaf(x.x, x.x, x.y * x.y);
-            float p = 1.f;
-            for (int e = 0; e < bb; ++e) p *= r;
-            v = make_float2(p * x.x, p * x.y);
-        }
-        psi[bb * kPsiStride + w] = v;
-    }
-    for (int i = threadIdx.x; i < R; i += blockDim.x) {
-        float2 v = make_float2(0.f, 0.f);
-        if (pr.t && n0 + i < pr.n) v = pr.t[n0 + i];
-        tv[i] = v;
-    }
-}
-
-}  // namespace
-
-// ------------------------------------------------------------------ tensor cores
-// Operand generation.  Every real-form column of A is one of 15 "series" --
-// Re / Im of psi_b(u_j) for b < 6, Re / Im of t, or the constant 1 -- read at
-// row rr from element w = rr + off, off = T-1-k for the tap-k column and T-1
-// for the unshifted ones (element w of a stage is sample n0 - (T-1) + w).  So
-// each stage converts every basis value to its hi / lo pair once, into a
-// series array in shared memory, and an operand chunk (8 BF16 or 4 TF32 rows
-// of one column) is a few 32-bit shared loads and two 16-byte stores.  BF16
-// series are kept twice, as 16-bit arrays starting at element 0 and at
-// element 1, so a chunk at any offset reads whole aligned words.  The global
-// loads of the next stage are issued before the current stage is generated.
-//
-// Accumulation.  The tensor core's FP32 accumulator drops low-order bits on
-// every MMA step, a bias that grows with the number of steps summed into one
-// accumulator.  So each accumulation covers a chunk of kChunk stages only:
-// after a chunk, every thread adds its share of the tensor-memory
-// accumulators (one lane quarter, 144 of the 288 columns) into FP32
-// sums with round-to-nearest (D0 in registers, D1 in shared memory), and the
-// next chunk starts from zero.
-constexpr int kChunk = 4;
-constexpr int kAccCols = 104;   // per generator thread: half of D0's 208 columns of its lane
-constexpr int kD1Cols = 80;     // D1 running sums in shared memory: 128 lanes x 80 columns
-constexpr int kD1Half = 40;
-constexpr int kSeries = 15;     // 2 per basis order (6), 2 for t, 1 constant
-constexpr int kSerLen = 72;     // elements per series (>= 64 + kMaxT - 1, even)
+// ------------------------------------------------------------------ the basis
+// Every distinct column is one of 15 "series" -- Re / Im of psi_b(u_j) for
+// b < 6, Re / Im of t, or the constant 1 -- read at stage row rr from element
+// w = rr + off, off = T-1-k for a tap-k column and T-1 for the others.
+// Element w of a stage is sample n0 - (T-1) + w.
+constexpr int kSeries = 15;
+constexpr int kSerT = 12;      // Re t = 12, Im t = 13
+constexpr int kSerOne = 14;
+constexpr int kSerLen = 72;    // elements per series (>= 64 + kMaxT - 1, even)
 // Per series: BF16: hi, hi shifted by one, lo, lo shifted by one (16-bit each);
 // TF32: hi, lo (32-bit each).  Both 4 * kSerLen * 2 bytes.
 constexpr int kSerBytes = 4 * kSerLen * 2;
 constexpr int kStagingBytes = kSeries * kSerBytes;
+constexpr int kPsiStride = 64 + kMaxT - 1;
 
-// Column map entry: series | off << 8 | flags << 16 (bit 0 negate, bit 1 zero column).
-__device__ __forceinline__ int column_map(int c, int K, int Bp, int T)
+__device__ __forceinline__ void distinct_source(int d, int B, int T, int &series, int &off)
 {
-    const ColumnDecode d = decode_column(c, K, Bp, T);
-    int series, off = T - 1, flags = 0;
-    if (d.is_t) {
-        series = d.imag ? 13 : 12;
-    } else if (d.one) {
-        series = 14;
-        if (d.imag) flags |= 2;
+    const int BT = B * T;
+    if (d < 2 * BT) {
+        const int im = d >= BT ? 1 : 0, dd = im ? d - BT : d;
+        series = 2 * (dd / T) + im;
+        off = T - 1 - dd % T;
     } else {
-        series = 2 * d.b + (d.imag ? 1 : 0);
-        off = T - 1 - d.k;
-        if (d.imag && d.conj) flags |= 1;
+        series = d == 2 * BT ? kSerOne : kSerT + (d - 2 * BT - 1);
+        off = T - 1;
     }
-    return series | (off << 8) | (flags << 16);
 }
 
-struct Prefetch {
-    float2 u;     // basis sample, element w = tid (threads 0 .. kSerLen-1)
-    float2 t;     // target of row tid - 128 (threads 128 .. 128 + R - 1)
-    bool urow, trow;
-};
+// Series work of a stage is spread over the 512 threads: threads
+// 0 .. 6 kSerLen - 1 own element w = tid % kSerLen of the psi series of order
+// b = tid / kSerLen (Re and Im); threads 6 kSerLen .. 511 own target row
+// rr = tid - 6 kSerLen (Re t, Im t and the constant).
+constexpr int kPsiThreads = kMaxB * kSerLen;   // 432
+static_assert(512 - kPsiThreads >= 64, "a target row per remaining thread");
 
-template <int R>
-__device__ __forceinline__ Prefetch prefetch_stage(const GramProblem &pr, int64_t n0, int T)
+// The raw samples of a stage (kSerLen basis samples from n0 - (T-1), then up
+// to 64 target samples from n0) are fetched kAhead stages in advance with
+// asynchronous 8-byte copies into a ring of shared-memory slots (zero-filled
+// outside the problem), one copy group per stage and thread.
+constexpr int kAhead = 3;
+constexpr int kRawSlots = kAhead + 1;
+constexpr int kRawLen = kSerLen + 64;
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, uint32_t src_bytes)
 {
-    Prefetch f{};
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// This thread's copies of the stage starting at row n0 into `slot`; `active`
+// false commits an empty group (keeps the per-thread group count uniform).
+template <int R>
+__device__ __forceinline__ void fetch_stage(float2 *slot, const GramProblem &pr, int64_t n0, int T, bool active)
+{
     const int tid = threadIdx.x;
-    if (tid < kSerLen) {
-        const int64_t j = n0 - (T - 1) + tid;
-        f.urow = tid < R + T - 1 && j >= 0 && j < pr.n;
-        if (f.urow) f.u = pr.u[j];
+    if (active) {
+        if (tid < kSerLen) {
+            const int64_t j = n0 - (T - 1) + tid;
+            const bool v = tid < R + T - 1 && j >= 0 && j < pr.n;
+            cp_async8(smem_addr(slot + tid), v ? pr.u + j : pr.u, v ? 8u : 0u);
+        } else if (tid >= kPsiThreads && tid - kPsiThreads < R) {
+            const int r = tid - kPsiThreads;
+            const int64_t j = n0 + r;
+            const bool v = pr.t != nullptr && j < pr.n;
+            cp_async8(smem_addr(slot + kSerLen + r), v ? pr.t + j : pr.u, v ? 8u : 0u);
+        }
     }
-    if (tid >= 128 && tid < 128 + R) {
-        const int64_t j = n0 + (tid - 128);
-        f.trow = j < pr.n;
-        if (f.trow && pr.t) f.t = pr.t[j];
-    }
-    return f;
+    cp_async_commit();
 }
 
 template <int FMT>
@@ -191,344 +109,379 @@ __device__ __forceinline__ void put_series(unsigned char *stg, int series, int w
     }
 }
 
-// Convert the prefetched samples of a stage into the series arrays.
+// Convert the raw samples of a stage (rows from n0) into the series arrays.
 template <int FMT, int R>
-__device__ __forceinline__ void stage_series(unsigned char *stg, const Prefetch &f, int T, int B)
+__device__ __forceinline__ void stage_series(unsigned char *stg, const float2 *slot, int64_t n0, int64_t n, int B,
+                                             int T)
 {
     const int tid = threadIdx.x;
-    if (tid < kSerLen) {
-        const float r = fmaf(f.u.x, f.u.x, f.u.y * f.u.y);
-        float p = 1.f;
-        for (int b = 0; b < B; ++b) {   // psi_b = |u|^{2b} u, low order first
-            put_series<FMT>(stg, 2 * b, tid, f.urow ? p * f.u.x : 0.f);
-            put_series<FMT>(stg, 2 * b + 1, tid, f.urow ? p * f.u.y : 0.f);
-            p *= r;
-        }
-    }
-    if (tid >= 128 && tid < 128 + R) {
-        const int w = tid - 128 + (T - 1);
-        put_series<FMT>(stg, 12, w, f.trow ? f.t.x : 0.f);
-        put_series<FMT>(stg, 13, w, f.trow ? f.t.y : 0.f);
-        put_series<FMT>(stg, 14, w, f.trow ? 1.f : 0.f);
-    }
-}
-
-// One 16-byte chunk (rows ch*EPC .. +EPC) of real-form column c, hi and lo.
-template <int FMT>
-__device__ __forceinline__ void make_chunk(const unsigned char *stg, int cm, int ch, int nvalid, uint4 &H, uint4 &L)
-{
-    const int series = cm & 0xFF, off = (cm >> 8) & 0xFF, flags = cm >> 16;
-    const unsigned char *base = stg + series * kSerBytes;
-    uint32_t h[4], l[4];
-    if constexpr (FMT == kFmtBF16) {
-        const int o = ch * 8 + off;
-        const uint32_t *hw = reinterpret_cast<const uint32_t *>(base) + ((o & 1) ? kSerLen / 2 + (o - 1) / 2 : o / 2);
-        const uint32_t *lw = hw + kSerLen;   // lo arrays follow the two hi arrays
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            h[q] = hw[q];
-            l[q] = lw[q];
-        }
-        if (flags & 1) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                h[q] ^= 0x80008000u;
-                l[q] ^= 0x80008000u;
-            }
-        }
-        if (nvalid < 64) {   // last stage of the problem: rows past the end are zero
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r0 = ch * 8 + 2 * q;
-                const uint32_t m = (r0 < nvalid ? 0x0000FFFFu : 0u) | (r0 + 1 < nvalid ? 0xFFFF0000u : 0u);
-                h[q] &= m;
-                l[q] &= m;
-            }
+    if (tid < kPsiThreads) {
+        const int w = tid % kSerLen, b = tid / kSerLen;
+        if (b < B) {
+            const float2 u = slot[w];   // zero outside the problem
+            const float r = fmaf(u.x, u.x, u.y * u.y);
+            float p = 1.f;
+            for (int e = 0; e < b; ++e) p *= r;   // r^b, low order first as in the filter
+            put_series<FMT>(stg, 2 * b, w, p * u.x);   // psi_b = |u|^{2b} u
+            put_series<FMT>(stg, 2 * b + 1, w, p * u.y);
         }
     } else {
-        const int o = ch * 4 + off;
-        const uint32_t *hw = reinterpret_cast<const uint32_t *>(base) + o;
-        const uint32_t *lw = hw + kSerLen;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            h[q] = hw[q];
-            l[q] = lw[q];
-        }
-        if (flags & 1) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                h[q] ^= 0x80000000u;
-                l[q] ^= 0x80000000u;
-            }
-        }
-        if (nvalid < 32) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (ch * 4 + q >= nvalid) h[q] = l[q] = 0u;
+        const int rr = tid - kPsiThreads;
+        if (rr < R) {
+            const int w = rr + T - 1;
+            const float2 t = slot[kSerLen + rr];
+            put_series<FMT>(stg, kSerT, w, t.x);
+            put_series<FMT>(stg, kSerT + 1, w, t.y);
+            put_series<FMT>(stg, kSerOne, w, n0 + rr < n ? 1.f : 0.f);
         }
     }
-    if (flags & 2) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) h[q] = l[q] = 0u;
-    }
-    H = make_uint4(h[0], h[1], h[2], h[3]);
-    L = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Named barrier 1 over the eight generator warps, with an OR vote of `pred`.
-__device__ __forceinline__ bool gen_sync_or(bool pred)
-{
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred)
-        : "memory");
-    return r != 0;
-}
+}  // namespace
 
-// Warp roles: warps 0-7 generate operands and own the FP32 running sums;
-// warp 8 (lane 0) issues the MMAs.  Barriers: full[s] (8 generator arrivals:
-// stage s written), empty[s] (MMA commit: stage s consumed), chunk_done (MMA
-// commit after a chunk's last stage), tmem_free (8 generator arrivals: the
-// chunk has been drained from tensor memory).
+// ------------------------------------------------------------------ tensor cores
+// Operand generation.  Each stage converts every basis value to its hi / lo
+// pair once, into a series array in shared memory; an operand chunk (8 BF16 or
+// 4 TF32 rows of one distinct column) is then four 32-bit shared loads per
+// half and two 16-byte stores.  BF16 series are kept twice, as 16-bit arrays
+// starting at element 0 and at element 1, so a chunk at any offset reads whole
+// aligned words.  Every generator thread owns up to four fixed chunks (the
+// addresses are computed once); the global loads of the next stage are issued
+// before the current stage is generated.
+//
+// Products.  X = hi + lo; the split product hi^T hi + hi^T lo + lo^T hi is
+// P + Q + Q^T with P = hi^T hi, Q = hi^T lo.  The hi and lo tiles of a stage
+// are adjacent in shared memory, so one MMA with A = hi (128 operand rows) and
+// B = [hi; lo] (256 rows) produces [P | Q] in a 128 x 256 accumulator: one
+// MMA per K step (a tcgen05 MMA with M = 128 takes the same time for any N up
+// to 256, so the full width is used).
+//
+// Accumulation.  The tensor core's FP32 accumulator drops low-order bits on
+// every MMA step, a bias that grows with the number of steps summed into one
+// accumulator.  So each accumulation covers a chunk of kChunk stages only and
+// is then added, with round-to-nearest, into FP32 running sums in registers:
+// every thread owns one tensor-memory lane (a distinct column) and one piece
+// of its columns -- P [0, 64), P [64, 112), Q [128, 192) or Q [192, 240) --
+// loaded in parts aligned to their width.  Two accumulators in tensor memory
+// (2 x 256 columns) alternate between chunks, so the MMAs of one chunk run
+// while the previous one is drained.
+//
+// Roles.  All sixteen warps generate operands and drain accumulators; thread 0
+// also issues the MMAs of a stage once the barrier at the top of the next
+// iteration has shown that every thread has written it.  Sixteen warps (four
+// per SM sub-partition) at 128 registers each fill the register file.
+constexpr int kThreads = 512;
+constexpr int kOpTile = 16384;            // 128 operand rows x 128 bytes
+constexpr int kStageBytes = 2 * kOpTile;  // hi tile, then lo tile
+constexpr int kStages = 4;
+constexpr int kChunk = 4;
+// A chunk is drained kStages stages after its last one was generated, and its
+// accumulator is reused by the chunk two later, whose first stage is issued
+// kChunk + 1 stages after that last one.
+static_assert(kStages <= kChunk + 1, "drain must precede the reuse of an accumulator");
+constexpr int kAccN = 256;                // accumulator columns: P in [0, 128), Q in [128, 256)
+constexpr int kAccPer = 64;               // sums per thread (a piece of 64 or 48 columns)
+constexpr int kTasks = 2;                 // operand chunks per thread (8 D <= 792 <= 2 x 512)
+constexpr int kTmemCols = 2 * kAccN;
+
+// Barriers: empty[s] (MMA commit: stage s consumed), acc_full[b] (MMA commit:
+// a chunk's sum is complete in accumulator b), fin (MMA commit: everything
+// issued has completed, before tensor memory is released).
 template <int FMT>
-__global__ void __launch_bounds__(kGramThreads + 32, 1) gram_tc_kernel(GramArgs a)
+__global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a)
 {
-    constexpr int R = (FMT == kFmtBF16) ? 64 : 32;    // rows per stage: 128 bytes per operand row
-    constexpr int NK = 4;                             // MMAs along K per stage (K = 16 bf16 / 8 tf32)
+    constexpr int R = (FMT == kFmtBF16) ? 64 : 32;   // rows per stage: 128 bytes per operand row
+    constexpr int NK = 4;                            // MMAs along K per stage (K = 16 bf16 / 8 tf32)
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *stages = smem;
-    unsigned char *staging = smem + kStages * kStageBytes;              // 2 x kStagingBytes
-    int *colmap = reinterpret_cast<int *>(staging + 2 * kStagingBytes);  // [256]
-    float *d1sum = reinterpret_cast<float *>(colmap + 256);               // [128][kD1Cols]
-    uint64_t *full = reinterpret_cast<uint64_t *>(d1sum + 128 * kD1Cols);
-    uint64_t *empty = full + kStages;
-    uint64_t *chunk_done = empty + kStages;
-    uint64_t *tmem_free = chunk_done + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_free + 1);
+    unsigned char *staging = smem + kStages * kStageBytes;   // 2 x kStagingBytes
+    float2 *raw = reinterpret_cast<float2 *>(staging + 2 * kStagingBytes);   // kRawSlots x kRawLen
+    uint64_t *empty = reinterpret_cast<uint64_t *>(raw + kRawSlots * kRawLen);
+    uint64_t *acc_full = empty + kStages;
+    uint64_t *fin = acc_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int prob = blockIdx.x / a.cpp, chunk = blockIdx.x % a.cpp;
     const GramProblem pr = a.probs[prob];
-    const int K = a.K, C = 2 * K + 2, T = a.T, B = a.Bp > a.Bq ? a.Bp : a.Bq;
-    const bool two = C > 128;
-    const int N0 = ((C + 15) / 16) * 16;
-    const int N1 = two ? N0 - 128 : 0;
+    const int T = a.T, B = a.Bp > a.Bq ? a.Bp : a.Bq;
+    const int D = gram_distinct(B, T);
     const int64_t nblk = (pr.n + R - 1) / R;
     const int64_t b0 = nblk * chunk / a.cpp, b1 = nblk * (chunk + 1) / a.cpp;
     const int nits = (int)(b1 - b0);
     const int nchunks = (nits + kChunk - 1) / kChunk;
 
-    for (int i = tid; i < kStages * kStageBytes / 16; i += blockDim.x)
+    // Operand rows >= D are never written and stay zero.
+    for (int i = tid; i < kStages * kStageBytes / 16; i += kThreads)
         reinterpret_cast<uint4 *>(stages)[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int c = tid; c < 256; c += blockDim.x) colmap[c] = c < C ? column_map(c, K, a.Bp, T) : 0;
-    for (int i = tid; i < 128 * kD1Cols; i += blockDim.x) d1sum[i] = 0.f;
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_addr(&full[s]), 8);
-            mbar_init(smem_addr(&empty[s]), 1);
-        }
-        mbar_init(smem_addr(chunk_done), 1);
-        mbar_init(smem_addr(tmem_free), 8);
+        for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&empty[s]), 1);
+        for (int b = 0; b < 2; ++b) mbar_init(smem_addr(&acc_full[b]), 1);
+        mbar_init(smem_addr(fin), 1);
         fence_barrier_init();
     }
-    if (warp == 8) {
-        tmem_alloc(smem_addr(tmem_slot), 512);
+    if (warp == 0) {
+        tmem_alloc(smem_addr(tmem_slot), kTmemCols);
         tmem_relinquish();
     }
-    if (nits > 0 && warp < 8) stage_series<FMT, R>(staging, prefetch_stage<R>(pr, b0 * R, T), T, B);
+#pragma unroll
+    for (int j = 0; j <= kAhead; ++j) fetch_stage<R>(raw + j * kRawLen, pr, (b0 + j) * R, T, j < nits);
+    cp_async_wait<kAhead>();   // stage 0 has landed (this thread's copies)
+    __syncthreads();
+    if (nits > 0) stage_series<FMT, R>(staging, raw, b0 * R, pr.n, B, T);
     fence_async_shared();
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    bool failed = false;
-    if (warp == 8) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            const uint32_t idesc0 = umma_idesc(FMT, 128, N0);
-            const uint32_t idesc1 = two ? umma_idesc(FMT, 128, N1) : 0u;
-            int commits = 0;
-            bool issued_all = true;
-            for (int it = 0; it < nits; ++it) {
-                const int s = it % kStages;
-                if (!mbar_wait(smem_addr(&full[s]), (uint32_t)((it / kStages) & 1), a.status)) {
-                    issued_all = false;
-                    break;
-                }
-                if (it > 0 && it % kChunk == 0 &&
-                    !mbar_wait(smem_addr(tmem_free), (uint32_t)((it / kChunk - 1) & 1), a.status)) {
-                    issued_all = false;
-                    break;
-                }
-                tc_fence_after_sync();
-                const uint32_t hb = smem_addr(stages + s * kStageBytes), lb = hb + kBuf;
-                const uint32_t pa[3] = {hb, hb, lb}, pb[3] = {hb, lb, hb};   // hi*hi + hi*lo + lo*hi
-                uint32_t accumulate = (it % kChunk == 0) ? 0u : 1u;
+    const int quarter = warp & 3, piece = warp >> 2;
+    const int row = 32 * quarter + lane;   // tensor-memory lane = distinct column
+    // piece 0: P [0, 64), 1: P [64, 112), 2: Q [128, 192), 3: Q [192, 240)
+    const int pcol = (piece >> 1) * 128 + (piece & 1) * 64;
+    const bool wide = (piece & 1) == 0;   // 64 columns, else 48
+    const uint32_t lane_taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)pcol;
+    float acc[kAccPer];
 #pragma unroll
-                for (int kk = 0; kk < NK; ++kk) {
+    for (int i = 0; i < kAccPer; ++i) acc[i] = 0.f;
+
+    // This thread's operand chunks: task tid + 256 q = (column << 3) | chunk.
+    int src[kTasks], dst[kTasks], chk[kTasks];
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const uint32_t ka = pa[q] + kk * 32, kb = pb[q] + kk * 32;
-                        if constexpr (FMT == kFmtBF16) {
-                            umma_bf16(tmem, umma_desc_sw128(ka), umma_desc_sw128(kb), idesc0, accumulate);
-                            if (two)
-                                umma_bf16(tmem + (uint32_t)N0, umma_desc_sw128(ka + kTile),
-                                          umma_desc_sw128(kb + kTile), idesc1, accumulate);
-                        } else {
-                            umma_tf32(tmem, umma_desc_sw128(ka), umma_desc_sw128(kb), idesc0, accumulate);
-                            if (two)
-                                umma_tf32(tmem + (uint32_t)N0, umma_desc_sw128(ka + kTile),
-                                          umma_desc_sw128(kb + kTile), idesc1, accumulate);
-                        }
-                        accumulate = 1;
-                    }
-                }
-                umma_commit(smem_addr(&empty[s]));
-                if ((it + 1) % kChunk == 0 || it + 1 == nits) {
-                    umma_commit(smem_addr(chunk_done));
-                    ++commits;
-                }
-            }
-            // Every MMA issued must be complete before tensor memory is released.
-            // Normally the last chunk's commit covers them all (the generators
-            // wait on that same phase).  After a failure, commit once more and
-            // wait for that phase.
-            if (issued_all) {
-                if (nits > 0) mbar_wait(smem_addr(chunk_done), (uint32_t)((commits - 1) & 1), a.status);
+    for (int q = 0; q < kTasks; ++q) {
+        const int task = tid + kThreads * q;
+        src[q] = -1;
+        dst[q] = 0;
+        chk[q] = 0;
+        if (task < 8 * D) {
+            const int d = task >> 3, ch = task & 7;
+            int series, off;
+            distinct_source(d, B, T, series, off);
+            int word;
+            if constexpr (FMT == kFmtBF16) {
+                const int o = ch * 8 + off;
+                word = (o & 1) ? kSerLen / 2 + (o - 1) / 2 : o / 2;
             } else {
-                umma_commit(smem_addr(chunk_done));
-                mbar_wait(smem_addr(chunk_done), (uint32_t)(commits & 1), a.status);
+                word = ch * 4 + off;
             }
-        }
-        __syncwarp();
-    } else {
-        // ------------------------------------------------------------ generators
-        const int quarter = warp & 3, half = warp >> 2;
-        const int row = 32 * quarter + lane;   // tensor-memory lane
-        const uint32_t lane_taddr = tmem + ((uint32_t)(32 * quarter) << 16);
-        float acc[kAccCols];
-#pragma unroll
-        for (int i = 0; i < kAccCols; ++i) acc[i] = 0.f;
-
-        auto drain = [&](int c) -> bool {
-            const bool ok = mbar_wait(smem_addr(chunk_done), (uint32_t)(c & 1), a.status);
-            tc_fence_after_sync();
-            if (ok) {
-#pragma unroll
-                for (int cc = 0; cc < kAccCols / 8; ++cc) {
-                    if (half * kAccCols + cc * 8 < N0) {
-                        float v[8];
-                        tmem_ld8(lane_taddr + (uint32_t)(half * kAccCols + cc * 8), v);
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) acc[cc * 8 + q] += v[q];
-                    }
-                }
-                if (two) {
-                    float *d1row = d1sum + row * kD1Cols + half * kD1Half;
-#pragma unroll
-                    for (int cc = 0; cc < kD1Half / 8; ++cc) {
-                        if (half * kD1Half + cc * 8 < N1) {
-                            float v[8];
-                            tmem_ld8(lane_taddr + (uint32_t)(N0 + half * kD1Half + cc * 8), v);
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) d1row[cc * 8 + q] += v[q];
-                        }
-                    }
-                }
-            }
-            tc_fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_addr(tmem_free));
-            return ok;
-        };
-
-        for (int it = 0; it < nits; ++it) {
-            const int s = it % kStages;
-            bool ok = true;
-            if (it >= kStages) ok = mbar_wait(smem_addr(&empty[s]), (uint32_t)(((it / kStages) - 1) & 1), a.status);
-            if (gen_sync_or(!ok)) {   // also: every generator finished the previous stage
-                failed = true;
-                break;
-            }
-            const int64_t n0 = (b0 + it) * R;
-            Prefetch nxt{};
-            if (it + 1 < nits) nxt = prefetch_stage<R>(pr, n0 + R, T);   // in flight during generation
-            const unsigned char *stg = staging + (it & 1) * kStagingBytes;
-            unsigned char *hi = stages + s * kStageBytes;
-            unsigned char *lo = hi + kBuf;
-            const int64_t rem = pr.n - n0;
-            const int nvalid = rem < R ? (int)rem : R;
-            for (int task = tid; task < C * 8; task += kGramThreads) {
-                const int c = task >> 3, ch = task & 7;
-                uint4 H, L;
-                make_chunk<FMT>(stg, colmap[c], ch, nvalid, H, L);
-                const uint32_t off = sw128_offset(c, ch);
-                *reinterpret_cast<uint4 *>(hi + off) = H;
-                *reinterpret_cast<uint4 *>(lo + off) = L;
-            }
-            if (it + 1 < nits) stage_series<FMT, R>(staging + ((it + 1) & 1) * kStagingBytes, nxt, T, B);
-            fence_async_shared();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_addr(&full[s]));
-            if (it > 0 && it % kChunk == 0) {   // drain the previous chunk while this stage is queued
-                const bool okd = drain(it / kChunk - 1);
-                if (gen_sync_or(!okd)) {
-                    failed = true;
-                    break;
-                }
-            }
-        }
-        if (!failed && nits > 0) failed = gen_sync_or(!drain(nchunks - 1));
-
-        float *part = a.partials + (size_t)blockIdx.x * kGramRows * kGramCols;
-        const bool zero = failed || nits == 0;
-#pragma unroll
-        for (int i = 0; i < kAccCols; ++i) {
-            const int c = half * kAccCols + i;   // column of D0
-            if (c < N0) part[(size_t)row * kGramCols + c] = zero ? 0.f : acc[i];
-        }
-        for (int i = 0; i < kD1Half; ++i) {
-            const int c = half * kD1Half + i;   // column of D1 (real-form column 128 + c)
-            if (c < N1) part[(size_t)(128 + row) * kGramCols + 128 + c] = zero ? 0.f : d1sum[row * kD1Cols + c];
+            src[q] = series * (kSerBytes / 4) + word;
+            dst[q] = (int)sw128_offset(d, ch);
+            chk[q] = ch;
         }
     }
+
+    // MMAs of stage j (thread 0, after a barrier that followed every thread's
+    // writes of that stage and every drain of the accumulator it reuses).
+    const uint32_t idesc = umma_idesc(FMT, 128, kAccN);   // M = 128, N = 256
+    int issued = 0;
+    auto issue = [&](int j) {
+        const int s = j % kStages, c = j / kChunk, buf = c & 1;
+        tc_fence_after_sync();
+        const uint32_t hb = smem_addr(stages + s * kStageBytes);   // hi rows 0-127, lo rows 128-255
+        const uint32_t dacc = tmem + (uint32_t)(buf * kAccN);
+#pragma unroll
+        for (int kk = 0; kk < NK; ++kk) {
+            const uint64_t desc = umma_desc_sw128(hb + kk * 32);
+            const uint32_t accumulate = (j % kChunk == 0 && kk == 0) ? 0u : 1u;
+            if constexpr (FMT == kFmtBF16)
+                umma_bf16(dacc, desc, desc, idesc, accumulate);
+            else
+                umma_tf32(dacc, desc, desc, idesc, accumulate);
+        }
+        ++issued;
+        umma_commit(smem_addr(&empty[s]));
+        if ((j + 1) % kChunk == 0 || j + 1 == nits) umma_commit(smem_addr(&acc_full[buf]));
+    };
+
+    auto drain = [&](int c) -> bool {
+        const int buf = c & 1;
+        const bool ok = mbar_wait(smem_addr(&acc_full[buf]), (uint32_t)((c >> 1) & 1), a.status);
+        tc_fence_after_sync();
+        if (ok) {
+            const uint32_t ta = lane_taddr + (uint32_t)(buf * kAccN);
+            float v[32];
+            tmem_ld32(ta, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[i] += v[i];
+            if (wide) {
+                tmem_ld32(ta + 32, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) acc[32 + i] += v[i];
+            } else {
+                float w[16];
+                tmem_ld16(ta + 32, w);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc[32 + i] += w[i];
+            }
+        }
+        tc_fence_before_sync();
+        return ok;
+    };
+
+    bool failed = false;
+    int next_drain = 0;
+    bool drained_ok = true;   // drains of the previous iteration
+    for (int it = 0; it < nits; ++it) {
+        const int s = it % kStages;
+        bool ok = drained_ok;
+        if (it >= kStages)
+            ok = mbar_wait(smem_addr(&empty[s]), (uint32_t)(((it / kStages) - 1) & 1), a.status) && ok;
+        cp_async_wait<kAhead - 1>();   // this thread's copies of stage it + 1 have landed
+        // every thread has written stage it - 1, drained what it had to, and
+        // its copies of stage it + 1 are visible
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0 && it > 0) issue(it - 1);
+        const int64_t n0 = (b0 + it) * R;
+        // the slot of stage it (read in the previous iteration) receives stage it + kAhead + 1
+        fetch_stage<R>(raw + (it % kRawSlots) * kRawLen, pr, n0 + (int64_t)(kAhead + 1) * R, T,
+                       it + kAhead + 1 < nits);
+        const uint32_t *stw = reinterpret_cast<const uint32_t *>(staging + (it & 1) * kStagingBytes);
+        unsigned char *hi = stages + s * kStageBytes;
+        unsigned char *lo = hi + kOpTile;
+        const int64_t rem = pr.n - n0;
+        const int nvalid = rem < R ? (int)rem : R;
+#pragma unroll
+        for (int q = 0; q < kTasks; ++q) {
+            if (src[q] < 0) continue;
+            const uint32_t *hw = stw + src[q];
+            const uint32_t *lw = hw + kSerLen;   // lo arrays follow the hi arrays
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                h[k] = hw[k];
+                l[k] = lw[k];
+            }
+            if (nvalid < R) {   // last stage of the problem: rows past the end are zero
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    uint32_t m;
+                    if constexpr (FMT == kFmtBF16) {
+                        const int r0 = chk[q] * 8 + 2 * k;
+                        m = (r0 < nvalid ? 0x0000FFFFu : 0u) | (r0 + 1 < nvalid ? 0xFFFF0000u : 0u);
+                    } else {
+                        m = chk[q] * 4 + k < nvalid ? 0xFFFFFFFFu : 0u;
+                    }
+                    h[k] &= m;
+                    l[k] &= m;
+                }
+            }
+            *reinterpret_cast<uint4 *>(hi + dst[q]) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(lo + dst[q]) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+        if (it + 1 < nits)
+            stage_series<FMT, R>(staging + ((it + 1) & 1) * kStagingBytes, raw + ((it + 1) % kRawSlots) * kRawLen,
+                                 n0 + R, pr.n, B, T);
+        fence_async_shared();
+        // Drain every chunk whose last stage was consumed kStages stages ago:
+        // its MMAs are complete (this stage's empty wait saw them).  A failed
+        // drain is voted on at the top of the next iteration.
+        while (next_drain < nchunks) {
+            const int last = min((next_drain + 1) * kChunk, nits) - 1;
+            if (last + kStages > it) break;
+            drained_ok = drain(next_drain++) && drained_ok;
+        }
+    }
+    if (!failed && nits > 0) {
+        if (__syncthreads_or(!drained_ok)) {
+            failed = true;
+        } else {
+            if (tid == 0) issue(nits - 1);
+            while (next_drain < nchunks) drained_ok = drain(next_drain++) && drained_ok;
+            failed = __syncthreads_or(!drained_ok);
+        }
+    }
+    cp_async_wait<0>();   // no copy into this CTA's shared memory outlives it
+    // Every MMA issued must be complete before tensor memory is released.
+    if (tid == 0 && issued > 0) {
+        umma_commit(smem_addr(fin));
+        mbar_wait(smem_addr(fin), 0u, a.status);
+    }
+
+    float *part = a.partials + (size_t)blockIdx.x * kGramRows * kGramPartCols;
+    const bool zero = failed || nits == 0;
+#pragma unroll
+    for (int i = 0; i < kAccPer; ++i)   // P -> partial columns [0, 112), Q -> [112, 224)
+        if (wide || i < 48) part[(size_t)row * kGramPartCols + (piece >> 1) * kGramS + (piece & 1) * 64 + i] = zero ? 0.f : acc[i];
+
     tc_fence_before_sync();
     __syncthreads();
-    if (warp == 8) {
+    if (warp == 0) {
         tc_fence_after_sync();
-        tmem_dealloc(tmem, 512);
+        tmem_dealloc(tmem, kTmemCols);
     }
 }
 
 size_t gram_tc_smem()
 {
-    return 1024 + (size_t)kStages * kStageBytes + 2 * (size_t)kStagingBytes + 256 * 4 + 128 * kD1Cols * 4 + 128;
+    return 1024 + (size_t)kStages * kStageBytes + 2 * (size_t)kStagingBytes + (size_t)kRawSlots * kRawLen * 8 +
+           (kStages + 3) * 8 + 16;
 }
 
 // ------------------------------------------------------------------ FP32 CUDA cores
-// Each CTA stages 64 rows of A (row-major, 256 padded columns, FP32) in shared
-// memory; thread t owns one 8 x 8 block (I, J), I <= J, of the upper triangle
-// of S and accumulates it over the rows.
+// Each CTA stages 64 rows of the distinct columns (row-major, padded to 104,
+// FP32) in shared memory; thread t owns one 8 x 8 block (I, J), I <= J, of the
+// upper triangle of S and accumulates it over the rows.
 constexpr int kF32Rows = 64;
-constexpr int kF32Threads = 352;   // >= 25 * 26 / 2 = 325 diagonal-and-upper 8 x 8 blocks
+constexpr int kF32Stride = 104;   // D <= 99, padded to whole 8-column blocks
+constexpr int kF32Threads = 96;   // >= 13 * 14 / 2 = 91 diagonal-and-upper 8 x 8 blocks
 
-__global__ void __launch_bounds__(kF32Threads, 1) gram_fp32_kernel(GramArgs a)
+// Fill psi[b][w] = |u|^{2b} u for samples n0 - (T-1) + w (zero outside [0, n)) and tv[rr] = t.
+template <int R>
+__device__ __forceinline__ void stage_basis(const GramProblem &pr, int64_t n0, int T, int B, float2 *psi, float2 *tv)
+{
+    const int W = R + T - 1;
+    for (int i = threadIdx.x; i < W * B; i += blockDim.x) {
+        const int bb = i / W, w = i % W;
+        const int64_t j = n0 - (T - 1) + w;
+        float2 v = make_float2(0.f, 0.f);
+        if (j >= 0 && j < pr.n) {
+            const float2 x = pr.u[j];
+            const float r = fmaf(x.x, x.x, x.y * x.y);
+            float p = 1.f;
+            for (int e = 0; e < bb; ++e) p *= r;
+            v = make_float2(p * x.x, p * x.y);
+        }
+        psi[bb * kPsiStride + w] = v;
+    }
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        float2 v = make_float2(0.f, 0.f);
+        if (pr.t && n0 + i < pr.n) v = pr.t[n0 + i];
+        tv[i] = v;
+    }
+}
+
+// Value of distinct column d at stage row rr (sample n0 + rr).
+__device__ __forceinline__ float distinct_value(int d, int B, int T, const float2 *psi, const float2 *tv, int rr,
+                                                bool valid)
+{
+    const int BT = B * T;
+    if (!valid || d >= 2 * BT + 3) return 0.f;
+    if (d < 2 * BT) {
+        const int im = d >= BT, dd = im ? d - BT : d;
+        const float2 p = psi[(dd / T) * kPsiStride + rr + (T - 1) - dd % T];
+        return im ? p.y : p.x;
+    }
+    if (d == 2 * BT) return 1.f;
+    return d == 2 * BT + 1 ? tv[rr].x : tv[rr].y;
+}
+
+__global__ void __launch_bounds__(kF32Threads) gram_fp32_kernel(GramArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_f[];
-    float *Atile = reinterpret_cast<float *>(smem_f);                    // [kF32Rows][256]
-    float2 *psi = reinterpret_cast<float2 *>(Atile + kF32Rows * 256);  // [kMaxB][kPsiStride]
+    float *Atile = reinterpret_cast<float *>(smem_f);                           // [kF32Rows][kF32Stride]
+    float2 *psi = reinterpret_cast<float2 *>(Atile + kF32Rows * kF32Stride);  // [kMaxB][kPsiStride]
     float2 *tv = psi + kMaxB * kPsiStride;
 
     const int tid = threadIdx.x;
     const int prob = blockIdx.x / a.cpp, chunk = blockIdx.x % a.cpp;
     const GramProblem pr = a.probs[prob];
-    const int K = a.K, C = 2 * K + 2, T = a.T, B = a.Bp > a.Bq ? a.Bp : a.Bq;
-    const int nb8 = (C + 7) / 8;
+    const int T = a.T, B = a.Bp > a.Bq ? a.Bp : a.Bq;
+    const int D = gram_distinct(B, T);
+    const int nb8 = (D + 7) / 8;
     // block (I, J) of this thread: enumerate the upper triangle row by row
     int I = -1, J = -1;
     {
@@ -556,17 +509,15 @@ __global__ void __launch_bounds__(kF32Threads, 1) gram_fp32_kernel(GramArgs a)
         __syncthreads();
         stage_basis<kF32Rows>(pr, n0, T, B, psi, tv);
         __syncthreads();
-        for (int e = tid; e < kF32Rows * 256; e += kF32Threads) {
-            const int rr = e >> 8, c = e & 255;
-            float v = 0.f;
-            if (c < C) v = column_value(decode_column(c, K, a.Bp, T), psi, tv, rr, T, n0 + rr < pr.n);
-            Atile[e] = v;
+        for (int e = tid; e < kF32Rows * kF32Stride; e += kF32Threads) {
+            const int rr = e / kF32Stride, d = e % kF32Stride;
+            Atile[e] = distinct_value(d, B, T, psi, tv, rr, n0 + rr < pr.n);
         }
         __syncthreads();
         if (I >= 0) {
             for (int rr = 0; rr < kF32Rows; ++rr) {
-                const float4 *row = reinterpret_cast<const float4 *>(Atile + rr * 256);
-                const float4 a0 = row[2 * I], a1 = row[2 * I + 1], b0v = row[2 * J], b1v = row[2 * J + 1];
+                const float4 *rowp = reinterpret_cast<const float4 *>(Atile + rr * kF32Stride);
+                const float4 a0 = rowp[2 * I], a1 = rowp[2 * I + 1], b0v = rowp[2 * J], b1v = rowp[2 * J + 1];
                 const float ai[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                 const float bj[8] = {b0v.x, b0v.y, b0v.z, b0v.w, b1v.x, b1v.y, b1v.z, b1v.w};
 #pragma unroll
@@ -576,19 +527,34 @@ __global__ void __launch_bounds__(kF32Threads, 1) gram_fp32_kernel(GramArgs a)
             }
         }
     }
-    float *part = a.partials + (size_t)blockIdx.x * kGramRows * kGramCols;
+    // P = the sums (upper blocks; the rest of P is never read), Q = 0.
+    float *part = a.partials + (size_t)blockIdx.x * kGramRows * kGramPartCols;
+    for (int e = tid; e < kGramRows * kGramS; e += kF32Threads)
+        part[(size_t)(e / kGramS) * kGramPartCols + kGramS + e % kGramS] = 0.f;
     if (I >= 0) {
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int r = 8 * I + i, c = 8 * J + j;
-                if (r < kGramRows && c < kGramCols) part[(size_t)r * kGramCols + c] = acc[i][j];
+                if (r < kGramS && c < kGramS) part[(size_t)r * kGramPartCols + c] = acc[i][j];
             }
     }
 }
 
-size_t gram_fp32_smem() { return (size_t)kF32Rows * 256 * 4 + (kMaxB * kPsiStride + 64) * 8; }
+size_t gram_fp32_smem() { return (size_t)kF32Rows * kF32Stride * 4 + (kMaxB * kPsiStride + 64) * 8; }
+
+int gram_ctas_per_problem(int precision, int sm_count, int nprob, int64_t n)
+{
+    // tensor kernel: one CTA per SM in total; FP32 kernel: four (small CTAs);
+    // at least one per problem, no more than row blocks
+    const int total = precision == kPrecFP32 ? 4 * sm_count : sm_count;
+    int cpp = total / (nprob > 0 ? nprob : 1);
+    if (cpp < 1) cpp = 1;
+    const int64_t blocks = (n + 63) / 64;
+    if (cpp > blocks) cpp = (int)(blocks > 1 ? blocks : 1);
+    return cpp;
+}
 
 cudaError_t launch_gram(int precision, const GramArgs &a, cudaStream_t s)
 {
@@ -614,7 +580,7 @@ cudaError_t launch_gram(int precision, const GramArgs &a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set[ai] = true;
     }
-    kern<<<grid, kGramThreads + 32, gram_tc_smem(), s>>>(a);
+    kern<<<grid, kThreads, gram_tc_smem(), s>>>(a);
     count_launch();
     return cudaGetLastError();
 }

@@ -45,7 +45,8 @@ def _gram_check(P, Q, M, n, precision, seed):
 
 @pytest.mark.parametrize("precision", ["fp32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("P,Q,M,n", [(5, 3, 4, 5003), (1, 0, 0, 100), (9, 9, 4, 20011), (9, 9, 6, 3001),
-                                     (11, 11, 7, 4099), (3, 1, 2, 63), (7, 7, 3, 1)])
+                                     (11, 11, 7, 4099), (3, 1, 2, 63), (7, 7, 3, 1), (3, 7, 2, 2001),
+                                     (1, 5, 3, 777), (11, 11, 7, 64 * 152 * 4 + 13)])
 def test_gram_against_oracle(P, Q, M, n, precision):
     _gram_check(P, Q, M, n, precision, seed=P * 100 + M * 10 + n % 7)
 
@@ -140,3 +141,18 @@ def test_estimate_batched_matches_single():
         np.testing.assert_allclose(hb[i].cpu().numpy(), hs.cpu().numpy(), rtol=0, atol=1e-5)
         e = np.linalg.norm(hb[i].cpu().numpy() - theta) / np.linalg.norm(theta)
         assert e < 1e-4, (i, e)
+
+
+def test_gram_without_host_readback_matches():
+    """want_tt=False: same G and g, no host synchronisation inside the call."""
+    P, Q, M, n = 9, 9, 4, 30011
+    u, t, _ = _ls_problem(P, Q, M, n, seed=5)
+    f = dpd.DPD(P, Q, M)
+    ud, td = torch.from_numpy(u).cuda(), torch.from_numpy(t).cuda()
+    for prec in ("fp32", "tf32x3", "bf16x3"):
+        G1, g1, tt1 = f.gram(ud, td, precision=prec)
+        G2, g2, tt2 = f.gram(ud, td, precision=prec, want_tt=False)
+        torch.cuda.synchronize()
+        assert tt2 is None and tt1 > 0
+        assert torch.equal(G1, G2) and torch.equal(g1, g2)
+    f.close()
