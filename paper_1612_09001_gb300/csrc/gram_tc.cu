@@ -162,7 +162,7 @@ __device__ __forceinline__ void stage_series(unsigned char *stg, const float2 *s
 // is then added, with round-to-nearest, into FP32 running sums in registers:
 // every thread owns one tensor-memory lane (a distinct column) and one piece
 // of its columns -- P [0, 64), P [64, 112), Q [128, 192) or Q [192, 240) --
-// loaded in parts aligned to their width.  Two accumulators in tensor memory
+// read as 64 columns with one wait (the 48-column pieces read 16 unused ones).  Two accumulators in tensor memory
 // (2 x 256 columns) alternate between chunks, so the MMAs of one chunk run
 // while the previous one is drained.
 //
@@ -174,7 +174,7 @@ constexpr int kThreads = 512;
 constexpr int kOpTile = 16384;            // 128 operand rows x 128 bytes
 constexpr int kStageBytes = 2 * kOpTile;  // hi tile, then lo tile
 constexpr int kStages = 4;
-constexpr int kChunk = 4;
+constexpr int kChunk = 8;
 // A chunk is drained kStages stages after its last one was generated, and its
 // accumulator is reused by the chunk two later, whose first stage is issued
 // kChunk + 1 stages after that last one.
@@ -299,21 +299,10 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a)
         const bool ok = mbar_wait(smem_addr(&acc_full[buf]), (uint32_t)((c >> 1) & 1), a.status);
         tc_fence_after_sync();
         if (ok) {
-            const uint32_t ta = lane_taddr + (uint32_t)(buf * kAccN);
-            float v[32];
-            tmem_ld32(ta, v);
+            float v[64];
+            tmem_ld64(lane_taddr + (uint32_t)(buf * kAccN), v);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) acc[i] += v[i];
-            if (wide) {
-                tmem_ld32(ta + 32, v);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) acc[32 + i] += v[i];
-            } else {
-                float w[16];
-                tmem_ld16(ta + 32, w);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) acc[32 + i] += w[i];
-            }
+            for (int i = 0; i < 64; ++i) acc[i] += v[i];
         }
         tc_fence_before_sync();
         return ok;
