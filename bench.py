@@ -54,7 +54,7 @@ def parse():
                     help="skip the batched / adjoint / Gram side measurements")
     ap.add_argument("--fwd-launch", default=None, metavar="MODE,V,WARPS,STAGES",
                     help="fix the forward launch shape instead of tuning it (profiling runs)")
-    ap.add_argument("--pattern", choices=["batched", "adjoint", "gram"], default=None,
+    ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "gram"], default=None,
                     help="run only this side measurement (1 GPU) and print its JSON; for profiling")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up for at least this long so clocks settle and get sampled")
@@ -228,6 +228,54 @@ def _time_graph(fn, reps, dev):
     e1.record(cur)
     torch.cuda.synchronize(dev)
     return e0.elapsed_time(e1) * 1e-3 / reps
+
+
+def measure_small(dev, calls=200):
+    """2^16 clipped-Gaussian samples, P=Q=5, M=2 (L2-resident, launch-bound):
+    microseconds per dpd_apply, back to back and replayed from a CUDA graph."""
+    import torch
+    import dpd_synth as synth
+    import paper_1612_09001_gb300 as dpd
+    n = 1 << 16
+    x = torch.from_numpy(synth.clipped_gaussian(n, 0.3, key=(0, 0))).to(dev)
+    y = torch.empty_like(x)
+    f = dpd.DPD(5, 5, 2)
+    f.set_coeffs(synth.coeffs(5, 5, 2, key=(0, 1)))
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        for _ in range(10):
+            f.apply(x, out=y, stream=s)
+    s.synchronize()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e3
+
+    def plain():
+        for _ in range(calls):
+            f.apply(x, out=y, stream=s)
+
+    t_plain = timed(plain) / calls
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(calls):
+            f.apply(x, out=y, stream=s)
+    def replay():
+        with torch.cuda.stream(s):   # a graph replays on the current stream
+            g.replay()
+
+    replay()
+    s.synchronize()
+    t_graph = timed(replay) / calls
+    f.sync_status(s)
+    return {"workload": "2^16 clipped Gaussian (RMS 0.3), P=Q=5, M=2 (K=19), L2-resident",
+            "us_per_call_plain": t_plain, "us_per_call_graph": t_graph,
+            "gsamples_per_s_graph": n / (t_graph * 1e-6) / 1e9, "calls": calls}
 
 
 def measure_batched(dev, reps=20):
@@ -553,6 +601,7 @@ def run_ours(args, world, rank, local):
         b = measure_batched(dev)
         b["hbm_frac_persistent"] = b["hbm_frac_persistent"] / peaks["hbm_gbs"]
         patterns["batched"] = b
+        patterns["small_2p16"] = measure_small(dev)
         patterns["adjoint"] = measure_direct(dev)
         patterns["gram"] = measure_gram(dev)
 
@@ -590,7 +639,8 @@ def main():
         import torch
         dev = torch.device("cuda", local)
         torch.cuda.set_device(dev)
-        fn = {"batched": measure_batched, "adjoint": measure_direct, "gram": measure_gram}[args.pattern]
+        fn = {"small": measure_small, "batched": measure_batched, "adjoint": measure_direct,
+              "gram": measure_gram}[args.pattern]
         print(json.dumps({"pattern": args.pattern, "result": fn(dev)}, default=float))
         return 0
     return run_ours(args, world, rank, local)

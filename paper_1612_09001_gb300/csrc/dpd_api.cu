@@ -201,6 +201,28 @@ dpd_status dpd_set_coeffs(dpd_handle h, const void *coeffs, int K, int where, vo
     return DPD_OK;
 }
 
+// Launch shape for n samples.  With the default shape, an input too short to
+// give every SM a few tiles gets 4 samples per thread and fewer warps per tile
+// (tiles of 128 to 512 samples): such calls are bound by latency, and more,
+// smaller tiles spread them over more SMs.
+static dpd::FwdLaunch launch_for(dpd_handle h, int64_t n)
+{
+    dpd::FwdLaunch L = h->fwd;
+    if (!h->host_tab_valid) L.mode &= ~dpd::kModeParamCoef;
+    const int64_t tile = (int64_t)L.warps * 32 * L.V;
+    if (h->fwd_auto && (n + tile - 1) / tile < 4 * (int64_t)h->sm_count) {
+        L.V = 4;
+        L.warps = 1;
+        for (int w : {4, 2})
+            if ((n + w * 128 - 1) / (w * 128) * 2 >= 3 * (int64_t)h->sm_count) {
+                L.warps = w;
+                break;
+            }
+        L.stages = L.warps >= 4 ? 3 : 2;
+    }
+    return L;
+}
+
 dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stream)
 {
     if (!h || n < 0) return DPD_ERR_INVALID_ARGUMENT;
@@ -218,8 +240,7 @@ dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stre
     a.status = h->d_status;
     a.vec_store = aligned(y, 16) ? 1 : 0;
     a.host_tab = h->host_tab_valid ? &h->h_tab : nullptr;
-    dpd::FwdLaunch L = h->fwd;
-    if (!h->host_tab_valid) L.mode &= ~dpd::kModeParamCoef;
+    dpd::FwdLaunch L = launch_for(h, n);
     if (!aligned(x, 16)) {
         // 8-byte aligned input: plain-load kernel (built for V = 4)
         L.use_tma = 0;
@@ -482,6 +503,7 @@ dpd_status dpd_set_fwd_launch(dpd_handle h, int mode, int V, int warps, int stag
     h->fwd.stages = stages;
     h->fwd.ctas_per_sm = ctas_per_sm;
     h->fwd.use_tma = use_tma;
+    h->fwd_auto = false;
     return DPD_OK;
 }
 

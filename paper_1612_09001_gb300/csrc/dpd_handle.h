@@ -52,6 +52,7 @@ struct dpd_filter {
     bool host_tab_valid;  // h_tab mirrors d_tab (coefficients were set from host memory)
     dpd::HostTab h_tab;
     dpd::FwdLaunch fwd;
+    bool fwd_auto = true;   // default launch shape: shrink the tile for short inputs (off once set explicitly)
     dpd::AdjLaunch adj;
     EstimateWorkspace est;
     HostPipeline host;
