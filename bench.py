@@ -391,17 +391,24 @@ def measure_gram(dev, reps=5):
         e1.record()
         torch.cuda.synchronize(dev)
         t_gram = e0.elapsed_time(e1) * 1e-3 / reps
-        t0 = time.perf_counter()
-        h, st = f.estimate(ud, td, precision=prec, refine_iters=3)
-        t_est = time.perf_counter() - t0
-        err = float(np.linalg.norm(h.cpu().numpy() - theta) / np.linalg.norm(theta))
+        est = {}
+        for basis in ("monomial", "orthogonal"):
+            t0 = time.perf_counter()
+            h, st = f.estimate(ud, td, precision=prec, refine_iters=3, basis=basis)
+            t_est = time.perf_counter() - t0
+            h0, _ = f.estimate(ud, td, precision=prec, refine_iters=0, basis=basis)
+            est[basis] = {"estimate_ms_3_refinements": t_est * 1e3,
+                          "coef_rel_error_vs_true": float(np.linalg.norm(h.cpu().numpy() - theta) / np.linalg.norm(theta)),
+                          "coef_rel_error_no_refinement": float(np.linalg.norm(h0.cpu().numpy() - theta)
+                                                                / np.linalg.norm(theta)),
+                          "cond_est_DGD": st["cond_est"], "rel_residual": st["rel_residual"]}
+        f.set_estimate_basis("monomial")
         executed = None
         if prec != "fp32":   # one 128 x 256 MMA per K step
             executed = 2.0 * n * 128 * 256
         out["single"][prec] = {"gram_ms": t_gram * 1e3, "gram_tflops_useful": useful / t_gram / 1e12,
                                "tensor_tflops_executed": (executed / t_gram / 1e12) if executed else None,
-                               "estimate_ms_3_refinements": t_est * 1e3, "coef_rel_error_vs_true": err,
-                               "cond_est_DGD": st["cond_est"], "rel_residual": st["rel_residual"]}
+                               "estimate": est}
     # batch: 256 antennas x 2^16 rows
     nb, nr = 256, 1 << 16
     us, ts, thetas = [], [], []
@@ -414,19 +421,25 @@ def measure_gram(dev, reps=5):
         thetas.append(thb)
     useful_b = 8.0 * nb * nr * K * K
     for prec in ("tf32x3", "bf16x3"):
-        f.estimate_batched(us, ts, precision=prec, refine_iters=0)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        f.estimate_batched(us, ts, precision=prec, refine_iters=0)   # Gram + FP64 Cholesky + solve, one launch each
-        t_b = time.perf_counter() - t0
-        hb, info = f.estimate_batched(us, ts, precision=prec, refine_iters=2)
-        hb = hb.cpu().numpy()
-        errs = [float(np.linalg.norm(hb[i] - thetas[i]) / np.linalg.norm(thetas[i])) for i in range(nb)]
-        out["batch"][prec] = {"problems": nb, "rows_each": nr, "gram_and_solve_ms": t_b * 1e3,
-                              "tflops_useful": useful_b / t_b / 1e12,
-                              "coef_rel_error_median_2_refinements": float(np.median(errs)),
-                              "coef_rel_error_max_2_refinements": float(np.max(errs)),
-                              "not_spd": int(sum(1 for i in info if i))}
+        out["batch"][prec] = {}
+        for basis in ("monomial", "orthogonal"):
+            f.set_estimate_basis(basis)
+            f.estimate_batched(us, ts, precision=prec, refine_iters=0)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            f.estimate_batched(us, ts, precision=prec, refine_iters=0)   # (basis,) Gram, FP64 Cholesky, solve
+            t_b = time.perf_counter() - t0
+            r = {"problems": nb, "rows_each": nr, "gram_and_solve_ms": t_b * 1e3,
+                 "tflops_useful": useful_b / t_b / 1e12}
+            for it in (0, 2):
+                hb, info = f.estimate_batched(us, ts, precision=prec, refine_iters=it)
+                hb = hb.cpu().numpy()
+                errs = [float(np.linalg.norm(hb[i] - thetas[i]) / np.linalg.norm(thetas[i])) for i in range(nb)]
+                r[f"coef_rel_error_median_{it}_refinements"] = float(np.median(errs))
+                r[f"coef_rel_error_max_{it}_refinements"] = float(np.max(errs))
+                r["not_spd"] = int(sum(1 for i in info if i))
+            out["batch"][prec][basis] = r
+        f.set_estimate_basis("monomial")
     peaks, kind = measured_peaks()
     bf = out["single"]["bf16x3"]
     bf["tensor_frac_of_bf16_peak"] = bf["tensor_tflops_executed"] / peaks.get("bf16_tflops", 1900.0)

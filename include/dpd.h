@@ -238,6 +238,26 @@ enum { DPD_PREC_FP32 = 0, DPD_PREC_TF32X3 = 1, DPD_PREC_BF16X3 = 2 };
 dpd_status dpd_gram(dpd_handle h, const void *u, const void *t, int64_t n, int precision, void *G, void *g,
                     double *tt, void *stream);
 
+/* Bases of the least-squares estimate. */
+enum { DPD_BASIS_MONOMIAL = 0, DPD_BASIS_ORTHOGONAL = 1 };
+
+/*
+ * Basis in which dpd_estimate and dpd_estimate_batched solve the least-squares
+ * problem (the handle's state; default DPD_BASIS_MONOMIAL).
+ *   DPD_BASIS_ORTHOGONAL : the statistically orthogonal polynomials of Sec. 2.1,
+ *       psi_p(x) = sum_{m <= p} u_{m,p} |x|^{m-1} x, with u_{m,p} computed from
+ *       the estimation input itself: the power sums of |u|^2 give the Gram
+ *       matrix of the monomials, whose Cholesky factor L yields U = L^{-T}
+ *       (FP64 on the host), so the basis functions are orthonormal over u.
+ *       Both branches and every tap use the same U.  The Gram matrix is
+ *       formed and solved in that basis (much better conditioned), and the
+ *       coefficients are converted back, h = W h_orth, so the output is always
+ *       in the monomial stacking order of Sec. 2.2 that dpd_set_coeffs takes.
+ *       One extra synchronisation per call (the power sums are read back).
+ * dpd_gram always uses the monomials.
+ */
+dpd_status dpd_set_estimate_basis(dpd_handle h, int basis);
+
 /*
  * Least-squares coefficients (Sec. 2.2): h = argmin ||Psi(u) h - t||_2, i.e.
  * (Psi^H Psi) h = Psi^H t.  The Gram matrix is formed in `precision`, the

@@ -18,6 +18,7 @@ from . import _lib
 from ._lib import DPDError, DPD_HOST, DPD_DEVICE, DPD_PREC_FP32, DPD_PREC_TF32X3, DPD_PREC_BF16X3  # noqa: F401
 
 PRECISIONS = {"fp32": DPD_PREC_FP32, "tf32x3": DPD_PREC_TF32X3, "bf16x3": DPD_PREC_BF16X3}
+BASES = {"monomial": _lib.DPD_BASIS_MONOMIAL, "orthogonal": _lib.DPD_BASIS_ORTHOGONAL}
 
 __all__ = ["DPD", "BatchedPlan", "DPDError", "num_coeffs", "kernel_launches", "lib"]
 
@@ -166,10 +167,17 @@ class DPD:
             ctypes.byref(tt) if (t is not None and want_tt) else None, _stream_ptr(stream)))
         return G, g, (tt.value if (t is not None and want_tt) else None)
 
-    def estimate(self, u, t, precision="tf32x3", refine_iters=2, stream=None):
-        """Least-squares coefficients (complex64 CUDA tensor of K) and stats
-        (condition estimate of the equilibrated Gram matrix, relative residual)."""
+    def set_estimate_basis(self, basis):
+        """Basis of the least-squares estimates: "monomial" or "orthogonal" (Sec. 2.1)."""
+        _lib.check("dpd_set_estimate_basis", self._lib.dpd_set_estimate_basis(self._h, BASES[basis]))
+
+    def estimate(self, u, t, precision="tf32x3", refine_iters=2, stream=None, basis=None):
+        """Least-squares coefficients (complex64 CUDA tensor of K, monomial stacking order) and
+        stats (condition estimate of the equilibrated Gram matrix of the basis used, relative
+        residual).  basis: "monomial" or "orthogonal" sets the handle's estimate basis first."""
         import torch
+        if basis is not None:
+            self.set_estimate_basis(basis)
         _check_samples(u, "u")
         _check_samples(t, "t")
         h = torch.empty(self.K, dtype=torch.complex64, device=u.device)
@@ -179,9 +187,11 @@ class DPD:
             PRECISIONS[precision], refine_iters, ctypes.c_void_p(h.data_ptr()), stats, _stream_ptr(stream)))
         return h, {"cond_est": stats[0], "rel_residual": stats[1]}
 
-    def estimate_batched(self, us, ts, precision="tf32x3", refine_iters=2, stream=None):
+    def estimate_batched(self, us, ts, precision="tf32x3", refine_iters=2, stream=None, basis=None):
         """Independent estimates for lists of (u, t); returns (count x K complex64 tensor, info list)."""
         import torch
+        if basis is not None:
+            self.set_estimate_basis(basis)
         if len(us) != len(ts) or not us:
             raise ValueError("us and ts must be non-empty lists of the same length")
         for u, t in zip(us, ts):

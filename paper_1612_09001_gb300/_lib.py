@@ -26,6 +26,7 @@ STATUS = {
 DPD_HOST, DPD_DEVICE = 0, 1
 DPD_PREC_FP32, DPD_PREC_TF32X3, DPD_PREC_BF16X3 = 0, 1, 2
 DPD_HOST_PIPELINED, DPD_HOST_ZERO_COPY = 0, 1
+DPD_BASIS_MONOMIAL, DPD_BASIS_ORTHOGONAL = 0, 1
 
 
 class DPDError(RuntimeError):
@@ -51,6 +52,7 @@ SIGNATURES = {
     "dpd_apply": [_vp, _vp, _vp, _i64, _vp],
     "dpd_apply_host": [_vp, _vp, _vp, _i64, _i, _vp],
     "dpd_apply_stream": [_vp, _vp, _vp, _i64, _vp],
+    "dpd_set_estimate_basis": [_vp, _i],
     "dpd_reset_stream": [_vp, _vp],
     "dpd_set_fwd_launch": [_vp, _i, _i, _i, _i, _i, _i],
     "dpd_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],

@@ -70,7 +70,12 @@ struct GramArgs {
     int Bp, Bq, T, K;
     float *partials;       // [nprob * cpp][kGramRows][kGramPartCols]
     int *status;
+    // Basis of the psi columns: per problem a kMaxB x kMaxB matrix U (row-major,
+    // U[a][b] multiplies |u|^{2a} u in basis function b, upper triangular), or
+    // null for the monomials |u|^{2b} u themselves.
+    const float *ubasis;
 };
+constexpr int kUSize = kMaxB * kMaxB;
 
 // Precision of the Gram contraction.
 enum : int { kPrecFP32 = 0, kPrecTF32x3 = 1, kPrecBF16x3 = 2 };
@@ -82,6 +87,17 @@ cudaError_t launch_gram_reduce(const float *partials, int nprob, int cpp, int D,
 // G (K x K, row-major), g (K) and t^H t per problem from S.
 cudaError_t launch_gram_assemble(const double *S, int nprob, int K, int Bp, int B, int T, double2 *G, double2 *g,
                                  double *tt, cudaStream_t s);
+// Power sums of r = |u|^2 per problem: mom[p][k - 1] = sum_n r_n^k, k = 1 .. 2 kMaxB - 1,
+// FP64 in a fixed order (part: nprob * kMomBlocks * kMomK doubles of scratch).
+constexpr int kMomK = 2 * kMaxB - 1;
+constexpr int kMomBlocks = 64;
+cudaError_t launch_moments(const GramProblem *probs, int nprob, double *part, double *mom, cudaStream_t s);
+// Coefficient vectors between the monomial basis and the basis U (both
+// branches, every tap; the constant unchanged), per problem:
+//   to_monomial: out = W in       (h = W h_U)
+//   otherwise:   out = W^T in     (g_U = W^T g for right-hand sides)
+cudaError_t launch_basis_transform(const double2 *in, double2 *out, const double *U, int nprob, int K, int Bp,
+                                   int Bq, int T, int to_monomial, cudaStream_t s);
 // CTAs per row chunk the launch wants for nprob problems of up to n rows.
 int gram_ctas_per_problem(int precision, int sm_count, int nprob, int64_t n);
 // Equilibrated Cholesky factorisation of every G: D G D = L L^H, D = diag(G)^{-1/2}.

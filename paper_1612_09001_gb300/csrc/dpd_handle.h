@@ -23,6 +23,12 @@ struct EstimateWorkspace {
     float *tab = nullptr;         // their forward table
     float2 *y = nullptr, *e = nullptr;
     double *norm_part = nullptr;  // 2 * 1024 partial sums + 2 results
+    // orthogonal-polynomial basis (DPD_BASIS_ORTHOGONAL)
+    float *ubasis = nullptr;      // [nprob][kUSize] basis coefficients used by the Gram kernels
+    double *ubasis64 = nullptr;   // the same values in FP64, for the coefficient transforms
+    double *mom = nullptr;        // [nprob][kMomK] power sums of |u|^2
+    double *mom_part = nullptr;   // [nprob][kMomBlocks][kMomK]
+    double2 *hm64 = nullptr;      // [nprob][K] monomial-basis coefficients / transformed right-hand sides
 };
 
 // Device staging of dpd_apply_host's copy / compute pipeline, created on first use.
@@ -52,7 +58,8 @@ struct dpd_filter {
     bool host_tab_valid;  // h_tab mirrors d_tab (coefficients were set from host memory)
     dpd::HostTab h_tab;
     dpd::FwdLaunch fwd;
-    bool fwd_auto = true;   // default launch shape: shrink the tile for short inputs (off once set explicitly)
+    bool fwd_auto = true;
+    int est_basis = 0;      // DPD_BASIS_MONOMIAL or DPD_BASIS_ORTHOGONAL (least-squares estimates)   // default launch shape: shrink the tile for short inputs (off once set explicitly)
     dpd::AdjLaunch adj;
     EstimateWorkspace est;
     HostPipeline host;

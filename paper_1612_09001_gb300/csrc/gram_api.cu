@@ -42,6 +42,9 @@ dpd_status reserve(dpd_handle h, int nprob, int cpp, int64_t nsamp)
         ok = ok && grow(w.d, 0, np * K) && grow(w.tt, 0, np) && grow(w.info, 0, np);
         ok = ok && grow(w.hf, 0, (size_t)K) && grow(w.tab, 0, (size_t)dpd::wl_table_floats(h->B, h->T));
         ok = ok && grow(w.norm_part, 0, (size_t)2 * 1024 + 2);
+        ok = ok && grow(w.ubasis, 0, np * dpd::kUSize) && grow(w.ubasis64, 0, np * dpd::kUSize);
+        ok = ok && grow(w.mom, 0, np * dpd::kMomK) && grow(w.mom_part, 0, np * dpd::kMomBlocks * dpd::kMomK);
+        ok = ok && grow(w.hm64, 0, np * K);
         if (!ok) return DPD_ERR_ALLOC;
         w.nprob = nprob;
         w.cpp = cpp;
@@ -56,6 +59,84 @@ dpd_status reserve(dpd_handle h, int nprob, int cpp, int64_t nsamp)
 }
 
 bool valid_precision(int p) { return p == DPD_PREC_FP32 || p == DPD_PREC_TF32X3 || p == DPD_PREC_BF16X3; }
+
+bool ortho(dpd_handle h) { return h->est_basis == DPD_BASIS_ORTHOGONAL; }
+
+// Basis of statistically orthogonal polynomials (Sec. 2.1) for every problem
+// in w.probs: with mu_k = sum_n r_n^k (r = |u|^2), the moment matrix
+// M[a][b] = mu_{a+b+1} / n is the Gram matrix of the monomials |u|^{2a} u;
+// M = L L^T (FP64 Cholesky on the host) and U = L^{-T} make
+// sum_a U[a][b] |u|^{2a} u orthonormal.  U is rounded to FP32 for the Gram
+// kernels and the same values are kept in FP64 for the coefficient
+// transforms.  A problem whose moment matrix is not positive definite keeps
+// the monomials (U = I).
+dpd_status compute_basis(dpd_handle h, const std::vector<int64_t> &n, cudaStream_t s)
+{
+    EstimateWorkspace &w = h->est;
+    const int nprob = (int)n.size(), B = h->B;
+    if (dpd::launch_moments(static_cast<const dpd::GramProblem *>(w.probs), nprob, w.mom_part, w.mom, s) !=
+        cudaSuccess)
+        return DPD_ERR_CUDA;
+    std::vector<double> mom((size_t)nprob * dpd::kMomK);
+    if (cudaMemcpyAsync(mom.data(), w.mom, sizeof(double) * mom.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return DPD_ERR_CUDA;
+    std::vector<float> uf((size_t)nprob * dpd::kUSize, 0.f);
+    std::vector<double> ud((size_t)nprob * dpd::kUSize, 0.0);
+    for (int p = 0; p < nprob; ++p) {
+        double M[dpd::kMaxB][dpd::kMaxB], L[dpd::kMaxB][dpd::kMaxB] = {}, U[dpd::kMaxB][dpd::kMaxB] = {};
+        for (int a = 0; a < B; ++a)
+            for (int b = 0; b < B; ++b) M[a][b] = mom[(size_t)p * dpd::kMomK + a + b] / (double)n[p];
+        bool spd = true;
+        for (int i = 0; i < B && spd; ++i)
+            for (int j = 0; j <= i; ++j) {
+                double v = M[i][j];
+                for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+                if (i == j) {
+                    if (!(v > 0.0) || !std::isfinite(v)) {
+                        spd = false;
+                        break;
+                    }
+                    L[i][i] = std::sqrt(v);
+                } else {
+                    L[i][j] = v / L[j][j];
+                }
+            }
+        if (spd) {   // U = L^{-T}: L^T U = I, solved column by column (back substitution)
+            for (int b = 0; b < B; ++b)
+                for (int a = B - 1; a >= 0; --a) {
+                    double v = a == b ? 1.0 : 0.0;
+                    for (int k = a + 1; k < B; ++k) v -= L[k][a] * U[k][b];
+                    U[a][b] = v / L[a][a];
+                }
+        }
+        for (int a = 0; a < dpd::kMaxB; ++a)
+            for (int b = 0; b < dpd::kMaxB; ++b) {
+                const double v = (a < B && b < B) ? (spd ? U[a][b] : (a == b ? 1.0 : 0.0)) : 0.0;
+                uf[(size_t)p * dpd::kUSize + a * dpd::kMaxB + b] = (float)v;
+                ud[(size_t)p * dpd::kUSize + a * dpd::kMaxB + b] = (double)(float)v;
+            }
+    }
+    if (cudaMemcpyAsync(w.ubasis, uf.data(), sizeof(float) * uf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(w.ubasis64, ud.data(), sizeof(double) * ud.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return DPD_ERR_CUDA;
+    return DPD_OK;
+}
+
+// FP64 coefficients of problems [p0, p0 + np) in the monomial basis (w.hm64).
+const double2 *monomial_h(dpd_handle h, int p0, int np, cudaStream_t s, dpd_status &st)
+{
+    EstimateWorkspace &w = h->est;
+    const size_t off = (size_t)p0 * h->K;
+    st = DPD_OK;
+    if (!ortho(h)) return w.h64 + off;
+    if (dpd::launch_basis_transform(w.h64 + off, w.hm64 + off, w.ubasis64 + (size_t)p0 * dpd::kUSize, np, h->K,
+                                    h->Bp, h->Bq, h->T, 1, s) != cudaSuccess)
+        st = DPD_ERR_CUDA;
+    return w.hm64 + off;
+}
 
 int gram_cpp(dpd_handle h, int nprob, int64_t n, int precision)
 {
@@ -76,6 +157,7 @@ dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_
     a.K = h->K;
     a.partials = w.partials;
     a.status = h->d_status;
+    a.ubasis = ortho(h) ? w.ubasis : nullptr;
     if (dpd::launch_gram(precision, a, s) != cudaSuccess) return DPD_ERR_CUDA;
     const int D = dpd::gram_distinct(h->B, h->T);
     if (dpd::launch_gram_reduce(w.partials, nprob, cpp, D, w.S, s) != cudaSuccess) return DPD_ERR_CUDA;
@@ -88,8 +170,10 @@ dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_
 dpd_status residual_of(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, cudaStream_t s)
 {
     EstimateWorkspace &w = h->est;
-    const int K = h->K;
-    if (dpd::launch_h_to_f32(w.h64 + (size_t)p * K, K, w.hf, s) != cudaSuccess) return DPD_ERR_CUDA;
+    dpd_status st = DPD_OK;
+    const double2 *hm = monomial_h(h, p, 1, s, st);
+    if (st != DPD_OK) return st;
+    if (dpd::launch_h_to_f32(hm, h->K, w.hf, s) != cudaSuccess) return DPD_ERR_CUDA;
     if (dpd::launch_wl_table(w.hf, h->Bp, h->Bq, h->T, w.tab, nullptr, s) != cudaSuccess) return DPD_ERR_CUDA;
     dpd::FwdArgs fa;
     fa.x = u;
@@ -132,7 +216,14 @@ dpd_status refine_once(dpd_handle h, int p, const float2 *u, const float2 *t, in
     if (al.gh_blocks < 1) al.gh_blocks = 1;
     if (dpd::launch_adj_any(h->B, aa, al, h->T, h->Bp, h->Bq, K, h->sm_count, s) != cudaSuccess) return DPD_ERR_CUDA;
     if (dpd::launch_adj_finalize64(h->d_partials, al.gh_blocks, K, w.delta, s) != cudaSuccess) return DPD_ERR_CUDA;
-    if (dpd::launch_chol_solve(w.L + (size_t)p * K * K, w.d + (size_t)p * K, w.info + p, w.delta, 1, K,
+    const double2 *rhs = w.delta;   // Psi^H (t - Psi h) in the monomial basis
+    if (ortho(h)) {                 // W^T of it, the right-hand side in the working basis
+        if (dpd::launch_basis_transform(w.delta, w.hm64 + (size_t)p * K, w.ubasis64 + (size_t)p * dpd::kUSize, 1,
+                                        K, h->Bp, h->Bq, h->T, 0, s) != cudaSuccess)
+            return DPD_ERR_CUDA;
+        rhs = w.hm64 + (size_t)p * K;
+    }
+    if (dpd::launch_chol_solve(w.L + (size_t)p * K * K, w.d + (size_t)p * K, w.info + p, rhs, 1, K,
                                w.h64 + (size_t)p * K, 1, s) != cudaSuccess)
         return DPD_ERR_CUDA;
     return DPD_OK;
@@ -256,10 +347,22 @@ void free_estimate_workspace(EstimateWorkspace &w)
     cudaFree(w.y);
     cudaFree(w.e);
     cudaFree(w.norm_part);
+    cudaFree(w.ubasis);
+    cudaFree(w.ubasis64);
+    cudaFree(w.mom);
+    cudaFree(w.mom_part);
+    cudaFree(w.hm64);
     w = EstimateWorkspace();
 }
 
 extern "C" {
+
+dpd_status dpd_set_estimate_basis(dpd_handle h, int basis)
+{
+    if (!h || (basis != DPD_BASIS_MONOMIAL && basis != DPD_BASIS_ORTHOGONAL)) return DPD_ERR_INVALID_ARGUMENT;
+    h->est_basis = basis;
+    return DPD_OK;
+}
 
 dpd_status dpd_gram(dpd_handle h, const void *u, const void *t, int64_t n, int precision, void *G, void *g,
                     double *tt, void *stream)
@@ -296,6 +399,7 @@ dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, i
     EstimateWorkspace &w = h->est;
     const dpd::GramProblem pr{static_cast<const float2 *>(u), static_cast<const float2 *>(t), n};
     if (cudaMemcpyAsync(w.probs, &pr, sizeof(pr), cudaMemcpyHostToDevice, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (ortho(h) && (st = compute_basis(h, std::vector<int64_t>{n}, s)) != DPD_OK) return st;
     if ((st = run_gram(h, 1, cpp, precision, s)) != DPD_OK) return st;
     if (dpd::launch_chol(w.G, 1, h->K, w.L, w.d, w.info, s) != cudaSuccess) return DPD_ERR_CUDA;
     if (dpd::launch_chol_solve(w.L, w.d, w.info, w.g, 1, h->K, w.h64, 0, s) != cudaSuccess) return DPD_ERR_CUDA;
@@ -306,7 +410,9 @@ dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, i
     if (info != 0) return DPD_ERR_NOT_SPD;
     for (int i = 0; i < refine_iters; ++i)
         if ((st = refine_once(h, 0, pr.u, pr.t, n, s)) != DPD_OK) return st;
-    if (dpd::launch_h_to_f32(w.h64, h->K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
+    const double2 *hm = monomial_h(h, 0, 1, s, st);
+    if (st != DPD_OK) return st;
+    if (dpd::launch_h_to_f32(hm, h->K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return DPD_ERR_CUDA;
     if (stats) return stats_of(h, 0, pr.u, pr.t, n, stats, s);
     return DPD_OK;
@@ -332,6 +438,7 @@ dpd_status dpd_estimate_batched(dpd_handle h, const void *const *u, const void *
     EstimateWorkspace &w = h->est;
     if (cudaMemcpy(w.probs, probs.data(), sizeof(dpd::GramProblem) * count, cudaMemcpyHostToDevice) != cudaSuccess)
         return DPD_ERR_CUDA;
+    if (ortho(h) && (st = compute_basis(h, std::vector<int64_t>(n, n + count), s)) != DPD_OK) return st;
     if ((st = run_gram(h, count, cpp, precision, s)) != DPD_OK) return st;
     if (dpd::launch_chol(w.G, count, h->K, w.L, w.d, w.info, s) != cudaSuccess) return DPD_ERR_CUDA;
     if (dpd::launch_chol_solve(w.L, w.d, w.info, w.g, count, h->K, w.h64, 0, s) != cudaSuccess) return DPD_ERR_CUDA;
@@ -344,7 +451,9 @@ dpd_status dpd_estimate_batched(dpd_handle h, const void *const *u, const void *
     for (int it = 0; it < refine_iters; ++it)
         for (int p = 0; p < count; ++p)
             if (info[p] == 0 && (st = refine_once(h, p, probs[p].u, probs[p].t, probs[p].n, s)) != DPD_OK) return st;
-    if (dpd::launch_h_to_f32(w.h64, count * h->K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
+    const double2 *hm = monomial_h(h, 0, count, s, st);
+    if (st != DPD_OK) return st;
+    if (dpd::launch_h_to_f32(hm, count * h->K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return DPD_ERR_CUDA;
     if (info_out) std::copy(info.begin(), info.end(), info_out);
     return any_bad ? DPD_ERR_NOT_SPD : DPD_OK;

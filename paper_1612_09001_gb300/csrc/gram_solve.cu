@@ -38,6 +38,93 @@ cudaError_t launch_gram_reduce(const float *partials, int nprob, int cpp, int D,
     return cudaGetLastError();
 }
 
+__global__ void moments_kernel(const GramProblem *__restrict__ probs, double *__restrict__ part)
+{
+    const GramProblem pr = probs[blockIdx.y];
+    double acc[kMomK];
+#pragma unroll
+    for (int k = 0; k < kMomK; ++k) acc[k] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pr.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 x = pr.u[i];
+        const float r = fmaf(x.x, x.x, x.y * x.y);
+        float p = r;
+#pragma unroll
+        for (int k = 0; k < kMomK; ++k) {
+            acc[k] += (double)p;
+            p *= r;
+        }
+    }
+    __shared__ double red[kMomK][256];
+#pragma unroll
+    for (int k = 0; k < kMomK; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int stride = blockDim.x / 2; stride > 0; stride >>= 1) {
+        if ((int)threadIdx.x < stride)
+#pragma unroll
+            for (int k = 0; k < kMomK; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + stride];
+        __syncthreads();
+    }
+    if (threadIdx.x < kMomK)
+        part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kMomK + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void moments_sum_kernel(const double *__restrict__ part, int blocks, double *__restrict__ mom)
+{
+    const int p = blockIdx.x, k = threadIdx.x;
+    if (k >= kMomK) return;
+    double s = 0.0;
+    for (int b = 0; b < blocks; ++b) s += part[((size_t)p * blocks + b) * kMomK + k];
+    mom[(size_t)p * kMomK + k] = s;
+}
+
+cudaError_t launch_moments(const GramProblem *probs, int nprob, double *part, double *mom, cudaStream_t s)
+{
+    moments_kernel<<<dim3(kMomBlocks, nprob), 256, 0, s>>>(probs, part);
+    count_launch();
+    moments_sum_kernel<<<nprob, 32, 0, s>>>(part, kMomBlocks, mom);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void basis_transform_kernel(const double2 *__restrict__ in, double2 *__restrict__ out,
+                                       const double *__restrict__ Uall, int K, int Bp, int Bq, int T, int to_monomial)
+{
+    const int p = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= K) return;
+    const double2 *x = in + (size_t)p * K;
+    const double *U = Uall + (size_t)p * kUSize;
+    double2 v;
+    if (j == K - 1) {
+        v = x[j];
+    } else {
+        const bool conj = j >= Bp * T;
+        const int base = conj ? Bp * T : 0, nb = conj ? Bq : Bp, jj = j - base, a = jj / T, k = jj % T;
+        v = make_double2(0.0, 0.0);
+        if (to_monomial) {   // h[(a, k)] = sum_{b >= a} U[a][b] h_U[(b, k)]
+            for (int b = a; b < nb; ++b) {
+                const double u = U[a * kMaxB + b];
+                v.x += u * x[base + b * T + k].x;
+                v.y += u * x[base + b * T + k].y;
+            }
+        } else {             // g_U[(a, k)] = sum_{c <= a} U[c][a] g[(c, k)]
+            for (int c = 0; c <= a; ++c) {
+                const double u = U[c * kMaxB + a];
+                v.x += u * x[base + c * T + k].x;
+                v.y += u * x[base + c * T + k].y;
+            }
+        }
+    }
+    out[(size_t)p * K + j] = v;
+}
+
+cudaError_t launch_basis_transform(const double2 *in, double2 *out, const double *U, int nprob, int K, int Bp,
+                                   int Bq, int T, int to_monomial, cudaStream_t s)
+{
+    basis_transform_kernel<<<dim3((K + 127) / 128, nprob), 128, 0, s>>>(in, out, U, K, Bp, Bq, T, to_monomial);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // <x, y> for two signed distinct-column references: S = P + Q + Q^T from the
 // summed blocks (P upper triangle in columns [0, kGramS), Q in [kGramS, 2 kGramS)).
 __device__ __forceinline__ double dot(const double *SPQ, ColRef x, ColRef y)

@@ -112,7 +112,7 @@ __device__ __forceinline__ void put_series(unsigned char *stg, int series, int w
 // Convert the raw samples of a stage (rows from n0) into the series arrays.
 template <int FMT, int R>
 __device__ __forceinline__ void stage_series(unsigned char *stg, const float2 *slot, int64_t n0, int64_t n, int B,
-                                             int T)
+                                             int T, const float *su)
 {
     const int tid = threadIdx.x;
     if (tid < kPsiThreads) {
@@ -121,8 +121,13 @@ __device__ __forceinline__ void stage_series(unsigned char *stg, const float2 *s
             const float2 u = slot[w];   // zero outside the problem
             const float r = fmaf(u.x, u.x, u.y * u.y);
             float p = 1.f;
-            for (int e = 0; e < b; ++e) p *= r;   // r^b, low order first as in the filter
-            put_series<FMT>(stg, 2 * b, w, p * u.x);   // psi_b = |u|^{2b} u
+            if (su) {   // sum_{a <= b} U[a][b] r^a by Horner's rule
+                p = su[b * kMaxB + b];
+                for (int a = b - 1; a >= 0; --a) p = fmaf(p, r, su[a * kMaxB + b]);
+            } else {
+                for (int e = 0; e < b; ++e) p *= r;   // r^b, low order first as in the filter
+            }
+            put_series<FMT>(stg, 2 * b, w, p * u.x);   // psi_b = |u|^{2b} u (or its combination)
             put_series<FMT>(stg, 2 * b + 1, w, p * u.y);
         }
     } else {
@@ -201,6 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a)
     uint64_t *acc_full = empty + kStages;
     uint64_t *fin = acc_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
+    float *su_buf = reinterpret_cast<float *>(tmem_slot + 4);   // basis coefficients U (kUSize)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int prob = blockIdx.x / a.cpp, chunk = blockIdx.x % a.cpp;
@@ -212,6 +218,11 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a)
     const int nits = (int)(b1 - b0);
     const int nchunks = (nits + kChunk - 1) / kChunk;
 
+    const float *su = nullptr;
+    if (a.ubasis) {
+        if (tid < kUSize) su_buf[tid] = a.ubasis[(size_t)prob * kUSize + tid];
+        su = su_buf;
+    }
     // Operand rows >= D are never written and stay zero.
     for (int i = tid; i < kStages * kStageBytes / 16; i += kThreads)
         reinterpret_cast<uint4 *>(stages)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -229,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a)
     for (int j = 0; j <= kAhead; ++j) fetch_stage<R>(raw + j * kRawLen, pr, (b0 + j) * R, T, j < nits);
     cp_async_wait<kAhead>();   // stage 0 has landed (this thread's copies)
     __syncthreads();
-    if (nits > 0) stage_series<FMT, R>(staging, raw, b0 * R, pr.n, B, T);
+    if (nits > 0) stage_series<FMT, R>(staging, raw, b0 * R, pr.n, B, T, su);
     fence_async_shared();
     tc_fence_before_sync();
     __syncthreads();
@@ -363,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a)
         }
         if (it + 1 < nits)
             stage_series<FMT, R>(staging + ((it + 1) & 1) * kStagingBytes, raw + ((it + 1) % kRawSlots) * kRawLen,
-                                 n0 + R, pr.n, B, T);
+                                 n0 + R, pr.n, B, T, su);
         fence_async_shared();
         // Drain every chunk whose last stage was consumed kStages stages ago:
         // its MMAs are complete (this stage's empty wait saw them).  A failed
@@ -407,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a)
 size_t gram_tc_smem()
 {
     return 1024 + (size_t)kStages * kStageBytes + 2 * (size_t)kStagingBytes + (size_t)kRawSlots * kRawLen * 8 +
-           (kStages + 3) * 8 + 16;
+           (kStages + 3) * 8 + 16 + kUSize * 4;
 }
 
 // ------------------------------------------------------------------ FP32 CUDA cores
@@ -420,7 +431,8 @@ constexpr int kF32Threads = 96;   // >= 13 * 14 / 2 = 91 diagonal-and-upper 8 x 
 
 // Fill psi[b][w] = |u|^{2b} u for samples n0 - (T-1) + w (zero outside [0, n)) and tv[rr] = t.
 template <int R>
-__device__ __forceinline__ void stage_basis(const GramProblem &pr, int64_t n0, int T, int B, float2 *psi, float2 *tv)
+__device__ __forceinline__ void stage_basis(const GramProblem &pr, int64_t n0, int T, int B, float2 *psi, float2 *tv,
+                                            const float *su)
 {
     const int W = R + T - 1;
     for (int i = threadIdx.x; i < W * B; i += blockDim.x) {
@@ -431,7 +443,12 @@ __device__ __forceinline__ void stage_basis(const GramProblem &pr, int64_t n0, i
             const float2 x = pr.u[j];
             const float r = fmaf(x.x, x.x, x.y * x.y);
             float p = 1.f;
-            for (int e = 0; e < bb; ++e) p *= r;
+            if (su) {   // sum_{a <= bb} U[a][bb] r^a by Horner's rule
+                p = su[bb * kMaxB + bb];
+                for (int a2 = bb - 1; a2 >= 0; --a2) p = fmaf(p, r, su[a2 * kMaxB + bb]);
+            } else {
+                for (int e = 0; e < bb; ++e) p *= r;
+            }
             v = make_float2(p * x.x, p * x.y);
         }
         psi[bb * kPsiStride + w] = v;
@@ -464,6 +481,7 @@ __global__ void __launch_bounds__(kF32Threads) gram_fp32_kernel(GramArgs a)
     float *Atile = reinterpret_cast<float *>(smem_f);                           // [kF32Rows][kF32Stride]
     float2 *psi = reinterpret_cast<float2 *>(Atile + kF32Rows * kF32Stride);  // [kMaxB][kPsiStride]
     float2 *tv = psi + kMaxB * kPsiStride;
+    float *su_buf = reinterpret_cast<float *>(tv + 64);   // basis coefficients U (kUSize)
 
     const int tid = threadIdx.x;
     const int prob = blockIdx.x / a.cpp, chunk = blockIdx.x % a.cpp;
@@ -471,6 +489,11 @@ __global__ void __launch_bounds__(kF32Threads) gram_fp32_kernel(GramArgs a)
     const int T = a.T, B = a.Bp > a.Bq ? a.Bp : a.Bq;
     const int D = gram_distinct(B, T);
     const int nb8 = (D + 7) / 8;
+    const float *su = nullptr;
+    if (a.ubasis) {
+        for (int i = tid; i < kUSize; i += kF32Threads) su_buf[i] = a.ubasis[(size_t)prob * kUSize + i];
+        su = su_buf;   // read after the first __syncthreads of the row loop
+    }
     // block (I, J) of this thread: enumerate the upper triangle row by row
     int I = -1, J = -1;
     {
@@ -496,7 +519,7 @@ __global__ void __launch_bounds__(kF32Threads) gram_fp32_kernel(GramArgs a)
     for (int64_t blk = b0; blk < b1; ++blk) {
         const int64_t n0 = blk * kF32Rows;
         __syncthreads();
-        stage_basis<kF32Rows>(pr, n0, T, B, psi, tv);
+        stage_basis<kF32Rows>(pr, n0, T, B, psi, tv, su);
         __syncthreads();
         for (int e = tid; e < kF32Rows * kF32Stride; e += kF32Threads) {
             const int rr = e / kF32Stride, d = e % kF32Stride;
@@ -531,7 +554,7 @@ __global__ void __launch_bounds__(kF32Threads) gram_fp32_kernel(GramArgs a)
     }
 }
 
-size_t gram_fp32_smem() { return (size_t)kF32Rows * kF32Stride * 4 + (kMaxB * kPsiStride + 64) * 8; }
+size_t gram_fp32_smem() { return (size_t)kF32Rows * kF32Stride * 4 + (kMaxB * kPsiStride + 64) * 8 + kUSize * 4; }
 
 int gram_ctas_per_problem(int precision, int sm_count, int nprob, int64_t n)
 {
