@@ -54,7 +54,7 @@ def parse():
                     help="skip the batched / adjoint / Gram side measurements")
     ap.add_argument("--fwd-launch", default=None, metavar="MODE,V,WARPS,STAGES",
                     help="fix the forward launch shape instead of tuning it (profiling runs)")
-    ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "gram"], default=None,
+    ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "gram", "ila"], default=None,
                     help="run only this side measurement (1 GPU) and print its JSON; for profiling")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up for at least this long so clocks settle and get sampled")
@@ -276,6 +276,42 @@ def measure_small(dev, calls=200):
     return {"workload": "2^16 clipped Gaussian (RMS 0.3), P=Q=5, M=2 (K=19), L2-resident",
             "us_per_call_plain": t_plain, "us_per_call_graph": t_graph,
             "gsamples_per_s_graph": n / (t_graph * 1e-6) / 1e9, "calls": calls}
+
+
+def measure_ila(dev, n=1 << 20):
+    """Indirect learning (Sec. 2.2) around the Eq. 3 WARP PA on LTE-like signals
+    (one 10 MHz carrier; two 3 MHz carriers 10 MHz apart; 4x oversampled, RMS 0.2):
+    time per ILA iteration and out-of-band suppression (the paper's Fig. 8 test)."""
+    import torch
+    import dpd_synth as synth
+    import paper_1612_09001_gb300 as dpd
+    from paper_1612_09001_gb300 import direct, spectrum
+    P, Q, M = 7, 3, 1
+    tx, G = direct.warp_pa_transmitter(device=dev)
+    out = {"model": f"DPD P={P} Q={Q} M={M}; PA of Eq. 3; 3 ILA iterations, TF32x3, orthogonal basis",
+           "signals": {}}
+    for name, gen in (("10MHz_single", synth.lte_single), ("2x3MHz_noncontiguous", synth.lte_two)):
+        x, band = gen(n, key=(8, 0), rms=0.2)
+        xd = torch.from_numpy(x).to(dev)
+        direct.ila_train(xd, tx, P, Q, M, gain=G, iterations=1, precision="tf32x3", basis="orthogonal")
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h, hist = direct.ila_train(xd, tx, P, Q, M, gain=G, iterations=3, precision="tf32x3", basis="orthogonal")
+        torch.cuda.synchronize(dev)
+        t_ila = (time.perf_counter() - t0) / 3
+        f = dpd.DPD(P, Q, M)
+        f.set_coeffs(h)
+        y_plain = (tx.apply(xd) / G).cpu().numpy()
+        y_dpd = (tx.apply(f.apply(xd)) / G).cpu().numpy()
+        f.close()
+        rep = spectrum.suppression_report(x, y_plain, y_dpd, band)
+        out["signals"][name] = {"samples": n, "ms_per_ila_iteration": t_ila * 1e3,
+                                "nmse_db_per_iteration": [r["nmse_db_before"] for r in hist],
+                                "oob_total_dbc": {k: rep[k]["oob_total_dbc"] for k in ("input", "no_dpd", "dpd")},
+                                "oob_peak_dbc": {k: rep[k]["oob_peak_dbc"] for k in ("input", "no_dpd", "dpd")},
+                                "suppression_total_db": rep["suppression_total_db"],
+                                "suppression_peak_db": rep["suppression_peak_db"]}
+    return out
 
 
 def measure_batched(dev, reps=20):
@@ -617,6 +653,7 @@ def run_ours(args, world, rank, local):
         patterns["small_2p16"] = measure_small(dev)
         patterns["adjoint"] = measure_direct(dev)
         patterns["gram"] = measure_gram(dev)
+        patterns["ila_spectral"] = measure_ila(dev)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -653,7 +690,7 @@ def main():
         dev = torch.device("cuda", local)
         torch.cuda.set_device(dev)
         fn = {"small": measure_small, "batched": measure_batched, "adjoint": measure_direct,
-              "gram": measure_gram}[args.pattern]
+              "gram": measure_gram, "ila": measure_ila}[args.pattern]
         print(json.dumps({"pattern": args.pattern, "result": fn(dev)}, default=float))
         return 0
     return run_ours(args, world, rank, local)

@@ -87,6 +87,42 @@ def ofdm2(n: int, key=(0, 0), rms: float = 0.25, shift: float = 0.3) -> np.ndarr
     return z.astype(np.complex64)
 
 
+# LTE-like uplink test signals for the spectral-suppression experiment (the
+# paper's 10 MHz carrier and two non-contiguous 3 MHz carriers 10 MHz apart).
+# The spectrum is built for the whole sequence at once (QPSK on the occupied
+# subcarriers of one long FFT, 15 kHz spacing at a 61.44 MHz sample rate, i.e.
+# four times oversampled) so the input itself has no out-of-band power and the
+# PA's spectral regrowth stays inside the band.  Each generator returns the
+# samples (complex64, scaled to the RMS) and the in-band bins of a 4096-point
+# spectrum.
+LTE_NFFT = 4096
+
+
+def _banded(g: np.random.Generator, n: int, centres, half: int, rms: float):
+    N = -(-n // LTE_NFFT) * LTE_NFFT
+    scale = N // LTE_NFFT
+    spec = np.zeros(N, dtype=np.complex128)
+    band = np.zeros(LTE_NFFT, bool)
+    for c in centres:
+        k = c * scale + np.arange(-half * scale, half * scale + 1)
+        spec[k % N] = ((2 * g.integers(0, 2, k.size) - 1) + 1j * (2 * g.integers(0, 2, k.size) - 1)) / math.sqrt(2.0)
+        band[(c + np.arange(-half, half + 1)) % LTE_NFFT] = True
+    z = np.fft.ifft(spec)[:n]
+    z *= rms / math.sqrt(np.mean(np.abs(z) ** 2))
+    return z.astype(np.complex64), band
+
+
+def lte_single(n: int, key=(0, 0), rms: float = 0.2):
+    """One 10 MHz carrier: 600 subcarriers around DC."""
+    return _banded(_rng(key), n, (0,), 300, rms)
+
+
+def lte_two(n: int, key=(0, 0), rms: float = 0.2):
+    """Two 3 MHz carriers (180 subcarriers each) centred 10 MHz apart
+    (+-5 MHz = +-333 subcarriers)."""
+    return _banded(_rng(key), n, (333, -333), 90, rms)
+
+
 def coeffs(P: int, Q: int, M: int, key=(0, 1), f_std=1e-2, g_std=1e-3,
            c=1e-3 * (1 + 1j)) -> np.ndarray:
     """Coefficient vector in the paper's stacking order.

@@ -124,11 +124,37 @@ class DirectLearner:
 
 def indirect_learning(x, tx, P, Q, M, gain=1.0, iterations=3, precision="tf32x3", refine_iters=2):
     """ILA (Sec. 2.2): returns the coefficient vector after `iterations` LS fits."""
+    return ila_train(x, tx, P, Q, M, gain, iterations, precision, refine_iters)[0]
+
+
+def ila_train(x, tx, P, Q, M, gain=1.0, iterations=3, precision="tf32x3", refine_iters=2, basis="monomial"):
+    """The indirect-learning loop of Sec. 2.2 / Fig. 1(b), every step on the GPU.
+    Iteration i: z = DPD^(i-1)(x) (x itself first), s = TX(z) / G, and the
+    post-distorter fit h^(i) = argmin ||Psi(s) h - z|| (dpd_estimate), which
+    becomes the predistorter.  Returns (h, history) with, per iteration, the
+    NMSE of TX(DPD(x)) / G against x before the fit and the condition estimate
+    and relative residual of the fit."""
     est = DPD(P, Q, M)
+    est.set_estimate_basis(basis)
     h = None
-    for _ in range(iterations):
+    history = []
+    for i in range(iterations):
         z = x if h is None else est.apply(x)
         s = tx.apply(z) / gain
-        h, _ = est.estimate(s.contiguous(), z.contiguous(), precision=precision, refine_iters=refine_iters)
+        rec = {"iteration": i + 1, "nmse_db_before": nmse_db(s, x)}
+        h, st = est.estimate(s.contiguous(), z.contiguous(), precision=precision, refine_iters=refine_iters)
         est.set_coeffs(h)
-    return h
+        rec.update(st)
+        history.append(rec)
+    history.append({"iteration": iterations + 1, "nmse_db_before": nmse_db(tx.apply(est.apply(x)) / gain, x)})
+    est.close()
+    return h, history
+
+
+def warp_pa_transmitter(device="cuda"):
+    """The memoryless 5th-order WARP PA of Eq. 3 as a one-stage transmitter
+    (an APH filter with P = 5, Q = 0, M = 0 and coefficients alpha_1, alpha_3,
+    alpha_5); its small-signal gain is alpha_1."""
+    alpha = [0.9490 - 0.0197j, 0.4885 + 0.1071j, -1.0156 - 0.0474j]   # Eq. 3
+    st = dict(P=5, Q=0, M=0, h=alpha + [0.0])
+    return Transmitter([st], device=device), alpha[0]
