@@ -54,7 +54,7 @@ def parse():
                     help="skip the batched / adjoint / Gram side measurements")
     ap.add_argument("--fwd-launch", default=None, metavar="MODE,V,WARPS,STAGES",
                     help="fix the forward launch shape instead of tuning it (profiling runs)")
-    ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "gram", "ila"], default=None,
+    ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "gram", "ila", "cpu"], default=None,
                     help="run only this side measurement (1 GPU) and print its JSON; for profiling")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up for at least this long so clocks settle and get sampled")
@@ -311,6 +311,34 @@ def measure_ila(dev, n=1 << 20):
                                 "oob_peak_dbc": {k: rep[k]["oob_peak_dbc"] for k in ("input", "no_dpd", "dpd")},
                                 "suppression_total_db": rep["suppression_total_db"],
                                 "suppression_peak_db": rep["suppression_peak_db"]}
+    return out
+
+
+def measure_cpu_simd(n=1 << 24):
+    """The portable SIMD + OpenMP CPU filter on the host cores (a like-for-like
+    CPU comparison, not the oracle): the benchmark workload and the paper's
+    Table 2 model (P=5, Q=3, L=5) on 1, 4 and all threads."""
+    import numpy as np
+    import dpd_synth as synth
+    from paper_1612_09001_gb300 import build, cpu
+    build.build_cpu()
+    x = synth.ofdm2(n, key=(0, 0))
+    y = np.empty_like(x)
+    out = {"host_threads": cpu.max_threads(), "samples": n, "dtype": "f32", "results": {}}
+    for name, (P, Q, M) in (("P9_Q9_M4", (9, 9, 4)), ("table2_P5_Q3_L5", (5, 3, 4))):
+        h = synth.coeffs(P, Q, M, key=(0, 1))
+        r = {}
+        for th in sorted({1, 4, cpu.max_threads()}):
+            cpu.apply(x[: 1 << 16], h, P, Q, M, threads=th, out=y[: 1 << 16])
+            reps, t0 = 0, time.perf_counter()
+            while True:
+                cpu.apply(x, h, P, Q, M, threads=th, out=y)
+                reps += 1
+                el = time.perf_counter() - t0
+                if el > 1.0 or reps >= 20:
+                    break
+            r[f"{th}_threads_gsamples_per_s"] = reps * n / el / 1e9
+        out["results"][name] = r
     return out
 
 
@@ -654,6 +682,8 @@ def run_ours(args, world, rank, local):
         patterns["adjoint"] = measure_direct(dev)
         patterns["gram"] = measure_gram(dev)
         patterns["ila_spectral"] = measure_ila(dev)
+        if world == 1:
+            patterns["cpu_simd"] = measure_cpu_simd()
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -685,12 +715,15 @@ def main():
     world, rank, local = dist_init()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.pattern == "cpu":
+        print(json.dumps({"pattern": "cpu", "result": measure_cpu_simd()}))
+        return 0
     if args.pattern:
         import torch
         dev = torch.device("cuda", local)
         torch.cuda.set_device(dev)
         fn = {"small": measure_small, "batched": measure_batched, "adjoint": measure_direct,
-              "gram": measure_gram, "ila": measure_ila}[args.pattern]
+              "gram": measure_gram, "ila": measure_ila, "cpu": lambda d: measure_cpu_simd()}[args.pattern]
         print(json.dumps({"pattern": args.pattern, "result": fn(dev)}, default=float))
         return 0
     return run_ours(args, world, rank, local)

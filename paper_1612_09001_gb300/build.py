@@ -1,9 +1,12 @@
-"""Build libdpd.so in-tree with nvcc for sm_103a.
+"""Build libdpd.so in-tree with nvcc for sm_103a, and the portable CPU
+library libdpd_cpu.so with the host C compiler.
 
 Each translation unit under ``csrc/`` is compiled to an object file in
 ``_build/`` (in parallel, skipped when up to date), then linked into
 ``lib/libdpd.so``.  The CUDA runtime is linked statically, so the library only
-needs the driver at run time.
+needs the driver at run time.  ``cpu/dpd_cpu.c`` becomes ``lib/libdpd_cpu.so``
+(C11, OpenMP, GCC vector extensions; no architecture flags, so the same source
+builds on x86-64 and AArch64).
 """
 from __future__ import annotations
 
@@ -19,6 +22,8 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "lib")
 LIB_PATH = os.path.join(LIB_DIR, "libdpd.so")
+CPU_SRC = os.path.join(HERE, "cpu", "dpd_cpu.c")
+CPU_LIB_PATH = os.path.join(LIB_DIR, "libdpd_cpu.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -63,6 +68,22 @@ def _compile(src, verbose_ptxas=False):
     return obj, r.stderr
 
 
+def build_cpu(force: bool = False) -> str:
+    """lib/libdpd_cpu.so from cpu/dpd_cpu.c with the host C compiler."""
+    os.makedirs(LIB_DIR, exist_ok=True)
+    deps = [CPU_SRC, os.path.join(INCLUDE, "dpd_cpu.h")]
+    if force or _stale(CPU_LIB_PATH, deps):
+        cc = os.environ.get("CC", "gcc")
+        tmp = CPU_LIB_PATH + f".tmp{os.getpid()}"
+        cmd = [cc, "-O3", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=fast", "-Wall",
+               "-o", tmp, CPU_SRC]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"{cc} failed for {CPU_SRC}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, CPU_LIB_PATH)
+    return CPU_LIB_PATH
+
+
 def build(jobs: int | None = None, verbose_ptxas: bool = False, force: bool = False) -> str:
     os.makedirs(OBJ_DIR, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
@@ -93,3 +114,4 @@ def build(jobs: int | None = None, verbose_ptxas: bool = False, force: bool = Fa
 if __name__ == "__main__":
     v = "-v" in sys.argv
     print(build(verbose_ptxas=v, force="--force" in sys.argv), file=sys.stderr)
+    print(build_cpu(force="--force" in sys.argv), file=sys.stderr)
