@@ -30,6 +30,16 @@ def test_binding_covers_header():
     assert set(header_functions()) == set(_lib.SIGNATURES)
 
 
+def test_cpu_library_exports_its_header():
+    from paper_1612_09001_gb300 import cpu
+    build.build_cpu()
+    names = header_functions("dpd_cpu.h")
+    assert set(names) == {"dpd_cpu_apply", "dpd_cpu_max_threads"}
+    lib = cpu.load()
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/dpd_cpu.h but not exported"
+
+
 def test_status_strings(lib):
     for code, name in _lib.STATUS.items():
         assert lib.dpd_status_string(code).decode() == name

@@ -32,12 +32,13 @@ def assert_parity(got, ref, tol=TOL, what=""):
     assert emax <= tol * max(scale, 1e-30), f"{what}: max element error {emax:.3e} > {tol:.0e} * {scale:.3e}"
 
 
-def header_functions():
-    """Names of the functions declared in include/*.h."""
+def header_functions(header="dpd.h"):
+    """Names of the functions declared in include/<header> (the GPU library's
+    dpd.h by default; dpd_cpu.h is the CPU library's)."""
     names = []
     inc = os.path.join(ROOT, "include")
     for fn in sorted(os.listdir(inc)):
-        if not fn.endswith(".h"):
+        if fn != header:
             continue
         src = open(os.path.join(inc, fn)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
