@@ -196,6 +196,19 @@ dpd_status dpd_apply_stream(dpd_handle h, const void *x, void *y, int64_t n, voi
 dpd_status dpd_reset_stream(dpd_handle h, void *stream);
 
 /*
+ * Direct-learning loss and its gradient in one pass (not in the paper, whose
+ * coefficients are found by indirect learning, Sec. 2.2):
+ *   loss[0] = scale * sum_n |y_n - g x_n|^2            (FP64 sum, fixed order, stored as float)
+ *   gy[n]   = 2 scale (y_n - g x_n)  (dL/dRe + j dL/dIm), when gy is non-null
+ * with g = gain_re + j gain_im.  y, x, gy: device complex64 (n each, 8-byte
+ * aligned; gy must not overlap x or y); loss: one device float.  Uses the
+ * handle's scratch, so calls on one handle must be ordered on one stream.
+ * Allocation-free and capturable.
+ */
+dpd_status dpd_sq_error(dpd_handle h, const void *y, const void *x, int64_t n, float gain_re, float gain_im,
+                        double scale, float *loss, void *gy, void *stream);
+
+/*
  * Launch shape of dpd_apply for this handle (used by the autotuner):
  *   mode        bit 0: coefficients passed by value as kernel parameters (used
  *               only after dpd_set_coeffs from host memory; otherwise ignored);

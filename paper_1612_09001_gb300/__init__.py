@@ -105,6 +105,7 @@ class DPD:
         h = h.contiguous()
         where = DPD_DEVICE if h.is_cuda else DPD_HOST
         self._coef_ref = h   # keep a device source alive until the kernel that reads it has run
+        self._installed = None   # autograd's record of the installed tensor
         _lib.check("dpd_set_coeffs", self._lib.dpd_set_coeffs(
             self._h, ctypes.c_void_p(h.data_ptr()), self.K, where, _stream_ptr(stream)))
 
@@ -227,6 +228,25 @@ class DPD:
             self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.numel(),
             _stream_ptr(stream)))
         return out
+
+    def sq_error(self, y, x, gain=1.0, scale=1.0, loss=None, gy=None, stream=None):
+        """loss = scale * sum |y - gain x|^2 (one-element float32 CUDA tensor) and, when gy
+        is given, gy = 2 scale (y - gain x); one pass on the device (dpd_sq_error)."""
+        import torch
+        _check_samples(y, "y")
+        _check_samples(x, "x")
+        if y.numel() != x.numel():
+            raise ValueError("y and x must have the same length")
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=y.device)
+        if gy is not None:
+            _check_samples(gy, "gy")
+        g = complex(gain)
+        _lib.check("dpd_sq_error", self._lib.dpd_sq_error(
+            self._h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()), y.numel(), g.real, g.imag,
+            float(scale), ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(gy.data_ptr() if gy is not None else None),
+            _stream_ptr(stream)))
+        return loss
 
     def reset_stream(self, stream=None):
         _lib.check("dpd_reset_stream", self._lib.dpd_reset_stream(self._h, _stream_ptr(stream)))

@@ -17,10 +17,20 @@ class DPDFunction(torch.autograd.Function):
     ``DPD`` handle of the right (P, Q, M); x and h complex64 CUDA tensors."""
 
     @staticmethod
+    def _install(filt: DPD, h):
+        """set_coeffs unless h (same tensor, unchanged since) is already installed:
+        fixed stages (a transmitter model) then cost no table rebuild per call.
+        A tensor modified in place bumps its version and is installed again."""
+        key = (id(h), h.data_ptr(), h._version)
+        if getattr(filt, "_installed", None) != key:
+            filt.set_coeffs(h)
+            filt._installed = key
+
+    @staticmethod
     def forward(ctx, x, h, filt: DPD):
         _check_samples(x, "x")
         _check_samples(h, "h")
-        filt.set_coeffs(h)
+        DPDFunction._install(filt, h)
         y = filt.apply(x)
         ctx.save_for_backward(x, h)
         ctx.filt = filt
@@ -35,7 +45,7 @@ class DPDFunction(torch.autograd.Function):
         gx = torch.empty_like(x) if need_x else None
         gh = torch.empty_like(h) if need_h else None
         if need_x:
-            filt.set_coeffs(h)
+            DPDFunction._install(filt, h)
         if need_x or need_h:
             filt.grad(x, gy, gh=gh, gx=gx)
         return gx, gh, None

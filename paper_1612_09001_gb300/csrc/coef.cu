@@ -58,23 +58,45 @@ cudaError_t launch_wl_table(const float2 *h, int Bp, int Bq, int T, float *tab, 
     return cudaGetLastError();
 }
 
+// One block per coefficient: thread t sums rows t, t + 256, ... in order, then a
+// fixed shared-memory tree combines the 256 sums (deterministic, FP64).
 __global__ void adj_finalize_kernel(const float2 *__restrict__ partials, int rows, int K,
-                                    float2 *__restrict__ gh)
+                                    float2 *__restrict__ gh, double2 *__restrict__ gh64)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= K) return;
+    const int i = blockIdx.x, t = threadIdx.x;
     double re = 0.0, im = 0.0;
-    for (int r = 0; r < rows; ++r) {
+    for (int r = t; r < rows; r += 256) {
         const float2 v = partials[(size_t)r * K + i];
         re += v.x;
         im += v.y;
     }
-    gh[i] = make_float2((float)re, (float)im);
+    __shared__ double sre[256], sim[256];
+    sre[t] = re;
+    sim[t] = im;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) {
+            sre[t] += sre[t + w];
+            sim[t] += sim[t + w];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (gh) gh[i] = make_float2((float)sre[0], (float)sim[0]);
+        if (gh64) gh64[i] = make_double2(sre[0], sim[0]);
+    }
 }
 
 cudaError_t launch_adj_finalize(const float2 *partials, int rows, int K, float2 *gh, cudaStream_t s)
 {
-    adj_finalize_kernel<<<(K + 127) / 128, 128, 0, s>>>(partials, rows, K, gh);
+    adj_finalize_kernel<<<K, 256, 0, s>>>(partials, rows, K, gh, nullptr);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_finalize64(const float2 *partials, int rows, int K, double2 *out, cudaStream_t s)
+{
+    adj_finalize_kernel<<<K, 256, 0, s>>>(partials, rows, K, nullptr, out);
     count_launch();
     return cudaGetLastError();
 }

@@ -128,12 +128,14 @@ dpd_status dpd_create(int P, int Q, int M, dpd_handle *out)
     f->d_adj_tab = nullptr;
     f->d_partials = nullptr;
     f->d_hist = nullptr;
+    f->d_loss_part = nullptr;
     if (cudaMalloc(&f->d_h, sizeof(float2) * f->K) != cudaSuccess ||
         cudaMalloc(&f->d_tab, sizeof(float) * dpd::wl_table_floats(f->B, f->T)) != cudaSuccess ||
         cudaMalloc(&f->d_adj_tab, sizeof(float) * dpd::adj_table_floats(f->B, f->T)) != cudaSuccess ||
         cudaMalloc(&f->d_partials, sizeof(float2) * (size_t)f->rows_max * f->K) != cudaSuccess ||
         cudaMalloc(&f->d_status, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&f->d_hist, sizeof(float2) * dpd::kHalo) != cudaSuccess) {
+        cudaMalloc(&f->d_hist, sizeof(float2) * dpd::kHalo) != cudaSuccess ||
+        cudaMalloc(&f->d_loss_part, sizeof(double) * dpd::kLossBlocks) != cudaSuccess) {
         dpd_destroy(f);
         return DPD_ERR_ALLOC;
     }
@@ -155,6 +157,7 @@ dpd_status dpd_destroy(dpd_handle h)
     cudaFree(h->d_partials);
     cudaFree(h->d_status);
     cudaFree(h->d_hist);
+    cudaFree(h->d_loss_part);
     free_estimate_workspace(h->est);
     free_host_pipeline(h->host);
     delete h;
@@ -481,6 +484,20 @@ dpd_status dpd_apply_stream(dpd_handle h, const void *x, void *y, int64_t n, voi
     if (st != DPD_OK) return st;
     return cuda_status(dpd::launch_stream_head(h->d_tab, h->B, h->T, static_cast<const float2 *>(x), n, h->d_hist,
                                                static_cast<float2 *>(y), static_cast<cudaStream_t>(stream)));
+}
+
+dpd_status dpd_sq_error(dpd_handle h, const void *y, const void *x, int64_t n, float gain_re, float gain_im,
+                        double scale, float *loss, void *gy, void *stream)
+{
+    if (!h || n < 0 || !loss || !aligned(loss, 4)) return DPD_ERR_INVALID_ARGUMENT;
+    if (n > 0 && (!y || !x || !aligned(y, 8) || !aligned(x, 8))) return DPD_ERR_INVALID_ARGUMENT;
+    if (n > (int64_t)(INT64_MAX / sizeof(float2))) return DPD_ERR_INVALID_ARGUMENT;
+    const size_t bytes = (size_t)n * sizeof(float2);
+    if (gy && (!aligned(gy, 8) || overlap(gy, bytes, x, bytes) || overlap(gy, bytes, y, bytes)))
+        return DPD_ERR_INVALID_ARGUMENT;
+    return cuda_status(dpd::launch_sq_error(static_cast<const float2 *>(y), static_cast<const float2 *>(x), n,
+                                            make_float2(gain_re, gain_im), scale, h->d_loss_part, loss,
+                                            static_cast<float2 *>(gy), static_cast<cudaStream_t>(stream)));
 }
 
 dpd_status dpd_reset_stream(dpd_handle h, void *stream)

@@ -51,6 +51,7 @@ struct dpd_filter {
     float *d_tab;     // widely-linear table for the forward kernels
     int *d_status;    // kernel error word
     float2 *d_hist;   // streaming history: the kHalo input samples before the next dpd_apply_stream
+    double *d_loss_part;   // dpd_sq_error: per-block FP64 partial sums (kLossBlocks)
     float *d_adj_tab; // adjoint (derivative-polynomial) table
     float2 *d_partials;  // coefficient-gradient workspace: rows_max x K complex
     int rows_max;
@@ -70,6 +71,10 @@ void free_host_pipeline(HostPipeline &p);
 
 
 namespace dpd {
+constexpr int kLossBlocks = 296;   // 2 per SM at 148-152 SMs
+// loss[0] = (float)(scale * sum |y - g x|^2) (FP64 sum, fixed order); gy = 2 scale (y - g x) if non-null.
+cudaError_t launch_sq_error(const float2 *y, const float2 *x, int64_t n, float2 g, double scale, double *part,
+                            float *loss, float2 *gy, cudaStream_t s);
 // Streaming head: recompute y[0 .. min(T-1, n)) with the kHalo samples in hist
 // as the history before x[0] (the forward kernels assume zero history), then
 // hist <- the last kHalo samples of (hist ++ x).  One warp; runs after the

@@ -394,24 +394,4 @@ cudaError_t launch_sqnorm2(const float2 *e, const float2 *t, int64_t n, double *
     return cudaGetLastError();
 }
 
-__global__ void adj_finalize64_kernel(const float2 *__restrict__ partials, int rows, int K, double2 *__restrict__ out)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= K) return;
-    double re = 0.0, im = 0.0;
-    for (int r = 0; r < rows; ++r) {
-        const float2 v = partials[(size_t)r * K + i];
-        re += v.x;
-        im += v.y;
-    }
-    out[i] = make_double2(re, im);
-}
-
-cudaError_t launch_adj_finalize64(const float2 *partials, int rows, int K, double2 *out, cudaStream_t s)
-{
-    adj_finalize64_kernel<<<(K + 127) / 128, 128, 0, s>>>(partials, rows, K, out);
-    count_launch();
-    return cudaGetLastError();
-}
-
 }  // namespace dpd

@@ -52,4 +52,53 @@ cudaError_t launch_stream_head(const float *tab, int B, int T, const float2 *x, 
     return cudaGetLastError();
 }
 
+// Squared-error loss of direct learning and its gradient in one pass: each
+// block sums |e|^2 (FP32 products, FP64 sums) over a grid-stride range and
+// combines its threads with a fixed shared-memory tree; one more block adds the
+// block sums in order.
+__global__ void sq_error_kernel(const float2 *__restrict__ y, const float2 *__restrict__ x, int64_t n, float2 g,
+                                double scale, double *__restrict__ part, float2 *__restrict__ gy)
+{
+    const float s2 = (float)(2.0 * scale);
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 a = x[i], b = y[i];
+        const float er = b.x - (g.x * a.x - g.y * a.y), ei = b.y - (g.x * a.y + g.y * a.x);
+        acc += (double)(er * er + ei * ei);
+        if (gy) gy[i] = make_float2(s2 * er, s2 * ei);
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void sq_error_sum_kernel(const double *__restrict__ part, int blocks, double scale, float *loss)
+{
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < blocks; b += 256) acc += part[b];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss[0] = (float)(scale * red[0]);
+}
+
+cudaError_t launch_sq_error(const float2 *y, const float2 *x, int64_t n, float2 g, double scale, double *part,
+                            float *loss, float2 *gy, cudaStream_t s)
+{
+    sq_error_kernel<<<kLossBlocks, 256, 0, s>>>(y, x, n, g, scale, part, gy);
+    count_launch();
+    sq_error_sum_kernel<<<1, 256, 0, s>>>(part, kLossBlocks, scale, loss);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace dpd

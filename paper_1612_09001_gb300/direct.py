@@ -27,6 +27,23 @@ from . import DPD
 from .autograd import DPDFunction
 
 
+class SqErrorLoss(torch.autograd.Function):
+    """L = scale * ||y - gain x||^2 with its gradient produced in the same device
+    pass (dpd_sq_error); backward scales the saved gradient by dL."""
+
+    @staticmethod
+    def forward(ctx, y, x, filt, gain, scale):
+        gy = torch.empty_like(y)
+        loss = filt.sq_error(y, x, gain=gain, scale=scale, gy=gy)
+        ctx.save_for_backward(gy)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, gl):
+        (gy,) = ctx.saved_tensors
+        return gy * gl, None, None, None, None
+
+
 class Transmitter:
     """A chain of fixed APH filter stages, each given as dict(P, Q, M, h)."""
 
@@ -62,16 +79,28 @@ class DirectLearner:
         if h0 is None:
             h0 = torch.zeros(self.filt.K, dtype=torch.complex64, device=x.device)
             h0[0] = 1.0   # start from the identity predistorter
-        self.h = torch.nn.Parameter(h0.clone().contiguous())
+        # The parameter is the real view (K x 2) of h: Adam treats complex
+        # parameters as their real views anyway, and real ones can use the
+        # single-kernel (fused) implementation.
+        self.param = torch.nn.Parameter(torch.view_as_real(h0.clone().contiguous()).clone())
         self.gain = gain
         self.scale = 1.0 / float(x.abs().pow(2).sum())
-        self.opt = torch.optim.Adam([self.h], lr=lr, capturable=True)
+        self.opt = torch.optim.Adam([self.param], lr=lr, capturable=True, fused=True)
         self.graph = None
         self.static_loss = None
 
+    @property
+    def h(self):
+        """The predistorter coefficients (complex view of the parameter)."""
+        return torch.view_as_complex(self.param)
+
+    def h_grad(self):
+        """Gradient of the last loss with respect to h (complex, dL/dRe + j dL/dIm)."""
+        return torch.view_as_complex(self.param.grad)
+
     def loss(self):
         y = self.tx(DPDFunction.apply(self.x, self.h, self.filt))
-        return torch.view_as_real(y - self.gain * self.x).pow(2).sum() * self.scale
+        return SqErrorLoss.apply(y, self.x, self.filt, self.gain, self.scale)
 
     def _step(self):
         self.opt.zero_grad(set_to_none=False)
