@@ -26,7 +26,7 @@ CACHE = os.environ.get("DPD_TUNE_CACHE", os.path.join(os.path.expanduser("~"), "
 
 FWD_CANDIDATES = [dict(mode=m, V=V, warps=w, stages=s, ctas_per_sm=c, use_tma=1)
                   for m in (3, 2) for V in (8, 4) for w in (4, 8, 12) for s in (3, 4) for c in (0,)]
-BATCH_CANDIDATES = [(V, w, s, c) for V in (8, 4) for w in (4, 8) for s in (3, 4) for c in (0,)]
+BATCH_CANDIDATES = [(V, w, s, c) for V in (8, 4) for w in (4, 8, 12) for s in (2, 3, 4) for c in (0,)]
 
 
 def _time(fn, reps=5, inner=5):
