@@ -19,26 +19,30 @@ __global__ void wl_table_kernel(const float2 *__restrict__ h, int Bp, int Bq, in
         tab[wl_index(B, k, m, 2)] = A.y + C.y;      // P2 = Im(A+C)
         tab[wl_index(B, k, m, 3)] = A.x - C.x;      // P3 = Re(A-C)
         if (adj) {
+            // Per tap: for each power m the quadruple {Q0, Q3, Q1, Q2} of the
+            // bracket conj(E) g + H conj(g) = {Q0 c + Q1 d, Q2 c + Q3 d}
+            // (g = c + j d), then for each m < B-1 the quadruple {S0, S3, S1, S2}
+            // of conj(G) g + F conj(g): the pairs {Q0, Q3}, {Q1, Q2} multiply
+            // {c, d} and {d, c} in packed f32x2 FMAs.
             const int per_tap = 4 * B + 4 * (B - 1);
             float *q = adj + per_tap * k;
             // E_m = (m+1) h_m, H_m = (m+1) hbar_m  (coefficients of r^m)
             const float s = (float)(m + 1);
             const float Er = s * A.x, Ei = s * A.y, Hr = s * C.x, Hi = s * C.y;
-            q[0 * B + m] = Er + Hr;
-            q[1 * B + m] = Ei + Hi;
-            q[2 * B + m] = Hi - Ei;
-            q[3 * B + m] = Er - Hr;
+            q[4 * m + 0] = Er + Hr;   // Q0
+            q[4 * m + 1] = Er - Hr;   // Q3
+            q[4 * m + 2] = Ei + Hi;   // Q1
+            q[4 * m + 3] = Hi - Ei;   // Q2
             if (m < B - 1) {
                 // F_m = (m+1) h_{m+1}, G_m = (m+1) hbar_{m+1}
                 const float2 A1 = (m + 1 < Bp) ? h[(m + 1) * T + k] : make_float2(0.f, 0.f);
                 const float2 C1 = (m + 1 < Bq) ? h[(Bp + m + 1) * T + k] : make_float2(0.f, 0.f);
                 const float Fr = s * A1.x, Fi = s * A1.y, Gr = s * C1.x, Gi = s * C1.y;
                 float *r = q + 4 * B;
-                const int RB = B - 1;
-                r[0 * RB + m] = Gr + Fr;
-                r[1 * RB + m] = Gi + Fi;
-                r[2 * RB + m] = Fi - Gi;
-                r[3 * RB + m] = Gr - Fr;
+                r[4 * m + 0] = Gr + Fr;   // S0
+                r[4 * m + 1] = Gr - Fr;   // S3
+                r[4 * m + 2] = Gi + Fi;   // S1
+                r[4 * m + 3] = Fi - Gi;   // S2
             }
         }
     }

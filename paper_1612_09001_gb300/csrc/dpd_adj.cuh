@@ -12,14 +12,22 @@
 //   gx_i = sum_k conj(dy_{i+k}/dx_i) gy_{i+k} + (dy_{i+k}/dconj(x_i)) conj(gy_{i+k})
 //        = sum_k [conj(E_k) g + H_k conj(g)] + x_i^2 [conj(G_k) g + F_k conj(g)],  g = gy_{i+k}
 // Each bracket is widely linear in g, so it is evaluated like the forward
-// filter: four real Horner polynomials per bracket (table built by
-// adj_table_kernel).  The coefficient gradient is the correlation
+// filter: four real Horner polynomials per bracket, run as two packed f32x2
+// Horner chains whose results multiply the window sample {c, d} and its swap
+// {d, c} (table built by wl_table_kernel, one float4 per power).  The coefficient gradient is the correlation
 //   gh_{(p,k)} = sum_j r_j^b conj(x_j) gy_{j+k},  gh_{(q,k)} = sum_j r_j^b x_j gy_{j+k},
 //   gh_c = sum_n gy_n,
 // i.e. conj(Psi)^T gy with the basis matrix Psi of Eq. 2, accumulated per
 // thread, reduced per CTA in a fixed order into a partials workspace and summed
 // over CTAs in FP64 by adj_finalize_kernel.  The basis is recomputed from x:
 // nothing from the forward pass is stored.
+//
+// Data movement.  For 16-byte aligned x and gy both gradients run as persistent
+// kernels fed like the forward filter: one producer thread streams tiles of x
+// and of gy (plus kHalo samples of look-ahead) into a ring of shared-memory
+// slots with bulk copies completed on mbarriers, and the consumer warps read
+// their windows from shared memory.  Other alignments (and callers without an
+// error word) use the plain-load kernels, which read through L1.
 #pragma once
 
 #include "dpd_device.cuh"
@@ -27,228 +35,574 @@
 
 namespace dpd {
 
+constexpr int kAdjV = 4;          // samples per thread (plain-load kernels, staged gx)
+constexpr int kAdjGhV = 4;        // samples per thread of the staged gh kernel
+constexpr int kAdjWarps = 8;      // consumer warps of the staged kernels
+constexpr int kAdjStages = 4;     // ring slots of the staged gx kernel
+constexpr int kAdjGhStages = 4;   // ring slots of the staged gh kernel
+
+// NS consecutive complex samples p[base .. base+NS-1] (zero past n).  When the
+// buffer is 16-byte aligned, base is even and the rounded-up window lies inside
+// the buffer, they are fetched as float4 pairs; otherwise sample by sample.
+template <int NS>
+__device__ __forceinline__ void adj_load_window(const float2 *__restrict__ p, int64_t base, int64_t n,
+                                                bool vec, float2 (&out)[NS])
+{
+    constexpr int NV = (NS + 1) / 2;
+    if (vec && (base & 1) == 0 && base + 2 * NV <= n) {
+        const float4 *q = reinterpret_cast<const float4 *>(p + base);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            const float4 t = __ldg(q + j);
+            out[2 * j] = make_float2(t.x, t.y);
+            if (2 * j + 1 < NS) out[2 * j + 1] = make_float2(t.z, t.w);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) out[j] = base + j < n ? __ldg(p + base + j) : make_float2(0.f, 0.f);
+    }
+}
+
+// NS samples of a shared-memory slot from element `off`: float4 pairs when off
+// is even (the slot holds the rounded-up window), else one by one.
+template <int NS>
+__device__ __forceinline__ void adj_slot_window(const float2 *slot, int off, float2 (&out)[NS])
+{
+    if ((off & 1) == 0) {
+        const float4 *q = reinterpret_cast<const float4 *>(slot + off);
+#pragma unroll
+        for (int j = 0; j < (NS + 1) / 2; ++j) {
+            const float4 t = q[j];
+            out[2 * j] = make_float2(t.x, t.y);
+            if (2 * j + 1 < NS) out[2 * j + 1] = make_float2(t.z, t.w);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) out[j] = slot[off + j];
+    }
+}
+
+// ---------------------------------------------------------------- staged tiles
+// A slot holds x[s0, s0 + S) and, from element S on, gy[s0, s0 + S + kHalo);
+// near the end of the signal only the even-length prefix that exists is copied.
+__host__ __device__ constexpr int adj_slot_elems(int S) { return 2 * S + kHalo; }
+
+__device__ __forceinline__ void adj_slot_counts(int64_t s0, int S, int64_t n, int &xc, int &gc)
+{
+    const int64_t rem = n - s0;
+    xc = (int)((rem < S ? rem : (int64_t)S) & ~int64_t(1));
+    gc = (int)((rem < S + kHalo ? rem : (int64_t)(S + kHalo)) & ~int64_t(1));
+}
+
+// NS samples of `src` from global index `g` whose slot copy starts at element
+// `base` of the slot and holds `cnt` samples from global index s0.
+template <int NS>
+__device__ __forceinline__ void adj_slot_window_tail(const float2 *slot_part, int64_t s0, int cnt,
+                                                     const float2 *__restrict__ src, int64_t g, int64_t n,
+                                                     float2 (&out)[NS])
+{
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        const int64_t gj = g + j;
+        float2 v = make_float2(0.f, 0.f);
+        if (gj - s0 < cnt)
+            v = slot_part[gj - s0];
+        else if (gj < n)
+            v = __ldg(src + gj);
+        out[j] = v;
+    }
+}
+
+// The producer thread: stream every tile of this CTA into the ring.  Waits are
+// bounded; after a failed wait the copies already issued are allowed to land
+// before returning.
+__device__ __forceinline__ void adj_produce(const AdjArgs &a, float2 *ring, uint64_t *bars, int stages, int S,
+                                            int64_t ntiles)
+{
+    const int slot_elems = adj_slot_elems(S);
+    int64_t it = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int s = (int)(it % stages);
+        const uint32_t ph = (uint32_t)((it / stages) & 1);
+        if (it >= stages && !mbar_wait(smem_addr(&bars[stages + s]), ph ^ 1u, a.status)) {
+            ok = false;
+            break;
+        }
+        const int64_t s0 = tile * S;
+        int xc, gc;
+        adj_slot_counts(s0, S, a.n, xc, gc);
+        const uint32_t fb = smem_addr(&bars[s]);
+        mbar_arrive_expect_tx(fb, (uint32_t)(xc + gc) * (uint32_t)sizeof(float2));
+        float2 *slot = ring + (size_t)s * slot_elems;
+        if (xc) bulk_copy_g2s(smem_addr(slot), a.x + s0, (uint32_t)xc * sizeof(float2), fb);
+        if (gc) bulk_copy_g2s(smem_addr(slot + S), a.gy + s0, (uint32_t)gc * sizeof(float2), fb);
+    }
+    if (!ok) {
+        const int64_t first = it > stages ? it - stages : 0;
+        for (int64_t j = first; j < it; ++j)
+            mbar_wait(smem_addr(&bars[j % stages]), (uint32_t)((j / stages) & 1), a.status);
+    }
+}
+
+// Shared-memory bytes of a staged kernel: barriers, reduction scratch, ring.
+__host__ __device__ constexpr size_t adj_staged_smem(int S, int stages, int scratch_floats)
+{
+    return 128 + (((size_t)scratch_floats * 4 + 127) / 128) * 128 +
+           (size_t)stages * (size_t)adj_slot_elems(S) * sizeof(float2);
+}
+
 // ---------------------------------------------------------------- input gradient
+// gx for the V samples i0.. from their x (xs) and the gy window g (samples
+// i0 .. i0 + V + T - 2).  tab: the adjoint table of one model (shared memory).
+template <int B, int T, int V>
+__device__ __forceinline__ void gx_compute(const float *tab, const float2 (&xs)[V],
+                                           const float2 (&g)[V + T - 1], float2 (&acc)[V])
+{
+    constexpr int QB = B, RB = B - 1;       // coefficients per Q / S polynomial
+    constexpr int PER_TAP = 4 * QB + 4 * RB;
+    constexpr int W = V + T - 1;
+    float2 gs[W];   // window samples swapped: {d, c}
+#pragma unroll
+    for (int j = 0; j < W; ++j) gs[j] = make_float2(g[j].y, g[j].x);
+    float ur[V], ui[V], rr[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const float2 q = xs[v];
+        rr[v] = fmaf(q.x, q.x, q.y * q.y);
+        ur[v] = fmaf(q.x, q.x, -q.y * q.y);   // x^2
+        ui[v] = 2.f * q.x * q.y;
+    }
+    // {Re, Im} of the gradient of each sample, and of the tap sum of the second
+    // bracket (its factor x^2 does not depend on the tap, so it is applied once
+    // after the tap loop).  Every tap advances all V samples together with
+    // packed f32x2 FMAs (coefficient pairs adjacent in the table).
+    float2 ws[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        acc[v] = make_float2(0.f, 0.f);
+        ws[v] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+        const float4 *cq = reinterpret_cast<const float4 *>(tab + PER_TAP * k);
+        float2 pa[V], pb[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            pa[v] = make_float2(cq[QB - 1].x, cq[QB - 1].y);
+            pb[v] = make_float2(cq[QB - 1].z, cq[QB - 1].w);
+        }
+#pragma unroll
+        for (int m = QB - 2; m >= 0; --m) {
+            const float4 c4 = cq[m];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float2 rr2 = make_float2(rr[v], rr[v]);
+                pa[v] = __ffma2_rn(pa[v], rr2, make_float2(c4.x, c4.y));
+                pb[v] = __ffma2_rn(pb[v], rr2, make_float2(c4.z, c4.w));
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            acc[v] = __ffma2_rn(pa[v], g[v + k], acc[v]);    // {Q0 c, Q3 d}
+            acc[v] = __ffma2_rn(pb[v], gs[v + k], acc[v]);   // {Q1 d, Q2 c}
+        }
+        if constexpr (RB > 0) {
+            const float4 *cs = cq + QB;
+            float2 sa[V], sb[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                sa[v] = make_float2(cs[RB - 1].x, cs[RB - 1].y);
+                sb[v] = make_float2(cs[RB - 1].z, cs[RB - 1].w);
+            }
+#pragma unroll
+            for (int m = RB - 2; m >= 0; --m) {
+                const float4 c4 = cs[m];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const float2 rr2 = make_float2(rr[v], rr[v]);
+                    sa[v] = __ffma2_rn(sa[v], rr2, make_float2(c4.x, c4.y));
+                    sb[v] = __ffma2_rn(sb[v], rr2, make_float2(c4.z, c4.w));
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                // conj(G) g + F conj(g) = {S0 c + S1 d, S2 c + S3 d}
+                ws[v] = __ffma2_rn(sa[v], g[v + k], ws[v]);    // {S0 c, S3 d}
+                ws[v] = __ffma2_rn(sb[v], gs[v + k], ws[v]);   // {S1 d, S2 c}
+            }
+        }
+    }
+    if constexpr (RB > 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            // acc += x^2 ws (complex):  {ur wr - ui wi, ur wi + ui wr}
+            acc[v] = __ffma2_rn(make_float2(ur[v], ur[v]), ws[v], acc[v]);
+            acc[v] = __ffma2_rn(make_float2(-ui[v], ui[v]), make_float2(ws[v].y, ws[v].x), acc[v]);
+        }
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void gx_store(float2 *__restrict__ gx, int64_t i0, int64_t n, bool vec,
+                                         const float2 (&acc)[V], bool streaming)
+{
+    if (vec && i0 + V <= n) {
+        float4 *o = reinterpret_cast<float4 *>(gx + i0);
+#pragma unroll
+        for (int j = 0; j < V / 2; ++j) {
+            const float4 q = make_float4(acc[2 * j].x, acc[2 * j].y, acc[2 * j + 1].x, acc[2 * j + 1].y);
+            if (streaming)
+                st_stream_f4(o + j, q);
+            else
+                o[j] = q;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if (i0 + v < n) gx[i0 + v] = acc[v];
+    }
+}
+
+template <int B, int T>
+__host__ __device__ constexpr int adj_tab_padded() { return ((adj_table_floats(B, T) + 3) / 4) * 4; }
+
+// Plain-load variant (any 8-byte alignment): grid-stride over V-sample runs.
 template <int B, int T, int V>
 __global__ void __launch_bounds__(256) adj_gx_kernel(AdjArgs a)
 {
     constexpr int W = V + T - 1;            // gy window: samples i0 .. i0 + V + T - 2
-    constexpr int QB = B, RB = B - 1;       // coefficients per Q / R polynomial
-    constexpr int PER_TAP = 4 * QB + 4 * RB;
-    constexpr int TABF = PER_TAP * T;
-    __shared__ __align__(16) float tab[((TABF + 3) / 4) * 4 + 4];
+    constexpr int TABF = adj_table_floats(B, T);
+    __shared__ __align__(16) float tab[adj_tab_padded<B, T>()];
     for (int i = threadIdx.x; i < TABF; i += blockDim.x) tab[i] = a.adj_tab[i];
     __syncthreads();
 
+    static_assert(V % 2 == 0, "V samples are stored as float4 pairs");
+    const bool vec_in = ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.gy)) & 15) == 0;
+    const bool vec_out = (reinterpret_cast<uintptr_t>(a.gx) & 15) == 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * V;
     for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V; i0 < a.n; i0 += stride) {
-        float xr[V], xi[V], ur[V], ui[V], rr[V];
-        float gr[W], gi[W];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            float2 q = make_float2(0.f, 0.f);
-            if (i0 + v < a.n) q = __ldg(a.x + i0 + v);
-            xr[v] = q.x;
-            xi[v] = q.y;
-            rr[v] = fmaf(q.x, q.x, q.y * q.y);
-            ur[v] = fmaf(q.x, q.x, -q.y * q.y);   // x^2
-            ui[v] = 2.f * q.x * q.y;
+        float2 xs[V], g[W], acc[V];
+        adj_load_window<V>(a.x, i0, a.n, vec_in, xs);
+        adj_load_window<W>(a.gy, i0, a.n, vec_in, g);
+        gx_compute<B, T, V>(tab, xs, g, acc);
+        gx_store<V>(a.gx, i0, a.n, vec_out, acc, false);
+    }
+}
+
+// Staged variant: persistent CTAs of kAdjWarps consumer warps + 1 producer warp
+// walk tiles of S = kAdjWarps * 32 * V samples.  x and gy 16-byte aligned.
+template <int B, int T, int V>
+__global__ void __launch_bounds__(32 * (kAdjWarps + 1)) adj_gx_tma_kernel(AdjArgs a, int stages, int64_t ntiles)
+{
+    constexpr int W = V + T - 1;
+    constexpr int TABF = adj_table_floats(B, T);
+    constexpr int S = kAdjWarps * 32 * V;
+    static_assert(T - 1 <= kHalo, "look-ahead must fit the slot");
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);   // full[s], empty[s]
+    float *tab = reinterpret_cast<float *>(smem + 128);
+    float2 *ring = reinterpret_cast<float2 *>(smem + adj_staged_smem(S, 0, adj_tab_padded<B, T>()));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(smem_addr(&bars[s]), 1);
+            mbar_init(smem_addr(&bars[stages + s]), kAdjWarps);
         }
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            float2 q = make_float2(0.f, 0.f);
-            if (i0 + j < a.n) q = __ldg(a.gy + i0 + j);
-            gr[j] = q.x;
-            gi[j] = q.y;
+        fence_barrier_init();
+    }
+    for (int i = tid; i < TABF; i += blockDim.x) tab[i] = a.adj_tab[i];
+    __syncthreads();
+    if (warp == kAdjWarps) {
+        if (lane == 0) adj_produce(a, ring, bars, stages, S, ntiles);
+        return;
+    }
+    const bool vec_out = (reinterpret_cast<uintptr_t>(a.gx) & 15) == 0;
+    const int slot_elems = adj_slot_elems(S);
+    int64_t it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int s = (int)(it % stages);
+        if (!mbar_wait(smem_addr(&bars[s]), (uint32_t)((it / stages) & 1), a.status)) return;
+        const float2 *slot = ring + (size_t)s * slot_elems;
+        const int64_t s0 = tile * S;
+        const int off = tid * V;
+        const bool full = s0 + S + kHalo <= a.n;
+        float2 xs[V], g[W];
+        if (full) {
+            adj_slot_window<V>(slot, off, xs);
+            adj_slot_window<W>(slot + S, off, g);
+        } else {
+            int xc, gc;
+            adj_slot_counts(s0, S, a.n, xc, gc);
+            adj_slot_window_tail<V>(slot, s0, xc, a.x, s0 + off, a.n, xs);
+            adj_slot_window_tail<W>(slot + S, s0, gc, a.gy, s0 + off, a.n, g);
         }
-        float oR[V], oI[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            oR[v] = 0.f;
-            oI[v] = 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < T; ++k) {
-            const float *tk = tab + PER_TAP * k;
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const float c = gr[v + k], d = gi[v + k], r = rr[v];
-                float q0 = tk[0 * QB + QB - 1], q1 = tk[1 * QB + QB - 1];
-                float q2 = tk[2 * QB + QB - 1], q3 = tk[3 * QB + QB - 1];
-#pragma unroll
-                for (int m = QB - 2; m >= 0; --m) {
-                    q0 = fmaf(q0, r, tk[0 * QB + m]);
-                    q1 = fmaf(q1, r, tk[1 * QB + m]);
-                    q2 = fmaf(q2, r, tk[2 * QB + m]);
-                    q3 = fmaf(q3, r, tk[3 * QB + m]);
-                }
-                oR[v] = fmaf(q0, c, oR[v]);
-                oR[v] = fmaf(q1, d, oR[v]);
-                oI[v] = fmaf(q2, c, oI[v]);
-                oI[v] = fmaf(q3, d, oI[v]);
-                if constexpr (RB > 0) {
-                    const float *rk = tk + 4 * QB;
-                    float s0 = rk[0 * RB + RB - 1], s1 = rk[1 * RB + RB - 1];
-                    float s2 = rk[2 * RB + RB - 1], s3 = rk[3 * RB + RB - 1];
-#pragma unroll
-                    for (int m = RB - 2; m >= 0; --m) {
-                        s0 = fmaf(s0, r, rk[0 * RB + m]);
-                        s1 = fmaf(s1, r, rk[1 * RB + m]);
-                        s2 = fmaf(s2, r, rk[2 * RB + m]);
-                        s3 = fmaf(s3, r, rk[3 * RB + m]);
-                    }
-                    const float wr = fmaf(s0, c, s1 * d);   // conj(G) g + F conj(g)
-                    const float wi = fmaf(s2, c, s3 * d);
-                    oR[v] = fmaf(ur[v], wr, oR[v]);
-                    oR[v] = fmaf(-ui[v], wi, oR[v]);
-                    oI[v] = fmaf(ur[v], wi, oI[v]);
-                    oI[v] = fmaf(ui[v], wr, oI[v]);
-                }
-            }
-        }
-        (void)xr;
-        (void)xi;
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-            if (i0 + v < a.n) a.gx[i0 + v] = make_float2(oR[v], oI[v]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));
+        float2 acc[V];
+        gx_compute<B, T, V>(tab, xs, g, acc);
+        gx_store<V>(a.gx, s0 + off, a.n, vec_out, acc, true);
     }
 }
 
 // ---------------------------------------------------------------- coefficient gradient
-// Grid (blocks, tap groups): group g owns taps [g*TG, g*TG + TG) of every branch;
-// group 0 also owns the LO-leakage term.  Each CTA writes one row of partials
-// (K complex), only at the indices of its group.
+// Tap groups: group y owns taps [y*TG, y*TG + TG) of every branch; group 0 also
+// owns the LO-leakage term.  Each CTA writes one row of partials (K complex),
+// only at the indices of its group.
+//
+// With a_b = r^b Re x, c_b = r^b Im x and g = gy_{j+k} = c + j d, both branches
+// follow from two packed correlations per (b, k):
+//   X_{b,k} = sum_j {a_b, c_b}_j * {c, d},   Y_{b,k} = sum_j {a_b, c_b}_j * {d, c},
+//   main  sum r^b conj(x) g = {X.x + X.y, Y.x - Y.y},
+//   conj  sum r^b x g       = {X.x - X.y, Y.x + Y.y},
+// so every (sample, b, tap) costs two packed f32x2 FMAs whose operands are the
+// packed power {a_b, c_b} and the window sample as stored or swapped (once per
+// window sample): no per-product broadcasts.  Accumulators per thread:
+// [b*TG + kk] X, [B*TG + b*TG + kk] Y, last sum g (for c).
 template <int B, int TG, int V>
-__global__ void __launch_bounds__(256) adj_gh_kernel(AdjArgs a, int T, int Bp, int Bq, int K)
+__device__ __forceinline__ void gh_accumulate(const float2 (&xs)[V], const float2 (&g)[V + TG - 1], bool group0,
+                                              float2 (&acc2)[2 * B * TG + 1])
 {
-    constexpr int NA = 4 * B * TG + 2;   // main + conj accumulators (complex) + c
-    const int k0 = blockIdx.y * TG;
-    float acc[NA];
+    constexpr int NP = 2 * B * TG + 1;
+    constexpr int NG = V + TG - 1;
+    if (group0) {
 #pragma unroll
-    for (int i = 0; i < NA; ++i) acc[i] = 0.f;
-
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * V;
-    for (int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V; j0 < a.n; j0 += stride) {
-        float xr[V], xi[V], gr[V + TG - 1], gi[V + TG - 1];
+        for (int v = 0; v < V; ++v)   // the gy window starts at the sample itself for group 0
+            acc2[NP - 1] = __fadd2_rn(acc2[NP - 1], g[v]);
+    }
+    float2 gs[NG];
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            float2 q = make_float2(0.f, 0.f);
-            if (j0 + v < a.n) q = __ldg(a.x + j0 + v);
-            xr[v] = q.x;
-            xi[v] = q.y;
-        }
+    for (int j = 0; j < NG; ++j) gs[j] = make_float2(g[j].y, g[j].x);
 #pragma unroll
-        for (int j = 0; j < V + TG - 1; ++j) {
-            float2 q = make_float2(0.f, 0.f);
-            const int64_t g = j0 + k0 + j;
-            if (g < a.n) q = __ldg(a.gy + g);
-            gr[j] = q.x;
-            gi[j] = q.y;
-        }
-        if (blockIdx.y == 0) {
+    for (int v = 0; v < V; ++v) {
+        const float r = fmaf(xs[v].x, xs[v].x, xs[v].y * xs[v].y);
+        float2 p = xs[v];   // {a_b, c_b}
 #pragma unroll
-            for (int v = 0; v < V; ++v) {   // gy window starts at j0 for group 0
-                acc[NA - 2] += gr[v];
-                acc[NA - 1] += gi[v];
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const float r = fmaf(xr[v], xr[v], xi[v] * xi[v]);
+        for (int b = 0; b < B; ++b) {
+            if (b > 0) p = __fmul2_rn(p, make_float2(r, r));
 #pragma unroll
             for (int kk = 0; kk < TG; ++kk) {
-                const float c = gr[v + kk], d = gi[v + kk];
-                const float ac_ = xr[v] * c, bd = xi[v] * d, ad = xr[v] * d, bc = xi[v] * c;
-                const float m_re = ac_ + bd, m_im = ad - bc;   // conj(x) g
-                const float c_re = ac_ - bd, c_im = ad + bc;   // x g
-                float w = 1.f;
-#pragma unroll
-                for (int b = 0; b < B; ++b) {
-                    float *am = acc + 2 * (b * TG + kk);
-                    float *aq = acc + 2 * B * TG + 2 * (b * TG + kk);
-                    am[0] = fmaf(w, m_re, am[0]);
-                    am[1] = fmaf(w, m_im, am[1]);
-                    aq[0] = fmaf(w, c_re, aq[0]);
-                    aq[1] = fmaf(w, c_im, aq[1]);
-                    w *= r;
-                }
+                acc2[b * TG + kk] = __ffma2_rn(p, g[v + kk], acc2[b * TG + kk]);
+                acc2[B * TG + b * TG + kk] = __ffma2_rn(p, gs[v + kk], acc2[B * TG + b * TG + kk]);
             }
-        }
-    }
-
-    // Fixed-order reduction: warp butterfly, then warps in index order.
-    __shared__ float red[8][NA];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < NA; ++i) {
-        float v = acc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc[i] = v;
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int i = 0; i < NA; ++i) red[warp][i] = acc[i];
-    }
-    __syncthreads();
-    const int nw = blockDim.x >> 5;
-    float2 *row = a.partials + (size_t)blockIdx.x * K;
-    for (int i = threadIdx.x; i < NA; i += blockDim.x) {
-        float s = 0.f;
-        for (int w2 = 0; w2 < nw; ++w2) s += red[w2][i];
-        int idx = -1;
-        if (i < 2 * B * TG) {
-            const int b = (i >> 1) / TG, kk = (i >> 1) % TG;
-            if (b < Bp && k0 + kk < T) idx = b * T + k0 + kk;
-        } else if (i < 4 * B * TG) {
-            const int e = (i - 2 * B * TG) >> 1;
-            const int b = e / TG, kk = e % TG;
-            if (b < Bq && k0 + kk < T) idx = (Bp + b) * T + k0 + kk;
-        } else if (blockIdx.y == 0) {
-            idx = (Bp + Bq) * T;
-        }
-        if (idx >= 0) {
-            if (i & 1)
-                row[idx].y = s;
-            else
-                row[idx].x = s;
         }
     }
 }
 
-#define DPD_ADJ_GX_CASE(BB, TT)                                                                    \
-    case TT: {                                                                                     \
-        int occ = 0;                                                                               \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adj_gx_kernel<BB, TT, 4>, 256, 0);     \
-        if (occ < 1) occ = 1;                                                                      \
-        const int64_t need = (a.n + 1023) / 1024;                                                  \
-        int64_t grid = (int64_t)sm_count * occ;                                                    \
-        if (grid > need) grid = need;                                                              \
-        adj_gx_kernel<BB, TT, 4><<<(unsigned)grid, 256, 0, s>>>(a);                                \
-        count_launch();                                                                            \
-        return cudaGetLastError();                                                                 \
-    }
-
-template <int B, int TG>
-cudaError_t launch_adj_gh_tg(const AdjArgs &a, int gx_blocks, int T, int Bp, int Bq, int K,
-                             cudaStream_t s)
+// Fixed-order reduction of the accumulators of `nw` warps (threads tid < 32*nw
+// take part; `red` holds nw * NA floats), then one row of partials.  NAMED:
+// synchronise on named barrier 1 (the staged kernels, whose producer warp has
+// left) instead of __syncthreads.
+template <int B, int TG, bool NAMED>
+__device__ __forceinline__ void gh_reduce_row(float2 (&acc2)[2 * B * TG + 1], float *red, int nw, int tid, int k0,
+                                              bool group0, int T, int Bp, int Bq, float2 *row)
 {
-    const int groups = (T + TG - 1) / TG;
-    dim3 grid((unsigned)gx_blocks, (unsigned)groups);
-    adj_gh_kernel<B, TG, 4><<<grid, 256, 0, s>>>(a, T, Bp, Bq, K);
+    constexpr int NP = 2 * B * TG + 1;
+    constexpr int NA = 2 * NP;
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        float2 v = acc2[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        }
+        acc2[i] = v;
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            red[warp * NA + 2 * i] = acc2[i].x;
+            red[warp * NA + 2 * i + 1] = acc2[i].y;
+        }
+    }
+    if constexpr (NAMED)
+        asm volatile("bar.sync 1, %0;" ::"r"(nw * 32) : "memory");
+    else
+        __syncthreads();
+    // One (b, kk) pair per thread: X and Y summed over the warps in index
+    // order, then both branches.
+    for (int e = tid; e <= B * TG; e += nw * 32) {
+        float q[4] = {0.f, 0.f, 0.f, 0.f};
+        const int i0 = e < B * TG ? 2 * e : 2 * (NP - 1), i1 = 2 * (B * TG + e);
+        for (int w2 = 0; w2 < nw; ++w2) {
+            const float *rw = red + w2 * NA;
+            q[0] += rw[i0];
+            q[1] += rw[i0 + 1];
+            if (e < B * TG) {
+                q[2] += rw[i1];
+                q[3] += rw[i1 + 1];
+            }
+        }
+        if (e == B * TG) {
+            if (group0) row[(Bp + Bq) * T] = make_float2(q[0], q[1]);
+            continue;
+        }
+        const int b = e / TG, kk = e % TG;
+        if (k0 + kk >= T) continue;
+        if (b < Bp) row[b * T + k0 + kk] = make_float2(q[0] + q[1], q[2] - q[3]);
+        if (b < Bq) row[(Bp + b) * T + k0 + kk] = make_float2(q[0] - q[1], q[2] + q[3]);
+    }
+}
+
+// Plain-load variant: grid (blocks, tap groups), 256 threads.
+template <int B, int TG, int V>
+__global__ void __launch_bounds__(256) adj_gh_kernel(AdjArgs a, int T, int Bp, int Bq, int K)
+{
+    constexpr int NA = 4 * B * TG + 2;
+    constexpr int NP = NA / 2;
+    const int k0 = blockIdx.y * TG;
+    float2 acc2[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) acc2[i] = make_float2(0.f, 0.f);
+
+    const bool vec_in = ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.gy)) & 15) == 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * V;
+    for (int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V; j0 < a.n; j0 += stride) {
+        float2 xs[V], g[V + TG - 1];
+        adj_load_window<V>(a.x, j0, a.n, vec_in, xs);
+        adj_load_window<V + TG - 1>(a.gy, j0 + k0, a.n, vec_in, g);
+        gh_accumulate<B, TG, V>(xs, g, blockIdx.y == 0, acc2);
+    }
+    __shared__ float red[8 * NA];
+    gh_reduce_row<B, TG, false>(acc2, red, blockDim.x >> 5, threadIdx.x, k0, blockIdx.y == 0, T, Bp, Bq,
+                                a.partials + (size_t)blockIdx.x * K);
+}
+
+// Staged variant: grid (blocks, tap groups) of persistent CTAs (kAdjWarps
+// consumer warps + 1 producer warp); every CTA streams all tiles of its
+// blockIdx.x share.  x and gy 16-byte aligned.
+template <int B, int TG, int V>
+__global__ void __launch_bounds__(32 * (kAdjWarps + 1))
+    adj_gh_tma_kernel(AdjArgs a, int stages, int64_t ntiles, int T, int Bp, int Bq, int K)
+{
+    constexpr int NA = 4 * B * TG + 2;
+    constexpr int NP = NA / 2;
+    constexpr int S = kAdjWarps * 32 * V;
+    constexpr int NG = V + TG - 1;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);   // full[s], empty[s]
+    float *red = reinterpret_cast<float *>(smem + 128);
+    float2 *ring = reinterpret_cast<float2 *>(smem + adj_staged_smem(S, 0, kAdjWarps * NA));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int k0 = blockIdx.y * TG;
+    const bool group0 = blockIdx.y == 0;
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(smem_addr(&bars[s]), 1);
+            mbar_init(smem_addr(&bars[stages + s]), kAdjWarps);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (warp == kAdjWarps) {
+        if (lane == 0) adj_produce(a, ring, bars, stages, S, ntiles);
+        return;
+    }
+    float2 acc2[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) acc2[i] = make_float2(0.f, 0.f);
+    const int slot_elems = adj_slot_elems(S);
+    int64_t it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int s = (int)(it % stages);
+        // A failed wait (error word set) ends this warp's tiles; it still joins
+        // the reduction so that no consumer waits for it.
+        if (!mbar_wait(smem_addr(&bars[s]), (uint32_t)((it / stages) & 1), a.status)) break;
+        const float2 *slot = ring + (size_t)s * slot_elems;
+        const int64_t s0 = tile * S;
+        const int off = tid * V;
+        float2 xs[V], g[NG];
+        if (s0 + S + kHalo <= a.n) {
+            adj_slot_window<V>(slot, off, xs);
+            adj_slot_window<NG>(slot + S, off + k0, g);
+        } else {
+            int xc, gc;
+            adj_slot_counts(s0, S, a.n, xc, gc);
+            adj_slot_window_tail<V>(slot, s0, xc, a.x, s0 + off, a.n, xs);
+            adj_slot_window_tail<NG>(slot + S, s0, gc, a.gy, s0 + off + k0, a.n, g);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));
+        gh_accumulate<B, TG, V>(xs, g, group0, acc2);
+    }
+    gh_reduce_row<B, TG, true>(acc2, red, kAdjWarps, tid, k0, group0, T, Bp, Bq,
+                               a.partials + (size_t)blockIdx.x * K);
+}
+
+// ---------------------------------------------------------------- launches
+inline bool adj_staged_ok(const AdjArgs &a)
+{
+    return a.status != nullptr &&
+           ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.gy)) & 15) == 0;
+}
+
+template <int B, int T>
+cudaError_t launch_adj_gx_t(const AdjArgs &a, int sm_count, cudaStream_t s)
+{
+    constexpr int V = kAdjV;
+    if (adj_staged_ok(a)) {
+        constexpr int S = kAdjWarps * 32 * V;
+        const size_t smem = adj_staged_smem(S, kAdjStages, adj_tab_padded<B, T>());
+        static const cudaError_t attr = cudaFuncSetAttribute(
+            adj_gx_tma_kernel<B, T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (attr != cudaSuccess) return attr;
+        static const int occ = [smem] {
+            int o = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, adj_gx_tma_kernel<B, T, V>, 32 * (kAdjWarps + 1), smem);
+            return o < 1 ? 1 : o;
+        }();
+        const int64_t ntiles = (a.n + S - 1) / S;
+        int64_t grid = (int64_t)sm_count * occ;
+        if (grid > ntiles) grid = ntiles;
+        adj_gx_tma_kernel<B, T, V><<<(unsigned)grid, 32 * (kAdjWarps + 1), smem, s>>>(a, kAdjStages, ntiles);
+        count_launch();
+        return cudaGetLastError();
+    }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adj_gx_kernel<B, T, V>, 256, 0);
+    if (occ < 1) occ = 1;
+    const int64_t need = (a.n + 256 * V - 1) / (256 * V);
+    int64_t grid = (int64_t)sm_count * occ;
+    if (grid > need) grid = need;
+    adj_gx_kernel<B, T, V><<<(unsigned)grid, 256, 0, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
 
-// gh: choose the tap-group size (1, 2 or 4 taps per group) and the CTA count.
-template <int B>
-cudaError_t launch_adj_gh(const AdjArgs &a, const AdjLaunch &L, int T, int Bp, int Bq, int K,
-                          cudaStream_t s)
+template <int B, int TG>
+cudaError_t launch_adj_gh_tg(const AdjArgs &a, int blocks, int T, int Bp, int Bq, int K, cudaStream_t s)
 {
-    const int blocks = L.gh_blocks;   // already clamped by the caller; = rows of partials
+    const int groups = (T + TG - 1) / TG;
+    dim3 grid((unsigned)blocks, (unsigned)groups);
+    if (adj_staged_ok(a)) {
+        constexpr int V = kAdjGhV;
+        constexpr int S = kAdjWarps * 32 * V;
+        constexpr int NA = 4 * B * TG + 2;
+        const size_t smem = adj_staged_smem(S, kAdjGhStages, kAdjWarps * NA);
+        static const cudaError_t attr = cudaFuncSetAttribute(
+            adj_gh_tma_kernel<B, TG, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (attr != cudaSuccess) return attr;
+        const int64_t ntiles = (a.n + S - 1) / S;
+        adj_gh_tma_kernel<B, TG, V><<<grid, 32 * (kAdjWarps + 1), smem, s>>>(a, kAdjGhStages, ntiles, T, Bp, Bq, K);
+        count_launch();
+        return cudaGetLastError();
+    }
+    adj_gh_kernel<B, TG, kAdjV><<<grid, 256, 0, s>>>(a, T, Bp, Bq, K);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// gh: the tap-group size (1, 2 or 4 taps per group) and the CTAs per group
+// (= rows of partials, already clamped by the caller).
+template <int B>
+cudaError_t launch_adj_gh(const AdjArgs &a, const AdjLaunch &L, int T, int Bp, int Bq, int K, cudaStream_t s)
+{
     switch (L.tap_group) {
-    case 1: return launch_adj_gh_tg<B, 1>(a, blocks, T, Bp, Bq, K, s);
-    case 2: return launch_adj_gh_tg<B, 2>(a, blocks, T, Bp, Bq, K, s);
-    case 4: return launch_adj_gh_tg<B, 4>(a, blocks, T, Bp, Bq, K, s);
+    case 1: return launch_adj_gh_tg<B, 1>(a, L.gh_blocks, T, Bp, Bq, K, s);
+    case 2: return launch_adj_gh_tg<B, 2>(a, L.gh_blocks, T, Bp, Bq, K, s);
+    case 4: return launch_adj_gh_tg<B, 4>(a, L.gh_blocks, T, Bp, Bq, K, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -257,14 +611,14 @@ template <int B>
 cudaError_t launch_adj_gx(const AdjArgs &a, int T, int sm_count, cudaStream_t s)
 {
     switch (T) {
-        DPD_ADJ_GX_CASE(B, 1)
-        DPD_ADJ_GX_CASE(B, 2)
-        DPD_ADJ_GX_CASE(B, 3)
-        DPD_ADJ_GX_CASE(B, 4)
-        DPD_ADJ_GX_CASE(B, 5)
-        DPD_ADJ_GX_CASE(B, 6)
-        DPD_ADJ_GX_CASE(B, 7)
-        DPD_ADJ_GX_CASE(B, 8)
+    case 1: return launch_adj_gx_t<B, 1>(a, sm_count, s);
+    case 2: return launch_adj_gx_t<B, 2>(a, sm_count, s);
+    case 3: return launch_adj_gx_t<B, 3>(a, sm_count, s);
+    case 4: return launch_adj_gx_t<B, 4>(a, sm_count, s);
+    case 5: return launch_adj_gx_t<B, 5>(a, sm_count, s);
+    case 6: return launch_adj_gx_t<B, 6>(a, sm_count, s);
+    case 7: return launch_adj_gx_t<B, 7>(a, sm_count, s);
+    case 8: return launch_adj_gx_t<B, 8>(a, sm_count, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -120,8 +120,12 @@ dpd_status dpd_create(int P, int Q, int M, dpd_handle *out)
         return DPD_ERR_CUDA;
     }
     f->rows_max = 4 * f->sm_count;
-    f->adj.gh_blocks = 2 * f->sm_count;
-    f->adj.tap_group = f->B <= 2 ? 4 : 2;
+    // Coefficient-gradient schedule: models of up to 4 taps and 4 branch pairs
+    // keep all taps in one group (one CTA per SM); larger ones split the taps
+    // in pairs over two CTAs per SM and group.
+    const bool one_group = f->T <= 4 && f->B <= 4;
+    f->adj.tap_group = one_group ? 4 : 2;
+    f->adj.gh_blocks = (one_group ? 1 : 2) * f->sm_count;
     f->d_h = nullptr;
     f->d_tab = nullptr;
     f->d_status = nullptr;

@@ -61,8 +61,9 @@ struct FwdArgs {
 };
 
 // Floats of the adjoint table: per tap, four polynomials of B coefficients
-// (Q0..Q3 for conj(E) g + H conj(g)) and four of B-1 (R0..R3 for
-// conj(G) g + F conj(g)); see dpd_adj.cuh.
+// (Q0..Q3 for conj(E) g + H conj(g)) and four of B-1 (S0..S3 for
+// conj(G) g + F conj(g)), stored power-major as quadruples {Q0, Q3, Q1, Q2}
+// then {S0, S3, S1, S2}; see dpd_adj.cuh.
 __host__ __device__ constexpr int adj_table_floats(int B, int T) { return (4 * B + 4 * (B - 1)) * T; }
 
 struct AdjArgs {

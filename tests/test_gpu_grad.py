@@ -76,6 +76,33 @@ def test_grad_sizes_and_tap_schedules(n, launch):
     check_gh(gh, x, h, gy, P, Q, M)
 
 
+@pytest.mark.parametrize("n", [1, 9, 1031, 2 * 1024 + 9, 20011])
+@pytest.mark.parametrize("shift", [(0, 0, 1), (1, 0, 0), (0, 1, 0), (1, 1, 1)])
+def test_grad_alignment_paths(n, shift):
+    """16-byte aligned x and gy take the staged (bulk-copy ring) kernels, any
+    other 8-byte alignment the plain-load kernels; gx may be 8-byte aligned in
+    both.  Sizes straddle the 1024-sample tile and its 8-sample look-ahead."""
+    P, Q, M = 9, 7, 5
+    x, h, gy = make(P, Q, M, n, 7 * n + sum(shift))
+    f = dpd.DPD(P, Q, M)
+    f.set_coeffs(torch.from_numpy(h).cuda())
+
+    def placed(a, off):
+        buf = torch.zeros(len(a) + 1, dtype=torch.complex64, device="cuda")
+        v = buf[off:off + len(a)]
+        v.copy_(torch.from_numpy(a).cuda())
+        return v
+
+    xd, gyd = placed(x, shift[0]), placed(gy, shift[1])
+    gx = placed(np.full(n, 5 + 5j, np.complex64), shift[2])
+    gh = torch.full((f.K,), complex(5, 5), dtype=torch.complex64, device="cuda")
+    f.grad(xd, gyd, gh=gh, gx=gx)
+    f.sync_status()
+    _, gx_ref = oracle.grad(x, h, gy, P, Q, M, want_h=False)
+    assert_parity(gx.cpu().numpy(), gx_ref, what=f"gx n={n} shift={shift}")
+    check_gh(gh.cpu().numpy(), x, h, gy, P, Q, M)
+
+
 def test_grad_only_h_or_only_x_and_no_coeffs_for_h():
     P, Q, M = 5, 5, 2
     x, h, gy = make(P, Q, M, 7777, 1)
