@@ -54,8 +54,11 @@ def parse():
                     help="skip the batched / adjoint / Gram side measurements")
     ap.add_argument("--fwd-launch", default=None, metavar="MODE,V,WARPS,STAGES",
                     help="fix the forward launch shape instead of tuning it (profiling runs)")
-    ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "gram", "ila", "cpu"], default=None,
+    ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "grad", "gram", "ila", "cpu", "sweep",
+                                          "oracle"],
+                    default=None,
                     help="run only this side measurement (1 GPU) and print its JSON; for profiling")
+    ap.add_argument("--grad-log2n", type=int, default=24, help="samples (log2) of --pattern grad")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up for at least this long so clocks settle and get sampled")
     return ap.parse_args()
@@ -174,6 +177,76 @@ def cpu_oracle_throughput(n_sample: int, min_seconds: float, nthreads: int = 0):
     return reps * n_sample / el / 1e9, el, reps, oracle.threads(nthreads)
 
 
+def cpu_oracle_configs(nthreads_multi: int):
+    """The FP64 oracle, as it stands, on bounded samples of every workload:
+    median of 5 timed runs, with all host cores and with one thread."""
+    import numpy as np
+    import oracle
+    import dpd_synth as synth
+
+    def med(fn, nt):
+        fn(nt)
+        ts = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            fn(nt)
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts)
+
+    out = {"kind": "oracle", "threads_multi": oracle.threads(nthreads_multi), "cpu": _cpu_model(),
+           "note": "median of 5 runs; value = units / median seconds"}
+    x0 = synth.clipped_gaussian(1 << 16, 0.3, key=(0, 0))
+    h0 = synth.coeffs(5, 5, 2, key=(0, 1))
+    x1 = synth.ofdm2(1 << 20, key=(0, 0))
+    h1 = synth.coeffs(P, Q, M, key=(0, 1))
+    specs = synth.batch_streams(64, seed=0)
+    cut = 1 << 14
+    h3 = synth.coeffs(7, 7, 3, key=(0, 1))
+    x3 = x1[: 1 << 18]
+    g3 = synth.ofdm2(1 << 18, key=(0, 2))
+    u4, th4 = synth.ls_problem(1 << 15)
+    t4 = oracle.apply(u4, th4, 11, 11, 7, nthreads=nthreads_multi)
+    cases = [
+        ("cfg0_2p16_P5M2", "full 2^16 samples", 1 << 16, "Gsamples/s",
+         lambda nt: oracle.apply(x0, h0, 5, 5, 2, nthreads=nt)),
+        ("cfg1_2p24_P9M4", "first 2^20 of the 2^24 samples", 1 << 20, "Gsamples/s",
+         lambda nt: oracle.apply(x1, h1, P, Q, M, nthreads=nt)),
+        ("cfg2_batched_64", f"first {cut} samples of each of the 64 streams", sum(min(cut, len(sp['x'])) for sp in specs),
+         "Gsamples/s",
+         lambda nt: [oracle.apply(sp["x"][:cut], sp["h"], sp["P"], sp["Q"], sp["M"], nthreads=nt) for sp in specs]),
+        ("cfg3_fwd_grad_P7M3", "forward + coefficient and input gradient, first 2^18 samples", 1 << 18,
+         "Gsamples/s",
+         lambda nt: (oracle.apply(x3, h3, 7, 7, 3, nthreads=nt), oracle.grad(x3, h3, g3, 7, 7, 3, nthreads=nt))),
+        ("cfg4_ls_P11M7", "Gram + FP64 Cholesky solve, 2^15 of the 2^22 rows, K=97", 1 << 15, "Grows/s",
+         lambda nt: oracle.ls(u4, t4, 11, 11, 7, nthreads=nt)),
+    ]
+    res = {}
+    for name, sample, units, unit, fn in cases:
+        tm = med(fn, nthreads_multi)
+        t1 = med(fn, 1)
+        res[name] = {"sample": sample, "unit": unit, "multi": units / tm / 1e9, "single_thread": units / t1 / 1e9,
+                     "seconds_multi": tm, "seconds_single": t1}
+    out["configs"] = res
+    return out
+
+
+def _cpu_model():
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key, _, val = line.partition(":")
+                key, val = key.strip().lower(), val.strip()
+                if key == "model name":
+                    return val
+                if key == "cpu part":
+                    return f"{arm_parts.get(val, 'Arm')} (CPU part {val})"
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -228,6 +301,78 @@ def _time_graph(fn, reps, dev):
     e1.record(cur)
     torch.cuda.synchronize(dev)
     return e0.elapsed_time(e1) * 1e-3 / reps
+
+
+def measure_sweep(dev, log2_min=10, log2_max=26):
+    """Throughput against length (the paper's throughput-vs-samples experiment):
+    graph-replayed dpd_apply at N = 2^10 .. 2^26, at the 2^16 workload's model
+    (clipped Gaussian, P=Q=5, M=2) and at the 2^24 workload's (OFDM, P=Q=9, M=4).
+    Up to 2^22 samples the data stay in L2 between replays."""
+    import torch
+    import dpd_synth as synth
+    import paper_1612_09001_gb300 as dpd
+    nmax = 1 << log2_max
+    out = {"unit": "Gsamples/s", "timing": "CUDA graph of 20 calls, replayed; events on the replay stream"}
+    for name, (Pm, Qm, Mm), gen in (("P5M2_clipped_gaussian", (5, 5, 2), lambda n: synth.clipped_gaussian(n, 0.3, key=(0, 0))),
+                                     ("P9M4_ofdm", (9, 9, 4), lambda n: synth.ofdm2(n, key=(0, 0)))):
+        xa = torch.from_numpy(gen(nmax)).to(dev)
+        ya = torch.empty_like(xa)
+        f = dpd.DPD(Pm, Qm, Mm)
+        f.set_coeffs(synth.coeffs(Pm, Qm, Mm, key=(0, 1)))
+        rows = []
+        for lg in range(log2_min, log2_max + 1):
+            n = 1 << lg
+            x, y = xa[:n], ya[:n]
+            calls = 20
+            reps = max(3, min(200, (1 << 27) // (n * calls)))
+
+            def body():
+                for _ in range(calls):
+                    f.apply(x, out=y)
+
+            t = _time_graph(body, reps, dev) / calls
+            rows.append({"log2_n": lg, "us_per_call": t * 1e6, "gsamples_per_s": n / t / 1e9})
+        f.sync_status()
+        f.close()
+        out[name] = rows
+        del xa, ya
+    return out
+
+
+def measure_grad(dev, log2_n=24, reps=20):
+    """dpd_grad alone (the adjoint kernels): input gradient, coefficient
+    gradient and both, on 2^log2_n OFDM samples with an OFDM-like output
+    gradient, at the 2^24 workload's model and at the direct-learning model."""
+    import torch
+    import dpd_synth as synth
+    import paper_1612_09001_gb300 as dpd
+    n = 1 << log2_n
+    x = torch.from_numpy(synth.ofdm2(n, key=(0, 0))).to(dev)
+    gy = torch.from_numpy(synth.ofdm2(n, key=(0, 1))).to(dev)
+    gx = torch.empty_like(x)
+    out = {"n": n, "unit": "us per call", "timing": f"{reps} back-to-back calls after 3 warm-up calls, CUDA events"}
+    for (Pm, Qm, Mm) in ((9, 9, 4), (7, 7, 3)):
+        f = dpd.DPD(Pm, Qm, Mm)
+        f.set_coeffs(synth.coeffs(Pm, Qm, Mm, key=(0, 1)))
+        gh = torch.empty(f.K, dtype=torch.complex64, device=dev)
+        row = {}
+        for name, kw in (("gx", dict(gx=gx)), ("gh", dict(gh=gh)), ("gx_and_gh", dict(gx=gx, gh=gh))):
+            for _ in range(3):
+                f.grad(x, gy, **kw)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                f.grad(x, gy, **kw)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            us = e0.elapsed_time(e1) * 1e3 / reps
+            row[name] = {"us": us, "gsamples_per_s": n / us / 1e3}
+        f.sync_status()
+        f.close()
+        out[f"P{Pm}Q{Qm}M{Mm}"] = row
+    return out
 
 
 def measure_small(dev, calls=200):
@@ -680,16 +825,20 @@ def run_ours(args, world, rank, local):
         patterns["batched"] = b
         patterns["small_2p16"] = measure_small(dev)
         patterns["adjoint"] = measure_direct(dev)
+        patterns["grad_kernels"] = measure_grad(dev)
         patterns["gram"] = measure_gram(dev)
         patterns["ila_spectral"] = measure_ila(dev)
+        patterns["length_sweep"] = measure_sweep(dev)
         if world == 1:
             patterns["cpu_simd"] = measure_cpu_simd()
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, el, reps, cores = cpu_oracle_throughput(1 << 22, 10.0)
+        ncores = os.cpu_count() or 1
+        v, el, reps, cores = cpu_oracle_throughput(1 << 22, 10.0, nthreads=ncores)
         cpu = {"value": v, "unit": "Gsamples/s", "cores": cores, "kind": "oracle",
-               "sample": f"first 2^22 samples of the workload, repeated {reps}x ({el:.1f} s), FP64 C oracle"}
+               "sample": f"first 2^22 samples of the workload, repeated {reps}x ({el:.1f} s), FP64 C oracle",
+               "all_workloads": cpu_oracle_configs(ncores)}
 
     line = {
         "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": K,
@@ -718,12 +867,16 @@ def main():
     if args.pattern == "cpu":
         print(json.dumps({"pattern": "cpu", "result": measure_cpu_simd()}))
         return 0
+    if args.pattern == "oracle":
+        print(json.dumps({"pattern": "oracle", "result": cpu_oracle_configs(os.cpu_count() or 1)}))
+        return 0
     if args.pattern:
         import torch
         dev = torch.device("cuda", local)
         torch.cuda.set_device(dev)
         fn = {"small": measure_small, "batched": measure_batched, "adjoint": measure_direct,
-              "gram": measure_gram, "ila": measure_ila, "cpu": lambda d: measure_cpu_simd()}[args.pattern]
+              "gram": measure_gram, "ila": measure_ila, "sweep": measure_sweep,
+              "grad": lambda d: measure_grad(d, args.grad_log2n)}[args.pattern]
         print(json.dumps({"pattern": args.pattern, "result": fn(dev)}, default=float))
         return 0
     return run_ours(args, world, rank, local)
