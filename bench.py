@@ -59,6 +59,8 @@ def parse():
                     default=None,
                     help="run only this side measurement (1 GPU) and print its JSON; for profiling")
     ap.add_argument("--grad-log2n", type=int, default=24, help="samples (log2) of --pattern grad")
+    ap.add_argument("--batched-launch", default=None, metavar="V,WARPS,STAGES,CTAS_PER_SM",
+                    help="fix the batched launch shape of --pattern batched instead of tuning it (profiling runs)")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up for at least this long so clocks settle and get sampled")
     return ap.parse_args()
@@ -487,7 +489,7 @@ def measure_cpu_simd(n=1 << 24):
     return out
 
 
-def measure_batched(dev, reps=20):
+def measure_batched(dev, reps=20, launch=None):
     """64 antenna streams, lengths U[2^12, 2^20], P in {5,7,9}, M in {2..6}:
     one persistent launch (CUDA graph) against 64 plain launches."""
     import torch
@@ -504,7 +506,11 @@ def measure_batched(dev, reps=20):
     total = sum(len(sp["x"]) for sp in specs)
     plan = dpd.BatchedPlan(streams)
     from paper_1612_09001_gb300 import tune
-    best, _ = tune.tune_batched(plan)          # tile / stage / grid picked by timing, before the timed region
+    if launch:                                 # fixed shape (profiling runs)
+        best = tuple(launch)
+        plan.set_launch(*best)
+    else:                                      # tile / stage / grid picked by timing, before the timed region
+        best, _ = tune.tune_batched(plan)
     l0 = dpd.kernel_launches()
     t_plan = _time_graph(lambda: plan.execute(), reps, dev)
     launches_plan = (dpd.kernel_launches() - l0) // 2   # captured twice (warm-up + capture)
@@ -536,7 +542,7 @@ def measure_batched(dev, reps=20):
             "persistent_launch_shape": {"V": best[0], "warps": best[1], "stages": best[2], "ctas_per_sm": best[3]},
             "plain_64_launches": total / t_plain / 1e9, "plain_64_in_one_graph": total / t_graph64 / 1e9,
             "persistent_us": t_plan * 1e6, "plain_64_us": t_plain * 1e6, "plain_64_graph_us": t_graph64 * 1e6,
-            "hbm_frac_persistent": 16 * total / t_plan / 1e9}
+            "hbm_gbs_persistent": 16 * total / t_plan / 1e9}
 
 
 def measure_direct(dev, steps=300):
@@ -821,7 +827,7 @@ def run_ours(args, world, rank, local):
     patterns = {}
     if not args.no_patterns:
         b = measure_batched(dev)
-        b["hbm_frac_persistent"] = b["hbm_frac_persistent"] / peaks["hbm_gbs"]
+        b["hbm_frac_persistent"] = b["hbm_gbs_persistent"] / peaks["hbm_gbs"]
         patterns["batched"] = b
         patterns["small_2p16"] = measure_small(dev)
         patterns["adjoint"] = measure_direct(dev)
@@ -874,7 +880,9 @@ def main():
         import torch
         dev = torch.device("cuda", local)
         torch.cuda.set_device(dev)
-        fn = {"small": measure_small, "batched": measure_batched, "adjoint": measure_direct,
+        blaunch = [int(v) for v in args.batched_launch.split(",")] if args.batched_launch else None
+        fn = {"small": measure_small, "batched": lambda d: measure_batched(d, launch=blaunch),
+              "adjoint": measure_direct,
               "gram": measure_gram, "ila": measure_ila, "sweep": measure_sweep,
               "grad": lambda d: measure_grad(d, args.grad_log2n)}[args.pattern]
         print(json.dumps({"pattern": args.pattern, "result": fn(dev)}, default=float))

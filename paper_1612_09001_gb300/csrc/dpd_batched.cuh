@@ -7,8 +7,12 @@
 // with two bulk copies completed on the slot's mbarrier: the stream's
 // widely-linear coefficient table (see dpd_internal.h) and the tile with its
 // kHalo samples of history (zero before the stream's first sample, Eq. 2).
-// Consumer warps dispatch on the item's (B, T) to the same per-sample compute
-// as the single-stream kernel, with coefficients read from the slot.
+// The producer also writes the item's description (pointers, length, tile
+// start, model, validity) into the slot's header before it arrives on the
+// barrier, so the consumers read it from shared memory instead of every
+// thread loading the item and stream records from global memory.  Consumer
+// warps dispatch on the item's (B, T) to the same per-sample compute as the
+// single-stream kernel, with coefficients read from the slot.
 #pragma once
 
 #include "dpd_fwd.cuh"
@@ -41,9 +45,22 @@ struct BatchArgs {
 
 constexpr int kBatchTabBytes = ((kMaxTabFloats * 4 + 15) / 16) * 16;   // table area of a slot
 
+// Item description written by the producer at the start of a slot.
+struct BatchSlotHeader {
+    const float2 *x;
+    float2 *y;
+    int64_t n;     // stream length
+    int64_t s0;    // first sample of the tile
+    int bt;        // B * 16 + T
+    int ok;        // item passed item_ok (else skipped by both sides)
+};
+constexpr int kBatchHdrBytes = 64;
+static_assert(sizeof(BatchSlotHeader) <= kBatchHdrBytes, "slot header");
+
+// Slot: header, table, tile (kHalo history samples + S samples).
 __host__ __device__ constexpr size_t batch_slot_bytes(int S)
 {
-    return (size_t)kBatchTabBytes + (size_t)(kHalo + S) * sizeof(float2);
+    return (size_t)kBatchHdrBytes + (size_t)kBatchTabBytes + (size_t)(kHalo + S) * sizeof(float2);
 }
 
 // Range checks of a work item against the plan (stream index, table inside
@@ -59,27 +76,27 @@ __device__ __forceinline__ bool item_ok(const BatchArgs &a, const BatchItem &w, 
 }
 
 template <int B, int T, int V>
-__device__ __forceinline__ void batched_item(const unsigned char *slot, const BatchStream &st, int64_t s0,
-                                             int S, int t_in_tile)
+__device__ __forceinline__ void batched_item(const unsigned char *slot, const BatchSlotHeader &hd, int S,
+                                             int t_in_tile)
 {
     constexpr int W = V + T - 1;
-    const float *tab = reinterpret_cast<const float *>(slot);
-    const float2 *xs = reinterpret_cast<const float2 *>(slot + kBatchTabBytes);
+    const float *tab = reinterpret_cast<const float *>(slot + kBatchHdrBytes);
+    const float2 *xs = reinterpret_cast<const float2 *>(slot + kBatchHdrBytes + kBatchTabBytes);
     float wr[W], wi[W];
-    const bool full = load_window<T, V>(xs, s0, S, st.n, st.x, t_in_tile, wr, wi);
+    const bool full = load_window<T, V>(xs, hd.s0, S, hd.n, hd.x, t_in_tile, wr, wi);
     float yr[V], yi[V];
     // Coefficients come from the slot (shared memory); the parameter-bank
     // table argument is not read in this mode.
     fwd_compute<B, T, V, kModePackedFma>(tab, *reinterpret_cast<const ParamTab<B, T> *>(tab), wr, wi, yr,
                                          yi);
-    const bool vec = full && ((reinterpret_cast<uintptr_t>(st.y) & 15u) == 0);
-    store_outputs<V>(st.y, s0 + (int64_t)t_in_tile * V, st.n, vec, yr, yi);
+    const bool vec = full && ((reinterpret_cast<uintptr_t>(hd.y) & 15u) == 0);
+    store_outputs<V>(hd.y, hd.s0 + (int64_t)t_in_tile * V, hd.n, vec, yr, yi);
 }
 
 #define DPD_BCASE(b, t)                                                                            \
     case (b) * 16 + (t):                                                                           \
         if constexpr ((b) <= BMAX && (t) <= TMAX) {                                                \
-            batched_item<(b), (t), V>(slot, st, s0, S, t_in_tile);                                 \
+            batched_item<(b), (t), V>(slot, hd, S, t_in_tile);                                     \
             break;                                                                                 \
         }                                                                                          \
         bad = true;                                                                                \
@@ -124,21 +141,31 @@ __global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int s
             const BatchItem w = a.items[i];
             const BatchStream st = a.streams[(w.stream >= 0 && w.stream < a.nstreams) ? w.stream : 0];
             const uint32_t fb = smem_addr(&bars[s]);
-            if (!item_ok(a, w, st, S)) {
+            unsigned char *slot = ring + (size_t)s * slot_bytes;
+            BatchSlotHeader *hd = reinterpret_cast<BatchSlotHeader *>(slot);
+            const bool good = item_ok(a, w, st, S);
+            hd->x = st.x;
+            hd->y = st.y;
+            hd->n = st.n;
+            hd->s0 = (int64_t)w.tile * S;
+            hd->bt = st.B * 16 + st.T;
+            hd->ok = good ? 1 : 0;
+            if (!good) {
                 atomicOr(a.status, kFlagBadWork);
-                mbar_arrive_expect_tx(fb, 0);   // complete the phase with no copies
+                mbar_arrive_expect_tx(fb, 0);   // complete the phase with no copies (releases the header)
                 continue;
             }
             int64_t lo, cnt;
             int off;
             tile_copy_range((int64_t)w.tile * S, S, st.n, lo, cnt, off);
             const uint32_t xbytes = (uint32_t)(cnt * (int64_t)sizeof(float2));
-            unsigned char *slot = ring + (size_t)s * slot_bytes;
+            // The arrive releases the header stores; the consumers' wait acquires them.
             mbar_arrive_expect_tx(fb, xbytes + (uint32_t)st.tab_bytes);
-            bulk_copy_g2s(smem_addr(slot), a.tabs + st.tab_off, (uint32_t)st.tab_bytes, fb);
+            bulk_copy_g2s(smem_addr(slot + kBatchHdrBytes), a.tabs + st.tab_off, (uint32_t)st.tab_bytes, fb);
             if (xbytes)
-                bulk_copy_g2s_stream(smem_addr(slot + kBatchTabBytes + (size_t)off * sizeof(float2)),
-                                     st.x + lo, xbytes, fb, pol);
+                bulk_copy_g2s_stream(
+                    smem_addr(slot + kBatchHdrBytes + kBatchTabBytes + (size_t)off * sizeof(float2)), st.x + lo,
+                    xbytes, fb, pol);
         }
         if (!ok) {
             const int first = it > stages ? it - stages : 0;
@@ -156,11 +183,9 @@ __global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int s
         const uint32_t ph = (uint32_t)((it / stages) & 1);
         if (!mbar_wait(smem_addr(&bars[s]), ph, a.status)) return;
         const unsigned char *slot = ring + (size_t)s * slot_bytes;
-        const BatchItem w = a.items[i];
-        const BatchStream st = a.streams[(w.stream >= 0 && w.stream < a.nstreams) ? w.stream : 0];
-        const int64_t s0 = (int64_t)w.tile * S;
-        bool bad = !item_ok(a, w, st, S);
-        if (!bad) switch (st.B * 16 + st.T) {
+        const BatchSlotHeader &hd = *reinterpret_cast<const BatchSlotHeader *>(slot);   // read in place
+        bool bad = hd.ok == 0;
+        if (!bad) switch (hd.bt) {
             DPD_BCASES(1)
             DPD_BCASES(2)
             DPD_BCASES(3)
@@ -169,9 +194,9 @@ __global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int s
             DPD_BCASES(6)
         default: bad = true;
         }
-        if (bad && lane == 0) atomicOr(a.status, kFlagBadWork);
+        if (bad && hd.ok != 0 && lane == 0) atomicOr(a.status, kFlagBadWork);   // model outside this kernel
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));   // slot (table + tile) no longer read
+        if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));   // slot (header, table, tile) no longer read
     }
 }
 
