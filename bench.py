@@ -154,6 +154,54 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(load)}
 
 
+class Ranks:
+    """The replicas' coordination: barrier, max over ranks, rank 0 prints.
+
+    With one process it does nothing.  Under torchrun every rank runs an
+    independent replica (no collective on the data path); only the timing uses
+    the process group: a barrier on both sides of the timed region and the
+    maximum of the per-rank durations.  backend "nccl" reduces a tensor on the
+    rank's GPU, "gloo" one in host memory (the CPU tests)."""
+
+    def __init__(self, world: int, rank: int, backend: str = "nccl", device=None):
+        self.world, self.rank, self.device = world, rank, device
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=device)
+            else:
+                dist.init_process_group(backend)
+            self.pg = dist
+
+    @property
+    def root(self) -> bool:
+        return self.rank == 0
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max_over_ranks(self, v: float) -> float:
+        if self.pg is None:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+            self.pg = None
+
+
+def whole_job_rate(world: int, steps: int, units_per_step: int, seconds_max: float) -> float:
+    """Units per second of the whole job: every rank processed steps x units in
+    at most seconds_max (weak scaling), in 1e9 units/s."""
+    return world * steps * units_per_step / seconds_max / 1e9
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -670,22 +718,8 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-        pg = dist
-
-    def barrier():
-        if pg is not None:
-            pg.barrier()
-
-    def max_over_ranks(v: float) -> float:
-        if pg is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(world, rank, "nccl", dev)
+    barrier, max_over_ranks = ranks.barrier, ranks.max_over_ranks
 
     n = N_SAMPLES
     x_host = synth.ofdm2(n, key=(rank, 0))
@@ -735,7 +769,7 @@ def run_ours(args, world, rank, local):
     f.sync_status()
     total = e_start.elapsed_time(e_end) * 1e-3
     total_max = max_over_ranks(total)
-    value = world * K * n / total_max / 1e9
+    value = whole_job_rate(world, K, n, total_max)
     mean_launch = total / K   # one kernel launch per step
 
     # ---- end to end through the library's host path (dpd_apply_host): pinned
@@ -786,23 +820,22 @@ def run_ours(args, world, rank, local):
 
     t_link = timed_host(link_copies)
     link_gbs = 2 * n * 8 / (t_link / K2) / 1e9
-    e2e = {"value": world * K2 * n / t_zc / 1e9, "unit": "Gsamples/s",
+    e2e = {"value": whole_job_rate(world, K2, n, t_zc), "unit": "Gsamples/s",
            "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
            "path": "dpd_apply_host (zero copy): one kernel reads the pinned host input and writes the pinned "
                    "host output in place over the CPU-GPU link, staged through shared memory in whole lines",
            "gpu_launches_per_step": e2e_launches,
            "link": {"h2d_plus_d2h_gbs": link_gbs, "frac": (2 * n * 8 / (t_zc / K2) / 1e9) / link_gbs,
                     "how": "cudaMemcpyAsync H2D and D2H of the same buffers concurrently on two streams"},
-           "pipelined_value": world * K2 * n / t_pipe / 1e9,
+           "pipelined_value": whole_job_rate(world, K2, n, t_pipe),
            "pipelined_path": "dpd_apply_host (pipelined): 2^21-sample chunks copied in, filtered and copied out "
                              "on three streams, overlapping both copy directions with the kernels",
-           "explicit_copy_value": world * K2 * n / t_cp / 1e9,
+           "explicit_copy_value": whole_job_rate(world, K2, n, t_cp),
            "explicit_copy_path": "cudaMemcpyAsync H2D -> dpd_apply -> cudaMemcpyAsync D2H, one after the other"}
 
-    if rank != 0:
+    if not ranks.root:
         f.close()
-        if pg is not None:
-            pg.destroy_process_group()
+        ranks.close()
         return 0
 
     peaks, peak_kind = measured_peaks()
@@ -860,8 +893,7 @@ def run_ours(args, world, rank, local):
     }
     print(json.dumps(line), flush=True)
     f.close()
-    if pg is not None:
-        pg.destroy_process_group()
+    ranks.close()
     return 0
 
 
