@@ -173,7 +173,7 @@ dpd_status dpd_grad(dpd_handle h, const void *x, const void *gy, int64_t n, void
 /*
  * Launch shape of dpd_grad's coefficient-gradient kernel (used by the
  * autotuner): gh_blocks CTAs per tap group (1 .. 4 * SM count), tap_group taps
- * per group (1, 2 or 4).
+ * per group (1 .. 5).  Returns DPD_ERR_INVALID_ARGUMENT outside those ranges.
  */
 dpd_status dpd_set_adj_launch(dpd_handle h, int gh_blocks, int tap_group);
 

@@ -602,7 +602,9 @@ cudaError_t launch_adj_gh(const AdjArgs &a, const AdjLaunch &L, int T, int Bp, i
     switch (L.tap_group) {
     case 1: return launch_adj_gh_tg<B, 1>(a, L.gh_blocks, T, Bp, Bq, K, s);
     case 2: return launch_adj_gh_tg<B, 2>(a, L.gh_blocks, T, Bp, Bq, K, s);
+    case 3: return launch_adj_gh_tg<B, 3>(a, L.gh_blocks, T, Bp, Bq, K, s);
     case 4: return launch_adj_gh_tg<B, 4>(a, L.gh_blocks, T, Bp, Bq, K, s);
+    case 5: return launch_adj_gh_tg<B, 5>(a, L.gh_blocks, T, Bp, Bq, K, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -120,12 +120,18 @@ dpd_status dpd_create(int P, int Q, int M, dpd_handle *out)
         return DPD_ERR_CUDA;
     }
     f->rows_max = 4 * f->sm_count;
-    // Coefficient-gradient schedule: models of up to 4 taps and 4 branch pairs
-    // keep all taps in one group (one CTA per SM); larger ones split the taps
-    // in pairs over two CTAs per SM and group.
-    const bool one_group = f->T <= 4 && f->B <= 4;
-    f->adj.tap_group = one_group ? 4 : 2;
-    f->adj.gh_blocks = (one_group ? 1 : 2) * f->sm_count;
+    // Coefficient-gradient schedule: as few tap groups as keep a thread's
+    // accumulators (4 B TG + 2 floats) within about a hundred registers, with
+    // the taps spread evenly over the groups; groups of 3 or more taps run one
+    // CTA per SM, smaller ones two.
+    {
+        int tg_max = 25 / f->B;
+        if (tg_max > 5) tg_max = 5;
+        if (tg_max < 1) tg_max = 1;
+        const int groups = (f->T + tg_max - 1) / tg_max;
+        f->adj.tap_group = (f->T + groups - 1) / groups;
+        f->adj.gh_blocks = (f->adj.tap_group >= 3 ? 1 : 2) * f->sm_count;
+    }
     f->d_h = nullptr;
     f->d_tab = nullptr;
     f->d_status = nullptr;
@@ -473,7 +479,7 @@ dpd_status dpd_set_adj_launch(dpd_handle h, int gh_blocks, int tap_group)
 {
     if (!h) return DPD_ERR_INVALID_ARGUMENT;
     if (gh_blocks < 1 || gh_blocks > h->rows_max) return DPD_ERR_INVALID_ARGUMENT;
-    if (tap_group != 1 && tap_group != 2 && tap_group != 4) return DPD_ERR_INVALID_ARGUMENT;
+    if (tap_group < 1 || tap_group > 5) return DPD_ERR_INVALID_ARGUMENT;
     h->adj.gh_blocks = gh_blocks;
     h->adj.tap_group = tap_group;
     return DPD_OK;

@@ -78,7 +78,7 @@ struct AdjArgs {
 
 struct AdjLaunch {
     int gh_blocks = 0;      // CTAs per tap group for the coefficient gradient (rows of partials)
-    int tap_group = 2;      // taps per group: 1, 2 or 4
+    int tap_group = 2;      // taps per group: 1 .. 5
 };
 
 template <int B>

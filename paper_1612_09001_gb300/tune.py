@@ -112,7 +112,7 @@ def tune_adjoint(filt, x, gy, candidates=None):
     gh = torch.empty(filt.K, dtype=torch.complex64, device=x.device)
     gx = torch.empty_like(x)
     results = []
-    for cand in candidates or [(b * sms, tg) for b in (1, 2, 4) for tg in (1, 2, 4)]:
+    for cand in candidates or [(b * sms, tg) for b in (1, 2, 4) for tg in (1, 2, 3, 4, 5)]:
         try:
             filt.set_adj_launch(*cand)
             ms = _time(lambda: filt.grad(x, gy, gh=gh, gx=gx))

@@ -66,7 +66,7 @@ def test_grad_parity(P, Q, M):
 
 
 @pytest.mark.parametrize("n", [1, 2, 5, 1023, 1024, 1025, 4097, 300001])
-@pytest.mark.parametrize("launch", [None, (1, 1), (3, 4), (37, 2), (600, 1)])
+@pytest.mark.parametrize("launch", [None, (1, 1), (3, 4), (37, 2), (600, 1), (5, 3), (150, 5)])
 def test_grad_sizes_and_tap_schedules(n, launch):
     P, Q, M = 7, 5, 6
     x, h, gy = make(P, Q, M, n, n)
@@ -101,6 +101,15 @@ def test_grad_alignment_paths(n, shift):
     _, gx_ref = oracle.grad(x, h, gy, P, Q, M, want_h=False)
     assert_parity(gx.cpu().numpy(), gx_ref, what=f"gx n={n} shift={shift}")
     check_gh(gh.cpu().numpy(), x, h, gy, P, Q, M)
+
+
+def test_adj_launch_limits():
+    f = dpd.DPD(5, 5, 2)
+    for bad in [(0, 2), (1, 0), (1, 6), (10 ** 6, 2)]:
+        with pytest.raises(dpd.DPDError):
+            f.set_adj_launch(*bad)
+    f.set_adj_launch(1, 5)
+    f.close()
 
 
 def test_grad_only_h_or_only_x_and_no_coeffs_for_h():
