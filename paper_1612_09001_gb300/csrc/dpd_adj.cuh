@@ -153,11 +153,19 @@ __host__ __device__ constexpr size_t adj_staged_smem(int S, int stages, int scra
 }
 
 // ---------------------------------------------------------------- input gradient
+// Adjoint table passed by value (kernel parameter bank).
+template <int B, int T>
+struct AdjParamTab {
+    float v[adj_table_floats(B, T)];
+};
+
 // gx for the V samples i0.. from their x (xs) and the gy window g (samples
-// i0 .. i0 + V + T - 2).  tab: the adjoint table of one model (shared memory).
-template <int B, int T, int V>
-__device__ __forceinline__ void gx_compute(const float *tab, const float2 (&xs)[V],
-                                           const float2 (&g)[V + T - 1], float2 (&acc)[V])
+// i0 .. i0 + V + T - 2).  The adjoint table of the model comes from shared
+// memory (tab) or, with PARAM, from the parameter bank (ptab), whose entries
+// the packed FMAs take as operands directly.
+template <int B, int T, int V, bool PARAM = false>
+__device__ __forceinline__ void gx_compute(const float *tab, const AdjParamTab<B, T> &ptab,
+                                           const float2 (&xs)[V], const float2 (&g)[V + T - 1], float2 (&acc)[V])
 {
     constexpr int QB = B, RB = B - 1;       // coefficients per Q / S polynomial
     constexpr int PER_TAP = 4 * QB + 4 * RB;
@@ -185,16 +193,27 @@ __device__ __forceinline__ void gx_compute(const float *tab, const float2 (&xs)[
     }
 #pragma unroll
     for (int k = 0; k < T; ++k) {
-        const float4 *cq = reinterpret_cast<const float4 *>(tab + PER_TAP * k);
+        // quadruple j of tap k's block: the Q quadruples, then the S ones
+        auto coef = [&](int j) -> float4 {
+            if constexpr (PARAM) {
+                const int o = PER_TAP * k + 4 * j;
+                return make_float4(ptab.v[o], ptab.v[o + 1], ptab.v[o + 2], ptab.v[o + 3]);
+            } else {
+                return reinterpret_cast<const float4 *>(tab + PER_TAP * k)[j];
+            }
+        };
         float2 pa[V], pb[V];
+        {
+            const float4 c4 = coef(QB - 1);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            pa[v] = make_float2(cq[QB - 1].x, cq[QB - 1].y);
-            pb[v] = make_float2(cq[QB - 1].z, cq[QB - 1].w);
+            for (int v = 0; v < V; ++v) {
+                pa[v] = make_float2(c4.x, c4.y);
+                pb[v] = make_float2(c4.z, c4.w);
+            }
         }
 #pragma unroll
         for (int m = QB - 2; m >= 0; --m) {
-            const float4 c4 = cq[m];
+            const float4 c4 = coef(m);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const float2 rr2 = make_float2(rr[v], rr[v]);
@@ -208,16 +227,18 @@ __device__ __forceinline__ void gx_compute(const float *tab, const float2 (&xs)[
             acc[v] = __ffma2_rn(pb[v], gs[v + k], acc[v]);   // {Q1 d, Q2 c}
         }
         if constexpr (RB > 0) {
-            const float4 *cs = cq + QB;
             float2 sa[V], sb[V];
+            {
+                const float4 c4 = coef(QB + RB - 1);
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                sa[v] = make_float2(cs[RB - 1].x, cs[RB - 1].y);
-                sb[v] = make_float2(cs[RB - 1].z, cs[RB - 1].w);
+                for (int v = 0; v < V; ++v) {
+                    sa[v] = make_float2(c4.x, c4.y);
+                    sb[v] = make_float2(c4.z, c4.w);
+                }
             }
 #pragma unroll
             for (int m = RB - 2; m >= 0; --m) {
-                const float4 c4 = cs[m];
+                const float4 c4 = coef(QB + m);
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const float2 rr2 = make_float2(rr[v], rr[v]);
@@ -285,15 +306,16 @@ __global__ void __launch_bounds__(256) adj_gx_kernel(AdjArgs a)
         float2 xs[V], g[W], acc[V];
         adj_load_window<V>(a.x, i0, a.n, vec_in, xs);
         adj_load_window<W>(a.gy, i0, a.n, vec_in, g);
-        gx_compute<B, T, V>(tab, xs, g, acc);
+        gx_compute<B, T, V>(tab, *reinterpret_cast<const AdjParamTab<B, T> *>(tab), xs, g, acc);
         gx_store<V>(a.gx, i0, a.n, vec_out, acc, false);
     }
 }
 
 // Staged variant: persistent CTAs of kAdjWarps consumer warps + 1 producer warp
 // walk tiles of S = kAdjWarps * 32 * V samples.  x and gy 16-byte aligned.
-template <int B, int T, int V>
-__global__ void __launch_bounds__(32 * (kAdjWarps + 1)) adj_gx_tma_kernel(AdjArgs a, int stages, int64_t ntiles)
+template <int B, int T, int V, bool PARAM>
+__global__ void __launch_bounds__(32 * (kAdjWarps + 1))
+    adj_gx_tma_kernel(AdjArgs a, int stages, int64_t ntiles, const __grid_constant__ AdjParamTab<B, T> ptab)
 {
     constexpr int W = V + T - 1;
     constexpr int TABF = adj_table_floats(B, T);
@@ -311,7 +333,8 @@ __global__ void __launch_bounds__(32 * (kAdjWarps + 1)) adj_gx_tma_kernel(AdjArg
         }
         fence_barrier_init();
     }
-    for (int i = tid; i < TABF; i += blockDim.x) tab[i] = a.adj_tab[i];
+    if constexpr (!PARAM)
+        for (int i = tid; i < TABF; i += blockDim.x) tab[i] = a.adj_tab[i];
     __syncthreads();
     if (warp == kAdjWarps) {
         if (lane == 0) adj_produce(a, ring, bars, stages, S, ntiles);
@@ -340,7 +363,7 @@ __global__ void __launch_bounds__(32 * (kAdjWarps + 1)) adj_gx_tma_kernel(AdjArg
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));
         float2 acc[V];
-        gx_compute<B, T, V>(tab, xs, g, acc);
+        gx_compute<B, T, V, PARAM>(tab, ptab, xs, g, acc);
         gx_store<V>(a.gx, s0 + off, a.n, vec_out, acc, true);
     }
 }
@@ -538,27 +561,40 @@ inline bool adj_staged_ok(const AdjArgs &a)
            ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.gy)) & 15) == 0;
 }
 
+template <int B, int T, int V, bool PARAM>
+cudaError_t launch_adj_gx_tma(const AdjArgs &a, const AdjParamTab<B, T> &ptab, int sm_count, cudaStream_t s)
+{
+    constexpr int S = kAdjWarps * 32 * V;
+    // The shared-memory table area is kept in both forms (it is small).
+    const size_t smem = adj_staged_smem(S, kAdjStages, adj_tab_padded<B, T>());
+    auto kern = adj_gx_tma_kernel<B, T, V, PARAM>;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
+    static const int occ = [smem, kern] {
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 32 * (kAdjWarps + 1), smem);
+        return o < 1 ? 1 : o;
+    }();
+    const int64_t ntiles = (a.n + S - 1) / S;
+    int64_t grid = (int64_t)sm_count * occ;
+    if (grid > ntiles) grid = ntiles;
+    kern<<<(unsigned)grid, 32 * (kAdjWarps + 1), smem, s>>>(a, kAdjStages, ntiles, ptab);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <int B, int T>
 cudaError_t launch_adj_gx_t(const AdjArgs &a, int sm_count, cudaStream_t s)
 {
     constexpr int V = kAdjV;
     if (adj_staged_ok(a)) {
-        constexpr int S = kAdjWarps * 32 * V;
-        const size_t smem = adj_staged_smem(S, kAdjStages, adj_tab_padded<B, T>());
-        static const cudaError_t attr = cudaFuncSetAttribute(
-            adj_gx_tma_kernel<B, T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (attr != cudaSuccess) return attr;
-        static const int occ = [smem] {
-            int o = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, adj_gx_tma_kernel<B, T, V>, 32 * (kAdjWarps + 1), smem);
-            return o < 1 ? 1 : o;
-        }();
-        const int64_t ntiles = (a.n + S - 1) / S;
-        int64_t grid = (int64_t)sm_count * occ;
-        if (grid > ntiles) grid = ntiles;
-        adj_gx_tma_kernel<B, T, V><<<(unsigned)grid, 32 * (kAdjWarps + 1), smem, s>>>(a, kAdjStages, ntiles);
-        count_launch();
-        return cudaGetLastError();
+        if (a.host_adj_tab) {
+            AdjParamTab<B, T> ptab;
+            for (int i = 0; i < adj_table_floats(B, T); ++i) ptab.v[i] = a.host_adj_tab[i];
+            return launch_adj_gx_tma<B, T, V, true>(a, ptab, sm_count, s);
+        }
+        return launch_adj_gx_tma<B, T, V, false>(a, AdjParamTab<B, T>{}, sm_count, s);
     }
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adj_gx_kernel<B, T, V>, 256, 0);

@@ -203,9 +203,13 @@ dpd_status dpd_set_coeffs(dpd_handle h, const void *coeffs, int K, int where, vo
     cudaError_t e = dpd::launch_wl_table(src, h->Bp, h->Bq, h->T, h->d_tab, h->d_adj_tab, s);
     if (e != cudaSuccess) return DPD_ERR_CUDA;
     if (where == DPD_HOST) {
-        // Keep a host copy of the table so that dpd_apply can pass it by value.
+        // Keep host copies of the tables so that dpd_apply and dpd_grad can pass
+        // them by value.
         e = cudaMemcpyAsync(h->h_tab.v, h->d_tab, sizeof(float) * dpd::wl_table_floats(h->B, h->T),
                             cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->h_adj_tab, h->d_adj_tab, sizeof(float) * dpd::adj_table_floats(h->B, h->T),
+                                cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return DPD_ERR_CUDA;
         h->host_tab_valid = true;
@@ -292,6 +296,7 @@ dpd_status dpd_grad(dpd_handle h, const void *x, const void *gy, int64_t n, void
     a.partials = gh ? h->d_partials : nullptr;
     a.adj_tab = h->d_adj_tab;
     a.status = h->d_status;
+    a.host_adj_tab = h->host_tab_valid ? h->h_adj_tab : nullptr;
     dpd::AdjLaunch L = h->adj;
     int64_t need = (n + 1023) / 1024;
     if (L.gh_blocks > need) L.gh_blocks = (int)need;

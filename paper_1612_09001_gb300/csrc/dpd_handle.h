@@ -56,8 +56,9 @@ struct dpd_filter {
     float2 *d_partials;  // coefficient-gradient workspace: rows_max x K complex
     int rows_max;
     bool has_coeffs;
-    bool host_tab_valid;  // h_tab mirrors d_tab (coefficients were set from host memory)
+    bool host_tab_valid;  // h_tab / h_adj_tab mirror d_tab / d_adj_tab (coefficients set from host memory)
     dpd::HostTab h_tab;
+    float h_adj_tab[dpd::kMaxAdjTabFloats];
     dpd::FwdLaunch fwd;
     bool fwd_auto = true;
     int est_basis = 0;      // DPD_BASIS_MONOMIAL or DPD_BASIS_ORTHOGONAL (least-squares estimates)   // default launch shape: shrink the tile for short inputs (off once set explicitly)

@@ -65,6 +65,7 @@ struct FwdArgs {
 // conj(G) g + F conj(g)), stored power-major as quadruples {Q0, Q3, Q1, Q2}
 // then {S0, S3, S1, S2}; see dpd_adj.cuh.
 __host__ __device__ constexpr int adj_table_floats(int B, int T) { return (4 * B + 4 * (B - 1)) * T; }
+constexpr int kMaxAdjTabFloats = adj_table_floats(6, 8);   // 352
 
 struct AdjArgs {
     const float2 *x;
@@ -74,6 +75,10 @@ struct AdjArgs {
     float2 *partials;       // nullable: per-CTA coefficient-gradient rows (rows x K)
     const float *adj_tab;   // device adjoint table
     int *status;
+    // Host copy of the adjoint table (coefficients set from host memory), or
+    // null: when present the input-gradient kernel takes its coefficients from
+    // the kernel parameter bank.
+    const float *host_adj_tab = nullptr;
 };
 
 struct AdjLaunch {

@@ -103,6 +103,27 @@ def test_grad_alignment_paths(n, shift):
     check_gh(gh.cpu().numpy(), x, h, gy, P, Q, M)
 
 
+@pytest.mark.parametrize("P,Q,M", [(9, 9, 4), (7, 0, 3), (1, 1, 0), (11, 11, 7), (3, 5, 2)])
+@pytest.mark.parametrize("n", [4099, 70001])
+def test_grad_host_coefficients_param_bank(P, Q, M, n):
+    """Coefficients set from host memory: the input gradient takes them from the
+    kernel parameter bank (device-set ones from shared memory); both against
+    the oracle."""
+    x, h, gy = make(P, Q, M, n, 31 * P + M + n)
+    xd, gyd = torch.from_numpy(x).cuda(), torch.from_numpy(gy).cuda()
+    _, gx_ref = oracle.grad(x, h, gy, P, Q, M, want_h=False)
+    for src in (h, torch.from_numpy(h).cuda()):
+        f = dpd.DPD(P, Q, M)
+        f.set_coeffs(src)
+        gx = torch.empty_like(xd)
+        gh = torch.empty(f.K, dtype=torch.complex64, device="cuda")
+        f.grad(xd, gyd, gh=gh, gx=gx)
+        f.sync_status()
+        f.close()
+        assert_parity(gx.cpu().numpy(), gx_ref, what=f"gx P={P} Q={Q} M={M} host={not torch.is_tensor(src)}")
+        check_gh(gh.cpu().numpy(), x, h, gy, P, Q, M)
+
+
 def test_adj_launch_limits():
     f = dpd.DPD(5, 5, 2)
     for bad in [(0, 2), (1, 0), (1, 6), (10 ** 6, 2)]:
