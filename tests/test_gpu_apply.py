@@ -52,12 +52,16 @@ def test_table2_p5_q3_l5_ragged():
     assert_parity(run_gpu(x, h, 5, 3, 4), oracle.apply(x, h, 5, 3, 4), what="table 2")
 
 
-def test_config1_full_size_ofdm_p9_m4():
-    """Full 2^24-sample OFDM workload at the benchmark's launch shape."""
+@pytest.mark.parametrize("launch", [None, dict(mode=3, V=8, warps=12, stages=3)], ids=["default", "tuned"])
+def test_config1_full_size_ofdm_p9_m4(launch):
+    """Full 2^24-sample OFDM workload, coefficients from host memory as the
+    benchmark installs them, at the default shape and at the shape the
+    autotuner picks on GB300 (parameter-bank packed FMAs, V 8, 12 consumer
+    warps, 3 stages)."""
     n = 1 << 24
     x = synth.ofdm2(n, key=(0, 0))
     h = synth.coeffs(9, 9, 4, key=(0, 1))
-    y = run_gpu(x, h, 9, 9, 4)
+    y = run_gpu(x, h, 9, 9, 4, launch=launch, host_coeffs=True)
     assert_parity(y, oracle.apply(x, h, 9, 9, 4), what="config 1")
 
 

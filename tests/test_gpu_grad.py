@@ -124,6 +124,28 @@ def test_grad_host_coefficients_param_bank(P, Q, M, n):
         check_gh(gh.cpu().numpy(), x, h, gy, P, Q, M)
 
 
+@pytest.mark.parametrize("P,Q,M", [(9, 9, 4), (7, 7, 3)])
+def test_grad_full_size_2p24(P, Q, M):
+    """Both gradients on the 2^24-sample OFDM signal with an OFDM output
+    gradient and host-set coefficients: the adjoint benchmark's workload and
+    launch path."""
+    n = 1 << 24
+    x = synth.ofdm2(n, key=(0, 0))
+    gy = synth.ofdm2(n, key=(0, 1))
+    h = synth.coeffs(P, Q, M, key=(0, 1))
+    f = dpd.DPD(P, Q, M)
+    f.set_coeffs(h)
+    xd, gyd = torch.from_numpy(x).cuda(), torch.from_numpy(gy).cuda()
+    gx = torch.empty_like(xd)
+    gh = torch.empty(f.K, dtype=torch.complex64, device="cuda")
+    f.grad(xd, gyd, gh=gh, gx=gx)
+    f.sync_status()
+    f.close()
+    _, gx_ref = oracle.grad(x, h, gy, P, Q, M, want_h=False)
+    assert_parity(gx.cpu().numpy(), gx_ref, what=f"gx 2^24 P={P} M={M}")
+    check_gh(gh.cpu().numpy(), x, h, gy, P, Q, M)
+
+
 def test_adj_launch_limits():
     f = dpd.DPD(5, 5, 2)
     for bad in [(0, 2), (1, 0), (1, 6), (10 ** 6, 2)]:
