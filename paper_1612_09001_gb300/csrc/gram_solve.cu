@@ -174,52 +174,84 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b)   // a * conj(b)
     return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
+// 1/sqrt(x) for a pivot x in (1e-30, 1e30): the FP32 hardware estimate refined
+// by two Newton-Raphson steps y <- y (3 - x y^2) / 2 in FP64 (each step squares
+// the relative error: about 2^-22 -> 2^-44 -> FP64 rounding).  Six FP64
+// operations on the factorisation's sequential path instead of a full FP64
+// square root and division.
+__device__ __forceinline__ double rsqrt_newton(double x)
+{
+    double y = (double)rsqrtf((float)x);
+    const double hx = 0.5 * x;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const double p = hx * y;
+        const double e = fma(-p, y, 0.5);   // 1/2 - x y^2 / 2
+        y = fma(y, e, y);
+    }
+    return y;
+}
+
 // One CTA per problem: A = D G D in shared memory, factored in place (right
-// looking, lower triangle), written to L; d = diag(G)^{-1/2}.
-__global__ void chol_kernel(const double2 *__restrict__ Gall, int K, double2 *__restrict__ Lall,
-                            double *__restrict__ dall, int *__restrict__ info)
+// looking, lower triangle), written to L; d = diag(G)^{-1/2}.  On this GPU FP64
+// runs at a small fraction of the FP32 rate (about two FMAs per clock per SM),
+// so the K^3/6 complex updates of one problem (K = 97: 0.6 M FP64 FMAs) and the
+// K sequential pivot steps bound the kernel: each complex update is four fused
+// multiply-adds, and the pivot's reciprocal root comes from rsqrt_newton.  Step
+// j: thread 0 takes the pivot; the threads scale column j; the trailing update
+// of rows i > j, columns j < k <= i runs on a 16 x 16 thread grid.
+__global__ void __launch_bounds__(256) chol_kernel(const double2 *__restrict__ Gall, int K,
+                                                   double2 *__restrict__ Lall, double *__restrict__ dall,
+                                                   int *__restrict__ info)
 {
     extern __shared__ double2 A[];   // K x K
     __shared__ double dsh[kMaxT * 12 + 1];
+    __shared__ double rinv;
     __shared__ int bad;
     const int p = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int tx = tid & 15, ty = tid >> 4, nty = nt >> 4;
     const double2 *G = Gall + (size_t)p * K * K;
     if (tid == 0) bad = 0;
+    __syncthreads();
     for (int i = tid; i < K; i += nt) {
         const double gii = G[(size_t)i * K + i].x;
         dsh[i] = gii > 0.0 ? 1.0 / sqrt(gii) : 0.0;
         if (!(gii > 0.0)) atomicMax(&bad, i + 1);
     }
     __syncthreads();
-    for (int e = tid; e < K * K; e += nt) {
-        const int i = e / K, j = e % K;
-        const double2 v = G[e];
-        A[e] = make_double2(v.x * dsh[i] * dsh[j], v.y * dsh[i] * dsh[j]);
-    }
+    for (int i = ty; i < K; i += nty)
+        for (int k = tx; k <= i; k += 16) {
+            const double2 v = G[(size_t)i * K + k];
+            const double sc = dsh[i] * dsh[k];
+            A[(size_t)i * K + k] = make_double2(v.x * sc, v.y * sc);
+        }
     __syncthreads();
     for (int j = 0; j < K && !bad; ++j) {
         if (tid == 0) {
             const double piv = A[(size_t)j * K + j].x;
-            if (!(piv > 0.0) || !isfinite(piv))
+            if (!(piv > 1e-30 && piv < 1e30)) {   // not positive definite (or numerically singular)
                 bad = j + 1;
-            else
-                A[(size_t)j * K + j] = make_double2(sqrt(piv), 0.0);
+            } else {
+                const double ri = rsqrt_newton(piv);
+                A[(size_t)j * K + j] = make_double2(piv * ri, 0.0);
+                rinv = ri;
+            }
         }
         __syncthreads();
         if (bad) break;
-        const double ljj = A[(size_t)j * K + j].x;
+        const double ri = rinv;
         for (int i = j + 1 + tid; i < K; i += nt) {
             const double2 v = A[(size_t)i * K + j];
-            A[(size_t)i * K + j] = make_double2(v.x / ljj, v.y / ljj);
+            A[(size_t)i * K + j] = make_double2(v.x * ri, v.y * ri);
         }
         __syncthreads();
-        const int m = K - j - 1;   // trailing update of the lower triangle
-        for (int e = tid; e < m * m; e += nt) {
-            const int i = j + 1 + e / m, k = j + 1 + e % m;
-            if (k <= i) {
-                const double2 u = cmulc(A[(size_t)i * K + j], A[(size_t)k * K + j]);
-                A[(size_t)i * K + k].x -= u.x;
-                A[(size_t)i * K + k].y -= u.y;
+        for (int i = j + 1 + ty; i < K; i += nty) {   // A[i][k] -= L[i][j] conj(L[k][j])
+            const double2 a = A[(size_t)i * K + j];
+            for (int k = j + 1 + tx; k <= i; k += 16) {
+                const double2 b = A[(size_t)k * K + j];
+                double2 &c = A[(size_t)i * K + k];
+                c.x = fma(-a.x, b.x, fma(-a.y, b.y, c.x));
+                c.y = fma(-a.y, b.x, fma(a.x, b.y, c.y));
             }
         }
         __syncthreads();
@@ -247,68 +279,78 @@ cudaError_t launch_chol(const double2 *G, int nprob, int K, double2 *L, double *
     return cudaGetLastError();
 }
 
-// One warp per problem: G x = rhs with G = D^{-1} L L^H D^{-1}:  x = D (L^H)^{-1} L^{-1} D rhs.
-__global__ void chol_solve_kernel(const double2 *__restrict__ Lall, const double *__restrict__ dall,
-                                  const int *__restrict__ info, const double2 *__restrict__ rhs, int K,
-                                  double2 *__restrict__ h, int accumulate)
+// One CTA per problem: G x = rhs with G = D^{-1} L L^H D^{-1}:
+// x = D (L^H)^{-1} L^{-1} D rhs.  The CTA stages L and the reciprocals of its
+// diagonal in shared memory, then runs both substitutions column by column
+// with element k of the right-hand side on thread k: each step finishes one
+// element, publishes it through shared memory and every later element takes
+// its update in parallel (one complex FMA per thread and step, one barrier).
+__global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restrict__ Lall,
+                                                         const double *__restrict__ dall,
+                                                         const int *__restrict__ info,
+                                                         const double2 *__restrict__ rhs, int K,
+                                                         double2 *__restrict__ h, int accumulate)
 {
-    __shared__ double2 w[12 * kMaxT + 1];
-    const int p = blockIdx.x, lane = threadIdx.x;
-    if (info[p] != 0) return;
+    extern __shared__ double2 Ls[];   // K x K, lower triangle used
+    __shared__ double inv[12 * kMaxT + 1];
+    __shared__ double2 piv[2];        // the element finished by the current step (double-buffered)
+    const int p = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    if (info[p] != 0) return;   // uniform over the CTA
     const double2 *L = Lall + (size_t)p * K * K;
     const double *d = dall + (size_t)p * K;
+    for (int e = tid; e < K * K; e += nt) Ls[e] = L[e];
+    __syncthreads();
+    for (int i = tid; i < K; i += nt) inv[i] = 1.0 / Ls[(size_t)i * K + i].x;
     const double2 *b = rhs + (size_t)p * K;
-    for (int i = lane; i < K; i += 32) w[i] = make_double2(b[i].x * d[i], b[i].y * d[i]);
-    __syncwarp();
+    const int k = tid;   // this thread's element (threads k >= K idle but join the barriers)
+    double2 w = k < K ? make_double2(b[k].x * d[k], b[k].y * d[k]) : make_double2(0.0, 0.0);
+    __syncthreads();
     for (int i = 0; i < K; ++i) {   // forward: L w = D b
-        double2 s = make_double2(0.0, 0.0);
-        for (int k = lane; k < i; k += 32) {
-            const double2 u = cmul(L[(size_t)i * K + k], w[k]);
-            s.x += u.x;
-            s.y += u.y;
+        if (k == i) {
+            w = make_double2(w.x * inv[i], w.y * inv[i]);
+            piv[i & 1] = w;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        __syncthreads();
+        if (k > i && k < K) {   // w_k -= L[k][i] w_i
+            const double2 l = Ls[(size_t)k * K + i], v = piv[i & 1];
+            w.x = fma(-l.x, v.x, fma(l.y, v.y, w.x));
+            w.y = fma(-l.x, v.y, fma(-l.y, v.x, w.y));
         }
-        if (lane == 0) {
-            const double lii = L[(size_t)i * K + i].x;
-            w[i] = make_double2((w[i].x - s.x) / lii, (w[i].y - s.y) / lii);
-        }
-        __syncwarp();
     }
     for (int i = K - 1; i >= 0; --i) {   // backward: L^H v = w
-        double2 s = make_double2(0.0, 0.0);
-        for (int k = i + 1 + lane; k < K; k += 32) {
-            const double2 l = L[(size_t)k * K + i];
-            const double2 u = make_double2(l.x * w[k].x + l.y * w[k].y, l.x * w[k].y - l.y * w[k].x);   // conj(l) w
-            s.x += u.x;
-            s.y += u.y;
+        if (k == i) {
+            w = make_double2(w.x * inv[i], w.y * inv[i]);
+            piv[i & 1] = w;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        __syncthreads();
+        if (k < i) {   // w_k -= conj(L[i][k]) v_i
+            const double2 l = Ls[(size_t)i * K + k], v = piv[i & 1];
+            w.x = fma(-l.x, v.x, fma(-l.y, v.y, w.x));
+            w.y = fma(-l.x, v.y, fma(l.y, v.x, w.y));
         }
-        if (lane == 0) {
-            const double lii = L[(size_t)i * K + i].x;
-            w[i] = make_double2((w[i].x - s.x) / lii, (w[i].y - s.y) / lii);
-        }
-        __syncwarp();
     }
-    double2 *out = h + (size_t)p * K;
-    for (int i = lane; i < K; i += 32) {
-        const double2 x = make_double2(w[i].x * d[i], w[i].y * d[i]);
+    if (k < K) {
+        double2 *out = h + (size_t)p * K;
+        const double2 x = make_double2(w.x * d[k], w.y * d[k]);
         if (accumulate)
-            out[i] = make_double2(out[i].x + x.x, out[i].y + x.y);
+            out[k] = make_double2(out[k].x + x.x, out[k].y + x.y);
         else
-            out[i] = x;
+            out[k] = x;
     }
 }
 
 cudaError_t launch_chol_solve(const double2 *L, const double *d, const int *info, const double2 *rhs, int nprob,
                               int K, double2 *h, int accumulate, cudaStream_t s)
 {
-    chol_solve_kernel<<<nprob, 32, 0, s>>>(L, d, info, rhs, K, h, accumulate);
+    const size_t smem = sizeof(double2) * K * K;
+    static size_t set = 0;
+    if (smem > set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set = smem;
+    }
+    chol_solve_kernel<<<nprob, 256, smem, s>>>(L, d, info, rhs, K, h, accumulate);
     count_launch();
     return cudaGetLastError();
 }
@@ -345,19 +387,33 @@ cudaError_t launch_residual(const float2 *t, const float2 *y, int64_t n, float2 
     return cudaGetLastError();
 }
 
-// Per-block FP64 sums of |e|^2 and |t|^2, then one fixed-order final sum.
 constexpr int kNormBlocks = 1024;
 
+// Per-block sums of |e|^2 and |t|^2, then one fixed-order final sum.  The
+// squares of the FP32 samples are formed and summed in FP32 over runs of 32
+// samples per thread, and the runs are added in FP64 (FP64 arithmetic on this
+// GPU is a small fraction of the FP32 rate); a run's FP32 sum carries at most
+// about 2e-6 relative error, well below what the reported ratio needs.
 __global__ void sqnorm2_kernel(const float2 *__restrict__ e, const float2 *__restrict__ t, int64_t n,
                                double *__restrict__ part)
 {
     __shared__ double se[256], st[256];
     double a = 0.0, b = 0.0;
+    float a32 = 0.f, b32 = 0.f;
+    int run = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float2 x = e[i], y = t[i];
-        a += (double)x.x * x.x + (double)x.y * x.y;
-        b += (double)y.x * y.x + (double)y.y * y.y;
+        a32 = fmaf(x.x, x.x, fmaf(x.y, x.y, a32));
+        b32 = fmaf(y.x, y.x, fmaf(y.y, y.y, b32));
+        if (++run == 32) {
+            a += (double)a32;
+            b += (double)b32;
+            a32 = b32 = 0.f;
+            run = 0;
+        }
     }
+    a += (double)a32;
+    b += (double)b32;
     se[threadIdx.x] = a;
     st[threadIdx.x] = b;
     __syncthreads();
@@ -374,22 +430,37 @@ __global__ void sqnorm2_kernel(const float2 *__restrict__ e, const float2 *__res
     }
 }
 
+// Fixed-order sum of the nb per-block pairs: thread t adds pairs t, t + 256,
+// ..., then a shared-memory tree (one block of 256 threads).
 __global__ void sum_pairs_kernel(const double *__restrict__ part, int nb, double *__restrict__ out)
 {
+    __shared__ double sa[256], sb[256];
     double a = 0.0, b = 0.0;
-    for (int i = 0; i < nb; ++i) {
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         a += part[2 * i];
         b += part[2 * i + 1];
     }
-    out[0] = a;
-    out[1] = b;
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sa[threadIdx.x] += sa[threadIdx.x + o];
+            sb[threadIdx.x] += sb[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sa[0];
+        out[1] = sb[0];
+    }
 }
 
 cudaError_t launch_sqnorm2(const float2 *e, const float2 *t, int64_t n, double *part, double *out, cudaStream_t s)
 {
     sqnorm2_kernel<<<kNormBlocks, 256, 0, s>>>(e, t, n, part);
     count_launch();
-    sum_pairs_kernel<<<1, 1, 0, s>>>(part, kNormBlocks, out);
+    sum_pairs_kernel<<<1, 256, 0, s>>>(part, kNormBlocks, out);
     count_launch();
     return cudaGetLastError();
 }

@@ -71,6 +71,22 @@ def test_estimate_recovers_model_coefficients(precision, tol):
     assert st["rel_residual"] < 1e-10 and st["cond_est"] >= 1.0
 
 
+@pytest.mark.parametrize("P,Q,M", [(5, 3, 4), (9, 9, 4), (11, 11, 7)])
+def test_condition_estimate_matches_numpy(P, Q, M):
+    """stats["cond_est"] (power iterations on the device Cholesky factor) is the
+    2-norm condition number of D G D, D = diag(G)^(-1/2), for the Gram matrix
+    of the same precision: compared with numpy's SVD-based cond."""
+    u, t, _ = _ls_problem(P, Q, M, 40000, 3)
+    f = dpd.DPD(P, Q, M)
+    ud, td = torch.from_numpy(u).cuda(), torch.from_numpy(t).cuda()
+    _, st = f.estimate(ud, td, precision="tf32x3", refine_iters=0)
+    G, _, _ = f.gram(ud, td, precision="tf32x3")
+    G = G.cpu().numpy()
+    dinv = 1.0 / np.sqrt(np.real(np.diag(G)))
+    ref = np.linalg.cond(G * dinv[:, None] * dinv[None, :])
+    assert abs(st["cond_est"] - ref) <= 1e-6 * ref, (st["cond_est"], ref)
+
+
 def test_estimate_full_size_p11_m7():
     """2^22 rows x 97 columns: recovery of the generating coefficients and
     sampled Gram entries (each an O(n) sum) against FP64 numpy."""
