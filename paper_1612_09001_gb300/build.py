@@ -103,7 +103,7 @@ def build(jobs: int | None = None, verbose_ptxas: bool = False, force: bool = Fa
                 sys.stderr.write(log)
     if _stale(LIB_PATH, objs):
         tmp = LIB_PATH + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
