@@ -37,7 +37,8 @@ namespace dpd {
 
 constexpr int kAdjV = 4;          // samples per thread (plain-load kernels, staged gx)
 constexpr int kAdjGhV = 4;        // samples per thread of the staged gh kernel
-constexpr int kAdjWarps = 8;      // consumer warps of the staged kernels
+constexpr int kAdjWarps = 8;      // consumer warps of the staged gx kernel
+constexpr int kAdjGhWarps = 10;   // consumer warps of the staged gh kernel
 constexpr int kAdjStages = 4;     // ring slots of the staged gx kernel
 constexpr int kAdjGhStages = 4;   // ring slots of the staged gh kernel
 
@@ -493,33 +494,33 @@ __global__ void __launch_bounds__(256) adj_gh_kernel(AdjArgs a, int T, int Bp, i
                                 a.partials + (size_t)blockIdx.x * K);
 }
 
-// Staged variant: grid (blocks, tap groups) of persistent CTAs (kAdjWarps
+// Staged variant: grid (blocks, tap groups) of persistent CTAs (kAdjGhWarps
 // consumer warps + 1 producer warp); every CTA streams all tiles of its
 // blockIdx.x share.  x and gy 16-byte aligned.
 template <int B, int TG, int V>
-__global__ void __launch_bounds__(32 * (kAdjWarps + 1))
+__global__ void __launch_bounds__(32 * (kAdjGhWarps + 1), 1)
     adj_gh_tma_kernel(AdjArgs a, int stages, int64_t ntiles, int T, int Bp, int Bq, int K)
 {
     constexpr int NA = 4 * B * TG + 2;
     constexpr int NP = NA / 2;
-    constexpr int S = kAdjWarps * 32 * V;
+    constexpr int S = kAdjGhWarps * 32 * V;
     constexpr int NG = V + TG - 1;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);   // full[s], empty[s]
     float *red = reinterpret_cast<float *>(smem + 128);
-    float2 *ring = reinterpret_cast<float2 *>(smem + adj_staged_smem(S, 0, kAdjWarps * NA));
+    float2 *ring = reinterpret_cast<float2 *>(smem + adj_staged_smem(S, 0, kAdjGhWarps * NA));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k0 = blockIdx.y * TG;
     const bool group0 = blockIdx.y == 0;
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(smem_addr(&bars[s]), 1);
-            mbar_init(smem_addr(&bars[stages + s]), kAdjWarps);
+            mbar_init(smem_addr(&bars[stages + s]), kAdjGhWarps);
         }
         fence_barrier_init();
     }
     __syncthreads();
-    if (warp == kAdjWarps) {
+    if (warp == kAdjGhWarps) {
         if (lane == 0) adj_produce(a, ring, bars, stages, S, ntiles);
         return;
     }
@@ -550,7 +551,7 @@ __global__ void __launch_bounds__(32 * (kAdjWarps + 1))
         if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));
         gh_accumulate<B, TG, V>(xs, g, group0, acc2);
     }
-    gh_reduce_row<B, TG, true>(acc2, red, kAdjWarps, tid, k0, group0, T, Bp, Bq,
+    gh_reduce_row<B, TG, true>(acc2, red, kAdjGhWarps, tid, k0, group0, T, Bp, Bq,
                                a.partials + (size_t)blockIdx.x * K);
 }
 
@@ -614,14 +615,14 @@ cudaError_t launch_adj_gh_tg(const AdjArgs &a, int blocks, int T, int Bp, int Bq
     dim3 grid((unsigned)blocks, (unsigned)groups);
     if (adj_staged_ok(a)) {
         constexpr int V = kAdjGhV;
-        constexpr int S = kAdjWarps * 32 * V;
+        constexpr int S = kAdjGhWarps * 32 * V;
         constexpr int NA = 4 * B * TG + 2;
-        const size_t smem = adj_staged_smem(S, kAdjGhStages, kAdjWarps * NA);
+        const size_t smem = adj_staged_smem(S, kAdjGhStages, kAdjGhWarps * NA);
         static const cudaError_t attr = cudaFuncSetAttribute(
             adj_gh_tma_kernel<B, TG, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (attr != cudaSuccess) return attr;
         const int64_t ntiles = (a.n + S - 1) / S;
-        adj_gh_tma_kernel<B, TG, V><<<grid, 32 * (kAdjWarps + 1), smem, s>>>(a, kAdjGhStages, ntiles, T, Bp, Bq, K);
+        adj_gh_tma_kernel<B, TG, V><<<grid, 32 * (kAdjGhWarps + 1), smem, s>>>(a, kAdjGhStages, ntiles, T, Bp, Bq, K);
         count_launch();
         return cudaGetLastError();
     }
