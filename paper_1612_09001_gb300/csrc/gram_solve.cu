@@ -281,10 +281,14 @@ cudaError_t launch_chol(const double2 *G, int nprob, int K, double2 *L, double *
 
 // One CTA per problem: G x = rhs with G = D^{-1} L L^H D^{-1}:
 // x = D (L^H)^{-1} L^{-1} D rhs.  The CTA stages L and the reciprocals of its
-// diagonal in shared memory, then runs both substitutions column by column
-// with element k of the right-hand side on thread k: each step finishes one
-// element, publishes it through shared memory and every later element takes
-// its update in parallel (one complex FMA per thread and step, one barrier).
+// diagonal in shared memory and solves in blocks of 32 rows.  A diagonal block
+// is one warp's sequential part (element b0 + l on lane l; each step scales one
+// element, broadcasts it by shuffle and updates the later lanes); the
+// off-diagonal update of the remaining rows is a block matrix-vector product
+// spread over the CTA (8 threads per row).  Two CTA barriers per block instead
+// of one per row.
+constexpr int kSolveNB = 32;
+
 __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restrict__ Lall,
                                                          const double *__restrict__ dall,
                                                          const int *__restrict__ info,
@@ -293,45 +297,93 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restri
 {
     extern __shared__ double2 Ls[];   // K x K, lower triangle used
     __shared__ double inv[12 * kMaxT + 1];
-    __shared__ double2 piv[2];        // the element finished by the current step (double-buffered)
+    __shared__ double2 wv[12 * kMaxT + 1];
     const int p = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int sub = tid & 7, grp = tid >> 3, ngrp = nt >> 3;   // 8 threads per row in the updates
     if (info[p] != 0) return;   // uniform over the CTA
     const double2 *L = Lall + (size_t)p * K * K;
     const double *d = dall + (size_t)p * K;
+    const double2 *b = rhs + (size_t)p * K;
     for (int e = tid; e < K * K; e += nt) Ls[e] = L[e];
+    for (int i = tid; i < K; i += nt) wv[i] = make_double2(b[i].x * d[i], b[i].y * d[i]);
     __syncthreads();
     for (int i = tid; i < K; i += nt) inv[i] = 1.0 / Ls[(size_t)i * K + i].x;
-    const double2 *b = rhs + (size_t)p * K;
-    const int k = tid;   // this thread's element (threads k >= K idle but join the barriers)
-    double2 w = k < K ? make_double2(b[k].x * d[k], b[k].y * d[k]) : make_double2(0.0, 0.0);
     __syncthreads();
-    for (int i = 0; i < K; ++i) {   // forward: L w = D b
-        if (k == i) {
-            w = make_double2(w.x * inv[i], w.y * inv[i]);
-            piv[i & 1] = w;
+
+    // forward: L w = D b
+    for (int b0 = 0; b0 < K; b0 += kSolveNB) {
+        const int nb = min(kSolveNB, K - b0);
+        if (warp == 0) {
+            double2 v = lane < nb ? wv[b0 + lane] : make_double2(0.0, 0.0);
+            for (int i = 0; i < nb; ++i) {
+                if (lane == i) v = make_double2(v.x * inv[b0 + i], v.y * inv[b0 + i]);
+                const double2 vi = make_double2(__shfl_sync(0xffffffffu, v.x, i), __shfl_sync(0xffffffffu, v.y, i));
+                if (lane > i && lane < nb) {   // v -= L[b0+lane][b0+i] vi
+                    const double2 l = Ls[(size_t)(b0 + lane) * K + b0 + i];
+                    v.x = fma(-l.x, vi.x, fma(l.y, vi.y, v.x));
+                    v.y = fma(-l.x, vi.y, fma(-l.y, vi.x, v.y));
+                }
+            }
+            if (lane < nb) wv[b0 + lane] = v;
         }
         __syncthreads();
-        if (k > i && k < K) {   // w_k -= L[k][i] w_i
-            const double2 l = Ls[(size_t)k * K + i], v = piv[i & 1];
-            w.x = fma(-l.x, v.x, fma(l.y, v.y, w.x));
-            w.y = fma(-l.x, v.y, fma(-l.y, v.x, w.y));
-        }
-    }
-    for (int i = K - 1; i >= 0; --i) {   // backward: L^H v = w
-        if (k == i) {
-            w = make_double2(w.x * inv[i], w.y * inv[i]);
-            piv[i & 1] = w;
+        for (int r0 = b0 + nb; r0 < K; r0 += ngrp) {   // rows below: w_r -= L[r][block] w[block]
+            const int r = r0 + grp;
+            double2 acc = make_double2(0.0, 0.0);
+            if (r < K)
+                for (int c = sub; c < nb; c += 8) {
+                    const double2 l = Ls[(size_t)r * K + b0 + c], v = wv[b0 + c];
+                    acc.x = fma(l.x, v.x, fma(-l.y, v.y, acc.x));
+                    acc.y = fma(l.x, v.y, fma(l.y, v.x, acc.y));
+                }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            }
+            if (r < K && sub == 0) wv[r] = make_double2(wv[r].x - acc.x, wv[r].y - acc.y);
         }
         __syncthreads();
-        if (k < i) {   // w_k -= conj(L[i][k]) v_i
-            const double2 l = Ls[(size_t)i * K + k], v = piv[i & 1];
-            w.x = fma(-l.x, v.x, fma(-l.y, v.y, w.x));
-            w.y = fma(-l.x, v.y, fma(l.y, v.x, w.y));
-        }
     }
-    if (k < K) {
-        double2 *out = h + (size_t)p * K;
-        const double2 x = make_double2(w.x * d[k], w.y * d[k]);
+    // backward: L^H v = w
+    for (int b0 = ((K - 1) / kSolveNB) * kSolveNB; b0 >= 0; b0 -= kSolveNB) {
+        const int nb = min(kSolveNB, K - b0);
+        if (warp == 0) {
+            double2 v = lane < nb ? wv[b0 + lane] : make_double2(0.0, 0.0);
+            for (int i = nb - 1; i >= 0; --i) {
+                if (lane == i) v = make_double2(v.x * inv[b0 + i], v.y * inv[b0 + i]);
+                const double2 vi = make_double2(__shfl_sync(0xffffffffu, v.x, i), __shfl_sync(0xffffffffu, v.y, i));
+                if (lane < i) {   // v -= conj(L[b0+i][b0+lane]) vi
+                    const double2 l = Ls[(size_t)(b0 + i) * K + b0 + lane];
+                    v.x = fma(-l.x, vi.x, fma(-l.y, vi.y, v.x));
+                    v.y = fma(-l.x, vi.y, fma(l.y, vi.x, v.y));
+                }
+            }
+            if (lane < nb) wv[b0 + lane] = v;
+        }
+        __syncthreads();
+        for (int r0 = 0; r0 < b0; r0 += ngrp) {   // rows above: w_r -= sum_c conj(L[b0+c][r]) w[b0+c]
+            const int r = r0 + grp;
+            double2 acc = make_double2(0.0, 0.0);
+            if (r < b0)
+                for (int c = sub; c < nb; c += 8) {
+                    const double2 l = Ls[(size_t)(b0 + c) * K + r], v = wv[b0 + c];
+                    acc.x = fma(l.x, v.x, fma(l.y, v.y, acc.x));
+                    acc.y = fma(l.x, v.y, fma(-l.y, v.x, acc.y));
+                }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            }
+            if (r < b0 && sub == 0) wv[r] = make_double2(wv[r].x - acc.x, wv[r].y - acc.y);
+        }
+        __syncthreads();
+    }
+    double2 *out = h + (size_t)p * K;
+    for (int k = tid; k < K; k += nt) {
+        const double2 x = make_double2(wv[k].x * d[k], wv[k].y * d[k]);
         if (accumulate)
             out[k] = make_double2(out[k].x + x.x, out[k].y + x.y);
         else
