@@ -280,13 +280,16 @@ cudaError_t launch_chol(const double2 *G, int nprob, int K, double2 *L, double *
 }
 
 // One CTA per problem: G x = rhs with G = D^{-1} L L^H D^{-1}:
-// x = D (L^H)^{-1} L^{-1} D rhs.  The CTA stages L and the reciprocals of its
-// diagonal in shared memory and solves in blocks of 32 rows.  A diagonal block
-// is one warp's sequential part (element b0 + l on lane l; each step scales one
-// element, broadcasts it by shuffle and updates the later lanes); the
-// off-diagonal update of the remaining rows is a block matrix-vector product
-// spread over the CTA (8 threads per row).  Two CTA barriers per block instead
-// of one per row.
+// x = D (L^H)^{-1} L^{-1} D rhs.  With L = U Lambda (U unit lower triangular,
+// Lambda = diag(L)): y = U^{-1} (D rhs), z = Lambda^{-2} y, v = U^{-H} z, x = D v,
+// so the sequential steps carry no division or scaling.  The CTA stages U
+// (the columns of L divided by their diagonal) in shared memory and solves in
+// blocks of 32 rows: a diagonal block is one warp's sequential part (element
+// b0 + l on lane l; each step broadcasts one finished element and the later
+// lanes take a complex FMA -- two dependent FP64 FMAs, the latency that bounds
+// the solve on this GPU, where a dependent FP64 FMA takes 64 cycles); the
+// update of the remaining rows is a block matrix-vector product spread over the
+// CTA (8 threads per row).
 constexpr int kSolveNB = 32;
 
 __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restrict__ Lall,
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restri
                                                          const double2 *__restrict__ rhs, int K,
                                                          double2 *__restrict__ h, int accumulate)
 {
-    extern __shared__ double2 Ls[];   // K x K, lower triangle used
+    extern __shared__ double2 Us[];   // K x K, strictly lower triangle used: U = L Lambda^{-1}
     __shared__ double inv[12 * kMaxT + 1];
     __shared__ double2 wv[12 * kMaxT + 1];
     const int p = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -305,37 +308,42 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restri
     const double2 *L = Lall + (size_t)p * K * K;
     const double *d = dall + (size_t)p * K;
     const double2 *b = rhs + (size_t)p * K;
-    for (int e = tid; e < K * K; e += nt) Ls[e] = L[e];
-    for (int i = tid; i < K; i += nt) wv[i] = make_double2(b[i].x * d[i], b[i].y * d[i]);
+    for (int i = tid; i < K; i += nt) {
+        inv[i] = 1.0 / L[(size_t)i * K + i].x;
+        wv[i] = make_double2(b[i].x * d[i], b[i].y * d[i]);
+    }
     __syncthreads();
-    for (int i = tid; i < K; i += nt) inv[i] = 1.0 / Ls[(size_t)i * K + i].x;
+    for (int e = tid; e < K * K; e += nt) {
+        const int i = e / K, k = e % K;
+        const double2 l = L[e];
+        Us[e] = k < i ? make_double2(l.x * inv[k], l.y * inv[k]) : make_double2(0.0, 0.0);
+    }
     __syncthreads();
 
-    // forward: L w = D b
+    // forward: U y = D b
     for (int b0 = 0; b0 < K; b0 += kSolveNB) {
         const int nb = min(kSolveNB, K - b0);
         if (warp == 0) {
             double2 v = lane < nb ? wv[b0 + lane] : make_double2(0.0, 0.0);
             for (int i = 0; i < nb; ++i) {
-                if (lane == i) v = make_double2(v.x * inv[b0 + i], v.y * inv[b0 + i]);
                 const double2 vi = make_double2(__shfl_sync(0xffffffffu, v.x, i), __shfl_sync(0xffffffffu, v.y, i));
-                if (lane > i && lane < nb) {   // v -= L[b0+lane][b0+i] vi
-                    const double2 l = Ls[(size_t)(b0 + lane) * K + b0 + i];
-                    v.x = fma(-l.x, vi.x, fma(l.y, vi.y, v.x));
-                    v.y = fma(-l.x, vi.y, fma(-l.y, vi.x, v.y));
+                if (lane > i && lane < nb) {   // v -= U[b0+lane][b0+i] vi
+                    const double2 u = Us[(size_t)(b0 + lane) * K + b0 + i];
+                    v.x = fma(-u.x, vi.x, fma(u.y, vi.y, v.x));
+                    v.y = fma(-u.x, vi.y, fma(-u.y, vi.x, v.y));
                 }
             }
             if (lane < nb) wv[b0 + lane] = v;
         }
         __syncthreads();
-        for (int r0 = b0 + nb; r0 < K; r0 += ngrp) {   // rows below: w_r -= L[r][block] w[block]
+        for (int r0 = b0 + nb; r0 < K; r0 += ngrp) {   // rows below: y_r -= U[r][block] y[block]
             const int r = r0 + grp;
             double2 acc = make_double2(0.0, 0.0);
             if (r < K)
                 for (int c = sub; c < nb; c += 8) {
-                    const double2 l = Ls[(size_t)r * K + b0 + c], v = wv[b0 + c];
-                    acc.x = fma(l.x, v.x, fma(-l.y, v.y, acc.x));
-                    acc.y = fma(l.x, v.y, fma(l.y, v.x, acc.y));
+                    const double2 u = Us[(size_t)r * K + b0 + c], v = wv[b0 + c];
+                    acc.x = fma(u.x, v.x, fma(-u.y, v.y, acc.x));
+                    acc.y = fma(u.x, v.y, fma(u.y, v.x, acc.y));
                 }
 #pragma unroll
             for (int o = 1; o < 8; o <<= 1) {
@@ -346,31 +354,35 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restri
         }
         __syncthreads();
     }
-    // backward: L^H v = w
+    for (int i = tid; i < K; i += nt) {   // z = Lambda^{-2} y
+        const double s = inv[i] * inv[i];
+        wv[i] = make_double2(wv[i].x * s, wv[i].y * s);
+    }
+    __syncthreads();
+    // backward: U^H v = z
     for (int b0 = ((K - 1) / kSolveNB) * kSolveNB; b0 >= 0; b0 -= kSolveNB) {
         const int nb = min(kSolveNB, K - b0);
         if (warp == 0) {
             double2 v = lane < nb ? wv[b0 + lane] : make_double2(0.0, 0.0);
             for (int i = nb - 1; i >= 0; --i) {
-                if (lane == i) v = make_double2(v.x * inv[b0 + i], v.y * inv[b0 + i]);
                 const double2 vi = make_double2(__shfl_sync(0xffffffffu, v.x, i), __shfl_sync(0xffffffffu, v.y, i));
-                if (lane < i) {   // v -= conj(L[b0+i][b0+lane]) vi
-                    const double2 l = Ls[(size_t)(b0 + i) * K + b0 + lane];
-                    v.x = fma(-l.x, vi.x, fma(-l.y, vi.y, v.x));
-                    v.y = fma(-l.x, vi.y, fma(l.y, vi.x, v.y));
+                if (lane < i) {   // v -= conj(U[b0+i][b0+lane]) vi
+                    const double2 u = Us[(size_t)(b0 + i) * K + b0 + lane];
+                    v.x = fma(-u.x, vi.x, fma(-u.y, vi.y, v.x));
+                    v.y = fma(-u.x, vi.y, fma(u.y, vi.x, v.y));
                 }
             }
             if (lane < nb) wv[b0 + lane] = v;
         }
         __syncthreads();
-        for (int r0 = 0; r0 < b0; r0 += ngrp) {   // rows above: w_r -= sum_c conj(L[b0+c][r]) w[b0+c]
+        for (int r0 = 0; r0 < b0; r0 += ngrp) {   // rows above: v_r -= sum_c conj(U[b0+c][r]) v[b0+c]
             const int r = r0 + grp;
             double2 acc = make_double2(0.0, 0.0);
             if (r < b0)
                 for (int c = sub; c < nb; c += 8) {
-                    const double2 l = Ls[(size_t)(b0 + c) * K + r], v = wv[b0 + c];
-                    acc.x = fma(l.x, v.x, fma(l.y, v.y, acc.x));
-                    acc.y = fma(l.x, v.y, fma(-l.y, v.x, acc.y));
+                    const double2 u = Us[(size_t)(b0 + c) * K + r], v = wv[b0 + c];
+                    acc.x = fma(u.x, v.x, fma(u.y, v.y, acc.x));
+                    acc.y = fma(u.x, v.y, fma(-u.y, v.x, acc.y));
                 }
 #pragma unroll
             for (int o = 1; o < 8; o <<= 1) {
