@@ -199,7 +199,8 @@ __device__ __forceinline__ double rsqrt_newton(double x)
 // K sequential pivot steps bound the kernel: each complex update is four fused
 // multiply-adds, and the pivot's reciprocal root comes from rsqrt_newton.  Step
 // j: thread 0 takes the pivot; the threads scale column j; the trailing update
-// of rows i > j, columns j < k <= i runs on a 16 x 16 thread grid.
+// of rows i > j, columns j < k <= i is split into equal contiguous runs of the
+// triangle, one per thread.
 __global__ void __launch_bounds__(256) chol_kernel(const double2 *__restrict__ Gall, int K,
                                                    double2 *__restrict__ Lall, double *__restrict__ dall,
                                                    int *__restrict__ info)
@@ -245,13 +246,37 @@ __global__ void __launch_bounds__(256) chol_kernel(const double2 *__restrict__ G
             A[(size_t)i * K + j] = make_double2(v.x * ri, v.y * ri);
         }
         __syncthreads();
-        for (int i = j + 1 + ty; i < K; i += nty) {   // A[i][k] -= L[i][j] conj(L[k][j])
-            const double2 a = A[(size_t)i * K + j];
-            for (int k = j + 1 + tx; k <= i; k += 16) {
-                const double2 b = A[(size_t)k * K + j];
-                double2 &c = A[(size_t)i * K + k];
-                c.x = fma(-a.x, b.x, fma(-a.y, b.y, c.x));
-                c.y = fma(-a.y, b.x, fma(a.x, b.y, c.y));
+        // A[i][k] -= L[i][j] conj(L[k][j]) over the m (m + 1) / 2 elements of the
+        // trailing lower triangle, row-major, each thread a contiguous run of
+        // them: every lane of a warp stays busy (an FP64 warp instruction costs
+        // the FP64 unit the same time however many lanes it has).
+        {
+            const int m = K - j - 1;
+            const int tot = m * (m + 1) / 2;
+            const int per = (tot + nt - 1) / nt;
+            int e = tid * per;
+            if (e < tot) {
+                // row r of the triangle holding element e: r (r + 1) / 2 <= e < (r + 1) (r + 2) / 2
+                int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                while ((r + 1) * (r + 2) / 2 <= e) ++r;
+                while (r * (r + 1) / 2 > e) --r;
+                int c = e - r * (r + 1) / 2;
+                const int end = min(e + per, tot);
+                int i = j + 1 + r;
+                double2 a = A[(size_t)i * K + j];
+                for (; e < end; ++e) {
+                    const int k = j + 1 + c;
+                    const double2 b = A[(size_t)k * K + j];
+                    double2 &cc = A[(size_t)i * K + k];
+                    cc.x = fma(-a.x, b.x, fma(-a.y, b.y, cc.x));
+                    cc.y = fma(-a.y, b.x, fma(a.x, b.y, cc.y));
+                    if (++c > r) {   // next row of the triangle
+                        c = 0;
+                        ++r;
+                        ++i;
+                        if (i < K) a = A[(size_t)i * K + j];
+                    }
+                }
             }
         }
         __syncthreads();
