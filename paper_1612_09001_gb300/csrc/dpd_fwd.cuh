@@ -257,6 +257,13 @@ __global__ void __launch_bounds__(32 * 17)
                 ok = false;
                 break;
             }
+            // Start-up: the second tile is requested only once the first has
+            // landed, so that every CTA's first tile is not queued behind the
+            // other CTAs' later ones when all of them fill their rings at once.
+            if (it == 1 && !mbar_wait(smem_addr(&bars[0]), 0u, a.status)) {
+                ok = false;
+                break;
+            }
             const int64_t s0 = tile * S;
             int64_t lo, cnt;
             int off;
