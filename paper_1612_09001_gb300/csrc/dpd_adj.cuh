@@ -130,6 +130,10 @@ __device__ __forceinline__ void adj_produce(const AdjArgs &a, float2 *ring, uint
             ok = false;
             break;
         }
+        if (it == 1 && !mbar_wait(smem_addr(&bars[0]), 0u, a.status)) {   // start-up: first tile first
+            ok = false;
+            break;
+        }
         const int64_t s0 = tile * S;
         int xc, gc;
         adj_slot_counts(s0, S, a.n, xc, gc);

@@ -138,6 +138,13 @@ __global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int s
                 ok = false;
                 break;
             }
+            // Start-up: the second item is requested once the first has landed
+            // (every CTA's first tile then arrives without queueing behind the
+            // grid's later ones).
+            if (it == 1 && !mbar_wait(smem_addr(&bars[0]), 0u, a.status)) {
+                ok = false;
+                break;
+            }
             const BatchItem w = a.items[i];
             const BatchStream st = a.streams[(w.stream >= 0 && w.stream < a.nstreams) ? w.stream : 0];
             const uint32_t fb = smem_addr(&bars[s]);
