@@ -14,13 +14,17 @@
 // Each bracket is widely linear in g, so it is evaluated like the forward
 // filter: four real Horner polynomials per bracket, run as two packed f32x2
 // Horner chains whose results multiply the window sample {c, d} and its swap
-// {d, c} (table built by wl_table_kernel, one float4 per power).  The coefficient gradient is the correlation
+// {d, c} (table built by wl_table_kernel, one float4 per power).
+//
+// The coefficient gradient is the correlation
 //   gh_{(p,k)} = sum_j r_j^b conj(x_j) gy_{j+k},  gh_{(q,k)} = sum_j r_j^b x_j gy_{j+k},
 //   gh_c = sum_n gy_n,
-// i.e. conj(Psi)^T gy with the basis matrix Psi of Eq. 2, accumulated per
-// thread, reduced per CTA in a fixed order into a partials workspace and summed
-// over CTAs in FP64 by adj_finalize_kernel.  The basis is recomputed from x:
-// nothing from the forward pass is stored.
+// i.e. conj(Psi)^T gy with the basis matrix Psi of Eq. 2.  Both branches come
+// from two packed real correlations per (power, tap) (gh_accumulate), taken
+// per thread over groups of up to five taps, reduced per CTA in a fixed order
+// into a partials workspace and summed over CTAs in FP64 by
+// adj_finalize_kernel.  The basis is recomputed from x: nothing from the
+// forward pass is stored.
 //
 // Data movement.  For 16-byte aligned x and gy both gradients run as persistent
 // kernels fed like the forward filter: one producer thread streams tiles of x
