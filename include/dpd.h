@@ -282,8 +282,9 @@ dpd_status dpd_set_estimate_basis(dpd_handle h, int basis);
  *   h_out : device, K complex64, written (the handle's own coefficients are
  *           left unchanged; install the result with dpd_set_coeffs)
  *   stats : host double[2] or NULL: [0] 2-norm condition number of D G D
- *           (power iterations with the FP64 Cholesky factor), [1] ||t - Psi h||^2 / ||t||^2
- *           of the returned h (FP32 residual, FP64 sums)
+ *           (Lanczos on the FP64 Cholesky factor, host; about 1e-11 relative),
+ *           [1] ||t - Psi h||^2 / ||t||^2 of the returned h (FP32 residual,
+ *           FP32 squares summed in runs of 32, runs summed in FP64)
  * Synchronises `stream`.  DPD_ERR_NOT_SPD if G is not positive definite
  * (e.g. u all zero).  Uses and may grow the handle's workspace.
  */
