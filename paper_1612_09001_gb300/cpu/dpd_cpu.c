@@ -9,8 +9,8 @@
  *
  * Data movement: each OpenMP thread takes blocks of kBlock samples, splits the
  * block and the 8 samples before it into real, imaginary and |x|^2 arrays
- * (zero before x[0]), and produces 8 outputs at a time from two 4-wide vectors
- * per quantity.  The window of tap k is the same arrays read k samples earlier
+ * (zero before x[0]), and produces 12 outputs at a time from three 4-wide
+ * vectors per quantity.  The window of tap k is the same arrays read k samples earlier
  * -- an unaligned vector load, the portable form of the paper's vext-style
  * regrouping of neighbouring vectors.  GCC vector extensions compile to NEON
  * on AArch64 and to SSE on x86-64; no architecture-specific code.
@@ -22,7 +22,7 @@
 
 typedef float v4f __attribute__((vector_size(16)));
 
-enum { kMaxB = 6, kMaxT = 8, kHist = 8, kBlock = 4096 };
+enum { kMaxB = 6, kMaxT = 8, kHist = 8, kBlock = 4096, kVec = 3, kStep = 4 * kVec };
 
 static inline v4f load4(const float *p)
 {
@@ -32,6 +32,83 @@ static inline v4f load4(const float *p)
 }
 
 static inline v4f splat(float s) { return (v4f){s, s, s, s}; }
+
+/*
+ * kStep = 12 outputs from the split arrays (element 0 is the block's first
+ * sample, elements -1 .. -kHist its history): three 4-wide vectors per
+ * quantity, so each Horner step has 12 independent FMA chains (enough to keep
+ * the vector FMA pipes of a core busy despite their latency).  BB, the number of
+ * powers, is a compile-time constant in each instance so that the Horner loop
+ * unrolls; T stays a run-time loop.
+ */
+#define DPD_CPU_BLOCK(BB)                                                                              \
+    static void filter_block_##BB(int T, const float tab[kMaxT][kMaxB][4], float cr, float ci,         \
+                                  const float *re, const float *im, const float *rr, int len, float *y) \
+    {                                                                                                  \
+        for (int j = 0; j < len; j += kStep) {                                                         \
+            v4f yr[kVec], yi[kVec];                                                                    \
+            for (int v = 0; v < kVec; ++v) {                                                           \
+                yr[v] = splat(cr);                                                                     \
+                yi[v] = splat(ci);                                                                     \
+            }                                                                                          \
+            for (int k = 0; k < T; ++k) {                                                              \
+                const int o = j - k;                                                                   \
+                v4f a[kVec], b[kVec], r[kVec], p0[kVec], p1[kVec], p2[kVec], p3[kVec];                 \
+                for (int v = 0; v < kVec; ++v) {                                                       \
+                    a[v] = load4(re + o + 4 * v);                                                      \
+                    b[v] = load4(im + o + 4 * v);                                                      \
+                    r[v] = load4(rr + o + 4 * v);                                                      \
+                    p0[v] = splat(tab[k][BB - 1][0]);                                                  \
+                    p1[v] = splat(tab[k][BB - 1][1]);                                                  \
+                    p2[v] = splat(tab[k][BB - 1][2]);                                                  \
+                    p3[v] = splat(tab[k][BB - 1][3]);                                                  \
+                }                                                                                      \
+                for (int m = BB - 2; m >= 0; --m) {                                                    \
+                    const v4f c0 = splat(tab[k][m][0]), c1 = splat(tab[k][m][1]);                      \
+                    const v4f c2 = splat(tab[k][m][2]), c3 = splat(tab[k][m][3]);                      \
+                    for (int v = 0; v < kVec; ++v) {                                                   \
+                        p0[v] = p0[v] * r[v] + c0;                                                     \
+                        p1[v] = p1[v] * r[v] + c1;                                                     \
+                        p2[v] = p2[v] * r[v] + c2;                                                     \
+                        p3[v] = p3[v] * r[v] + c3;                                                     \
+                    }                                                                                  \
+                }                                                                                      \
+                for (int v = 0; v < kVec; ++v) {                                                       \
+                    yr[v] += p0[v] * a[v] + p1[v] * b[v];                                              \
+                    yi[v] += p2[v] * a[v] + p3[v] * b[v];                                              \
+                }                                                                                      \
+            }                                                                                          \
+            float outr[kStep], outi[kStep];                                                            \
+            memcpy(outr, yr, sizeof outr);                                                             \
+            memcpy(outi, yi, sizeof outi);                                                             \
+            const int cnt = len - j < kStep ? len - j : kStep;                                         \
+            float *yp = y + 2 * j;                                                                     \
+            for (int q = 0; q < cnt; ++q) {                                                            \
+                yp[2 * q] = outr[q];                                                                   \
+                yp[2 * q + 1] = outi[q];                                                               \
+            }                                                                                          \
+        }                                                                                              \
+    }
+DPD_CPU_BLOCK(1)
+DPD_CPU_BLOCK(2)
+DPD_CPU_BLOCK(3)
+DPD_CPU_BLOCK(4)
+DPD_CPU_BLOCK(5)
+DPD_CPU_BLOCK(6)
+#undef DPD_CPU_BLOCK
+
+static void filter_block(int B, int T, const float tab[kMaxT][kMaxB][4], float cr, float ci, const float *re,
+                         const float *im, const float *rr, int len, float *y)
+{
+    switch (B) {
+    case 1: filter_block_1(T, tab, cr, ci, re, im, rr, len, y); break;
+    case 2: filter_block_2(T, tab, cr, ci, re, im, rr, len, y); break;
+    case 3: filter_block_3(T, tab, cr, ci, re, im, rr, len, y); break;
+    case 4: filter_block_4(T, tab, cr, ci, re, im, rr, len, y); break;
+    case 5: filter_block_5(T, tab, cr, ci, re, im, rr, len, y); break;
+    default: filter_block_6(T, tab, cr, ci, re, im, rr, len, y); break;
+    }
+}
 
 int dpd_cpu_max_threads(void) { return omp_get_max_threads(); }
 
@@ -64,7 +141,7 @@ int dpd_cpu_apply(int P, int Q, int M, const float *h, const float *x, float *y,
 
 #pragma omp parallel for schedule(static) num_threads(nth)
     for (int64_t blk = 0; blk < nblk; ++blk) {
-        float re[kHist + kBlock + 8], im[kHist + kBlock + 8], rr[kHist + kBlock + 8];
+        float re[kHist + kBlock + kStep], im[kHist + kBlock + kStep], rr[kHist + kBlock + kStep];
         const int64_t s0 = blk * kBlock;
         const int len = (int)(n - s0 < kBlock ? n - s0 : kBlock);
         for (int i = 0; i < kHist + len; ++i) {   /* element i is sample s0 - kHist + i */
@@ -74,45 +151,8 @@ int dpd_cpu_apply(int P, int Q, int M, const float *h, const float *x, float *y,
             im[i] = b;
             rr[i] = a * a + b * b;
         }
-        for (int i = kHist + len; i < kHist + kBlock + 8; ++i) re[i] = im[i] = rr[i] = 0.f;
-        for (int j = 0; j < len; j += 8) {
-            v4f yr0 = splat(cr), yi0 = splat(ci), yr1 = splat(cr), yi1 = splat(ci);
-            for (int k = 0; k < T; ++k) {
-                const int o = kHist + j - k;
-                const v4f a0 = load4(re + o), b0 = load4(im + o), r0 = load4(rr + o);
-                const v4f a1 = load4(re + o + 4), b1 = load4(im + o + 4), r1 = load4(rr + o + 4);
-                v4f p00 = splat(tab[k][B - 1][0]), p01 = splat(tab[k][B - 1][1]);
-                v4f p02 = splat(tab[k][B - 1][2]), p03 = splat(tab[k][B - 1][3]);
-                v4f p10 = p00, p11 = p01, p12 = p02, p13 = p03;
-                for (int m = B - 2; m >= 0; --m) {
-                    const v4f c0 = splat(tab[k][m][0]), c1 = splat(tab[k][m][1]);
-                    const v4f c2 = splat(tab[k][m][2]), c3 = splat(tab[k][m][3]);
-                    p00 = p00 * r0 + c0;
-                    p01 = p01 * r0 + c1;
-                    p02 = p02 * r0 + c2;
-                    p03 = p03 * r0 + c3;
-                    p10 = p10 * r1 + c0;
-                    p11 = p11 * r1 + c1;
-                    p12 = p12 * r1 + c2;
-                    p13 = p13 * r1 + c3;
-                }
-                yr0 += p00 * a0 + p01 * b0;
-                yi0 += p02 * a0 + p03 * b0;
-                yr1 += p10 * a1 + p11 * b1;
-                yi1 += p12 * a1 + p13 * b1;
-            }
-            float outr[8], outi[8];
-            memcpy(outr, &yr0, 16);
-            memcpy(outr + 4, &yr1, 16);
-            memcpy(outi, &yi0, 16);
-            memcpy(outi + 4, &yi1, 16);
-            const int cnt = len - j < 8 ? len - j : 8;
-            float *yp = y + 2 * (s0 + j);
-            for (int q = 0; q < cnt; ++q) {
-                yp[2 * q] = outr[q];
-                yp[2 * q + 1] = outi[q];
-            }
-        }
+        for (int i = kHist + len; i < kHist + kBlock + kStep; ++i) re[i] = im[i] = rr[i] = 0.f;
+        filter_block(B, T, tab, cr, ci, re + kHist, im + kHist, rr + kHist, len, y + 2 * s0);
     }
     return 0;
 }
