@@ -302,18 +302,19 @@ def run_reference(args, world, rank):
         return 0
     import oracle
     import dpd_synth as synth
-    n_sample = 1 << 18
+    n_sample = 1 << 20
+    nth = os.cpu_count() or 1   # every host core, as the main line's cpu_baseline
     x = synth.ofdm2(n_sample, key=(0, 0))
     h = synth.coeffs(P, Q, M, key=(0, 1))
     for _ in range(max(args.warmup, 0)):
-        oracle.apply(x, h, P, Q, M)
+        oracle.apply(x, h, P, Q, M, nthreads=nth)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.apply(x, h, P, Q, M)
+        oracle.apply(x, h, P, Q, M, nthreads=nth)
     el = time.perf_counter() - t0
     v = args.steps * n_sample / el / 1e9
-    cores = oracle.threads()
-    sample = f"first 2^18 samples of the workload per step, FP64 C oracle, {cores} threads"
+    cores = oracle.threads(nth)
+    sample = f"first 2^20 samples of the workload per step, FP64 C oracle, {cores} threads"
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "Gsamples/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
