@@ -135,6 +135,25 @@ def _column(u, P, Q, M, j):
     return out
 
 
+@pytest.mark.parametrize("P,Q,M", [(1, 0, 0), (7, 3, 1), (7, 7, 3), (9, 7, 6), (7, 7, 7)])
+def test_estimate_solve_block_edges(P, Q, M):
+    """K = 2, 13, 33, 64, 65: the triangular solves run in blocks of 32 rows, so
+    these sizes put the last block at one row, a partial block, a full block
+    and one past it; each estimate against numpy's lstsq on the same data, and
+    the batched form on two problems against the single one."""
+    u, t, _ = _ls_problem(P, Q, M, 30000, 5)
+    f = dpd.DPD(P, Q, M)
+    ud, td = torch.from_numpy(u).cuda(), torch.from_numpy(t).cuda()
+    h, _ = f.estimate(ud, td, precision="tf32x3", refine_iters=3)
+    ref = oracle.ls(u, t, P, Q, M)
+    e = np.linalg.norm(h.cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref)
+    assert e <= 1e-4, (P, Q, M, e)
+    hb, info = f.estimate_batched([ud, ud], [td, td], precision="tf32x3", refine_iters=3)
+    assert info == [0, 0]
+    eb = np.linalg.norm(hb.cpu().numpy().astype(np.complex128) - ref[None, :]) / np.linalg.norm(ref)
+    assert eb <= 2e-4, (P, Q, M, eb)
+
+
 def test_estimate_rejects_singular_gram():
     f = dpd.DPD(5, 5, 2)
     u = torch.zeros(4096, dtype=torch.complex64, device="cuda")
