@@ -65,8 +65,12 @@ class Transmitter:
 
 
 def nmse_db(y, ref):
-    e = (y - ref).abs().pow(2).sum()
-    return 10.0 * math.log10(float(e) / float(ref.abs().pow(2).sum()))
+    """10 log10(||y - ref||^2 / ||ref||^2): both sums of squares on the device,
+    read back together (one synchronisation)."""
+    d = torch.view_as_real((y - ref).reshape(-1))
+    r = torch.view_as_real(ref.reshape(-1).contiguous())
+    e, s = torch.stack([d.square().sum(), r.square().sum()]).tolist()
+    return 10.0 * math.log10(e / s)
 
 
 class DirectLearner:
