@@ -83,3 +83,15 @@ def test_reference_arm_under_torchrun_prints_once():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_oracle_timing_of_every_workload():
+    """bench.cpu_oracle_configs (the cpu_baseline's all_workloads object) on two
+    threads: every workload timed with all and with one thread."""
+    import bench
+    out = bench.cpu_oracle_configs(2)
+    assert out["kind"] == "oracle" and out["threads_multi"] == 2
+    names = {"cfg0_2p16_P5M2", "cfg1_2p24_P9M4", "cfg2_batched_64", "cfg3_fwd_grad_P7M3", "cfg4_ls_P11M7"}
+    assert set(out["configs"]) == names
+    for c in out["configs"].values():
+        assert c["multi"] > 0 and c["single_thread"] > 0 and c["sample"] and c["unit"]
