@@ -54,7 +54,8 @@ def parse():
                     help="skip the batched / adjoint / Gram side measurements")
     ap.add_argument("--fwd-launch", default=None, metavar="MODE,V,WARPS,STAGES",
                     help="fix the forward launch shape instead of tuning it (profiling runs)")
-    ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "grad", "gram", "ila", "cpu", "sweep",
+    ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "grad", "gram", "ila", "cpu", "sweep", "fma",
+                                          "estimate",
                                           "oracle"],
                     default=None,
                     help="run only this side measurement (1 GPU) and print its JSON; for profiling")
@@ -354,6 +355,52 @@ def _time_graph(fn, reps, dev):
     return e0.elapsed_time(e1) * 1e-3 / reps
 
 
+def measure_fma_ceiling(dev, reps=5, gpu_index=0):
+    """The FP32 FMA pipe's ceiling on this GPU: dpd_probe_fma (independent FMA
+    chains only, scalar and packed f32x2), 4 CTAs of 256 threads per SM, about
+    10 ms per launch, CUDA events, median of `reps` launches after two warm-up
+    launches, with the SM clock sampled during the launches."""
+    import ctypes
+    import torch
+    from paper_1612_09001_gb300 import _lib
+    lib = _lib.load()
+    props = torch.cuda.get_device_properties(dev)
+    blocks, iters = props.multi_processor_count * 4, 1 << 17
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    sp = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    fmas = blocks * 256 * iters * 16
+    out = {"kernel": "dpd_probe_fma", "blocks": blocks, "threads": 256, "fmas_per_launch": fmas,
+           "timing": f"CUDA events, median of {reps} launches after 2 warm-up launches"}
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    time.sleep(0.3)
+    for packed in (1, 0):
+        def launch():
+            _lib.check("dpd_probe_fma", lib.dpd_probe_fma(blocks, iters, packed, ctypes.c_void_p(sink.data_ptr()), sp))
+        for _ in range(2):
+            launch()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            launch()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        sec = statistics.median(ts)
+        out["packed" if packed else "scalar"] = {"ms": sec * 1e3, "fma_per_s": fmas / sec}
+    clk = sampler.stop()
+    out["clocks"] = clk
+    best = max(out["packed"]["fma_per_s"], out["scalar"]["fma_per_s"])
+    out["fma_per_s"] = best
+    out["tflops"] = 2.0 * best / 1e12
+    if clk and clk.get("sm_mhz"):
+        out["fma_per_clock_per_sm"] = best / (clk["sm_mhz"] * 1e6) / props.multi_processor_count
+    return out
+
+
 def measure_sweep(dev, log2_min=10, log2_max=26):
     """Throughput against length (the paper's throughput-vs-samples experiment):
     graph-replayed dpd_apply at N = 2^10 .. 2^26, at the 2^16 workload's model
@@ -422,6 +469,30 @@ def measure_grad(dev, log2_n=24, reps=20):
             row[name] = {"us": us, "gsamples_per_s": n / us / 1e3}
         f.sync_status()
         f.close()
+        # The allocation-free entry point (no handle: plain-load kernel) on the
+        # same inputs, for comparison with the handle's staged kernel.
+        import ctypes
+        from paper_1612_09001_gb300 import _lib
+        lib = _lib.load()
+        sp = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+        def noalloc():
+            _lib.check("dpd_grad_coeffs_noalloc", lib.dpd_grad_coeffs_noalloc(
+                Pm, Qm, Mm, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(gy.data_ptr()), n,
+                ctypes.c_void_p(gh.data_ptr()), sp))
+        for _ in range(3):
+            noalloc()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            noalloc()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        us = e0.elapsed_time(e1) * 1e3 / reps
+        row["gh_noalloc"] = {"us": us, "gsamples_per_s": n / us / 1e3,
+                             "kernel": "plain-load adj_gh_kernel (dpd_grad_coeffs_noalloc)"}
         out[f"P{Pm}Q{Qm}M{Mm}"] = row
     return out
 
@@ -594,7 +665,7 @@ def measure_batched(dev, reps=20, launch=None):
             "hbm_gbs_persistent": 16 * total / t_plan / 1e9}
 
 
-def measure_direct(dev, steps=300):
+def measure_direct(dev, steps=400, lr=5e-3):
     """Direct learning, 2^20 OFDM samples, DPD P=Q=7, M=3 through the synthetic
     I/Q + PA transmitter: one graph-replayed Adam step, and the NMSE reached
     against indirect learning (3 LS iterations)."""
@@ -606,7 +677,7 @@ def measure_direct(dev, steps=300):
     tx = Transmitter([t["iq"], t["pa"]], device=dev)
     x = torch.from_numpy(synth.ofdm2(1 << 20, key=(0, 0))).to(dev)
     base = nmse_db(tx.apply(x), x)
-    learner = DirectLearner(x, tx, 7, 7, 3, lr=2e-3).capture()
+    learner = DirectLearner(x, tx, 7, 7, 3, lr=lr).capture()
     l0 = dpd.kernel_launches()
     learner.step()
     torch.cuda.synchronize(dev)
@@ -621,7 +692,53 @@ def measure_direct(dev, steps=300):
     return {"workload": "2^20 OFDM samples, DPD P=Q=7 M=3 (K=33), transmitter: I/Q (g=1.02, 2 deg, LO 0.005) + PA P=7 M=3",
             "adjoint_step_ms": ms, "step": "graph replay: DPD -> I/Q -> PA -> loss -> adjoint PA, I/Q, DPD -> Adam",
             "nmse_db_no_dpd": base, "nmse_db_direct": direct, "direct_steps": steps + 54,
-            "nmse_db_ila_3_iterations": ila}
+            "direct_optimizer": f"Adam, learning rate {lr:g} (constant), graph-replayed steps",
+            "nmse_db_ila_3_iterations": ila, "direct_minus_ila_db": direct - ila}
+
+
+def measure_estimate(dev, reps=5, refine_iters=3):
+    """One least-squares estimate of 2^22 rows x K = 97 (P = Q = 11, M = 7,
+    BF16x3 and TF32x3, monomial basis, statistics on): wall time per call
+    (median of `reps` after two warm-up calls), the device time of the same
+    call (CUDA events around it), the library kernel launches it makes, and
+    the host time in between (wall minus device)."""
+    import numpy as np
+    import torch
+    import dpd_synth as synth
+    import paper_1612_09001_gb300 as dpd
+    P, Q, M, n = 11, 11, 7, 1 << 22
+    u, theta = synth.ls_problem(n, P, Q, M, seed=0)
+    ud = torch.from_numpy(u).to(dev)
+    g = dpd.DPD(P, Q, M)
+    g.set_coeffs(theta)
+    td = g.apply(ud)
+    f = dpd.DPD(P, Q, M)
+    out = {"workload": "LS estimate, Psi 2^22 rows x 97 complex columns (P=Q=11, M=7), t = Psi theta",
+           "refine_iters": refine_iters, "timing": f"median of {reps} calls after 2 warm-up calls"}
+    for prec in ("bf16x3", "tf32x3"):
+        for _ in range(2):
+            f.estimate(ud, td, precision=prec, refine_iters=refine_iters)
+        torch.cuda.synchronize(dev)
+        walls, devs = [], []
+        launches = 0
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            l0 = dpd.kernel_launches()
+            t0 = time.perf_counter()
+            e0.record()
+            h, st = f.estimate(ud, td, precision=prec, refine_iters=refine_iters)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            walls.append(time.perf_counter() - t0)
+            devs.append(e0.elapsed_time(e1) * 1e-3)
+            launches = dpd.kernel_launches() - l0
+        err = float(np.linalg.norm(h.cpu().numpy() - theta) / np.linalg.norm(theta))
+        out[prec] = {"wall_ms": statistics.median(walls) * 1e3, "events_ms": statistics.median(devs) * 1e3,
+                     "library_launches": launches, "coef_rel_error_vs_true": err, "cond_est_DGD": st["cond_est"]}
+    f.close()
+    g.close()
+    return out
 
 
 def measure_gram(dev, reps=5):
@@ -850,13 +967,20 @@ def run_ours(args, world, rank, local):
                 "kernel": kname, "bytes_per_sample": BYTES_PER_SAMPLE}
     sm_mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else peaks.get("sm_max_mhz", 2070.0)
     props = torch.cuda.get_device_properties(dev)
-    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    nominal = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    fma = measure_fma_ceiling(dev, gpu_index=local)
+    fp32_peak = fma["tflops"]
     rate = n / mean_launch
-    alu = {"fp32_peak_tflops": fp32_peak, "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+    alu = {"bound": "alu", "fp32_peak_tflops": fp32_peak,
+           "peak_basis": "measured: dpd_probe_fma (FMA chains only) on this GPU, CUDA events, median of 5",
+           "peak_probe": fma,
+           "nominal_tflops": nominal,
+           "nominal_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
            "flops_per_sample_alg1": FLOPS_ALG(P, Q, M), "flops_per_sample_executed": FLOPS_WL(P, Q, M),
            "achieved_tflops_alg1": rate * FLOPS_ALG(P, Q, M) / 1e12,
            "achieved_tflops_executed": rate * FLOPS_WL(P, Q, M) / 1e12,
-           "frac_executed": rate * FLOPS_WL(P, Q, M) / 1e12 / fp32_peak}
+           "frac_executed": rate * FLOPS_WL(P, Q, M) / 1e12 / fp32_peak,
+           "frac_executed_of_nominal": rate * FLOPS_WL(P, Q, M) / 1e12 / nominal}
 
     patterns = {}
     if not args.no_patterns:
@@ -917,7 +1041,9 @@ def main():
         fn = {"small": measure_small, "batched": lambda d: measure_batched(d, launch=blaunch),
               "adjoint": measure_direct,
               "gram": measure_gram, "ila": measure_ila, "sweep": measure_sweep,
-              "grad": lambda d: measure_grad(d, args.grad_log2n)}[args.pattern]
+              "grad": lambda d: measure_grad(d, args.grad_log2n),
+              "fma": lambda d: measure_fma_ceiling(d, gpu_index=local),
+              "estimate": measure_estimate}[args.pattern]
         print(json.dumps({"pattern": args.pattern, "result": fn(dev)}, default=float))
         return 0
     return run_ours(args, world, rank, local)

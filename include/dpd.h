@@ -62,9 +62,13 @@ typedef struct dpd_filter *dpd_handle;
 /*
  * Create a filter for main-branch order P, conjugate-branch order Q and memory
  * depth M (L = M + 1 taps per branch), on the current CUDA device.
- *   P, Q : odd, 1..11, or 0 for "no such branch" (not both 0).  The paper uses
- *          odd orders only (Sec. 2.1); even values give DPD_ERR_INVALID_ARGUMENT.
- *   M    : 0..7 (1 to 8 taps).
+ *   P, Q : odd, 1..11, or 0 for "no such branch".  The paper uses odd orders
+ *          only (Sec. 2.1): an even order, or one above 11, gives
+ *          DPD_ERR_UNSUPPORTED; a negative order, or P = Q = 0, gives
+ *          DPD_ERR_INVALID_ARGUMENT.
+ *   M    : 0..7 (1 to 8 taps); M > 7 gives DPD_ERR_UNSUPPORTED, M < 0
+ *          DPD_ERR_INVALID_ARGUMENT.
+ * dpd_plan_batched and dpd_grad_coeffs_noalloc check their models the same way.
  * The handle owns its device memory (coefficients, their transformed form, an
  * error word and the gradient workspace).  *out is set only on success.
  */
@@ -142,11 +146,20 @@ dpd_status dpd_apply_host(dpd_handle h, const void *x, void *y, int64_t n, int m
  * device, K complex64, overwritten, must not overlap x or gy.  n == 0 zeroes
  * gh.  Models beyond the scratch (K > 97) give DPD_ERR_UNSUPPORTED, as does a
  * device ordinal >= 64.  The first call on a device looks up the scratch's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls on a device share the scratch and each call
- * rewrites the rows it reads, so nothing carries over between calls, but calls
- * whose kernels overlap on the GPU (different streams, or different host
- * threads) race on it and must be serialised by the caller.
+ * device address (cudaGetSymbolAddress); with CUDA's lazy module loading that
+ * lookup also loads the library's device code, which reserves the scratch and
+ * the code on the device and may synchronise it.  So a caller that must not
+ * allocate later makes one call with n == 0 at start-up (it does this one-time
+ * set-up and zeroes gh), before any stream capture; each kernel is then
+ * loaded at its own first launch, so such a caller also runs each model once
+ * before streaming.  After that a call allocates nothing.  All calls on a
+ * device share the scratch and each call rewrites the rows it reads, so
+ * nothing carries over between calls, but calls whose kernels overlap on the
+ * GPU (different streams, or different host threads) race on it and must be
+ * serialised by the caller.  This entry point has no device error word: it
+ * runs the plain-load coefficient-gradient kernel (no bulk-copy ring and no
+ * bounded waits, so there is no timeout to report), which is slower than
+ * dpd_grad's staged kernel on 16-byte aligned buffers.
  */
 dpd_status dpd_grad_coeffs_noalloc(int P, int Q, int M, const void *x, const void *gy, int64_t n,
                                    void *gh, void *stream);
@@ -285,8 +298,11 @@ dpd_status dpd_set_estimate_basis(dpd_handle h, int basis);
  *           (Lanczos on the FP64 Cholesky factor, host; about 1e-11 relative),
  *           [1] ||t - Psi h||^2 / ||t||^2 of the returned h (FP32 residual,
  *           FP32 squares summed in runs of 32, runs summed in FP64)
- * Synchronises `stream`.  DPD_ERR_NOT_SPD if G is not positive definite
- * (e.g. u all zero).  Uses and may grow the handle's workspace.
+ * Synchronises `stream` once, at the end: the condition estimate runs on the
+ * host while the refinement runs on the device.  DPD_ERR_NOT_SPD if G is not
+ * positive definite (e.g. u all zero); h_out and stats are then unspecified.
+ * Uses and may grow the handle's workspace (device buffers and a few pinned
+ * host buffers).
  */
 dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, int precision, int refine_iters,
                         void *h_out, double *stats, void *stream);
@@ -345,8 +361,11 @@ dpd_status dpd_exec_batched(dpd_plan plan, void *stream);
 /*
  * Launch shape of dpd_exec_batched (autotuner): V in {4, 8} samples per thread,
  * warps 1..16 consumer warps (tile = warps*32*V samples; changing the tile
- * rebuilds the work list, synchronously), stages 2..8, ctas_per_sm >= 0 (0 = as
- * many as fit).  Default 8, 8, 4, 0.
+ * rebuilds the work list, synchronously, in a new device buffer), stages 2..8,
+ * ctas_per_sm >= 0 (0 = as many as fit).  Default 8, 8, 4, 0.  On any error the
+ * plan keeps its previous shape and work list.  A CUDA graph captured from
+ * dpd_exec_batched holds the shape and work list of its capture: capture again
+ * after changing the shape.
  */
 dpd_status dpd_plan_set_launch(dpd_plan plan, int V, int warps, int stages, int ctas_per_sm);
 
@@ -368,6 +387,19 @@ const char *dpd_status_string(dpd_status s);
 
 /* Number of kernels this library has launched in this process (all handles). */
 uint64_t dpd_kernel_launches(void);
+
+/*
+ * Measurement aid (not in the paper): the FP32 fused-multiply-add ceiling that
+ * bounds the filter and adjoint kernels, measured rather than taken from
+ * nominal lane counts.  Launches `blocks` CTAs of 256 threads on `stream`;
+ * every thread runs `iters` iterations of 16 independent FMAs (as 8 packed
+ * f32x2 FMAs when `packed` is non-zero, else 16 scalar ones) and writes one
+ * float to sink[block * 256 + thread].
+ *   sink : device, blocks * 256 floats, 4-byte aligned, owned by the caller.
+ * FMAs executed = blocks * 256 * iters * 16; time the launch with events on
+ * `stream`.  Allocates nothing, does not synchronise.
+ */
+dpd_status dpd_probe_fma(int blocks, int iters, int packed, void *sink, void *stream);
 
 #ifdef __cplusplus
 }

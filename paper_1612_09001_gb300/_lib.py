@@ -59,6 +59,7 @@ SIGNATURES = {
     "dpd_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "dpd_set_adj_launch": [_vp, _i, _i],
     "dpd_grad_coeffs_noalloc": [_i, _i, _i, _vp, _vp, _i64, _vp, _vp],
+    "dpd_probe_fma": [_i, _i, _i, _vp, _vp],
     "dpd_sync_status": [_vp, _vp],
     "dpd_gram": [_vp, _vp, _vp, _i64, _i, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp],
     "dpd_estimate": [_vp, _vp, _vp, _i64, _i, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp],

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/dpd.h"
+#include "dpd_model.h"
 #include "dpd_batched.cuh"
 
 namespace dpd {
@@ -25,7 +26,7 @@ struct dpd_plan_s {
     float *d_tabs = nullptr;
     float *d_h = nullptr;          // raw coefficients, 2*K floats per stream
     int *d_status = nullptr;
-    int nitems = 0, items_cap = 0;
+    int nitems = 0;
     int64_t tab_floats = 0;
     int small = 1;            // every stream has B <= 5 and T <= 7
     int V = 8, warps = 8, stages = 4, ctas_per_sm = 0;
@@ -34,7 +35,6 @@ struct dpd_plan_s {
 namespace {
 
 int nbranch(int order) { return order > 0 ? (order + 1) / 2 : 0; }
-bool valid_order(int o) { return o == 0 || (o > 0 && o <= 11 && (o % 2) == 1); }
 bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 bool overlap(const void *a, size_t na, const void *b, size_t nb)
 {
@@ -52,11 +52,14 @@ void free_plan(dpd_plan p)
     delete p;
 }
 
-// Work list for tile size S: streams by decreasing per-sample cost (B * T),
-// every tile of a stream in order.  Launched CTAs take items round-robin.
-dpd_status build_items(dpd_plan p)
+// Work list for tile size S = warps * 32 * V: streams by decreasing per-sample
+// cost (B * T), every tile of a stream in order.  Launched CTAs take items
+// round-robin.  The list goes to a new device buffer that replaces the plan's
+// only once it holds the list, so on failure the plan keeps its previous list
+// (and tiling) unchanged.
+dpd_status build_items(dpd_plan p, int V, int warps)
 {
-    const int S = p->warps * 32 * p->V;
+    const int S = warps * 32 * V;
     std::vector<int> order(p->streams.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -69,17 +72,17 @@ dpd_status build_items(dpd_plan p)
         for (int64_t t = 0; t < nt; ++t) items.push_back({si, (int)t});
     }
     if (items.size() > (size_t)INT32_MAX) return DPD_ERR_UNSUPPORTED;
-    if ((int)items.size() > p->items_cap) {
-        cudaFree(p->d_items);
-        p->d_items = nullptr;
-        const size_t cap = std::max<size_t>(items.size(), 1);
-        if (cudaMalloc(&p->d_items, cap * sizeof(dpd::BatchItem)) != cudaSuccess) return DPD_ERR_ALLOC;
-        p->items_cap = (int)cap;
-    }
+    dpd::BatchItem *d_new = nullptr;
+    const size_t cap = std::max<size_t>(items.size(), 1);
+    if (cudaMalloc(&d_new, cap * sizeof(dpd::BatchItem)) != cudaSuccess) return DPD_ERR_ALLOC;
     if (!items.empty() &&
-        cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(dpd::BatchItem), cudaMemcpyHostToDevice) !=
-            cudaSuccess)
+        cudaMemcpy(d_new, items.data(), items.size() * sizeof(dpd::BatchItem), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        cudaFree(d_new);
         return DPD_ERR_CUDA;
+    }
+    cudaFree(p->d_items);
+    p->d_items = d_new;
     p->nitems = (int)items.size();
     return DPD_OK;
 }
@@ -96,8 +99,9 @@ dpd_status dpd_plan_batched(const dpd_stream_desc *descs, int count, int where, 
     size_t hfloats = 0, tfloats = 0;
     for (int i = 0; i < count; ++i) {
         const dpd_stream_desc &d = descs[i];
-        if (!valid_order(d.P) || !valid_order(d.Q) || (d.P == 0 && d.Q == 0)) return DPD_ERR_INVALID_ARGUMENT;
-        if (d.M < 0 || d.M + 1 > dpd::kMaxT || d.n < 0 || !d.h) return DPD_ERR_INVALID_ARGUMENT;
+        const dpd_status mst = dpd::model_status(d.P, d.Q, d.M);
+        if (mst != DPD_OK) return mst;
+        if (d.n < 0 || !d.h) return DPD_ERR_INVALID_ARGUMENT;
         if (d.n > (int64_t)(INT64_MAX / sizeof(float2))) return DPD_ERR_INVALID_ARGUMENT;
         if (d.n > 0 && (!d.x || !d.y || !aligned(d.x, 16) || !aligned(d.y, 8))) return DPD_ERR_INVALID_ARGUMENT;
         if (!aligned(d.h, where == DPD_HOST ? 4 : 8)) return DPD_ERR_INVALID_ARGUMENT;
@@ -163,7 +167,7 @@ dpd_status dpd_plan_batched(const dpd_stream_desc *descs, int count, int where, 
         free_plan(p);
         return DPD_ERR_CUDA;
     }
-    dpd_status st = build_items(p);
+    dpd_status st = build_items(p, p->V, p->warps);
     if (st == DPD_OK && cudaDeviceSynchronize() != cudaSuccess) st = DPD_ERR_CUDA;
     if (st != DPD_OK) {
         free_plan(p);
@@ -178,18 +182,24 @@ dpd_status dpd_plan_set_launch(dpd_plan p, int V, int warps, int stages, int cta
     if (!p) return DPD_ERR_INVALID_ARGUMENT;
     if ((V != 4 && V != 8) || warps < 1 || warps > 16 || stages < 2 || stages > 8 || ctas_per_sm < 0)
         return DPD_ERR_INVALID_ARGUMENT;
-    const bool retile = (V != p->V || warps != p->warps);
+    if (V != p->V || warps != p->warps) {
+        // Re-tile first: the new shape is kept only once its work list is on
+        // the device; on failure the plan runs with its previous shape.
+        const dpd_status st = build_items(p, V, warps);
+        if (st != DPD_OK) return st;
+    }
     p->V = V;
     p->warps = warps;
     p->stages = stages;
     p->ctas_per_sm = ctas_per_sm;
-    return retile ? build_items(p) : DPD_OK;
+    return DPD_OK;
 }
 
 dpd_status dpd_exec_batched(dpd_plan p, void *stream)
 {
     if (!p) return DPD_ERR_INVALID_ARGUMENT;
     if (p->nitems == 0) return DPD_OK;
+    if (!p->d_items || !p->d_streams || !p->d_tabs || !p->d_status) return DPD_ERR_INVALID_ARGUMENT;
     dpd::BatchArgs a;
     a.streams = p->d_streams;
     a.items = p->d_items;

@@ -162,9 +162,10 @@ __host__ __device__ constexpr size_t adj_staged_smem(int S, int stages, int scra
 }
 
 // ---------------------------------------------------------------- input gradient
-// Adjoint table passed by value (kernel parameter bank).
+// Adjoint table passed by value (kernel parameter bank), 16-byte aligned so
+// that its packed pairs can be 64-bit constant operands.
 template <int B, int T>
-struct AdjParamTab {
+struct alignas(8) AdjParamTab {
     float v[adj_table_floats(B, T)];
 };
 
@@ -577,14 +578,14 @@ cudaError_t launch_adj_gx_tma(const AdjArgs &a, const AdjParamTab<B, T> &ptab, i
     // The shared-memory table area is kept in both forms (it is small).
     const size_t smem = adj_staged_smem(S, kAdjStages, adj_tab_padded<B, T>());
     auto kern = adj_gx_tma_kernel<B, T, V, PARAM>;
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static SmemAttr smem_rec;
+    cudaError_t attr = ensure_smem(smem_rec, (const void *)kern, smem);
     if (attr != cudaSuccess) return attr;
-    static const int occ = [smem, kern] {
-        int o = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 32 * (kAdjWarps + 1), smem);
-        return o < 1 ? 1 : o;
-    }();
+    static OccCache occ_rec;
+    int occ = 0;
+    attr = occupancy(occ_rec, (const void *)kern, 32 * (kAdjWarps + 1), smem, &occ);
+    if (attr != cudaSuccess) return attr;
+    if (occ < 1) occ = 1;
     const int64_t ntiles = (a.n + S - 1) / S;
     int64_t grid = (int64_t)sm_count * occ;
     if (grid > ntiles) grid = ntiles;
@@ -605,8 +606,10 @@ cudaError_t launch_adj_gx_t(const AdjArgs &a, int sm_count, cudaStream_t s)
         }
         return launch_adj_gx_tma<B, T, V, false>(a, AdjParamTab<B, T>{}, sm_count, s);
     }
+    static OccCache occ_rec;
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adj_gx_kernel<B, T, V>, 256, 0);
+    const cudaError_t oe = occupancy(occ_rec, (const void *)adj_gx_kernel<B, T, V>, 256, 0, &occ);
+    if (oe != cudaSuccess) return oe;
     if (occ < 1) occ = 1;
     const int64_t need = (a.n + 256 * V - 1) / (256 * V);
     int64_t grid = (int64_t)sm_count * occ;
@@ -626,8 +629,8 @@ cudaError_t launch_adj_gh_tg(const AdjArgs &a, int blocks, int T, int Bp, int Bq
         constexpr int S = kAdjGhWarps * 32 * V;
         constexpr int NA = 4 * B * TG + 2;
         const size_t smem = adj_staged_smem(S, kAdjGhStages, kAdjGhWarps * NA);
-        static const cudaError_t attr = cudaFuncSetAttribute(
-            adj_gh_tma_kernel<B, TG, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        static SmemAttr smem_rec;
+        const cudaError_t attr = ensure_smem(smem_rec, (const void *)adj_gh_tma_kernel<B, TG, V>, smem);
         if (attr != cudaSuccess) return attr;
         const int64_t ntiles = (a.n + S - 1) / S;
         adj_gh_tma_kernel<B, TG, V><<<grid, 32 * (kAdjGhWarps + 1), smem, s>>>(a, kAdjGhStages, ntiles, T, Bp, Bq, K);

@@ -9,7 +9,11 @@
 #include <cuda_runtime.h>
 
 #include "../../include/dpd.h"
+#include "dpd_model.h"
 #include "dpd_internal.h"
+
+static_assert(dpd::kModelMaxOrder == 2 * dpd::kMaxB - 1 && dpd::kModelMaxTaps == dpd::kMaxT,
+              "model limits match the kernels' limits");
 
 #include "dpd_handle.h"
 #include "dpd_zc.h"
@@ -64,8 +68,6 @@ namespace {
 
 int nbranch(int order) { return order > 0 ? (order + 1) / 2 : 0; }
 
-bool valid_order(int o) { return o == 0 || (o > 0 && o <= 11 && (o % 2) == 1); }
-
 bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 bool overlap(const void *a, size_t na, const void *b, size_t nb)
@@ -100,8 +102,8 @@ uint64_t dpd_kernel_launches(void) { return dpd::g_launches.load(std::memory_ord
 dpd_status dpd_create(int P, int Q, int M, dpd_handle *out)
 {
     if (!out) return DPD_ERR_INVALID_ARGUMENT;
-    if (!valid_order(P) || !valid_order(Q) || (P == 0 && Q == 0)) return DPD_ERR_INVALID_ARGUMENT;
-    if (M < 0 || M + 1 > dpd::kMaxT) return DPD_ERR_INVALID_ARGUMENT;
+    const dpd_status mst = dpd::model_status(P, Q, M);
+    if (mst != DPD_OK) return mst;
     dpd_filter *f = new (std::nothrow) dpd_filter();
     if (!f) return DPD_ERR_ALLOC;
     f->P = P;

@@ -218,14 +218,12 @@ cudaError_t launch_batched_impl(const BatchArgs &a, int warps, int stages, int c
     const int S = warps * 32 * V;
     const size_t smem = 128 + (size_t)stages * batch_slot_bytes(S);
     auto kern = fwd_batched_kernel<BMAX, TMAX, V>;
-    static size_t smem_set = 0;
-    if (smem > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_set = smem;
-    }
+    static SmemAttr smem_rec;
+    cudaError_t e = ensure_smem(smem_rec, (const void *)kern, smem);
+    if (e != cudaSuccess) return e;
+    static OccCache occ_rec;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    e = occupancy(occ_rec, (const void *)kern, threads, smem, &occ);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int cps = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;

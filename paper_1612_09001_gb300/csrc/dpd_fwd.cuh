@@ -27,9 +27,12 @@
 
 namespace dpd {
 
-// Coefficient table passed by value (kernel parameter bank).
+// Coefficient table passed by value (kernel parameter bank).  16-byte aligned
+// so that every {P0, P2} / {P1, P3} pair sits at an 8-byte aligned offset of
+// the bank, where a packed FMA can take it as a 64-bit constant operand (a
+// misaligned table costs a register move per pair).
 template <int B, int T>
-struct ParamTab {
+struct alignas(8) ParamTab {
     float v[wl_table_floats(B, T)];
 };
 
@@ -369,23 +372,13 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
             const int64_t ntiles = (a.n + S - 1) / S;
             const size_t smem = fwd_tma_smem<B, T, V>(L.warps, L.stages);
             auto kern = fwd_tma_kernel<B, T, V, MODE>;
-            static size_t smem_set = 0;   // per instantiation
-            if (smem > smem_set) {
-                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)smem);
-                if (e != cudaSuccess) return e;
-                smem_set = smem;
-            }
-            // Occupancy of the last shape launched from this host thread.
-            thread_local int occ_threads = -1;
-            thread_local size_t occ_smem = 0;
-            thread_local int occ = 0;
-            if (threads != occ_threads || smem != occ_smem) {
-                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
-                if (e != cudaSuccess) return e;
-                occ_threads = threads;
-                occ_smem = smem;
-            }
+            static SmemAttr smem_rec;   // per instantiation
+            cudaError_t ae = ensure_smem(smem_rec, (const void *)kern, smem);
+            if (ae != cudaSuccess) return ae;
+            static OccCache occ_rec;
+            int occ = 0;
+            ae = occupancy(occ_rec, (const void *)kern, threads, smem, &occ);
+            if (ae != cudaSuccess) return ae;
             if (occ < 1) return cudaErrorInvalidConfiguration;
             const int cps = (L.ctas_per_sm > 0 && L.ctas_per_sm < occ) ? L.ctas_per_sm : occ;
             int64_t grid = (int64_t)sm_count * cps;
@@ -411,13 +404,11 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
     }
     if constexpr (fwd_built<B, T, V, MODE, false>()) {
         const int threads = 256;
-        thread_local int occ = 0;
-        if (occ == 0) {
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, fwd_ldg_kernel<B, T, V, MODE>, threads, 0);
-            if (e != cudaSuccess) return e;
-            if (occ < 1) occ = 1;
-        }
+        static OccCache occ_rec;
+        int occ = 0;
+        cudaError_t oe = occupancy(occ_rec, (const void *)fwd_ldg_kernel<B, T, V, MODE>, threads, 0, &occ);
+        if (oe != cudaSuccess) return oe;
+        if (occ < 1) occ = 1;
         const int64_t need = (a.n + (int64_t)threads * V - 1) / ((int64_t)threads * V);
         int64_t grid = (int64_t)sm_count * occ;
         if (grid > need) grid = need;

@@ -29,6 +29,12 @@ struct EstimateWorkspace {
     double *mom = nullptr;        // [nprob][kMomK] power sums of |u|^2
     double *mom_part = nullptr;   // [nprob][kMomBlocks][kMomK]
     double2 *hm64 = nullptr;      // [nprob][K] monomial-basis coefficients / transformed right-hand sides
+    // pinned host copies read back by dpd_estimate (single problem)
+    int hK = 0;                   // K the host buffers were sized for
+    double2 *h_L = nullptr;       // Cholesky factor, K x K (condition estimate on the host)
+    int *h_info = nullptr;        // its pivot status
+    double *h_norm = nullptr;     // ||t - Psi h||^2, ||t||^2
+    cudaEvent_t ev_L = nullptr;   // h_L and h_info have landed
 };
 
 // Device staging of dpd_apply_host's copy / compute pipeline, created on first use.

@@ -2,7 +2,10 @@
 // translation units.  Not part of the public C ABI (include/dpd.h).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 namespace dpd {
@@ -108,5 +111,65 @@ cudaError_t launch_wl_table(const float2 *h, int Bp, int Bq, int T, float *tab, 
                             cudaStream_t s);
 
 void count_launch(int n = 1);
+
+// A kernel's dynamic shared-memory limit and its occupancy belong to each
+// device, so the launchers keep them per device ordinal (one record per kernel
+// instantiation); ordinals past kMaxDevices are served without a cache.
+constexpr int kMaxDevices = 64;
+
+struct SmemAttr {
+    std::atomic<size_t> set[kMaxDevices] = {};
+    std::mutex mu;
+};
+
+// Raise `kern`'s dynamic shared-memory limit on the current device to at least
+// `bytes` (never lowers it).
+inline cudaError_t ensure_smem(SmemAttr &rec, const void *kern, size_t bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices)
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (rec.set[dev].load(std::memory_order_acquire) >= bytes) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(rec.mu);
+    const size_t cur = rec.set[dev].load(std::memory_order_relaxed);
+    if (cur >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) rec.set[dev].store(bytes, std::memory_order_release);
+    return e;
+}
+
+// Resident CTAs per SM of `kern` at (threads, smem) on the current device,
+// remembered per device for the last shape asked.
+struct OccCache {
+    struct Entry {
+        int threads = -1;
+        size_t smem = 0;
+        int occ = 0;
+    };
+    Entry e[kMaxDevices];
+    std::mutex mu;
+};
+
+inline cudaError_t occupancy(OccCache &c, const void *kern, int threads, size_t smem, int *occ)
+{
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= kMaxDevices) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, threads, smem);
+    std::lock_guard<std::mutex> lock(c.mu);
+    OccCache::Entry &en = c.e[dev];
+    if (en.threads != threads || en.smem != smem) {
+        int o = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, threads, smem);
+        if (err != cudaSuccess) return err;
+        en.threads = threads;
+        en.smem = smem;
+        en.occ = o;
+    }
+    *occ = en.occ;
+    return cudaSuccess;
+}
 
 }  // namespace dpd

@@ -51,6 +51,21 @@ dpd_status reserve(dpd_handle h, int nprob, int cpp, int64_t nsamp)
         w.nprob = nprob;
         w.cpp = cpp;
     }
+    if (w.hK != K || !w.h_L) {
+        cudaFreeHost(w.h_L);
+        cudaFreeHost(w.h_info);
+        cudaFreeHost(w.h_norm);
+        w.h_L = nullptr;
+        w.h_info = nullptr;
+        w.h_norm = nullptr;
+        w.hK = 0;
+        if (cudaMallocHost(&w.h_L, sizeof(double2) * K * K) != cudaSuccess ||
+            cudaMallocHost(&w.h_info, sizeof(int)) != cudaSuccess ||
+            cudaMallocHost(&w.h_norm, 2 * sizeof(double)) != cudaSuccess)
+            return DPD_ERR_ALLOC;
+        w.hK = K;
+    }
+    if (!w.ev_L && cudaEventCreateWithFlags(&w.ev_L, cudaEventDisableTiming) != cudaSuccess) return DPD_ERR_CUDA;
     if (nsamp > w.nsamp) {
         cudaDeviceSynchronize();
         ok = grow(w.y, 0, (size_t)nsamp) && grow(w.e, 0, (size_t)nsamp);
@@ -234,7 +249,7 @@ dpd_status refine_once(dpd_handle h, int p, const float2 *u, const float2 *t, in
 // 2-norm condition number of A = L L^H (the equilibrated Gram matrix): the
 // largest eigenvalues of A and of A^{-1} (two triangular solves per product),
 // FP64 on the host.
-double cond_estimate(const std::vector<double2> &L, int K)
+double cond_estimate(const double2 *L, int K)
 {
     auto mulL = [&](const std::vector<double2> &x, bool herm) {   // L x or L^H x
         std::vector<double2> y((size_t)K, make_double2(0, 0));
@@ -378,25 +393,18 @@ double cond_estimate(const std::vector<double2> &L, int K)
     }
 }
 
-// Statistics of problem p: 2-norm condition number of the equilibrated Gram
-// matrix (Lanczos on its Cholesky factor, cond_estimate), and
-// ||t - Psi h||^2 / ||t||^2 with the FP32 residual of the final coefficients
-// summed in FP64 on the device.
-dpd_status stats_of(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, double *stats, cudaStream_t s)
+// Statistics of a problem: ||t - Psi h||^2 and ||t||^2 of the final
+// coefficients (FP32 residual summed in FP64 on the device), queued on s and
+// read back into the pinned w.h_norm.
+dpd_status queue_norms(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, cudaStream_t s)
 {
     EstimateWorkspace &w = h->est;
-    const int K = h->K;
     dpd_status st = residual_of(h, p, u, t, n, s);
     if (st != DPD_OK) return st;
     if (dpd::launch_sqnorm2(w.e, t, n, w.norm_part, w.norm_part + 2 * 1024, s) != cudaSuccess) return DPD_ERR_CUDA;
-    std::vector<double2> L((size_t)K * K);
-    double nrm[2] = {0, 0};
-    if (cudaStreamSynchronize(s) != cudaSuccess ||
-        cudaMemcpy(L.data(), w.L + (size_t)p * K * K, sizeof(double2) * K * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(nrm, w.norm_part + 2 * 1024, sizeof(nrm), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpyAsync(w.h_norm, w.norm_part + 2 * 1024, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
         return DPD_ERR_CUDA;
-    stats[0] = cond_estimate(L, K);
-    stats[1] = nrm[1] > 0 ? nrm[0] / nrm[1] : 0.0;
     return DPD_OK;
 }
 
@@ -434,6 +442,10 @@ void free_estimate_workspace(EstimateWorkspace &w)
     cudaFree(w.mom);
     cudaFree(w.mom_part);
     cudaFree(w.hm64);
+    cudaFreeHost(w.h_L);
+    cudaFreeHost(w.h_info);
+    cudaFreeHost(w.h_norm);
+    if (w.ev_L) cudaEventDestroy(w.ev_L);
     w = EstimateWorkspace();
 }
 
@@ -484,19 +496,32 @@ dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, i
     if (ortho(h) && (st = compute_basis(h, std::vector<int64_t>{n}, s)) != DPD_OK) return st;
     if ((st = run_gram(h, 1, cpp, precision, s)) != DPD_OK) return st;
     if (dpd::launch_chol(w.G, 1, h->K, w.L, w.d, w.info, s) != cudaSuccess) return DPD_ERR_CUDA;
-    if (dpd::launch_chol_solve(w.L, w.d, w.info, w.g, 1, h->K, w.h64, 0, s) != cudaSuccess) return DPD_ERR_CUDA;
-    int info = 0;
-    if (cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    // The factor and its pivot status go to pinned host memory while the
+    // device carries on: the solves skip a failed factorisation on the device,
+    // and the host condition estimate (Lanczos on L) runs during the
+    // refinement instead of after it.
+    const int K = h->K;
+    if (cudaMemcpyAsync(w.h_info, w.info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        (stats && cudaMemcpyAsync(w.h_L, w.L, sizeof(double2) * K * K, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+        cudaEventRecord(w.ev_L, s) != cudaSuccess)
         return DPD_ERR_CUDA;
-    if (info != 0) return DPD_ERR_NOT_SPD;
+    if (dpd::launch_chol_solve(w.L, w.d, w.info, w.g, 1, K, w.h64, 0, s) != cudaSuccess) return DPD_ERR_CUDA;
     for (int i = 0; i < refine_iters; ++i)
         if ((st = refine_once(h, 0, pr.u, pr.t, n, s)) != DPD_OK) return st;
     const double2 *hm = monomial_h(h, 0, 1, s, st);
     if (st != DPD_OK) return st;
-    if (dpd::launch_h_to_f32(hm, h->K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dpd::launch_h_to_f32(hm, K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (stats && (st = queue_norms(h, 0, pr.u, pr.t, n, s)) != DPD_OK) return st;
+    double cond = 0.0;
+    if (cudaEventSynchronize(w.ev_L) != cudaSuccess) return DPD_ERR_CUDA;
+    const int info = *w.h_info;
+    if (stats && info == 0) cond = cond_estimate(w.h_L, K);   // overlaps the queued device work
     if (cudaStreamSynchronize(s) != cudaSuccess) return DPD_ERR_CUDA;
-    if (stats) return stats_of(h, 0, pr.u, pr.t, n, stats, s);
+    if (info != 0) return DPD_ERR_NOT_SPD;
+    if (stats) {
+        stats[0] = cond;
+        stats[1] = w.h_norm[1] > 0 ? w.h_norm[0] / w.h_norm[1] : 0.0;
+    }
     return DPD_OK;
 }
 

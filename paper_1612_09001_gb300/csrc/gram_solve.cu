@@ -293,12 +293,9 @@ __global__ void __launch_bounds__(256) chol_kernel(const double2 *__restrict__ G
 cudaError_t launch_chol(const double2 *G, int nprob, int K, double2 *L, double *d, int *info, cudaStream_t s)
 {
     const size_t smem = sizeof(double2) * K * K;
-    static size_t set = 0;
-    if (smem > set) {
-        cudaError_t e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        set = smem;
-    }
+    static SmemAttr smem_rec;
+    const cudaError_t e = ensure_smem(smem_rec, (const void *)chol_kernel, smem);
+    if (e != cudaSuccess) return e;
     chol_kernel<<<nprob, 256, smem, s>>>(G, K, L, d, info);
     count_launch();
     return cudaGetLastError();
@@ -432,13 +429,9 @@ cudaError_t launch_chol_solve(const double2 *L, const double *d, const int *info
                               int K, double2 *h, int accumulate, cudaStream_t s)
 {
     const size_t smem = sizeof(double2) * K * K;
-    static size_t set = 0;
-    if (smem > set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        set = smem;
-    }
+    static SmemAttr smem_rec;
+    const cudaError_t e = ensure_smem(smem_rec, (const void *)chol_solve_kernel, smem);
+    if (e != cudaSuccess) return e;
     chol_solve_kernel<<<nprob, 256, smem, s>>>(L, d, info, rhs, K, h, accumulate);
     count_launch();
     return cudaGetLastError();

@@ -573,25 +573,18 @@ cudaError_t launch_gram(int precision, const GramArgs &a, cudaStream_t s)
     const int grid = a.nprob * a.cpp;
     if (grid <= 0) return cudaSuccess;
     if (precision == kPrecFP32) {
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(gram_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)gram_fp32_smem());
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
+        static SmemAttr smem_rec;
+        const cudaError_t e = ensure_smem(smem_rec, (const void *)gram_fp32_kernel, gram_fp32_smem());
+        if (e != cudaSuccess) return e;
         gram_fp32_kernel<<<grid, kF32Threads, gram_fp32_smem(), s>>>(a);
         count_launch();
         return cudaGetLastError();
     }
     auto kern = precision == kPrecBF16x3 ? gram_tc_kernel<kFmtBF16> : gram_tc_kernel<kFmtTF32>;
-    static bool attr_set[2] = {false, false};
+    static SmemAttr smem_rec[2];
     const int ai = precision == kPrecBF16x3 ? 0 : 1;
-    if (!attr_set[ai]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem());
-        if (e != cudaSuccess) return e;
-        attr_set[ai] = true;
-    }
+    const cudaError_t e = ensure_smem(smem_rec[ai], (const void *)kern, gram_tc_smem());
+    if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, gram_tc_smem(), s>>>(a);
     count_launch();
     return cudaGetLastError();

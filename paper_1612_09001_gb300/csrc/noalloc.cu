@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/dpd.h"
+#include "dpd_model.h"
 #include "dpd_adj.cuh"
 
 namespace {
@@ -44,8 +45,6 @@ dpd_status setup_device(int dev)
 
 int nbranch(int order) { return order > 0 ? (order + 1) / 2 : 0; }
 
-bool valid_order(int o) { return o == 0 || (o > 0 && o <= 11 && (o % 2) == 1); }
-
 bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
 bool overlap(const void *a, size_t na, const void *b, size_t nb)
@@ -73,8 +72,9 @@ cudaError_t launch_gh(int B, const dpd::AdjArgs &a, const dpd::AdjLaunch &L, int
 extern "C" dpd_status dpd_grad_coeffs_noalloc(int P, int Q, int M, const void *x, const void *gy, int64_t n,
                                               void *gh, void *stream)
 {
-    if (!valid_order(P) || !valid_order(Q) || (P == 0 && Q == 0)) return DPD_ERR_INVALID_ARGUMENT;
-    if (M < 0 || M + 1 > dpd::kMaxT || n < 0 || !gh || !aligned8(gh)) return DPD_ERR_INVALID_ARGUMENT;
+    const dpd_status mst = dpd::model_status(P, Q, M);
+    if (mst != DPD_OK) return mst;
+    if (n < 0 || !gh || !aligned8(gh)) return DPD_ERR_INVALID_ARGUMENT;
     const int Bp = nbranch(P), Bq = nbranch(Q), B = Bp > Bq ? Bp : Bq, T = M + 1;
     const int K = (Bp + Bq) * T + 1;
     if (K > kMaxK) return DPD_ERR_UNSUPPORTED;

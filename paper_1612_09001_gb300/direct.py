@@ -76,7 +76,7 @@ def nmse_db(y, ref):
 class DirectLearner:
     """Adam on the predistorter coefficients through the transmitter model."""
 
-    def __init__(self, x, tx, P, Q, M, gain=1.0, lr=1e-3, h0=None):
+    def __init__(self, x, tx, P, Q, M, gain=1.0, lr=1e-3, h0=None, eps=1e-8):
         self.x = x
         self.tx = tx
         self.filt = DPD(P, Q, M)
@@ -89,7 +89,10 @@ class DirectLearner:
         self.param = torch.nn.Parameter(torch.view_as_real(h0.clone().contiguous()).clone())
         self.gain = gain
         self.scale = 1.0 / float(x.abs().pow(2).sum())
-        self.opt = torch.optim.Adam([self.param], lr=lr, capturable=True, fused=True)
+        # The learning rate lives in device memory, so a captured step reads
+        # the current value and a schedule can change it between replays.
+        self.opt = torch.optim.Adam([self.param], lr=torch.tensor(float(lr), dtype=torch.float32, device=x.device),
+                                    eps=eps, capturable=True, fused=True)
         self.graph = None
         self.static_loss = None
 
@@ -132,9 +135,26 @@ class DirectLearner:
             return self.static_loss
         return self._step()
 
-    def train(self, steps):
+    @property
+    def lr(self):
+        return float(self.opt.param_groups[0]["lr"])
+
+    def set_lr(self, lr):
+        """Set the learning rate in place (a captured step follows it)."""
+        for g in self.opt.param_groups:
+            g["lr"].fill_(float(lr))
+
+    def train(self, steps, final_lr=None, decay_start=0.0):
+        """Run `steps` training steps (graph replays once captured).  With
+        final_lr the learning rate stays at its current value for the first
+        decay_start fraction of the steps, then decays geometrically to
+        final_lr at the last step.  Returns (step, loss) samples."""
         hist = []
+        lr0 = self.lr
+        i0 = int(decay_start * steps)
         for i in range(steps):
+            if final_lr is not None and i >= i0 and steps - 1 > i0:
+                self.set_lr(lr0 * (final_lr / lr0) ** ((i - i0) / (steps - 1 - i0)))
             loss = self.step()
             if i % max(1, steps // 20) == 0 or i == steps - 1:
                 hist.append((i, float(loss.detach())))

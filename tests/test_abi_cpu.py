@@ -47,7 +47,12 @@ def test_status_strings(lib):
 
 def test_create_rejects_bad_models(lib):
     h = ctypes.c_void_p()
-    for P, Q, M in [(2, 1, 1), (1, 4, 0), (0, 0, 1), (13, 1, 1), (1, 1, 8), (1, 1, -1), (-1, 1, 0)]:
+    # even orders (the paper's order sets are odd, Sec. 2.1) and models past the
+    # built range are unsupported (2); negative values and no branch at all are
+    # invalid (1)
+    for P, Q, M in [(2, 1, 1), (1, 4, 0), (13, 1, 1), (1, 1, 8), (12, 0, 0)]:
+        assert lib.dpd_create(P, Q, M, ctypes.byref(h)) == 2, (P, Q, M)
+    for P, Q, M in [(0, 0, 1), (1, 1, -1), (-1, 1, 0), (1, -3, 0)]:
         assert lib.dpd_create(P, Q, M, ctypes.byref(h)) == 1, (P, Q, M)
     assert lib.dpd_create(5, 5, 2, None) == 1
 

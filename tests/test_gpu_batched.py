@@ -112,8 +112,9 @@ def test_plan_argument_errors():
     assert plan([_lib.StreamDesc(x.data_ptr() + 8, y.data_ptr(), 1000, 5, 5, 2, h.data_ptr())]) == 1   # x not 16 B
     assert plan([_lib.StreamDesc(x.data_ptr(), x.data_ptr(), 1000, 5, 5, 2, h.data_ptr())]) == 1       # in place
     assert plan([ok, _lib.StreamDesc(y.data_ptr(), y.data_ptr() + 16, 10, 5, 5, 2, h.data_ptr())]) == 1  # y overlaps
-    assert plan([_lib.StreamDesc(x.data_ptr(), y.data_ptr(), 1000, 4, 5, 2, h.data_ptr())]) == 1       # even order
-    assert plan([_lib.StreamDesc(x.data_ptr(), y.data_ptr(), 1000, 5, 5, 8, h.data_ptr())]) == 1       # 9 taps
+    assert plan([_lib.StreamDesc(x.data_ptr(), y.data_ptr(), 1000, 4, 5, 2, h.data_ptr())]) == 2       # even order
+    assert plan([_lib.StreamDesc(x.data_ptr(), y.data_ptr(), 1000, 5, 5, 8, h.data_ptr())]) == 2       # 9 taps
+    assert plan([_lib.StreamDesc(x.data_ptr(), y.data_ptr(), 1000, 0, 0, 2, h.data_ptr())]) == 1       # no branch
     assert lib.dpd_exec_batched(None, None) == 1
     assert lib.dpd_plan_destroy(None) == 0
     with pytest.raises(ValueError):

@@ -37,13 +37,20 @@ def test_cascade_gradient_against_oracle(P, Q, M):
     assert rel_err(lr.h_grad().cpu().numpy(), gh_ref) <= 1e-5
 
 
+# Direct learning (Adam, learning rate 5e-3, 400 graph-replayed steps) ends
+# within this margin of the NMSE that three indirect-learning LS fits reach on
+# the same transmitter and signal (measured gap: 0.8 dB at 2^16 samples, 0.9 dB
+# at 2^20).
+DIRECT_VS_ILA_DB = 2.0
+
+
 def test_direct_learning_in_graph_improves_and_matches_ila():
     P, Q, M = 7, 7, 3
     n = 1 << 16
     x = torch.from_numpy(synth.ofdm2(n, key=(82, 0))).cuda()
     tx = Transmitter(_tx())
     base = nmse_db(tx.apply(x), x)
-    lr = DirectLearner(x, tx, P, Q, M, lr=2e-3).capture()
+    lr = DirectLearner(x, tx, P, Q, M, lr=5e-3).capture()
     lr.train(400)
     with torch.no_grad():
         direct = nmse_db(tx.apply(lr.filt.apply(x)), x)
@@ -55,6 +62,7 @@ def test_direct_learning_in_graph_improves_and_matches_ila():
     print(f"NMSE without DPD {base:.2f} dB, direct learning {direct:.2f} dB, ILA {ila:.2f} dB")
     assert direct < base - 10.0, (base, direct)
     assert ila < base - 10.0, (base, ila)
+    assert direct <= ila + DIRECT_VS_ILA_DB, (direct, ila)
     assert lr.time_step(10) > 0
 
 
