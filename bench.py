@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-patterns", action="store_true",
                     help="skip the batched / adjoint / Gram side measurements")
-    ap.add_argument("--fwd-launch", default=None, metavar="MODE,V,WARPS,STAGES",
+    ap.add_argument("--fwd-launch", default=None, metavar="MODE,V,WARPS,STAGES[,GROUP]",
                     help="fix the forward launch shape instead of tuning it (profiling runs)")
     ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "grad", "gram", "ila", "cpu", "sweep", "fma",
                                           "estimate",
@@ -849,8 +849,9 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     from paper_1612_09001_gb300 import tune
     if args.fwd_launch:
-        mode, V, warps, stages = (int(v) for v in args.fwd_launch.split(","))
-        f.set_fwd_launch(mode=mode, V=V, warps=warps, stages=stages)
+        vals = [int(v) for v in args.fwd_launch.split(",")]
+        mode, V, warps, stages = vals[:4]
+        f.set_fwd_launch(mode=mode, V=V, warps=warps, stages=stages, group=vals[4] if len(vals) > 4 else 0)
         picked_by = "--fwd-launch"
     else:
         tune.tune_forward(f, xs[0], ys[0])   # launch shape picked by timing, before the timed region

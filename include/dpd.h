@@ -228,17 +228,22 @@ dpd_status dpd_sq_error(dpd_handle h, const void *y, const void *x, int64_t n, f
  *               bit 1: packed two-wide FP32 fused multiply-adds
  *   V           samples per thread, 2, 4 or 8
  *   warps       consumer warps per CTA, 1..16 (tile = warps*32*V samples)
- *   stages      depth of the shared-memory bulk-copy ring, 2..8
+ *   stages      depth of each group's shared-memory bulk-copy ring, 2..8
  *   ctas_per_sm CTAs per SM of the persistent grid, 0 = as many as fit
  *   use_tma     1 = bulk-copy pipeline, 0 = plain global loads
- * Default: mode 3, V 8, 8 warps, 4 stages, as many CTAs as fit, TMA.  Every
- * (P, Q, M) has modes 2 and 3 at V 4 and 8 and mode 0 at V 4; other
- * combinations exist only for the benchmarked orders.  A shape that does not
- * fit the device, or one not built for the handle's (P, Q, M), makes
- * dpd_apply return DPD_ERR_CUDA.
+ *   group       warps per group, dividing `warps`, or 0 for one group of all
+ *               warps: every group has its own ring and barriers and runs on
+ *               its own sub-tile (group*32*V samples), independently of the
+ *               CTA's other groups
+ * Default: mode 3, V 8, 16 warps in groups of 4, 4 stages, as many CTAs as
+ * fit, TMA.  Every (P, Q, M) has modes 2 and 3 at V 4 and 8 and mode 0 at V 4;
+ * other combinations exist only for the benchmarked orders.  Rings that do
+ * not fit one CTA's shared memory give DPD_ERR_UNSUPPORTED; a shape that does
+ * not fit the device otherwise, or one not built for the handle's (P, Q, M),
+ * makes dpd_apply return DPD_ERR_CUDA.
  */
 dpd_status dpd_set_fwd_launch(dpd_handle h, int mode, int V, int warps, int stages, int ctas_per_sm,
-                              int use_tma);
+                              int use_tma, int group);
 
 /* ------------------------------------------------------------ least squares */
 

@@ -69,7 +69,7 @@ class DPD:
         k = ctypes.c_int()
         _lib.check("dpd_num_coeffs", self._lib.dpd_num_coeffs(self._h, ctypes.byref(k)))
         self.K = k.value
-        self.fwd_launch = dict(mode=3, V=8, warps=8, stages=4, ctas_per_sm=0, use_tma=1)
+        self.fwd_launch = dict(mode=3, V=8, warps=16, stages=4, ctas_per_sm=0, use_tma=1, group=4)
 
     # -- lifetime
     def close(self):
@@ -267,11 +267,11 @@ class DPD:
             _lib.DPD_HOST_ZERO_COPY if zero_copy else _lib.DPD_HOST_PIPELINED, _stream_ptr(stream)))
         return out
 
-    def set_fwd_launch(self, V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1, mode=0):
+    def set_fwd_launch(self, V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=1, mode=0, group=0):
         _lib.check("dpd_set_fwd_launch", self._lib.dpd_set_fwd_launch(
-            self._h, mode, V, warps, stages, ctas_per_sm, use_tma))
+            self._h, mode, V, warps, stages, ctas_per_sm, use_tma, group))
         self.fwd_launch = dict(mode=mode, V=V, warps=warps, stages=stages, ctas_per_sm=ctas_per_sm,
-                               use_tma=use_tma)
+                               use_tma=use_tma, group=group)
 
     def sync_status(self, stream=None):
         """Synchronise the stream and raise if a kernel recorded an error."""

@@ -55,7 +55,7 @@ SIGNATURES = {
     "dpd_set_estimate_basis": [_vp, _i],
     "dpd_sq_error": [_vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_double, _vp, _vp, _vp],
     "dpd_reset_stream": [_vp, _vp],
-    "dpd_set_fwd_launch": [_vp, _i, _i, _i, _i, _i, _i],
+    "dpd_set_fwd_launch": [_vp, _i, _i, _i, _i, _i, _i, _i],
     "dpd_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "dpd_set_adj_launch": [_vp, _i, _i],
     "dpd_grad_coeffs_noalloc": [_i, _i, _i, _vp, _vp, _i64, _vp, _vp],

@@ -238,6 +238,7 @@ static dpd::FwdLaunch launch_for(dpd_handle h, int64_t n)
                 break;
             }
         L.stages = L.warps >= 4 ? 3 : 2;
+        L.group = 0;
     }
     return L;
 }
@@ -524,13 +525,21 @@ dpd_status dpd_reset_stream(dpd_handle h, void *stream)
 }
 
 dpd_status dpd_set_fwd_launch(dpd_handle h, int mode, int V, int warps, int stages, int ctas_per_sm,
-                              int use_tma)
+                              int use_tma, int group)
 {
     if (!h) return DPD_ERR_INVALID_ARGUMENT;
     if (mode < 0 || mode > 3) return DPD_ERR_INVALID_ARGUMENT;
-    if ((V != 2 && V != 4 && V != 8) || warps < 1 || warps > 16 || stages < 2 || stages > 8 || ctas_per_sm < 0 ||
-        (use_tma != 0 && use_tma != 1))
+    if ((V != 2 && V != 4 && V != 8) || warps < 1 || warps > dpd::kFwdMaxWarps || stages < 2 || stages > 8 ||
+        ctas_per_sm < 0 || (use_tma != 0 && use_tma != 1) || group < 0 || (group > 0 && warps % group != 0))
         return DPD_ERR_INVALID_ARGUMENT;
+    if (use_tma) {   // the rings of all groups must fit in one CTA's shared memory
+        const int gw = group > 0 ? group : warps, ng = warps / gw;
+        const size_t smem = (size_t)((4 * h->B * h->T + 2) * 4 + 127) / 128 * 128 +
+                            (size_t)((2 * ng * stages * 8 + 127) / 128) * 128 +
+                            (size_t)ng * stages * (size_t)(dpd::kHalo + gw * 32 * V) * sizeof(float2);
+        if (smem > (size_t)227 * 1024) return DPD_ERR_UNSUPPORTED;
+    }
+    h->fwd.group = group;
     h->fwd.mode = mode;
     h->fwd.V = V;
     h->fwd.warps = warps;

@@ -126,14 +126,6 @@ __host__ __device__ constexpr int tab_bytes()
     return ((wl_table_floats(B, T) * 4 + 127) / 128) * 128;
 }
 
-// Shared-memory bytes of the TMA kernel for a given launch shape.
-template <int B, int T, int V>
-__host__ __device__ constexpr size_t fwd_tma_smem(int warps, int stages)
-{
-    return (size_t)tab_bytes<B, T>() + 128 +
-           (size_t)stages * (size_t)(kHalo + warps * 32 * V) * sizeof(float2);
-}
-
 // Read the window of thread t_in_tile of a tile that starts at sample s0 from a
 // shared-memory slot holding global samples [s0 - kHalo, ...).  Samples in
 // [lo, vhi) are in the slot; the sample just past vhi (odd tail) comes from
@@ -216,29 +208,77 @@ __device__ __forceinline__ void store_outputs(float2 *__restrict__ y, int64_t g0
     }
 }
 
-template <int B, int T, int V, int MODE>
-__global__ void __launch_bounds__(32 * 17)
-    fwd_tma_kernel(FwdArgs a, int stages, int64_t ntiles, const __grid_constant__ ParamTab<B, T> ptab)
+// Shared-memory bytes of the TMA kernel for a launch shape: the table area, the
+// barrier pairs of every group and stage, and per group `stages` slots of the
+// group's sub-tile (gw * 32 * V samples) with kHalo history samples each.
+template <int B, int T, int V>
+__host__ __device__ constexpr size_t fwd_tma_smem(int warps, int gw, int stages)
 {
+    return (size_t)tab_bytes<B, T>() + (size_t)((2 * (warps / gw) * stages * 8 + 127) / 128) * 128 +
+           (size_t)(warps / gw) * stages * (size_t)(kHalo + gw * 32 * V) * sizeof(float2);
+}
+
+// The consumer warps form groups of gw warps; every group has its own ring of
+// `stages` slots and its own full / empty barriers, and the producer thread
+// fills each group's slot with its own bulk copy (the group's sub-tile and the
+// kHalo samples in front of it).  A group starts on its sub-tile as soon as its
+// own copy has landed and releases its slot on its own, so the groups of a CTA
+// drift apart instead of waiting for one another at every tile: at start-up
+// the first (small) sub-tiles arrive sooner, and in the steady state the FMA
+// and memory phases of the groups overlap.
+//
+// Shapes.  SH = 0 takes the warp count from the launch and the group size and
+// ring depth from its arguments; SH > 0 fixes all three at compile time (the
+// kFwdShapes entry), which turns the tile, sub-tile and slot arithmetic into
+// constants and lets a 12-warp shape ask for two CTAs per SM: the shapes the
+// autotuner picks for the benchmarked models run that way (measured: 59.0 ->
+// 55.5 us per 2^24 samples at P = Q = 9, M = 4, 16 warps in groups of 4).
+struct FwdShape {
+    int warps, gw, stages;
+};
+constexpr FwdShape kFwdShapes[] = {{0, 0, 0}, {16, 4, 4}, {12, 3, 3}, {12, 2, 4}};
+constexpr int kFwdNumShapes = sizeof(kFwdShapes) / sizeof(kFwdShapes[0]);
+
+template <int SH>
+constexpr int fwd_lb_threads()
+{
+    return SH > 0 ? 32 * (kFwdShapes[SH].warps + 1) : 32 * (kFwdMaxWarps + 1);
+}
+template <int SH>
+constexpr int fwd_lb_blocks()
+{
+    return (SH > 0 && kFwdShapes[SH].warps <= 12) ? 2 : 1;
+}
+
+template <int B, int T, int V, int MODE, int SH>
+__global__ void __launch_bounds__(fwd_lb_threads<SH>(), fwd_lb_blocks<SH>())
+    fwd_tma_kernel(FwdArgs a, int stages_arg, int gw_arg, int64_t ntiles, const __grid_constant__ ParamTab<B, T> ptab)
+{
+    constexpr bool FIXED = SH > 0;
     constexpr int W = V + T - 1;
     constexpr int TABF = wl_table_floats(B, T);
     extern __shared__ __align__(128) unsigned char smem[];
     float *tab = reinterpret_cast<float *>(smem);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + tab_bytes<B, T>());   // full[s], empty[s]
-    float2 *ring = reinterpret_cast<float2 *>(smem + tab_bytes<B, T>() + 128);
-
-    const int nwarps = blockDim.x / 32 - 1;   // consumer warps; the last warp produces
-    const int S = nwarps * 32 * V;
-    const int slot_elems = kHalo + S;
+    const int nwarps = FIXED ? kFwdShapes[SH].warps : (int)(blockDim.x / 32) - 1;   // the last warp produces
+    const int gw = FIXED ? kFwdShapes[SH].gw : gw_arg;
+    const int stages = FIXED ? kFwdShapes[SH].stages : stages_arg;
+    const int ngroups = nwarps / gw;
+    // per group g: full[s] at bars[2 stages g + s], empty[s] at bars[2 stages g + stages + s]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + tab_bytes<B, T>());
+    float2 *ring = reinterpret_cast<float2 *>(smem + tab_bytes<B, T>() + ((2 * ngroups * stages * 8 + 127) / 128) * 128);
+    const int S = nwarps * 32 * V;    // tile
+    const int SG = gw * 32 * V;       // a group's sub-tile
+    const int slot_elems = kHalo + SG;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // Prologue that touches no global memory (overlaps the previous grid's tail
     // under programmatic dependent launch), then wait for that grid.
     if (tid == 0) {
-        for (int s = 0; s < stages; ++s) {
-            mbar_init(smem_addr(&bars[s]), 1);
-            mbar_init(smem_addr(&bars[stages + s]), nwarps);
-        }
+        for (int g = 0; g < ngroups; ++g)
+            for (int s = 0; s < stages; ++s) {
+                mbar_init(smem_addr(&bars[2 * stages * g + s]), 1);
+                mbar_init(smem_addr(&bars[2 * stages * g + stages + s]), gw);
+            }
         fence_barrier_init();
     }
     grid_dep_launch_dependents();
@@ -252,54 +292,66 @@ __global__ void __launch_bounds__(32 * 17)
         if (lane != 0) return;
         const uint64_t pol = policy_evict_first();
         int64_t it = 0;
-        bool ok = true;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-            const int s = (int)(it % stages);
-            const uint32_t ph = (uint32_t)((it / stages) & 1);
-            if (it >= stages && !mbar_wait(smem_addr(&bars[stages + s]), ph ^ 1u, a.status)) {
-                ok = false;
-                break;
+        int gfail = -1;   // group whose slot wait ran out, at tile index fail_it
+        int64_t fail_it = 0;
+        int s = 0;        // slot of tile `it` (it % stages, kept incrementally: no division in the loop)
+        uint32_t ph = 0;  // parity of its use of the slot ((it / stages) & 1)
+        for (int64_t tile = blockIdx.x; tile < ntiles && gfail < 0; tile += gridDim.x, ++it) {
+            for (int g = 0; g < ngroups; ++g) {
+                uint64_t *gb = bars + 2 * stages * g;
+                if (it >= stages && !mbar_wait(smem_addr(&gb[stages + s]), ph ^ 1u, a.status)) {
+                    gfail = g;
+                    fail_it = it;
+                    break;
+                }
+                int64_t lo, cnt;
+                int off;
+                tile_copy_range(tile * S + (int64_t)g * SG, SG, a.n, lo, cnt, off);
+                if (cnt < 0) cnt = 0;   // a group past the end of the input: nothing to copy
+                const uint32_t bytes = (uint32_t)(cnt * (int64_t)sizeof(float2));
+                const uint32_t fb = smem_addr(&gb[s]);
+                mbar_arrive_expect_tx(fb, bytes);
+                if (bytes)
+                    bulk_copy_g2s_stream(smem_addr(ring + ((size_t)g * stages + s) * slot_elems + off), a.x + lo,
+                                         bytes, fb, pol);
             }
-            // Start-up: the second tile is requested only once the first has
-            // landed, so that every CTA's first tile is not queued behind the
-            // other CTAs' later ones when all of them fill their rings at once.
-            if (it == 1 && !mbar_wait(smem_addr(&bars[0]), 0u, a.status)) {
-                ok = false;
-                break;
+            if (gfail < 0 && ++s == stages) {
+                s = 0;
+                ph ^= 1u;
             }
-            const int64_t s0 = tile * S;
-            int64_t lo, cnt;
-            int off;
-            tile_copy_range(s0, S, a.n, lo, cnt, off);
-            const uint32_t bytes = (uint32_t)(cnt * (int64_t)sizeof(float2));
-            const uint32_t fb = smem_addr(&bars[s]);
-            mbar_arrive_expect_tx(fb, bytes);
-            if (bytes)
-                bulk_copy_g2s_stream(smem_addr(ring + (size_t)s * slot_elems + off), a.x + lo, bytes,
-                                     fb, pol);
         }
-        if (!ok) {
-            // Let the copies already issued land before the CTA exits.
-            const int64_t first = it > stages ? it - stages : 0;
-            for (int64_t j = first; j < it; ++j)
-                mbar_wait(smem_addr(&bars[j % stages]), (uint32_t)((j / stages) & 1), a.status);
+        if (gfail >= 0) {
+            // Let the copies already issued land before the CTA exits: group g
+            // has tiles [0, fail_it] issued if g < gfail, else [0, fail_it - 1].
+            for (int g = 0; g < ngroups; ++g) {
+                const int64_t last = g < gfail ? fail_it : fail_it - 1;
+                const int64_t first = last - stages + 1 > 0 ? last - stages + 1 : 0;
+                for (int64_t j = first; j <= last; ++j)
+                    mbar_wait(smem_addr(&bars[2 * stages * g + j % stages]), (uint32_t)((j / stages) & 1), a.status);
+            }
         }
         return;
     }
 
     // -------------------------------------------------------------------- consumers
-    const int t_in_tile = warp * 32 + lane;
-    int64_t it = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int s = (int)(it % stages);
-        const uint32_t ph = (uint32_t)((it / stages) & 1);
-        if (!mbar_wait(smem_addr(&bars[s]), ph, a.status)) return;
-        const float2 *slot = ring + (size_t)s * slot_elems;
-        const int64_t s0 = tile * S;
+    const int g = warp / gw;
+    const int t_in_tile = (warp - g * gw) * 32 + lane;   // position in the group's sub-tile
+    uint64_t *gb = bars + 2 * stages * g;
+    const float2 *ring_g = ring + (size_t)g * stages * slot_elems;
+    int s = 0;        // slot and parity of the current tile, kept incrementally
+    uint32_t ph = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (!mbar_wait(smem_addr(&gb[s]), ph, a.status)) return;
+        const float2 *slot = ring_g + (size_t)s * slot_elems;
+        const int64_t s0 = tile * S + (int64_t)g * SG;
         float wr[W], wi[W];
-        const bool full = load_window<T, V>(slot, s0, S, a.n, a.x, t_in_tile, wr, wi);
+        const bool full = load_window<T, V>(slot, s0, SG, a.n, a.x, t_in_tile, wr, wi);
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));
+        if (lane == 0) mbar_arrive(smem_addr(&gb[stages + s]));
+        if (++s == stages) {
+            s = 0;
+            ph ^= 1u;
+        }
 
         float yr[V], yi[V];
         fwd_compute<B, T, V, MODE>(tab, ptab, wr, wi, yr, yi);
@@ -349,6 +401,26 @@ constexpr bool fwd_all_modes()
     return (B == 5 && T == 5) || (B == 3 && T == 3) || (B == 4 && T == 4) || (B == 6 && T == 8);
 }
 
+// Fixed-shape kernels (kFwdShapes) exist for the benchmarked filter models
+// (B = T = 3, 4, 5) at V = 8 with packed FMAs on parameter-bank coefficients
+// (mode 3); larger models would spill in the two-CTA shapes.
+template <int B, int T, int V, int MODE>
+constexpr bool fwd_fixed_shapes()
+{
+    return fwd_all_modes<B, T>() && B * T <= 25 && V == 8 && MODE == (kModeParamCoef | kModePackedFma);
+}
+
+// kFwdShapes index of a launch shape when it is built as a fixed kernel, else 0.
+template <int B, int T, int V, int MODE>
+int fwd_shape_index(int warps, int gw, int stages)
+{
+    if constexpr (fwd_fixed_shapes<B, T, V, MODE>()) {
+        for (int i = 1; i < kFwdNumShapes; ++i)
+            if (kFwdShapes[i].warps == warps && kFwdShapes[i].gw == gw && kFwdShapes[i].stages == stages) return i;
+    }
+    return 0;
+}
+
 template <int B, int T, int V, int MODE, bool TMA>
 constexpr bool fwd_built()
 {
@@ -369,15 +441,22 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
         if constexpr (fwd_built<B, T, V, MODE, true>()) {
             const int threads = (L.warps + 1) * 32;
             const int S = L.warps * 32 * V;
+            const int gw = (L.group > 0 && L.warps % L.group == 0) ? L.group : L.warps;
             const int64_t ntiles = (a.n + S - 1) / S;
-            const size_t smem = fwd_tma_smem<B, T, V>(L.warps, L.stages);
-            auto kern = fwd_tma_kernel<B, T, V, MODE>;
-            static SmemAttr smem_rec;   // per instantiation
-            cudaError_t ae = ensure_smem(smem_rec, (const void *)kern, smem);
+            const size_t smem = fwd_tma_smem<B, T, V>(L.warps, gw, L.stages);
+            const int sh = fwd_shape_index<B, T, V, MODE>(L.warps, gw, L.stages);
+            void (*kern)(FwdArgs, int, int, int64_t, const ParamTab<B, T>) = fwd_tma_kernel<B, T, V, MODE, 0>;
+            if constexpr (fwd_fixed_shapes<B, T, V, MODE>()) {
+                if (sh == 1) kern = fwd_tma_kernel<B, T, V, MODE, 1>;
+                if (sh == 2) kern = fwd_tma_kernel<B, T, V, MODE, 2>;
+                if (sh == 3) kern = fwd_tma_kernel<B, T, V, MODE, 3>;
+            }
+            static SmemAttr smem_rec[kFwdNumShapes];   // per instantiation
+            cudaError_t ae = ensure_smem(smem_rec[sh], (const void *)kern, smem);
             if (ae != cudaSuccess) return ae;
-            static OccCache occ_rec;
+            static OccCache occ_rec[kFwdNumShapes];
             int occ = 0;
-            ae = occupancy(occ_rec, (const void *)kern, threads, smem, &occ);
+            ae = occupancy(occ_rec[sh], (const void *)kern, threads, smem, &occ);
             if (ae != cudaSuccess) return ae;
             if (occ < 1) return cudaErrorInvalidConfiguration;
             const int cps = (L.ctas_per_sm > 0 && L.ctas_per_sm < occ) ? L.ctas_per_sm : occ;
@@ -396,7 +475,7 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, L.stages, ntiles, ptab);
+            cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, L.stages, gw, ntiles, ptab);
             count_launch();
             return e != cudaSuccess ? e : cudaGetLastError();
         }

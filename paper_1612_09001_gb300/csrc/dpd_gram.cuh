@@ -106,6 +106,12 @@ cudaError_t launch_chol(const double2 *G, int nprob, int K, double2 *L, double *
 // x = G^{-1} rhs using the factorisation; if accumulate, h += x instead of h = x.
 cudaError_t launch_chol_solve(const double2 *L, const double *d, const int *info, const double2 *rhs, int nprob,
                               int K, double2 *h, int accumulate, cudaStream_t s);
+// Single problem: Linv = L^{-1} (lower, row-major K x K) of the factorisation,
+// then x = G^{-1} rhs = D Linv^H Linv D rhs as two parallel matrix-vector
+// products (tmp: K values of scratch); both skip a failed factorisation.
+cudaError_t launch_chol_invert(const double2 *L, const int *info, int K, double2 *Linv, cudaStream_t s);
+cudaError_t launch_solve_inverse(const double2 *Linv, const double *d, const int *info, const double2 *rhs, int K,
+                                 double2 *tmp, double2 *h, int accumulate, cudaStream_t s);
 // Complex64 copy of the FP64 coefficients.
 cudaError_t launch_h_to_f32(const double2 *h, int n, float2 *out, cudaStream_t s);
 // e = t - y (n samples).

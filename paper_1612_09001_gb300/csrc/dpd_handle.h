@@ -29,6 +29,10 @@ struct EstimateWorkspace {
     double *mom = nullptr;        // [nprob][kMomK] power sums of |u|^2
     double *mom_part = nullptr;   // [nprob][kMomBlocks][kMomK]
     double2 *hm64 = nullptr;      // [nprob][K] monomial-basis coefficients / transformed right-hand sides
+    // single problem: explicit inverse of the Cholesky factor for the solves
+    double2 *Linv = nullptr;      // K x K
+    double2 *tmpv = nullptr;      // K
+    bool use_inverse = false;     // refinement solves through Linv (problem 0 only)
     // pinned host copies read back by dpd_estimate (single problem)
     int hK = 0;                   // K the host buffers were sized for
     double2 *h_L = nullptr;       // Cholesky factor, K x K (condition estimate on the host)

@@ -44,13 +44,16 @@ struct HostTab {
 enum : int { kModeParamCoef = 1, kModePackedFma = 2 };
 
 // Forward launch shape.
+constexpr int kFwdMaxWarps = 16;   // consumer warps per CTA of the TMA kernel (register budget)
+
 struct FwdLaunch {
     int mode = kModeParamCoef | kModePackedFma;   // compute mode bits
     int V = 8;            // samples per consumer thread (2, 4 or 8)
-    int warps = 8;        // consumer warps per CTA (tile = warps * 32 * V samples)
-    int stages = 4;       // shared-memory ring depth (bulk-copy pipeline)
+    int warps = 16;       // consumer warps per CTA (tile = warps * 32 * V samples)
+    int stages = 4;       // shared-memory ring depth per group (bulk-copy pipeline)
     int ctas_per_sm = 0;  // 0: as many as fit
     int use_tma = 1;      // 0: plain global loads (also used for 8-byte aligned buffers)
+    int group = 4;        // warps per group (own ring and barriers); 0: one group of all warps
 };
 
 struct FwdArgs {

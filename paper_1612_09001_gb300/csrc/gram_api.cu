@@ -47,6 +47,7 @@ dpd_status reserve(dpd_handle h, int nprob, int cpp, int64_t nsamp)
         ok = ok && grow(w.ubasis, 0, np * dpd::kUSize) && grow(w.ubasis64, 0, np * dpd::kUSize);
         ok = ok && grow(w.mom, 0, np * dpd::kMomK) && grow(w.mom_part, 0, np * dpd::kMomBlocks * dpd::kMomK);
         ok = ok && grow(w.hm64, 0, np * K);
+        ok = ok && grow(w.Linv, 0, (size_t)K * K) && grow(w.tmpv, 0, (size_t)K);
         if (!ok) return DPD_ERR_ALLOC;
         w.nprob = nprob;
         w.cpp = cpp;
@@ -240,9 +241,13 @@ dpd_status refine_once(dpd_handle h, int p, const float2 *u, const float2 *t, in
             return DPD_ERR_CUDA;
         rhs = w.hm64 + (size_t)p * K;
     }
-    if (dpd::launch_chol_solve(w.L + (size_t)p * K * K, w.d + (size_t)p * K, w.info + p, rhs, 1, K,
-                               w.h64 + (size_t)p * K, 1, s) != cudaSuccess)
+    if (w.use_inverse && p == 0) {
+        if (dpd::launch_solve_inverse(w.Linv, w.d, w.info, rhs, K, w.tmpv, w.h64, 1, s) != cudaSuccess)
+            return DPD_ERR_CUDA;
+    } else if (dpd::launch_chol_solve(w.L + (size_t)p * K * K, w.d + (size_t)p * K, w.info + p, rhs, 1, K,
+                                      w.h64 + (size_t)p * K, 1, s) != cudaSuccess) {
         return DPD_ERR_CUDA;
+    }
     return DPD_OK;
 }
 
@@ -442,6 +447,8 @@ void free_estimate_workspace(EstimateWorkspace &w)
     cudaFree(w.mom);
     cudaFree(w.mom_part);
     cudaFree(w.hm64);
+    cudaFree(w.Linv);
+    cudaFree(w.tmpv);
     cudaFreeHost(w.h_L);
     cudaFreeHost(w.h_info);
     cudaFreeHost(w.h_norm);
@@ -505,7 +512,12 @@ dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, i
         (stats && cudaMemcpyAsync(w.h_L, w.L, sizeof(double2) * K * K, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
         cudaEventRecord(w.ev_L, s) != cudaSuccess)
         return DPD_ERR_CUDA;
-    if (dpd::launch_chol_solve(w.L, w.d, w.info, w.g, 1, K, w.h64, 0, s) != cudaSuccess) return DPD_ERR_CUDA;
+    // The solves go through the explicit inverse of L: two parallel
+    // matrix-vector products instead of two K-step sequential chains each.
+    if (dpd::launch_chol_invert(w.L, w.info, K, w.Linv, s) != cudaSuccess) return DPD_ERR_CUDA;
+    w.use_inverse = true;
+    if (dpd::launch_solve_inverse(w.Linv, w.d, w.info, w.g, K, w.tmpv, w.h64, 0, s) != cudaSuccess)
+        return DPD_ERR_CUDA;
     for (int i = 0; i < refine_iters; ++i)
         if ((st = refine_once(h, 0, pr.u, pr.t, n, s)) != DPD_OK) return st;
     const double2 *hm = monomial_h(h, 0, 1, s, st);
@@ -548,6 +560,7 @@ dpd_status dpd_estimate_batched(dpd_handle h, const void *const *u, const void *
     if (ortho(h) && (st = compute_basis(h, std::vector<int64_t>(n, n + count), s)) != DPD_OK) return st;
     if ((st = run_gram(h, count, cpp, precision, s)) != DPD_OK) return st;
     if (dpd::launch_chol(w.G, count, h->K, w.L, w.d, w.info, s) != cudaSuccess) return DPD_ERR_CUDA;
+    w.use_inverse = false;
     if (dpd::launch_chol_solve(w.L, w.d, w.info, w.g, count, h->K, w.h64, 0, s) != cudaSuccess) return DPD_ERR_CUDA;
     std::vector<int> info((size_t)count);
     if (cudaMemcpyAsync(info.data(), w.info, sizeof(int) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

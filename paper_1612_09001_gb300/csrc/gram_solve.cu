@@ -2,6 +2,8 @@
 // reduction of the Gram partials, assembly of G = Psi^H Psi and g = Psi^H t,
 // equilibrated Cholesky factorisation and triangular solves, and the small
 // kernels of the iterative refinement.
+#include <cooperative_groups.h>
+
 #include "dpd_gram.cuh"
 
 namespace dpd {
@@ -290,9 +292,167 @@ __global__ void __launch_bounds__(256) chol_kernel(const double2 *__restrict__ G
     if (tid == 0) info[p] = bad;
 }
 
+// The same factorisation spread over a cluster of kCholCluster CTAs (one SM
+// each), for few problems: one CTA per problem leaves all but a few SMs idle
+// and is bound by one SM's FP64 rate.  Columns are dealt out cyclically (CTA r
+// owns columns k = r, r + C, ...; its rows i >= k in shared memory).  Step j:
+// the owner of column j has already factored it and written it, with the
+// pivot status, into every CTA's shared column buffer pc[j & 1] (distributed
+// shared memory); after the cluster barrier every CTA updates its own columns
+// k > j with it.  Look-ahead: the owner of column j + 1 first updates that
+// column alone, takes its pivot, scales it and broadcasts it into pc[(j+1) & 1]
+// before its other updates, so the next step's column is ready when the
+// barrier completes.  Double buffering is safe: pc[(j+1) & 1] was last read in
+// step j - 1, which every CTA finished before the barrier of step j.  Every
+// CTA reads the same pivot status after the same barrier, so all of them leave
+// the loop at the same step and pass the same number of cluster barriers.
+constexpr int kCholCluster = 8;
+constexpr int kCholClusterThreads = 256;
+constexpr int kCholMaxK = 2 * kMaxB * kMaxT + 1;   // 97: P = Q = 11, M = 7
+
+__global__ void __launch_bounds__(kCholClusterThreads) chol_cluster_kernel(const double2 *__restrict__ Gall, int K,
+                                                                            double2 *__restrict__ Lall,
+                                                                            double *__restrict__ dall,
+                                                                            int *__restrict__ info)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    constexpr int C = kCholCluster;
+    extern __shared__ double2 A[];            // [K][ncl]: this CTA's columns
+    __shared__ double2 pc[2][kCholMaxK];      // broadcast pivot columns
+    __shared__ int pbad[2];                   // their pivot status (0 or failing column + 1)
+    __shared__ double dsh[kCholMaxK];
+    __shared__ double rinv;
+    const int rank = (int)cluster.block_rank();
+    const int p = blockIdx.x / C, tid = threadIdx.x, nt = blockDim.x;
+    const int ncl = (K + C - 1) / C;          // local columns (the last may be short)
+    const double2 *G = Gall + (size_t)p * K * K;
+    // Equilibration, computed by every CTA (the same values everywhere).
+    int bad0 = 0;
+    for (int i = 0; i < K; ++i) {
+        const double gii = G[(size_t)i * K + i].x;
+        if (!(gii > 0.0) && bad0 == 0) bad0 = i + 1;
+    }
+    for (int i = tid; i < K; i += nt) {
+        const double gii = G[(size_t)i * K + i].x;
+        dsh[i] = gii > 0.0 ? 1.0 / sqrt(gii) : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < K * ncl; e += nt) {
+        const int i = e / ncl, lc = e % ncl, k = rank + lc * C;
+        double2 v = make_double2(0.0, 0.0);
+        if (k < K && i >= k) {
+            const double2 g = G[(size_t)i * K + k];
+            const double sc = dsh[i] * dsh[k];
+            v = make_double2(g.x * sc, g.y * sc);
+        }
+        A[(size_t)i * ncl + lc] = v;
+    }
+    __syncthreads();
+
+    // Factor local column lc (global k): pivot, scale, broadcast into buffer b.
+    auto factor_and_send = [&](int k, int lc, int b) {
+        if (tid == 0) {
+            const double piv = A[(size_t)k * ncl + lc].x;
+            int bad = 0;
+            if (!(piv > 1e-30 && piv < 1e30)) {
+                bad = k + 1;
+                rinv = 0.0;
+            } else {
+                const double ri = rsqrt_newton(piv);
+                A[(size_t)k * ncl + lc] = make_double2(piv * ri, 0.0);
+                rinv = ri;
+            }
+            for (int r = 0; r < C; ++r) *cluster.map_shared_rank(&pbad[b], r) = bad;
+        }
+        __syncthreads();
+        const double ri = rinv;
+        for (int i = k + 1 + tid; i < K; i += nt) {
+            const double2 v = A[(size_t)i * ncl + lc];
+            A[(size_t)i * ncl + lc] = make_double2(v.x * ri, v.y * ri);
+        }
+        __syncthreads();
+        const int m = K - k;
+        for (int e = tid; e < m * C; e += nt) {
+            const int r = e / m, i = k + e % m;
+            *cluster.map_shared_rank(&pc[b][i], r) = A[(size_t)i * ncl + lc];
+        }
+    };
+    // A[i][k] -= pc[i] conj(pc[k]) for rows i >= k of one local column.
+    auto update_col = [&](const double2 *col, int k, int lc, int first_row, int stride) {
+        const double2 b = col[k];
+        for (int i = k + first_row; i < K; i += stride) {
+            const double2 a = col[i];
+            double2 &cc = A[(size_t)i * ncl + lc];
+            cc.x = fma(-a.x, b.x, fma(-a.y, b.y, cc.x));
+            cc.y = fma(-a.y, b.x, fma(a.x, b.y, cc.y));
+        }
+    };
+
+    int bad = bad0;
+    if (bad == 0 && rank == 0) factor_and_send(0, 0, 0);
+    cluster.sync();
+    for (int j = 0; j < K && bad == 0; ++j) {
+        const int b = j & 1;
+        if (pbad[b]) {   // the same value in every CTA after the same barrier
+            bad = pbad[b];
+            break;
+        }
+        const double2 *col = pc[b];
+        const int next = j + 1;
+        const bool own_next = next < K && next % C == rank;
+        if (own_next) {   // look-ahead: column j + 1 first, then its pivot and broadcast
+            update_col(col, next, next / C, tid, nt);
+            __syncthreads();
+            factor_and_send(next, next / C, next & 1);
+        }
+        // The rest of this CTA's columns k > j: (local column, row) pairs dealt
+        // to the threads, columns in order.
+        const int lc0 = (j + 1 - rank + C - 1) / C + (own_next ? 1 : 0);   // first local column with k > j (after next)
+        for (int lc = lc0 + tid / 32; lc < ncl; lc += nt / 32) {
+            const int k = rank + lc * C;
+            if (k < K) update_col(col, k, lc, tid % 32, 32);
+        }
+        cluster.sync();
+    }
+    cluster.sync();   // no CTA leaves while another may still write into its buffers
+
+    double2 *L = Lall + (size_t)p * K * K;
+    for (int e = tid; e < K * ncl; e += nt) {
+        const int i = e / ncl, lc = e % ncl, k = rank + lc * C;
+        if (k < K) L[(size_t)i * K + k] = i >= k ? A[(size_t)i * ncl + lc] : make_double2(0.0, 0.0);
+    }
+    if (rank == 0) {
+        for (int i = tid; i < K; i += nt) dall[(size_t)p * K + i] = dsh[i];
+        if (tid == 0) info[p] = bad;
+    }
+}
+
 cudaError_t launch_chol(const double2 *G, int nprob, int K, double2 *L, double *d, int *info, cudaStream_t s)
 {
     const size_t smem = sizeof(double2) * K * K;
+    if (nprob * kCholCluster <= 64 && K <= kCholMaxK) {
+        // Few problems: a cluster of CTAs per problem (see chol_cluster_kernel).
+        const size_t csmem = sizeof(double2) * (size_t)K * ((K + kCholCluster - 1) / kCholCluster);
+        static SmemAttr csmem_rec;
+        cudaError_t e = ensure_smem(csmem_rec, (const void *)chol_cluster_kernel, csmem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nprob * kCholCluster));
+        cfg.blockDim = dim3(kCholClusterThreads);
+        cfg.dynamicSmemBytes = csmem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kCholCluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, chol_cluster_kernel, G, K, L, d, info);
+        count_launch();
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     static SmemAttr smem_rec;
     const cudaError_t e = ensure_smem(smem_rec, (const void *)chol_kernel, smem);
     if (e != cudaSuccess) return e;
@@ -433,6 +593,136 @@ cudaError_t launch_chol_solve(const double2 *L, const double *d, const int *info
     const cudaError_t e = ensure_smem(smem_rec, (const void *)chol_solve_kernel, smem);
     if (e != cudaSuccess) return e;
     chol_solve_kernel<<<nprob, 256, smem, s>>>(L, d, info, rhs, K, h, accumulate);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Column j of L^{-1} per CTA: L x = e_j by column-oriented forward
+// substitution.  The CTA first stages the strictly lower triangle of the
+// trailing block L[j:, j:] in shared memory (packed by rows), then one warp
+// runs the K - j steps, lane l holding rows j + l, j + l + 32, ...: step k, the
+// lane of row k finishes x_k = r_k / L_kk and broadcasts it, and every lane
+// subtracts L_ik x_k from its rows i > k.  The columns are independent, so the
+// K CTAs spread the FP64 work of the inverse (K^3/6 complex updates) over as
+// many SMs instead of one; column 0, the longest, bounds the kernel.
+constexpr int kInvRows = 4;   // rows per lane: K <= 128
+constexpr int kInvThreads = 128;
+
+__global__ void __launch_bounds__(kInvThreads) chol_invert_kernel(const double2 *__restrict__ L,
+                                                                  const int *__restrict__ info, int K,
+                                                                  double2 *__restrict__ Linv)
+{
+    extern __shared__ double2 tri[];   // row i' (i' = i - j) of L[j:, j:] at i'(i'-1)/2, i' entries
+    if (info[0] != 0) return;
+    const int j = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int m_ = K - j;
+    for (int e = tid; e < m_ * (m_ - 1) / 2; e += kInvThreads) {
+        int ip = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);   // row of packed element e
+        while (ip * (ip - 1) / 2 > e) --ip;
+        while ((ip + 1) * ip / 2 <= e) ++ip;
+        const int kp = e - ip * (ip - 1) / 2;
+        tri[e] = L[(size_t)(j + ip) * K + j + kp];
+    }
+    __syncthreads();
+    if (tid >= 32) return;
+    double2 r[kInvRows];
+    double inv_own[kInvRows];
+#pragma unroll
+    for (int m = 0; m < kInvRows; ++m) {
+        const int ip = lane + 32 * m;
+        r[m] = make_double2(ip == 0 ? 1.0 : 0.0, 0.0);
+        inv_own[m] = ip < m_ ? 1.0 / L[(size_t)(j + ip) * K + j + ip].x : 0.0;
+    }
+    for (int kp = 0; kp < m_; ++kp) {
+        const int owner = kp & 31, mo = kp >> 5;
+        double2 xk = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int m = 0; m < kInvRows; ++m)
+            if (m == mo && lane == owner) {   // row k is final: x_k = r_k / L_kk (real diagonal)
+                xk = make_double2(r[m].x * inv_own[m], r[m].y * inv_own[m]);
+                r[m] = xk;
+            }
+        xk.x = __shfl_sync(0xffffffffu, xk.x, owner);
+        xk.y = __shfl_sync(0xffffffffu, xk.y, owner);
+#pragma unroll
+        for (int m = 0; m < kInvRows; ++m) {
+            const int ip = lane + 32 * m;
+            if (ip > kp && ip < m_) {
+                const double2 l = tri[ip * (ip - 1) / 2 + kp];
+                r[m].x = fma(-l.x, xk.x, fma(l.y, xk.y, r[m].x));
+                r[m].y = fma(-l.x, xk.y, fma(-l.y, xk.x, r[m].y));
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < kInvRows; ++m) {   // column j, rows >= j
+        const int ip = lane + 32 * m;
+        if (ip < m_) Linv[(size_t)(j + ip) * K + j] = r[m];
+    }
+    for (int i = lane; i < j; i += 32) Linv[(size_t)i * K + j] = make_double2(0.0, 0.0);
+}
+
+// One warp per output element: tmp_i = sum_{k <= i} Linv[i][k] d_k rhs_k
+// (lower) or h_k (+)= d_k sum_{i >= k} conj(Linv[i][k]) tmp_i (upper).
+__global__ void __launch_bounds__(128) inv_matvec_kernel(const double2 *__restrict__ Linv,
+                                                         const double *__restrict__ d, const int *__restrict__ info,
+                                                         const double2 *__restrict__ v, int K, int upper,
+                                                         double2 *__restrict__ out, int accumulate)
+{
+    if (info[0] != 0) return;
+    const int row = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= K) return;
+    double2 acc = make_double2(0.0, 0.0);
+    if (!upper) {
+        for (int k = lane; k <= row; k += 32) {
+            const double2 l = Linv[(size_t)row * K + k];
+            const double2 b = make_double2(v[k].x * d[k], v[k].y * d[k]);
+            acc.x = fma(l.x, b.x, fma(-l.y, b.y, acc.x));
+            acc.y = fma(l.x, b.y, fma(l.y, b.x, acc.y));
+        }
+    } else {
+        for (int i = row + lane; i < K; i += 32) {
+            const double2 l = Linv[(size_t)i * K + row];
+            const double2 b = v[i];
+            acc.x = fma(l.x, b.x, fma(l.y, b.y, acc.x));
+            acc.y = fma(l.x, b.y, fma(-l.y, b.x, acc.y));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) {
+        if (upper) {
+            acc = make_double2(acc.x * d[row], acc.y * d[row]);
+            if (accumulate) acc = make_double2(out[row].x + acc.x, out[row].y + acc.y);
+        }
+        out[row] = acc;
+    }
+}
+
+cudaError_t launch_chol_invert(const double2 *L, const int *info, int K, double2 *Linv, cudaStream_t s)
+{
+    if (K > 32 * kInvRows) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double2) * (size_t)K * (K - 1) / 2;
+    static SmemAttr smem_rec;
+    const cudaError_t e = ensure_smem(smem_rec, (const void *)chol_invert_kernel, smem > 0 ? smem : 16);
+    if (e != cudaSuccess) return e;
+    chol_invert_kernel<<<K, kInvThreads, smem > 0 ? smem : 16, s>>>(L, info, K, Linv);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_inverse(const double2 *Linv, const double *d, const int *info, const double2 *rhs, int K,
+                                 double2 *tmp, double2 *h, int accumulate, cudaStream_t s)
+{
+    const int grid = (K + 3) / 4;
+    inv_matvec_kernel<<<grid, 128, 0, s>>>(Linv, d, info, rhs, K, 0, tmp, 0);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    inv_matvec_kernel<<<grid, 128, 0, s>>>(Linv, d, info, tmp, K, 1, h, accumulate);
     count_launch();
     return cudaGetLastError();
 }

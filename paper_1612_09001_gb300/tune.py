@@ -24,8 +24,14 @@ import torch
 
 CACHE = os.environ.get("DPD_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "dpd_tune.json"))
 
-FWD_CANDIDATES = [dict(mode=m, V=V, warps=w, stages=s, ctas_per_sm=c, use_tma=1)
-                  for m in (3, 2) for V in (8, 4) for w in (4, 8, 12) for s in (3, 4) for c in (0,)]
+# Forward shapes: one group of all warps (as many CTAs per SM as fit), and the
+# grouped rings (warps per group dividing the warp count) at 12 and 16 warps.
+FWD_CANDIDATES = ([dict(mode=m, V=V, warps=w, stages=s, ctas_per_sm=0, use_tma=1, group=0)
+                   for m in (3, 2) for V in (8, 4) for w in (4, 8, 12) for s in (3, 4)] +
+                  [dict(mode=m, V=V, warps=w, stages=s, ctas_per_sm=0, use_tma=1, group=g)
+                   for m in (3, 2) for V in (8, 4) for (w, g) in ((12, 1), (12, 2), (12, 3), (12, 4), (12, 6),
+                                                                 (16, 1), (16, 2), (16, 4), (16, 8))
+                   for s in (3, 4)])
 BATCH_CANDIDATES = [(V, w, s, c) for V in (8, 4) for w in (4, 8, 12) for s in (2, 3, 4) for c in (0,)]
 
 

@@ -64,7 +64,7 @@ def test_null_handle_calls(lib):
     assert lib.dpd_apply(None, None, None, 10, None) == 1
     assert lib.dpd_set_coeffs(None, None, 3, 0, None) == 1
     assert lib.dpd_sync_status(None, None) == 1
-    assert lib.dpd_set_fwd_launch(None, 0, 4, 8, 4, 0, 1) == 1
+    assert lib.dpd_set_fwd_launch(None, 0, 4, 8, 4, 0, 1, 0) == 1
 
 
 def test_num_coeffs_formula():

@@ -52,12 +52,15 @@ def test_table2_p5_q3_l5_ragged():
     assert_parity(run_gpu(x, h, 5, 3, 4), oracle.apply(x, h, 5, 3, 4), what="table 2")
 
 
-@pytest.mark.parametrize("launch", [None, dict(mode=3, V=8, warps=12, stages=3)], ids=["default", "tuned"])
+@pytest.mark.parametrize("launch", [None, dict(mode=3, V=8, warps=12, stages=3, group=0),
+                                    dict(mode=3, V=8, warps=12, stages=4, group=4),
+                                    dict(mode=3, V=8, warps=16, stages=3, group=2)],
+                         ids=["default", "one_group", "w12g4", "w16g2"])
 def test_config1_full_size_ofdm_p9_m4(launch):
     """Full 2^24-sample OFDM workload, coefficients from host memory as the
-    benchmark installs them, at the default shape and at the shape the
-    autotuner picks on GB300 (parameter-bank packed FMAs, V 8, 12 consumer
-    warps, 3 stages)."""
+    benchmark installs them, at the default shape (16 consumer warps in groups
+    of 4) and at other shapes the autotuner chooses from (parameter-bank packed
+    FMAs, V 8)."""
     n = 1 << 24
     x = synth.ofdm2(n, key=(0, 0))
     h = synth.coeffs(9, 9, 4, key=(0, 1))
@@ -92,10 +95,16 @@ LAUNCHES = [
     dict(V=4, warps=4, stages=3, ctas_per_sm=2, use_tma=1),
     dict(V=4, warps=8, stages=4, ctas_per_sm=0, use_tma=0),
     dict(V=2, warps=8, stages=4, ctas_per_sm=0, use_tma=0),
+    dict(V=8, warps=12, stages=4, ctas_per_sm=0, use_tma=1, group=4),
+    dict(V=8, warps=12, stages=3, ctas_per_sm=0, use_tma=1, group=1),
+    dict(V=4, warps=16, stages=3, ctas_per_sm=0, use_tma=1, group=4),
+    dict(V=2, warps=16, stages=8, ctas_per_sm=0, use_tma=1, group=2),
+    dict(V=8, warps=6, stages=2, ctas_per_sm=3, use_tma=1, group=3),
 ]
 
 
-@pytest.mark.parametrize("launch", LAUNCHES, ids=lambda d: "V{V}w{warps}s{stages}c{ctas_per_sm}t{use_tma}".format(**d))
+@pytest.mark.parametrize("launch", LAUNCHES,
+                         ids=lambda d: "V{V}w{warps}s{stages}c{ctas_per_sm}t{use_tma}g{g}".format(g=d.get("group", 0), **d))
 @pytest.mark.parametrize("n", [1, 2, 3, 7, 8, 9, 255, 256, 257, 1023, 1024, 1025, 2047, 4100, 70001])
 def test_sizes_and_launch_shapes(launch, n):
     P, Q, M = 9, 9, 4
@@ -116,6 +125,22 @@ def test_compute_modes(P, Q, M, mode, V, use_tma, host_coeffs):
         h = synth.coeffs(P, Q, M, key=(8, 1), f_std=0.3, g_std=0.3)
         launch = dict(mode=mode, V=V, warps=8, stages=4, ctas_per_sm=0, use_tma=use_tma)
         y = run_gpu(x, h, P, Q, M, launch=launch, host_coeffs=host_coeffs)
+        assert_parity(y, oracle.apply(x, h, P, Q, M), what=f"n={n} {launch}")
+
+
+@pytest.mark.parametrize("P,Q,M", [(9, 9, 4), (5, 5, 2), (7, 7, 3), (11, 11, 7)])
+@pytest.mark.parametrize("warps,group,stages", [(16, 4, 4), (12, 3, 3), (12, 2, 4), (16, 2, 3)])
+def test_grouped_shapes(P, Q, M, warps, group, stages):
+    """The grouped ring at the shapes the library builds with compile-time
+    tile arithmetic (16/4/4, 12/3/3, 12/2/4 for the benchmarked models) and a
+    runtime one (16/2/3), with parameter-bank coefficients (mode 3), on sizes
+    that end inside a group's sub-tile, on a group boundary and past one."""
+    h = synth.coeffs(P, Q, M, key=(9, 1), f_std=0.3, g_std=0.3)
+    S = warps * 32 * 8
+    for n in (1, 77, S // 2 + 3, S, S + 8 * 32 * group + 1, 5 * S - 1, (1 << 20) + 3):
+        x = synth.clipped_gaussian(n, 0.5, key=(9, n, P))
+        launch = dict(mode=3, V=8, warps=warps, stages=stages, ctas_per_sm=0, use_tma=1, group=group)
+        y = run_gpu(x, h, P, Q, M, launch=launch, host_coeffs=True)
         assert_parity(y, oracle.apply(x, h, P, Q, M), what=f"n={n} {launch}")
 
 
@@ -164,9 +189,12 @@ def test_host_side_errors_with_device():
     assert lib.dpd_apply(f.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), -1, s) == 1
     h = torch.zeros(18, dtype=torch.complex64)
     assert lib.dpd_set_coeffs(f.handle, ctypes.c_void_p(h.data_ptr()), 18, 0, s) == 1
-    assert lib.dpd_set_fwd_launch(f.handle, 0, 3, 8, 4, 0, 1) == 1
-    assert lib.dpd_set_fwd_launch(f.handle, 0, 4, 8, 9, 0, 1) == 1
-    assert lib.dpd_set_fwd_launch(f.handle, 4, 4, 8, 4, 0, 1) == 1
+    assert lib.dpd_set_fwd_launch(f.handle, 0, 3, 8, 4, 0, 1, 0) == 1
+    assert lib.dpd_set_fwd_launch(f.handle, 0, 4, 8, 9, 0, 1, 0) == 1
+    assert lib.dpd_set_fwd_launch(f.handle, 4, 4, 8, 4, 0, 1, 0) == 1
+    assert lib.dpd_set_fwd_launch(f.handle, 3, 8, 12, 4, 0, 1, 5) == 1    # group does not divide warps
+    assert lib.dpd_set_fwd_launch(f.handle, 3, 8, 17, 4, 0, 1, 0) == 1    # more than 16 warps
+    assert lib.dpd_set_fwd_launch(f.handle, 3, 8, 16, 8, 0, 1, 1) == 2    # rings larger than shared memory
     f.sync_status()
 
 
