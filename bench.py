@@ -60,7 +60,7 @@ def parse():
                     default=None,
                     help="run only this side measurement (1 GPU) and print its JSON; for profiling")
     ap.add_argument("--grad-log2n", type=int, default=24, help="samples (log2) of --pattern grad")
-    ap.add_argument("--batched-launch", default=None, metavar="V,WARPS,STAGES,CTAS_PER_SM",
+    ap.add_argument("--batched-launch", default=None, metavar="V,WARPS,STAGES,CTAS_PER_SM[,GROUP]",
                     help="fix the batched launch shape of --pattern batched instead of tuning it (profiling runs)")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
                     help="keep warming up for at least this long so clocks settle and get sampled")
@@ -659,7 +659,8 @@ def measure_batched(dev, reps=20, launch=None):
     return {"workload": "64 streams, n ~ U[2^12, 2^20], P=Q in {5,7,9}, M in {2..6}, clipped Gaussian RMS 0.3",
             "total_samples": total, "unit": "Gsamples/s",
             "persistent_graph": total / t_plan / 1e9, "persistent_launches_per_step": launches_plan,
-            "persistent_launch_shape": {"V": best[0], "warps": best[1], "stages": best[2], "ctas_per_sm": best[3]},
+            "persistent_launch_shape": {"V": best[0], "warps": best[1], "stages": best[2], "ctas_per_sm": best[3],
+                                        "group": best[4] if len(best) > 4 else 0},
             "plain_64_launches": total / t_plain / 1e9, "plain_64_in_one_graph": total / t_graph64 / 1e9,
             "persistent_us": t_plan * 1e6, "plain_64_us": t_plain * 1e6, "plain_64_graph_us": t_graph64 * 1e6,
             "hbm_gbs_persistent": 16 * total / t_plan / 1e9}

@@ -367,12 +367,15 @@ dpd_status dpd_exec_batched(dpd_plan plan, void *stream);
  * Launch shape of dpd_exec_batched (autotuner): V in {4, 8} samples per thread,
  * warps 1..16 consumer warps (tile = warps*32*V samples; changing the tile
  * rebuilds the work list, synchronously, in a new device buffer), stages 2..8,
- * ctas_per_sm >= 0 (0 = as many as fit).  Default 8, 8, 4, 0.  On any error the
- * plan keeps its previous shape and work list.  A CUDA graph captured from
- * dpd_exec_batched holds the shape and work list of its capture: capture again
- * after changing the shape.
+ * ctas_per_sm >= 0 (0 = as many as fit), group = warps per group dividing
+ * `warps` (every group has its own ring of slots and barriers and filters its
+ * own part of each work item) or 0 for one group.  Default 8, 8, 4, 0, 0.
+ * Rings larger than one CTA's shared memory give DPD_ERR_UNSUPPORTED.  On any
+ * error the plan keeps its previous shape and work list.  A CUDA graph
+ * captured from dpd_exec_batched holds the shape and work list of its
+ * capture: capture again after changing the shape.
  */
-dpd_status dpd_plan_set_launch(dpd_plan plan, int V, int warps, int stages, int ctas_per_sm);
+dpd_status dpd_plan_set_launch(dpd_plan plan, int V, int warps, int stages, int ctas_per_sm, int group);
 
 /* Synchronise `stream`, read and clear the plan's device error word (as dpd_sync_status). */
 dpd_status dpd_plan_sync_status(dpd_plan plan, void *stream);

@@ -323,8 +323,8 @@ class BatchedPlan:
     def execute(self, stream=None):
         _lib.check("dpd_exec_batched", self._lib.dpd_exec_batched(self._p, _stream_ptr(stream)))
 
-    def set_launch(self, V=8, warps=8, stages=4, ctas_per_sm=0):
-        _lib.check("dpd_plan_set_launch", self._lib.dpd_plan_set_launch(self._p, V, warps, stages, ctas_per_sm))
+    def set_launch(self, V=8, warps=8, stages=4, ctas_per_sm=0, group=0):
+        _lib.check("dpd_plan_set_launch", self._lib.dpd_plan_set_launch(self._p, V, warps, stages, ctas_per_sm, group))
 
     def sync_status(self, stream=None):
         _lib.check("dpd_plan_sync_status", self._lib.dpd_plan_sync_status(self._p, _stream_ptr(stream)))

@@ -66,7 +66,7 @@ SIGNATURES = {
     "dpd_estimate_batched": [_vp, _vp, _vp, _vp, _i, _i, _i, _vp, _pi, _vp],
     "dpd_plan_batched": [_vp, _i, _i, ctypes.POINTER(_vp)],
     "dpd_exec_batched": [_vp, _vp],
-    "dpd_plan_set_launch": [_vp, _i, _i, _i, _i],
+    "dpd_plan_set_launch": [_vp, _i, _i, _i, _i, _i],
     "dpd_plan_sync_status": [_vp, _vp],
     "dpd_plan_destroy": [_vp],
     "dpd_status_string": [_i],

@@ -29,7 +29,7 @@ struct dpd_plan_s {
     int nitems = 0;
     int64_t tab_floats = 0;
     int small = 1;            // every stream has B <= 5 and T <= 7
-    int V = 8, warps = 8, stages = 4, ctas_per_sm = 0;
+    int V = 8, warps = 8, stages = 4, ctas_per_sm = 0, group = 0;
 };
 
 namespace {
@@ -177,11 +177,13 @@ dpd_status dpd_plan_batched(const dpd_stream_desc *descs, int count, int where, 
     return DPD_OK;
 }
 
-dpd_status dpd_plan_set_launch(dpd_plan p, int V, int warps, int stages, int ctas_per_sm)
+dpd_status dpd_plan_set_launch(dpd_plan p, int V, int warps, int stages, int ctas_per_sm, int group)
 {
     if (!p) return DPD_ERR_INVALID_ARGUMENT;
-    if ((V != 4 && V != 8) || warps < 1 || warps > 16 || stages < 2 || stages > 8 || ctas_per_sm < 0)
+    if ((V != 4 && V != 8) || warps < 1 || warps > 16 || stages < 2 || stages > 8 || ctas_per_sm < 0 || group < 0 ||
+        (group > 0 && warps % group != 0))
         return DPD_ERR_INVALID_ARGUMENT;
+    if (dpd::batch_smem(warps, group > 0 ? group : warps, stages, V) > (size_t)227 * 1024) return DPD_ERR_UNSUPPORTED;
     if (V != p->V || warps != p->warps) {
         // Re-tile first: the new shape is kept only once its work list is on
         // the device; on failure the plan runs with its previous shape.
@@ -192,6 +194,7 @@ dpd_status dpd_plan_set_launch(dpd_plan p, int V, int warps, int stages, int cta
     p->warps = warps;
     p->stages = stages;
     p->ctas_per_sm = ctas_per_sm;
+    p->group = group;
     return DPD_OK;
 }
 
@@ -208,6 +211,7 @@ dpd_status dpd_exec_batched(dpd_plan p, void *stream)
     a.tabs = p->d_tabs;
     a.tab_floats = p->tab_floats;
     a.status = p->d_status;
+    a.gw = p->group;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = p->small ? dpd::launch_batched_57(a, p->V, p->warps, p->stages, p->ctas_per_sm, p->sm_count, s)
                              : dpd::launch_batched_68(a, p->V, p->warps, p->stages, p->ctas_per_sm, p->sm_count, s);

@@ -41,6 +41,7 @@ struct BatchArgs {
     const float *tabs;
     int64_t tab_floats;   // size of the table pool
     int *status;
+    int gw = 0;           // consumer warps per group (0: one group of all warps)
 };
 
 constexpr int kBatchTabBytes = ((kMaxTabFloats * 4 + 15) / 16) * 16;   // table area of a slot
@@ -96,7 +97,7 @@ __device__ __forceinline__ void batched_item(const unsigned char *slot, const Ba
 #define DPD_BCASE(b, t)                                                                            \
     case (b) * 16 + (t):                                                                           \
         if constexpr ((b) <= BMAX && (t) <= TMAX) {                                                \
-            batched_item<(b), (t), V>(slot, hd, S, t_in_tile);                                     \
+            batched_item<(b), (t), V>(slot, hd, SG, t_in_tile);                                    \
             break;                                                                                 \
         }                                                                                          \
         bad = true;                                                                                \
@@ -109,90 +110,106 @@ template <int BMAX, int TMAX, int V>
 __global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int stages)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);   // full[s], empty[s]
-    unsigned char *ring = smem + 128;
     const int nwarps = blockDim.x / 32 - 1;
-    const int S = nwarps * 32 * V;
-    const size_t slot_bytes = batch_slot_bytes(S);
+    const int gw = (a.gw > 0 && nwarps % a.gw == 0) ? a.gw : nwarps;   // warps per group
+    const int ngroups = nwarps / gw;
+    // per group g: full[s] at bars[2 stages g + s], empty[s] at bars[2 stages g + stages + s]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    unsigned char *ring = smem + ((2 * ngroups * stages * 8 + 127) / 128) * 128;
+    const int S = nwarps * 32 * V;    // the item's tile
+    const int SG = gw * 32 * V;       // a group's part of it
+    const size_t slot_bytes = batch_slot_bytes(SG);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int s = 0; s < stages; ++s) {
-            mbar_init(smem_addr(&bars[s]), 1);
-            mbar_init(smem_addr(&bars[stages + s]), nwarps);
-        }
+        for (int g = 0; g < ngroups; ++g)
+            for (int s = 0; s < stages; ++s) {
+                mbar_init(smem_addr(&bars[2 * stages * g + s]), 1);
+                mbar_init(smem_addr(&bars[2 * stages * g + stages + s]), gw);
+            }
         fence_barrier_init();
     }
     __syncthreads();
 
     if (warp == nwarps) {
         // ---------------------------------------------------------------- producer
+        // Every group's slot receives the item's header and table and the
+        // group's sub-tile (with its history), so each group runs on its own
+        // ring, independently of the CTA's other groups.
         if (lane != 0) return;
         const uint64_t pol = policy_evict_first();
-        int it = 0;
-        bool ok = true;
-        for (int i = blockIdx.x; i < a.nitems; i += gridDim.x, ++it) {
-            const int s = it % stages;
-            const uint32_t ph = (uint32_t)((it / stages) & 1);
-            if (it >= stages && !mbar_wait(smem_addr(&bars[stages + s]), ph ^ 1u, a.status)) {
-                ok = false;
-                break;
-            }
-            // Start-up: the second item is requested once the first has landed
-            // (every CTA's first tile then arrives without queueing behind the
-            // grid's later ones).
-            if (it == 1 && !mbar_wait(smem_addr(&bars[0]), 0u, a.status)) {
-                ok = false;
-                break;
-            }
+        int it = 0, gfail = -1, fail_it = 0;
+        int s = 0;          // slot of item `it`, kept incrementally
+        uint32_t ph = 0;
+        for (int i = blockIdx.x; i < a.nitems && gfail < 0; i += gridDim.x, ++it) {
             const BatchItem w = a.items[i];
             const BatchStream st = a.streams[(w.stream >= 0 && w.stream < a.nstreams) ? w.stream : 0];
-            const uint32_t fb = smem_addr(&bars[s]);
-            unsigned char *slot = ring + (size_t)s * slot_bytes;
-            BatchSlotHeader *hd = reinterpret_cast<BatchSlotHeader *>(slot);
             const bool good = item_ok(a, w, st, S);
-            hd->x = st.x;
-            hd->y = st.y;
-            hd->n = st.n;
-            hd->s0 = (int64_t)w.tile * S;
-            hd->bt = st.B * 16 + st.T;
-            hd->ok = good ? 1 : 0;
-            if (!good) {
-                atomicOr(a.status, kFlagBadWork);
-                mbar_arrive_expect_tx(fb, 0);   // complete the phase with no copies (releases the header)
-                continue;
+            if (!good) atomicOr(a.status, kFlagBadWork);
+            for (int g = 0; g < ngroups; ++g) {
+                uint64_t *gb = bars + 2 * stages * g;
+                if (it >= stages && !mbar_wait(smem_addr(&gb[stages + s]), ph ^ 1u, a.status)) {
+                    gfail = g;
+                    fail_it = it;
+                    break;
+                }
+                const uint32_t fb = smem_addr(&gb[s]);
+                unsigned char *slot = ring + ((size_t)g * stages + s) * slot_bytes;
+                BatchSlotHeader *hd = reinterpret_cast<BatchSlotHeader *>(slot);
+                const int64_t s0 = (int64_t)w.tile * S + (int64_t)g * SG;
+                hd->x = st.x;
+                hd->y = st.y;
+                hd->n = st.n;
+                hd->s0 = s0;
+                hd->bt = st.B * 16 + st.T;
+                hd->ok = good ? 1 : 0;
+                if (!good) {
+                    mbar_arrive_expect_tx(fb, 0);   // complete the phase with no copies (releases the header)
+                    continue;
+                }
+                int64_t lo = 0, cnt = 0;
+                int off = 0;
+                if (s0 < st.n) tile_copy_range(s0, SG, st.n, lo, cnt, off);
+                if (cnt < 0) cnt = 0;
+                const uint32_t xbytes = (uint32_t)(cnt * (int64_t)sizeof(float2));
+                // The arrive releases the header stores; the consumers' wait acquires them.
+                mbar_arrive_expect_tx(fb, xbytes + (uint32_t)st.tab_bytes);
+                bulk_copy_g2s(smem_addr(slot + kBatchHdrBytes), a.tabs + st.tab_off, (uint32_t)st.tab_bytes, fb);
+                if (xbytes)
+                    bulk_copy_g2s_stream(
+                        smem_addr(slot + kBatchHdrBytes + kBatchTabBytes + (size_t)off * sizeof(float2)), st.x + lo,
+                        xbytes, fb, pol);
             }
-            int64_t lo, cnt;
-            int off;
-            tile_copy_range((int64_t)w.tile * S, S, st.n, lo, cnt, off);
-            const uint32_t xbytes = (uint32_t)(cnt * (int64_t)sizeof(float2));
-            // The arrive releases the header stores; the consumers' wait acquires them.
-            mbar_arrive_expect_tx(fb, xbytes + (uint32_t)st.tab_bytes);
-            bulk_copy_g2s(smem_addr(slot + kBatchHdrBytes), a.tabs + st.tab_off, (uint32_t)st.tab_bytes, fb);
-            if (xbytes)
-                bulk_copy_g2s_stream(
-                    smem_addr(slot + kBatchHdrBytes + kBatchTabBytes + (size_t)off * sizeof(float2)), st.x + lo,
-                    xbytes, fb, pol);
+            if (gfail < 0 && ++s == stages) {
+                s = 0;
+                ph ^= 1u;
+            }
         }
-        if (!ok) {
-            const int first = it > stages ? it - stages : 0;
-            for (int j = first; j < it; ++j)
-                mbar_wait(smem_addr(&bars[j % stages]), (uint32_t)((j / stages) & 1), a.status);
+        if (gfail >= 0) {
+            // Let the copies already issued land before the CTA exits: group g
+            // has items [0, fail_it] issued if g < gfail, else [0, fail_it - 1].
+            for (int g = 0; g < ngroups; ++g) {
+                const int last = g < gfail ? fail_it : fail_it - 1;
+                const int first = last - stages + 1 > 0 ? last - stages + 1 : 0;
+                for (int j = first; j <= last; ++j)
+                    mbar_wait(smem_addr(&bars[2 * stages * g + j % stages]), (uint32_t)((j / stages) & 1), a.status);
+            }
         }
         return;
     }
 
     // -------------------------------------------------------------------- consumers
-    const int t_in_tile = warp * 32 + lane;
-    int it = 0;
-    for (int i = blockIdx.x; i < a.nitems; i += gridDim.x, ++it) {
-        const int s = it % stages;
-        const uint32_t ph = (uint32_t)((it / stages) & 1);
-        if (!mbar_wait(smem_addr(&bars[s]), ph, a.status)) return;
-        const unsigned char *slot = ring + (size_t)s * slot_bytes;
+    const int g = warp / gw;
+    const int t_in_tile = (warp - g * gw) * 32 + lane;   // position in the group's sub-tile
+    uint64_t *gb = bars + 2 * stages * g;
+    int s = 0;
+    uint32_t ph = 0;
+    for (int i = blockIdx.x; i < a.nitems; i += gridDim.x) {
+        if (!mbar_wait(smem_addr(&gb[s]), ph, a.status)) return;
+        const unsigned char *slot = ring + ((size_t)g * stages + s) * slot_bytes;
         const BatchSlotHeader &hd = *reinterpret_cast<const BatchSlotHeader *>(slot);   // read in place
         bool bad = hd.ok == 0;
-        if (!bad) switch (hd.bt) {
+        if (!bad && hd.s0 < hd.n) switch (hd.bt) {   // a group past the stream's end has nothing to do
             DPD_BCASES(1)
             DPD_BCASES(2)
             DPD_BCASES(3)
@@ -203,20 +220,32 @@ __global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int s
         }
         if (bad && hd.ok != 0 && lane == 0) atomicOr(a.status, kFlagBadWork);   // model outside this kernel
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));   // slot (header, table, tile) no longer read
+        if (lane == 0) mbar_arrive(smem_addr(&gb[stages + s]));   // slot (header, table, tile) no longer read
+        if (++s == stages) {
+            s = 0;
+            ph ^= 1u;
+        }
     }
 }
 
 #undef DPD_BCASES
 #undef DPD_BCASE
 
+// Shared-memory bytes of the batched kernel: barrier pairs of every group and
+// stage, then per group `stages` slots of its sub-tile.
+__host__ __device__ constexpr size_t batch_smem(int warps, int gw, int stages, int V)
+{
+    return (size_t)((2 * (warps / gw) * stages * 8 + 127) / 128) * 128 +
+           (size_t)(warps / gw) * stages * batch_slot_bytes(gw * 32 * V);
+}
+
 template <int BMAX, int TMAX, int V>
 cudaError_t launch_batched_impl(const BatchArgs &a, int warps, int stages, int ctas_per_sm, int sm_count,
                                 cudaStream_t s)
 {
     const int threads = (warps + 1) * 32;
-    const int S = warps * 32 * V;
-    const size_t smem = 128 + (size_t)stages * batch_slot_bytes(S);
+    const int gw = (a.gw > 0 && warps % a.gw == 0) ? a.gw : warps;
+    const size_t smem = batch_smem(warps, gw, stages, V);
     auto kern = fwd_batched_kernel<BMAX, TMAX, V>;
     static SmemAttr smem_rec;
     cudaError_t e = ensure_smem(smem_rec, (const void *)kern, smem);

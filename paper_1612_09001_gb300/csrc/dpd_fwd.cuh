@@ -340,7 +340,12 @@ __global__ void __launch_bounds__(fwd_lb_threads<SH>(), fwd_lb_blocks<SH>())
     const float2 *ring_g = ring + (size_t)g * stages * slot_elems;
     int s = 0;        // slot and parity of the current tile, kept incrementally
     uint32_t ph = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int64_t it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        if constexpr (FIXED) {   // constant ring depth: a cheap modulo
+            s = (int)(it % kFwdShapes[SH].stages);
+            ph = (uint32_t)((it / kFwdShapes[SH].stages) & 1);
+        }
         if (!mbar_wait(smem_addr(&gb[s]), ph, a.status)) return;
         const float2 *slot = ring_g + (size_t)s * slot_elems;
         const int64_t s0 = tile * S + (int64_t)g * SG;
@@ -348,7 +353,7 @@ __global__ void __launch_bounds__(fwd_lb_threads<SH>(), fwd_lb_blocks<SH>())
         const bool full = load_window<T, V>(slot, s0, SG, a.n, a.x, t_in_tile, wr, wi);
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&gb[stages + s]));
-        if (++s == stages) {
+        if (!FIXED && ++s == stages) {
             s = 0;
             ph ^= 1u;
         }

@@ -116,8 +116,10 @@ cudaError_t launch_solve_inverse(const double2 *Linv, const double *d, const int
 cudaError_t launch_h_to_f32(const double2 *h, int n, float2 *out, cudaStream_t s);
 // e = t - y (n samples).
 cudaError_t launch_residual(const float2 *t, const float2 *y, int64_t n, float2 *e, cudaStream_t s);
-// out[0] = sum |e|^2, out[1] = sum |t|^2 in FP64 (part: 2 * 1024 doubles of scratch).
-cudaError_t launch_sqnorm2(const float2 *e, const float2 *t, int64_t n, double *part, double *out, cudaStream_t s);
+// e = t - y together with out[0] = sum |e|^2, out[1] = sum |t|^2 in FP64
+// (part: 2 * 1024 doubles of scratch).
+cudaError_t launch_residual_norm(const float2 *t, const float2 *y, int64_t n, float2 *e, double *part, double *out,
+                                 cudaStream_t s);
 // Like launch_adj_finalize, summed to FP64.
 cudaError_t launch_adj_finalize64(const float2 *partials, int rows, int K, double2 *out, cudaStream_t s);
 

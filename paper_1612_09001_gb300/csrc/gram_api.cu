@@ -184,8 +184,10 @@ dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_
     return DPD_OK;
 }
 
-// e = t - Psi(u) h for the current FP64 coefficients of problem p (FP32 filter).
-dpd_status residual_of(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, cudaStream_t s)
+// e = t - Psi(u) h for the current FP64 coefficients of problem p (FP32 filter);
+// with `norms`, also ||e||^2 and ||t||^2 into w.norm_part + 2048.
+dpd_status residual_of(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, cudaStream_t s,
+                       bool norms = false)
 {
     EstimateWorkspace &w = h->est;
     dpd_status st = DPD_OK;
@@ -208,6 +210,10 @@ dpd_status residual_of(dpd_handle h, int p, const float2 *u, const float2 *t, in
         L.V = 4;
     }
     if (dpd::launch_fwd_any(h->B, h->T, fa, L, h->sm_count, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (norms)
+        return dpd::launch_residual_norm(t, w.y, n, w.e, w.norm_part, w.norm_part + 2 * 1024, s) == cudaSuccess
+                   ? DPD_OK
+                   : DPD_ERR_CUDA;
     if (dpd::launch_residual(t, w.y, n, w.e, s) != cudaSuccess) return DPD_ERR_CUDA;
     return DPD_OK;
 }
@@ -404,9 +410,8 @@ double cond_estimate(const double2 *L, int K)
 dpd_status queue_norms(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, cudaStream_t s)
 {
     EstimateWorkspace &w = h->est;
-    dpd_status st = residual_of(h, p, u, t, n, s);
+    dpd_status st = residual_of(h, p, u, t, n, s, true);
     if (st != DPD_OK) return st;
-    if (dpd::launch_sqnorm2(w.e, t, n, w.norm_part, w.norm_part + 2 * 1024, s) != cudaSuccess) return DPD_ERR_CUDA;
     if (cudaMemcpyAsync(w.h_norm, w.norm_part + 2 * 1024, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) !=
         cudaSuccess)
         return DPD_ERR_CUDA;

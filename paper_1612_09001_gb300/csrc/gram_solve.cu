@@ -761,22 +761,49 @@ cudaError_t launch_residual(const float2 *t, const float2 *y, int64_t n, float2 
 
 constexpr int kNormBlocks = 1024;
 
-// Per-block sums of |e|^2 and |t|^2, then one fixed-order final sum.  The
-// squares of the FP32 samples are formed and summed in FP32 over runs of 32
-// samples per thread, and the runs are added in FP64 (FP64 arithmetic on this
-// GPU is a small fraction of the FP32 rate); a run's FP32 sum carries at most
-// about 2e-6 relative error, well below what the reported ratio needs.
-__global__ void sqnorm2_kernel(const float2 *__restrict__ e, const float2 *__restrict__ t, int64_t n,
-                               double *__restrict__ part)
+__global__ void sum_pairs_kernel(const double *__restrict__ part, int nb, double *__restrict__ out)
+{
+    __shared__ double sa[256], sb[256];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sa[threadIdx.x] += sa[threadIdx.x + o];
+            sb[threadIdx.x] += sb[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sa[0];
+        out[1] = sb[0];
+    }
+}
+
+// Residual and both sums of squares in one pass: e = t - y, and per block
+// sum |e|^2 and sum |t|^2, then one fixed-order final sum (sum_pairs_kernel).
+// The squares of the FP32 samples are formed and summed in FP32 over runs of
+// 32 samples per thread, and the runs are added in FP64 (FP64 arithmetic on
+// this GPU is a small fraction of the FP32 rate); a run's FP32 sum carries at
+// most about 2e-6 relative error, well below what the reported ratio needs.
+__global__ void residual_norm_kernel(const float2 *__restrict__ t, const float2 *__restrict__ y, int64_t n,
+                                     float2 *__restrict__ e, double *__restrict__ part)
 {
     __shared__ double se[256], st[256];
     double a = 0.0, b = 0.0;
     float a32 = 0.f, b32 = 0.f;
     int run = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 x = e[i], y = t[i];
-        a32 = fmaf(x.x, x.x, fmaf(x.y, x.y, a32));
-        b32 = fmaf(y.x, y.x, fmaf(y.y, y.y, b32));
+        const float2 tv = t[i], yv = y[i];
+        const float2 ev = make_float2(tv.x - yv.x, tv.y - yv.y);
+        e[i] = ev;
+        a32 = fmaf(ev.x, ev.x, fmaf(ev.y, ev.y, a32));
+        b32 = fmaf(tv.x, tv.x, fmaf(tv.y, tv.y, b32));
         if (++run == 32) {
             a += (double)a32;
             b += (double)b32;
@@ -802,39 +829,15 @@ __global__ void sqnorm2_kernel(const float2 *__restrict__ e, const float2 *__res
     }
 }
 
-// Fixed-order sum of the nb per-block pairs: thread t adds pairs t, t + 256,
-// ..., then a shared-memory tree (one block of 256 threads).
-__global__ void sum_pairs_kernel(const double *__restrict__ part, int nb, double *__restrict__ out)
+cudaError_t launch_residual_norm(const float2 *t, const float2 *y, int64_t n, float2 *e, double *part, double *out,
+                                 cudaStream_t s)
 {
-    __shared__ double sa[256], sb[256];
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        a += part[2 * i];
-        b += part[2 * i + 1];
-    }
-    sa[threadIdx.x] = a;
-    sb[threadIdx.x] = b;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            sa[threadIdx.x] += sa[threadIdx.x + o];
-            sb[threadIdx.x] += sb[threadIdx.x + o];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        out[0] = sa[0];
-        out[1] = sb[0];
-    }
-}
-
-cudaError_t launch_sqnorm2(const float2 *e, const float2 *t, int64_t n, double *part, double *out, cudaStream_t s)
-{
-    sqnorm2_kernel<<<kNormBlocks, 256, 0, s>>>(e, t, n, part);
+    residual_norm_kernel<<<kNormBlocks, 256, 0, s>>>(t, y, n, e, part);
     count_launch();
     sum_pairs_kernel<<<1, 256, 0, s>>>(part, kNormBlocks, out);
     count_launch();
     return cudaGetLastError();
 }
+
 
 }  // namespace dpd

@@ -14,6 +14,11 @@ int main() {
     dpd_plan p = nullptr;
     int rc = dpd_plan_batched(d.data(), count, DPD_HOST, &p);
     printf("count %d rc %d\n", count, rc);
-    if (p) { rc = dpd_plan_set_launch(p, 4, 8, 4, 0); printf(" set_launch %d\n", rc); rc = dpd_exec_batched(p, nullptr); printf(" exec %d\n", rc); dpd_plan_destroy(p); }
+    if (p) {
+      rc = dpd_plan_set_launch(p, 4, 8, 4, 0, 0); printf(" set_launch %d\n", rc); rc = dpd_exec_batched(p, nullptr); printf(" exec %d\n", rc);
+      rc = dpd_plan_set_launch(p, 8, 12, 3, 0, 4); printf(" set_launch grouped %d\n", rc); rc = dpd_exec_batched(p, nullptr); printf(" exec %d\n", rc);
+      rc = dpd_plan_set_launch(p, 8, 12, 3, 0, 5); printf(" set_launch bad group %d\n", rc);
+      dpd_plan_destroy(p);
+    }
   }
 }
