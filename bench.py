@@ -775,9 +775,14 @@ def measure_gram(dev, reps=5):
         t_gram = e0.elapsed_time(e1) * 1e-3 / reps
         est = {}
         for basis in ("monomial", "orthogonal"):
-            t0 = time.perf_counter()
-            h, st = f.estimate(ud, td, precision=prec, refine_iters=3, basis=basis)
-            t_est = time.perf_counter() - t0
+            f.estimate(ud, td, precision=prec, refine_iters=3, basis=basis)
+            walls = []
+            for _ in range(reps):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                h, st = f.estimate(ud, td, precision=prec, refine_iters=3, basis=basis)
+                walls.append(time.perf_counter() - t0)
+            t_est = statistics.median(walls)
             h0, _ = f.estimate(ud, td, precision=prec, refine_iters=0, basis=basis)
             est[basis] = {"estimate_ms_3_refinements": t_est * 1e3,
                           "coef_rel_error_vs_true": float(np.linalg.norm(h.cpu().numpy() - theta) / np.linalg.norm(theta)),
@@ -802,17 +807,31 @@ def measure_gram(dev, reps=5):
         ts.append(g.apply(ubd))
         thetas.append(thb)
     useful_b = 8.0 * nb * nr * K * K
+    batch_refine = 2
+    out["batch_timing"] = (f"one estimate_batched call over all {nb} problems ((basis,) Gram, FP64 Cholesky, solve, "
+                           f"{batch_refine} refinements, info copied to the host): median of {reps} calls after 2 "
+                           f"warm-up calls; CUDA events around the call and wall time")
     for prec in ("tf32x3", "bf16x3"):
         out["batch"][prec] = {}
         for basis in ("monomial", "orthogonal"):
             f.set_estimate_basis(basis)
-            f.estimate_batched(us, ts, precision=prec, refine_iters=0)
+            for _ in range(2):
+                f.estimate_batched(us, ts, precision=prec, refine_iters=batch_refine)
             torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            f.estimate_batched(us, ts, precision=prec, refine_iters=0)   # (basis,) Gram, FP64 Cholesky, solve
-            t_b = time.perf_counter() - t0
-            r = {"problems": nb, "rows_each": nr, "gram_and_solve_ms": t_b * 1e3,
-                 "tflops_useful": useful_b / t_b / 1e12}
+            walls, devs = [], []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                t0 = time.perf_counter()
+                e0.record()
+                f.estimate_batched(us, ts, precision=prec, refine_iters=batch_refine)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                walls.append(time.perf_counter() - t0)
+                devs.append(e0.elapsed_time(e1) * 1e-3)
+            t_b = statistics.median(devs)
+            r = {"problems": nb, "rows_each": nr, "refine_iters": batch_refine, "events_ms": t_b * 1e3,
+                 "wall_ms": statistics.median(walls) * 1e3, "tflops_useful": useful_b / t_b / 1e12}
             for it in (0, 2):
                 hb, info = f.estimate_batched(us, ts, precision=prec, refine_iters=it)
                 hb = hb.cpu().numpy()

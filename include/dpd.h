@@ -226,7 +226,8 @@ dpd_status dpd_sq_error(dpd_handle h, const void *y, const void *x, int64_t n, f
  *   mode        bit 0: coefficients passed by value as kernel parameters (used
  *               only after dpd_set_coeffs from host memory; otherwise ignored);
  *               bit 1: packed two-wide FP32 fused multiply-adds
- *   V           samples per thread, 2, 4 or 8
+ *   V           samples per thread, 2, 4, 6 or 8 (with 6 the 16-byte window
+ *               loads of a warp are free of shared-memory bank conflicts)
  *   warps       consumer warps per CTA, 1..16 (tile = warps*32*V samples)
  *   stages      depth of each group's shared-memory bulk-copy ring, 2..8
  *   ctas_per_sm CTAs per SM of the persistent grid, 0 = as many as fit
@@ -236,8 +237,8 @@ dpd_status dpd_sq_error(dpd_handle h, const void *y, const void *x, int64_t n, f
  *               its own sub-tile (group*32*V samples), independently of the
  *               CTA's other groups
  * Default: mode 3, V 8, 16 warps in groups of 4, 4 stages, as many CTAs as
- * fit, TMA.  Every (P, Q, M) has modes 2 and 3 at V 4 and 8 and mode 0 at V 4;
- * other combinations exist only for the benchmarked orders.  Rings that do
+ * fit, TMA.  Every (P, Q, M) has modes 2 and 3 at V 4, 6 and 8 and mode 0 at
+ * V 4; other combinations exist only for the benchmarked orders.  Rings that do
  * not fit one CTA's shared memory give DPD_ERR_UNSUPPORTED; a shape that does
  * not fit the device otherwise, or one not built for the handle's (P, Q, M),
  * makes dpd_apply return DPD_ERR_CUDA.
@@ -364,7 +365,7 @@ dpd_status dpd_plan_batched(const dpd_stream_desc *descs, int count, int where, 
 dpd_status dpd_exec_batched(dpd_plan plan, void *stream);
 
 /*
- * Launch shape of dpd_exec_batched (autotuner): V in {4, 8} samples per thread,
+ * Launch shape of dpd_exec_batched (autotuner): V in {4, 6, 8} samples per thread,
  * warps 1..16 consumer warps (tile = warps*32*V samples; changing the tile
  * rebuilds the work list, synchronously, in a new device buffer), stages 2..8,
  * ctas_per_sm >= 0 (0 = as many as fit), group = warps per group dividing

@@ -180,7 +180,7 @@ dpd_status dpd_plan_batched(const dpd_stream_desc *descs, int count, int where, 
 dpd_status dpd_plan_set_launch(dpd_plan p, int V, int warps, int stages, int ctas_per_sm, int group)
 {
     if (!p) return DPD_ERR_INVALID_ARGUMENT;
-    if ((V != 4 && V != 8) || warps < 1 || warps > 16 || stages < 2 || stages > 8 || ctas_per_sm < 0 || group < 0 ||
+    if ((V != 4 && V != 6 && V != 8) || warps < 1 || warps > 16 || stages < 2 || stages > 8 || ctas_per_sm < 0 || group < 0 ||
         (group > 0 && warps % group != 0))
         return DPD_ERR_INVALID_ARGUMENT;
     if (dpd::batch_smem(warps, group > 0 ? group : warps, stages, V) > (size_t)227 * 1024) return DPD_ERR_UNSUPPORTED;

@@ -42,9 +42,10 @@ namespace dpd {
 constexpr int kAdjV = 4;          // samples per thread (plain-load kernels, staged gx)
 constexpr int kAdjGhV = 4;        // samples per thread of the staged gh kernel
 constexpr int kAdjWarps = 8;      // consumer warps of the staged gx kernel
-constexpr int kAdjGhWarps = 10;   // consumer warps of the staged gh kernel
+constexpr int kAdjGhWarps = 12;   // warps of the staged gh kernel (warp 0 also issues the copies)
 constexpr int kAdjStages = 4;     // ring slots of the staged gx kernel
 constexpr int kAdjGhStages = 4;   // ring slots of the staged gh kernel
+constexpr int kAdjGhSub = 2;      // sub-blocks of V samples per thread and staged gh tile
 
 // NS consecutive complex samples p[base .. base+NS-1] (zero past n).  When the
 // buffer is 16-byte aligned, base is even and the rounded-up window lies inside
@@ -88,15 +89,24 @@ __device__ __forceinline__ void adj_slot_window(const float2 *slot, int off, flo
 }
 
 // ---------------------------------------------------------------- staged tiles
-// A slot holds x[s0, s0 + S) and, from element S on, gy[s0, s0 + S + kHalo);
+// A slot holds x[s0, s0 + S) and, from element S on, gy[s0, s0 + S + halo);
 // near the end of the signal only the even-length prefix that exists is copied.
-__host__ __device__ constexpr int adj_slot_elems(int S) { return 2 * S + kHalo; }
+// The look-ahead `halo` (even) covers the furthest gy sample a consumer reads
+// for tile s0: kHalo for gx (T - 1 taps past its last sample, plus one for the
+// float4 rounding of the window), kAdjGhHalo for the tap-grouped gh kernels.
+__host__ __device__ constexpr int adj_slot_elems(int S, int halo = kHalo) { return 2 * S + halo; }
 
-__device__ __forceinline__ void adj_slot_counts(int64_t s0, int S, int64_t n, int &xc, int &gc)
+// The gh kernels read the window of taps k0 .. k0 + TG - 1 with k0 <= T - 1, so
+// their look-ahead reaches T + TG - 2 samples (+1 for the float4 rounding).
+constexpr int kAdjGhMaxTG = 5;
+constexpr int kAdjGhHalo = kMaxT + kAdjGhMaxTG - 1;
+static_assert(kAdjGhHalo % 2 == 0 && kHalo % 2 == 0, "slot parts must stay 16-byte aligned");
+
+__device__ __forceinline__ void adj_slot_counts(int64_t s0, int S, int64_t n, int &xc, int &gc, int halo = kHalo)
 {
     const int64_t rem = n - s0;
     xc = (int)((rem < S ? rem : (int64_t)S) & ~int64_t(1));
-    gc = (int)((rem < S + kHalo ? rem : (int64_t)(S + kHalo)) & ~int64_t(1));
+    gc = (int)((rem < S + halo ? rem : (int64_t)(S + halo)) & ~int64_t(1));
 }
 
 // NS samples of `src` from global index `g` whose slot copy starts at element
@@ -122,14 +132,18 @@ __device__ __forceinline__ void adj_slot_window_tail(const float2 *slot_part, in
 // bounded; after a failed wait the copies already issued are allowed to land
 // before returning.
 __device__ __forceinline__ void adj_produce(const AdjArgs &a, float2 *ring, uint64_t *bars, int stages, int S,
-                                            int64_t ntiles)
+                                            int64_t ntiles, int halo = kHalo)
 {
-    const int slot_elems = adj_slot_elems(S);
+    const int slot_elems = adj_slot_elems(S, halo);
     int64_t it = 0;
     bool ok = true;
+    int s = 0;          // slot and parity of tile `it`, kept incrementally (no division per tile)
+    uint32_t ph = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int s = (int)(it % stages);
-        const uint32_t ph = (uint32_t)((it / stages) & 1);
+        if (it > 0 && ++s == stages) {
+            s = 0;
+            ph ^= 1u;
+        }
         if (it >= stages && !mbar_wait(smem_addr(&bars[stages + s]), ph ^ 1u, a.status)) {
             ok = false;
             break;
@@ -140,7 +154,7 @@ __device__ __forceinline__ void adj_produce(const AdjArgs &a, float2 *ring, uint
         }
         const int64_t s0 = tile * S;
         int xc, gc;
-        adj_slot_counts(s0, S, a.n, xc, gc);
+        adj_slot_counts(s0, S, a.n, xc, gc, halo);
         const uint32_t fb = smem_addr(&bars[s]);
         mbar_arrive_expect_tx(fb, (uint32_t)(xc + gc) * (uint32_t)sizeof(float2));
         float2 *slot = ring + (size_t)s * slot_elems;
@@ -155,10 +169,10 @@ __device__ __forceinline__ void adj_produce(const AdjArgs &a, float2 *ring, uint
 }
 
 // Shared-memory bytes of a staged kernel: barriers, reduction scratch, ring.
-__host__ __device__ constexpr size_t adj_staged_smem(int S, int stages, int scratch_floats)
+__host__ __device__ constexpr size_t adj_staged_smem(int S, int stages, int scratch_floats, int halo = kHalo)
 {
     return 128 + (((size_t)scratch_floats * 4 + 127) / 128) * 128 +
-           (size_t)stages * (size_t)adj_slot_elems(S) * sizeof(float2);
+           (size_t)stages * (size_t)adj_slot_elems(S, halo) * sizeof(float2);
 }
 
 // ---------------------------------------------------------------- input gradient
@@ -352,10 +366,10 @@ __global__ void __launch_bounds__(32 * (kAdjWarps + 1))
     }
     const bool vec_out = (reinterpret_cast<uintptr_t>(a.gx) & 15) == 0;
     const int slot_elems = adj_slot_elems(S);
-    int64_t it = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int s = (int)(it % stages);
-        if (!mbar_wait(smem_addr(&bars[s]), (uint32_t)((it / stages) & 1), a.status)) return;
+    int s = 0;          // slot and parity of the current tile, kept incrementally
+    uint32_t ph = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (!mbar_wait(smem_addr(&bars[s]), ph, a.status)) return;
         const float2 *slot = ring + (size_t)s * slot_elems;
         const int64_t s0 = tile * S;
         const int off = tid * V;
@@ -372,6 +386,10 @@ __global__ void __launch_bounds__(32 * (kAdjWarps + 1))
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));
+        if (++s == stages) {
+            s = 0;
+            ph ^= 1u;
+        }
         float2 acc[V];
         gx_compute<B, T, V, PARAM>(tab, ptab, xs, g, acc);
         gx_store<V>(a.gx, s0 + off, a.n, vec_out, acc, true);
@@ -503,25 +521,46 @@ __global__ void __launch_bounds__(256) adj_gh_kernel(AdjArgs a, int T, int Bp, i
                                 a.partials + (size_t)blockIdx.x * K);
 }
 
-// Staged variant: grid (blocks, tap groups) of persistent CTAs (kAdjGhWarps
-// consumer warps + 1 producer warp); every CTA streams all tiles of its
-// blockIdx.x share.  x and gy 16-byte aligned.
+// Staged variant: grid (blocks, tap groups) of persistent CTAs of kAdjGhWarps
+// warps, every CTA streaming the tiles of its blockIdx.x share.  x and gy
+// 16-byte aligned.  With 2 B TG + 1 packed accumulators a thread takes about
+// 170 registers, so one CTA fits an SM; the bulk copies are issued by lane 0
+// of warp 0 between its own tiles instead of by a separate producer warp, so
+// that all twelve warps (three per SM sub-partition) accumulate.  Warp 0
+// refills the slot of tile i - 1 at the end of its tile i (once every warp
+// has released tile i - 1), with tile i - 1 + stages.
 template <int B, int TG, int V>
-__global__ void __launch_bounds__(32 * (kAdjGhWarps + 1), 1)
+__global__ void __launch_bounds__(32 * kAdjGhWarps, 1)
     adj_gh_tma_kernel(AdjArgs a, int stages, int64_t ntiles, int T, int Bp, int Bq, int K)
 {
     constexpr int NA = 4 * B * TG + 2;
     constexpr int NP = NA / 2;
-    constexpr int S = kAdjGhWarps * 32 * V;
+    constexpr int S = kAdjGhWarps * 32 * V * kAdjGhSub;
     constexpr int NG = V + TG - 1;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);   // full[s], empty[s]
     float *red = reinterpret_cast<float *>(smem + 128);
-    float2 *ring = reinterpret_cast<float2 *>(smem + adj_staged_smem(S, 0, kAdjGhWarps * NA));
+    static_assert(TG <= kAdjGhMaxTG, "tap group exceeds the staged look-ahead");
+    float2 *ring = reinterpret_cast<float2 *>(smem + adj_staged_smem(S, 0, kAdjGhWarps * NA, kAdjGhHalo));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k0 = blockIdx.y * TG;
     const bool group0 = blockIdx.y == 0;
-    if (tid == 0) {
+    const bool producer = tid == 0;
+    const int slot_elems = adj_slot_elems(S, kAdjGhHalo);
+    // Local tile i of this CTA is global tile blockIdx.x + i * gridDim.x.
+    const int64_t nlocal = ntiles > (int64_t)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto issue = [&](int64_t i) {   // producer: tile i into slot i % stages (its empty phase passed)
+        const int sl = (int)(i % stages);
+        const int64_t s0 = ((int64_t)blockIdx.x + i * gridDim.x) * S;
+        int xc, gc;
+        adj_slot_counts(s0, S, a.n, xc, gc, kAdjGhHalo);
+        const uint32_t fb = smem_addr(&bars[sl]);
+        float2 *slot = ring + (size_t)sl * slot_elems;
+        mbar_arrive_expect_tx(fb, (uint32_t)(xc + gc) * (uint32_t)sizeof(float2));
+        if (xc) bulk_copy_g2s(smem_addr(slot), a.x + s0, (uint32_t)xc * sizeof(float2), fb);
+        if (gc) bulk_copy_g2s(smem_addr(slot + S), a.gy + s0, (uint32_t)gc * sizeof(float2), fb);
+    };
+    if (producer) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(smem_addr(&bars[s]), 1);
             mbar_init(smem_addr(&bars[stages + s]), kAdjGhWarps);
@@ -529,39 +568,70 @@ __global__ void __launch_bounds__(32 * (kAdjGhWarps + 1), 1)
         fence_barrier_init();
     }
     __syncthreads();
-    if (warp == kAdjGhWarps) {
-        if (lane == 0) adj_produce(a, ring, bars, stages, S, ntiles);
-        return;
-    }
+    int64_t issued = 0;
+    if (producer)
+        for (; issued < stages && issued < nlocal; ++issued) issue(issued);
     float2 acc2[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) acc2[i] = make_float2(0.f, 0.f);
-    const int slot_elems = adj_slot_elems(S);
-    int64_t it = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int s = (int)(it % stages);
+    int s = 0;          // slot and parity of the current tile, kept incrementally
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int64_t i = 0; i < nlocal; ++i) {
         // A failed wait (error word set) ends this warp's tiles; it still joins
-        // the reduction so that no consumer waits for it.
-        if (!mbar_wait(smem_addr(&bars[s]), (uint32_t)((it / stages) & 1), a.status)) break;
-        const float2 *slot = ring + (size_t)s * slot_elems;
-        const int64_t s0 = tile * S;
-        const int off = tid * V;
-        float2 xs[V], g[NG];
-        if (s0 + S + kHalo <= a.n) {
-            adj_slot_window<V>(slot, off, xs);
-            adj_slot_window<NG>(slot + S, off + k0, g);
-        } else {
-            int xc, gc;
-            adj_slot_counts(s0, S, a.n, xc, gc);
-            adj_slot_window_tail<V>(slot, s0, xc, a.x, s0 + off, a.n, xs);
-            adj_slot_window_tail<NG>(slot + S, s0, gc, a.gy, s0 + off + k0, a.n, g);
+        // the reduction so that no warp waits for it.
+        if (!mbar_wait(smem_addr(&bars[s]), ph, a.status)) {
+            ok = false;
+            break;
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));
-        gh_accumulate<B, TG, V>(xs, g, group0, acc2);
+        const float2 *slot = ring + (size_t)s * slot_elems;
+        const int64_t s0 = ((int64_t)blockIdx.x + i * gridDim.x) * S;
+        const bool fast = s0 + S + kAdjGhHalo <= a.n;
+        int xc = S, gc = S + kAdjGhHalo;
+        if (!fast) adj_slot_counts(s0, S, a.n, xc, gc, kAdjGhHalo);
+        // Sub-block j of the tile: samples (j * threads + tid) * V ..; the slot
+        // is released once the last sub-block's windows are in registers.
+#pragma unroll 1
+        for (int j = 0; j < kAdjGhSub; ++j) {
+            const int off = (j * kAdjGhWarps * 32 + tid) * V;
+            float2 xs[V], g[NG];
+            if (fast) {
+                adj_slot_window<V>(slot, off, xs);
+                adj_slot_window<NG>(slot + S, off + k0, g);
+            } else {
+                adj_slot_window_tail<V>(slot, s0, xc, a.x, s0 + off, a.n, xs);
+                adj_slot_window_tail<NG>(slot + S, s0, gc, a.gy, s0 + off + k0, a.n, g);
+            }
+            if (j == kAdjGhSub - 1) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&bars[stages + s]));
+            }
+            gh_accumulate<B, TG, V>(xs, g, group0, acc2);
+        }
+        if (++s == stages) {
+            s = 0;
+            ph ^= 1u;
+        }
+        // Refill: tile i - 1 + stages into the slot of tile i - 1, once all
+        // warps have released that tile (empty phase (i - 1) / stages).
+        if (producer && i >= 1 && issued < nlocal) {
+            const int64_t done = i - 1;
+            if (!mbar_wait(smem_addr(&bars[stages + (int)(done % stages)]), (uint32_t)((done / stages) & 1),
+                           a.status)) {
+                ok = false;
+                break;
+            }
+            issue(issued++);
+        }
     }
-    gh_reduce_row<B, TG, true>(acc2, red, kAdjGhWarps, tid, k0, group0, T, Bp, Bq,
-                               a.partials + (size_t)blockIdx.x * K);
+    if (producer && !ok) {
+        // Let the copies already issued land before the CTA exits.
+        const int64_t first = issued > stages ? issued - stages : 0;
+        for (int64_t q = first; q < issued; ++q)
+            mbar_wait(smem_addr(&bars[q % stages]), (uint32_t)((q / stages) & 1), a.status);
+    }
+    gh_reduce_row<B, TG, false>(acc2, red, kAdjGhWarps, tid, k0, group0, T, Bp, Bq,
+                                a.partials + (size_t)blockIdx.x * K);
 }
 
 // ---------------------------------------------------------------- launches
@@ -626,14 +696,14 @@ cudaError_t launch_adj_gh_tg(const AdjArgs &a, int blocks, int T, int Bp, int Bq
     dim3 grid((unsigned)blocks, (unsigned)groups);
     if (adj_staged_ok(a)) {
         constexpr int V = kAdjGhV;
-        constexpr int S = kAdjGhWarps * 32 * V;
+        constexpr int S = kAdjGhWarps * 32 * V * kAdjGhSub;
         constexpr int NA = 4 * B * TG + 2;
-        const size_t smem = adj_staged_smem(S, kAdjGhStages, kAdjGhWarps * NA);
+        const size_t smem = adj_staged_smem(S, kAdjGhStages, kAdjGhWarps * NA, kAdjGhHalo);
         static SmemAttr smem_rec;
         const cudaError_t attr = ensure_smem(smem_rec, (const void *)adj_gh_tma_kernel<B, TG, V>, smem);
         if (attr != cudaSuccess) return attr;
         const int64_t ntiles = (a.n + S - 1) / S;
-        adj_gh_tma_kernel<B, TG, V><<<grid, 32 * (kAdjGhWarps + 1), smem, s>>>(a, kAdjGhStages, ntiles, T, Bp, Bq, K);
+        adj_gh_tma_kernel<B, TG, V><<<grid, 32 * kAdjGhWarps, smem, s>>>(a, kAdjGhStages, ntiles, T, Bp, Bq, K);
         count_launch();
         return cudaGetLastError();
     }

@@ -124,15 +124,15 @@ dpd_status dpd_create(int P, int Q, int M, dpd_handle *out)
     f->rows_max = 4 * f->sm_count;
     // Coefficient-gradient schedule: as few tap groups as keep a thread's
     // accumulators (4 B TG + 2 floats) within about a hundred registers, with
-    // the taps spread evenly over the groups; groups of 3 or more taps run one
-    // CTA per SM, smaller ones two.
+    // the taps spread evenly over the groups, and one CTA per SM (the staged
+    // kernel's ring takes most of an SM's shared memory).
     {
         int tg_max = 25 / f->B;
         if (tg_max > 5) tg_max = 5;
         if (tg_max < 1) tg_max = 1;
         const int groups = (f->T + tg_max - 1) / tg_max;
         f->adj.tap_group = (f->T + groups - 1) / groups;
-        f->adj.gh_blocks = (f->adj.tap_group >= 3 ? 1 : 2) * f->sm_count;
+        f->adj.gh_blocks = f->sm_count;
     }
     f->d_h = nullptr;
     f->d_tab = nullptr;
@@ -529,7 +529,7 @@ dpd_status dpd_set_fwd_launch(dpd_handle h, int mode, int V, int warps, int stag
 {
     if (!h) return DPD_ERR_INVALID_ARGUMENT;
     if (mode < 0 || mode > 3) return DPD_ERR_INVALID_ARGUMENT;
-    if ((V != 2 && V != 4 && V != 8) || warps < 1 || warps > dpd::kFwdMaxWarps || stages < 2 || stages > 8 ||
+    if ((V != 2 && V != 4 && V != 6 && V != 8) || warps < 1 || warps > dpd::kFwdMaxWarps || stages < 2 || stages > 8 ||
         ctas_per_sm < 0 || (use_tma != 0 && use_tma != 1) || group < 0 || (group > 0 && warps % group != 0))
         return DPD_ERR_INVALID_ARGUMENT;
     if (use_tma) {   // the rings of all groups must fit in one CTA's shared memory

@@ -396,8 +396,8 @@ __global__ void __launch_bounds__(256)
 }
 
 // Instantiated launch shapes.  Every (B, T) gets the default packed modes
-// (2: shared-memory coefficients, 3: parameter-bank coefficients) at V = 4 and
-// 8 plus the scalar mode 0 at V = 4; the plain-load kernel gets V = 4 in
+// (2: shared-memory coefficients, 3: parameter-bank coefficients) at V = 4, 6
+// and 8 plus the scalar mode 0 at V = 4; the plain-load kernel gets V = 4 in
 // modes 0, 2 and 3.  The (B, T) pairs of the benchmarked workloads
 // get every combination, for tuning and ablation.
 template <int B, int T>
@@ -431,7 +431,7 @@ constexpr bool fwd_built()
 {
     if (fwd_all_modes<B, T>()) return true;
     if (!TMA) return V == 4 && (MODE == 0 || MODE == 2 || MODE == 3);
-    return (V == 4 && MODE == 0) || ((V == 4 || V == 8) && (MODE == 2 || MODE == 3));
+    return (V == 4 && MODE == 0) || ((V == 4 || V == 6 || V == 8) && (MODE == 2 || MODE == 3));
 }
 
 template <int B, int T, int V, int MODE>
@@ -509,6 +509,7 @@ cudaError_t launch_fwd_mode(const FwdArgs &a, const FwdLaunch &L, int sm_count, 
     switch (L.V) {
     case 2: return launch_fwd_tv<B, T, 2, MODE>(a, L, sm_count, s);
     case 4: return launch_fwd_tv<B, T, 4, MODE>(a, L, sm_count, s);
+    case 6: return launch_fwd_tv<B, T, 6, MODE>(a, L, sm_count, s);
     case 8: return launch_fwd_tv<B, T, 8, MODE>(a, L, sm_count, s);
     default: return cudaErrorInvalidValue;
     }

@@ -54,8 +54,10 @@ def test_table2_p5_q3_l5_ragged():
 
 @pytest.mark.parametrize("launch", [None, dict(mode=3, V=8, warps=12, stages=3, group=0),
                                     dict(mode=3, V=8, warps=12, stages=4, group=4),
-                                    dict(mode=3, V=8, warps=16, stages=3, group=2)],
-                         ids=["default", "one_group", "w12g4", "w16g2"])
+                                    dict(mode=3, V=8, warps=16, stages=3, group=2),
+                                    dict(mode=3, V=6, warps=16, stages=4, group=4),
+                                    dict(mode=3, V=6, warps=12, stages=3, group=0)],
+                         ids=["default", "one_group", "w12g4", "w16g2", "v6w16g4", "v6w12"])
 def test_config1_full_size_ofdm_p9_m4(launch):
     """Full 2^24-sample OFDM workload, coefficients from host memory as the
     benchmark installs them, at the default shape (16 consumer warps in groups
@@ -100,6 +102,8 @@ LAUNCHES = [
     dict(V=4, warps=16, stages=3, ctas_per_sm=0, use_tma=1, group=4),
     dict(V=2, warps=16, stages=8, ctas_per_sm=0, use_tma=1, group=2),
     dict(V=8, warps=6, stages=2, ctas_per_sm=3, use_tma=1, group=3),
+    dict(V=6, warps=16, stages=4, ctas_per_sm=0, use_tma=1, group=4, mode=3),
+    dict(V=6, warps=5, stages=3, ctas_per_sm=2, use_tma=1, mode=3),
 ]
 
 
@@ -142,6 +146,19 @@ def test_grouped_shapes(P, Q, M, warps, group, stages):
         launch = dict(mode=3, V=8, warps=warps, stages=stages, ctas_per_sm=0, use_tma=1, group=group)
         y = run_gpu(x, h, P, Q, M, launch=launch, host_coeffs=True)
         assert_parity(y, oracle.apply(x, h, P, Q, M), what=f"n={n} {launch}")
+
+
+@pytest.mark.parametrize("P,Q,M", [(1, 1, 0), (3, 1, 1), (5, 5, 2), (7, 7, 3), (9, 9, 4), (11, 3, 5), (11, 11, 7), (0, 7, 6)])
+def test_six_samples_per_thread(P, Q, M):
+    """V = 6 (packed FMAs, parameter-bank or shared-memory coefficients):
+    every order and tap count, sizes that end inside a thread's six samples."""
+    h = synth.coeffs(P, Q, M, key=(10, 1), f_std=0.3, g_std=0.3)
+    for n in (1, 5, 6, 7, 191, 193, 3 * 1024 + 5, 100003):
+        x = synth.clipped_gaussian(n, 0.5, key=(10, n, P, M))
+        for host in (True, False):
+            launch = dict(mode=3, V=6, warps=8, stages=3, ctas_per_sm=0, use_tma=1, group=2)
+            y = run_gpu(x, h, P, Q, M, launch=launch, host_coeffs=host)
+            assert_parity(y, oracle.apply(x, h, P, Q, M), what=f"n={n} host={host} {launch}")
 
 
 @pytest.mark.parametrize("offset,out_offset", [(1, 0), (0, 1), (1, 1), (3, 2)])
