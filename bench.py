@@ -54,12 +54,14 @@ def parse():
                     help="skip the batched / adjoint / Gram side measurements")
     ap.add_argument("--fwd-launch", default=None, metavar="MODE,V,WARPS,STAGES[,GROUP]",
                     help="fix the forward launch shape instead of tuning it (profiling runs)")
-    ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "grad", "gram", "ila", "cpu", "sweep", "fma",
-                                          "estimate",
+    ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "grad", "gram", "gram_one", "ila", "cpu", "sweep",
+                                          "fma", "estimate",
                                           "oracle"],
                     default=None,
                     help="run only this side measurement (1 GPU) and print its JSON; for profiling")
     ap.add_argument("--grad-log2n", type=int, default=24, help="samples (log2) of --pattern grad")
+    ap.add_argument("--gram-precision", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3"],
+                    help="precision of --pattern gram_one")
     ap.add_argument("--batched-launch", default=None, metavar="V,WARPS,STAGES,CTAS_PER_SM[,GROUP]",
                     help="fix the batched launch shape of --pattern batched instead of tuning it (profiling runs)")
     ap.add_argument("--min-warmup-s", type=float, default=1.5,
@@ -742,6 +744,39 @@ def measure_estimate(dev, reps=5, refine_iters=3):
     return out
 
 
+def measure_gram_one(dev, precision, reps=10):
+    """The Gram contraction alone (dpd_gram: tensor or FP32 kernel, FP64
+    reduction and assembly) of 2^22 rows x K = 97 (P = Q = 11, M = 7) in one
+    precision: two warm-up calls, then `reps` back-to-back calls between CUDA
+    events."""
+    import torch
+    import dpd_synth as synth
+    import paper_1612_09001_gb300 as dpd
+    P, Q, M, n = 11, 11, 7, 1 << 22
+    u, theta = synth.ls_problem(n, P, Q, M, seed=0)
+    ud = torch.from_numpy(u).to(dev)
+    g = dpd.DPD(P, Q, M)
+    g.set_coeffs(theta)
+    td = g.apply(ud)
+    f = dpd.DPD(P, Q, M)
+    for _ in range(2):
+        f.gram(ud, td, precision=precision, want_tt=False)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        f.gram(ud, td, precision=precision, want_tt=False)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    f.sync_status()
+    ms = e0.elapsed_time(e1) / reps
+    f.close()
+    g.close()
+    return {"workload": "Psi 2^22 rows x 97 complex columns (P=Q=11, M=7)", "precision": precision,
+            "gram_ms": ms, "timing": f"{reps} back-to-back dpd_gram calls after 2 warm-up calls, CUDA events"}
+
+
 def measure_gram(dev, reps=5):
     """LS Gram of 2^22 rows x K=97 (P=Q=11, M=7) in every precision, and the
     batch of 256 estimations of 2^16 rows."""
@@ -1062,6 +1097,7 @@ def main():
         fn = {"small": measure_small, "batched": lambda d: measure_batched(d, launch=blaunch),
               "adjoint": measure_direct,
               "gram": measure_gram, "ila": measure_ila, "sweep": measure_sweep,
+              "gram_one": lambda d: measure_gram_one(d, args.gram_precision),
               "grad": lambda d: measure_grad(d, args.grad_log2n),
               "fma": lambda d: measure_fma_ceiling(d, gpu_index=local),
               "estimate": measure_estimate}[args.pattern]

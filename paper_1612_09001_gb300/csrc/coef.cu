@@ -6,14 +6,24 @@
 
 namespace dpd {
 
-__global__ void wl_table_kernel(const float2 *__restrict__ h, int Bp, int Bq, int T, int B,
-                                float *__restrict__ tab, float *__restrict__ adj)
+// Coefficient k of the stacked vector as FP32 (FP64 sources are rounded to
+// nearest, as the FP32 copy of an FP64 estimate is).
+__device__ __forceinline__ float2 coef_f32(const float2 *h, int i) { return h[i]; }
+__device__ __forceinline__ float2 coef_f32(const double2 *h, int i)
 {
+    return make_float2((float)h[i].x, (float)h[i].y);
+}
+
+template <typename H>
+__global__ void wl_table_kernel(const H *__restrict__ hin, int Bp, int Bq, int T, int B, float *__restrict__ tab,
+                                float *__restrict__ adj)
+{
+    auto h = [hin](int i) { return coef_f32(hin, i); };
     const int i = threadIdx.x;   // one thread per (tap k, order index m)
     if (i < T * B) {
         const int k = i / B, m = i % B;
-        const float2 A = (m < Bp) ? h[m * T + k] : make_float2(0.f, 0.f);          // h_{2m+1,k}
-        const float2 C = (m < Bq) ? h[(Bp + m) * T + k] : make_float2(0.f, 0.f);   // hbar_{2m+1,k}
+        const float2 A = (m < Bp) ? h(m * T + k) : make_float2(0.f, 0.f);          // h_{2m+1,k}
+        const float2 C = (m < Bq) ? h((Bp + m) * T + k) : make_float2(0.f, 0.f);   // hbar_{2m+1,k}
         tab[wl_index(B, k, m, 0)] = A.x + C.x;      // P0 = Re(A+C)
         tab[wl_index(B, k, m, 1)] = -(A.y - C.y);   // P1 = -Im(A-C)
         tab[wl_index(B, k, m, 2)] = A.y + C.y;      // P2 = Im(A+C)
@@ -35,8 +45,8 @@ __global__ void wl_table_kernel(const float2 *__restrict__ h, int Bp, int Bq, in
             q[4 * m + 3] = Hi - Ei;   // Q2
             if (m < B - 1) {
                 // F_m = (m+1) h_{m+1}, G_m = (m+1) hbar_{m+1}
-                const float2 A1 = (m + 1 < Bp) ? h[(m + 1) * T + k] : make_float2(0.f, 0.f);
-                const float2 C1 = (m + 1 < Bq) ? h[(Bp + m + 1) * T + k] : make_float2(0.f, 0.f);
+                const float2 A1 = (m + 1 < Bp) ? h((m + 1) * T + k) : make_float2(0.f, 0.f);
+                const float2 C1 = (m + 1 < Bq) ? h((Bp + m + 1) * T + k) : make_float2(0.f, 0.f);
                 const float Fr = s * A1.x, Fi = s * A1.y, Gr = s * C1.x, Gi = s * C1.y;
                 float *r = q + 4 * B;
                 r[4 * m + 0] = Gr + Fr;   // S0
@@ -47,7 +57,7 @@ __global__ void wl_table_kernel(const float2 *__restrict__ h, int Bp, int Bq, in
         }
     }
     if (i == 0) {
-        const float2 c = h[(Bp + Bq) * T];
+        const float2 c = h((Bp + Bq) * T);
         tab[4 * B * T] = c.x;
         tab[4 * B * T + 1] = c.y;
     }
@@ -57,7 +67,15 @@ cudaError_t launch_wl_table(const float2 *h, int Bp, int Bq, int T, float *tab, 
                             cudaStream_t s)
 {
     const int B = Bp > Bq ? Bp : Bq;
-    wl_table_kernel<<<1, 64, 0, s>>>(h, Bp, Bq, T, B, tab, adj_tab);
+    wl_table_kernel<float2><<<1, 64, 0, s>>>(h, Bp, Bq, T, B, tab, adj_tab);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wl_table_f64(const double2 *h, int Bp, int Bq, int T, float *tab, cudaStream_t s)
+{
+    const int B = Bp > Bq ? Bp : Bq;
+    wl_table_kernel<double2><<<1, 64, 0, s>>>(h, Bp, Bq, T, B, tab, nullptr);
     count_launch();
     return cudaGetLastError();
 }

@@ -526,9 +526,10 @@ __global__ void __launch_bounds__(256) adj_gh_kernel(AdjArgs a, int T, int Bp, i
 // 16-byte aligned.  With 2 B TG + 1 packed accumulators a thread takes about
 // 170 registers, so one CTA fits an SM; the bulk copies are issued by lane 0
 // of warp 0 between its own tiles instead of by a separate producer warp, so
-// that all twelve warps (three per SM sub-partition) accumulate.  Warp 0
-// refills the slot of tile i - 1 at the end of its tile i (once every warp
-// has released tile i - 1), with tile i - 1 + stages.
+// that all twelve warps (three per SM sub-partition) accumulate.  At the start
+// of its tile i warp 0 refills the slot of tile i - 1 (once every warp has
+// released it) with tile i - 1 + stages; the whole warp waits, so that its
+// lanes stay converged.
 template <int B, int TG, int V>
 __global__ void __launch_bounds__(32 * kAdjGhWarps, 1)
     adj_gh_tma_kernel(AdjArgs a, int stages, int64_t ntiles, int T, int Bp, int Bq, int K)
@@ -568,9 +569,10 @@ __global__ void __launch_bounds__(32 * kAdjGhWarps, 1)
         fence_barrier_init();
     }
     __syncthreads();
-    int64_t issued = 0;
-    if (producer)
-        for (; issued < stages && issued < nlocal; ++issued) issue(issued);
+    int64_t issued = 0;   // tiles issued so far (kept by every lane of warp 0)
+    if (warp == 0)
+        for (; issued < stages && issued < nlocal; ++issued)
+            if (producer) issue(issued);
     float2 acc2[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) acc2[i] = make_float2(0.f, 0.f);
@@ -583,6 +585,21 @@ __global__ void __launch_bounds__(32 * kAdjGhWarps, 1)
         if (!mbar_wait(smem_addr(&bars[s]), ph, a.status)) {
             ok = false;
             break;
+        }
+        // Refill: tile i - 1 + stages into the slot of tile i - 1, once all
+        // warps have released that tile (empty phase (i - 1) / stages).
+        if (warp == 0 && i >= 1 && issued < nlocal) {
+            const int64_t done = i - 1;
+            bool w = mbar_wait(smem_addr(&bars[stages + (int)(done % stages)]), (uint32_t)((done / stages) & 1),
+                               a.status);
+            w = __shfl_sync(0xffffffffu, w, 0);   // lane 0's outcome for the whole warp
+            if (!w) {
+                ok = false;
+                break;
+            }
+            if (producer) issue(issued);
+            ++issued;
+            __syncwarp();
         }
         const float2 *slot = ring + (size_t)s * slot_elems;
         const int64_t s0 = ((int64_t)blockIdx.x + i * gridDim.x) * S;
@@ -611,17 +628,6 @@ __global__ void __launch_bounds__(32 * kAdjGhWarps, 1)
         if (++s == stages) {
             s = 0;
             ph ^= 1u;
-        }
-        // Refill: tile i - 1 + stages into the slot of tile i - 1, once all
-        // warps have released that tile (empty phase (i - 1) / stages).
-        if (producer && i >= 1 && issued < nlocal) {
-            const int64_t done = i - 1;
-            if (!mbar_wait(smem_addr(&bars[stages + (int)(done % stages)]), (uint32_t)((done / stages) & 1),
-                           a.status)) {
-                ok = false;
-                break;
-            }
-            issue(issued++);
         }
     }
     if (producer && !ok) {

@@ -124,15 +124,16 @@ dpd_status dpd_create(int P, int Q, int M, dpd_handle *out)
     f->rows_max = 4 * f->sm_count;
     // Coefficient-gradient schedule: as few tap groups as keep a thread's
     // accumulators (4 B TG + 2 floats) within about a hundred registers, with
-    // the taps spread evenly over the groups, and one CTA per SM (the staged
-    // kernel's ring takes most of an SM's shared memory).
+    // the taps spread evenly over the groups, and the CTAs of all groups in one
+    // wave of one CTA per SM (the staged kernel's ring takes most of an SM's
+    // shared memory): sm_count / groups CTAs per group.
     {
         int tg_max = 25 / f->B;
         if (tg_max > 5) tg_max = 5;
         if (tg_max < 1) tg_max = 1;
         const int groups = (f->T + tg_max - 1) / tg_max;
         f->adj.tap_group = (f->T + groups - 1) / groups;
-        f->adj.gh_blocks = f->sm_count;
+        f->adj.gh_blocks = f->sm_count / groups > 0 ? f->sm_count / groups : 1;
     }
     f->d_h = nullptr;
     f->d_tab = nullptr;

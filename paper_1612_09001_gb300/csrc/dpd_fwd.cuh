@@ -359,8 +359,30 @@ __global__ void __launch_bounds__(fwd_lb_threads<SH>(), fwd_lb_blocks<SH>())
         }
 
         float yr[V], yi[V];
-        fwd_compute<B, T, V, MODE>(tab, ptab, wr, wi, yr, yi);
-        store_outputs<V>(a.y, s0 + (int64_t)t_in_tile * V, a.n, full && a.vec_store, yr, yi);
+        fwd_compute<B, T, V, MODE & (kModeParamCoef | kModePackedFma)>(tab, ptab, wr, wi, yr, yi);
+        const int64_t g0 = s0 + (int64_t)t_in_tile * V;
+        if constexpr ((MODE & kModeSubtract) != 0) {   // y <- sub - y
+            if (full) {
+                const float4 *sp = reinterpret_cast<const float4 *>(a.sub + g0);
+#pragma unroll
+                for (int i = 0; i < V / 2; ++i) {
+                    const float4 q = __ldcs(sp + i);
+                    yr[2 * i] = q.x - yr[2 * i];
+                    yi[2 * i] = q.y - yi[2 * i];
+                    yr[2 * i + 1] = q.z - yr[2 * i + 1];
+                    yi[2 * i + 1] = q.w - yi[2 * i + 1];
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (g0 + v < a.n) {
+                        const float2 q = a.sub[g0 + v];
+                        yr[v] = q.x - yr[v];
+                        yi[v] = q.y - yi[v];
+                    }
+            }
+        }
+        store_outputs<V>(a.y, g0, a.n, full && a.vec_store, yr, yi);
     }
 }
 
@@ -429,6 +451,7 @@ int fwd_shape_index(int warps, int gw, int stages)
 template <int B, int T, int V, int MODE, bool TMA>
 constexpr bool fwd_built()
 {
+    if constexpr ((MODE & kModeSubtract) != 0) return TMA && V == 6 && MODE == (kModePackedFma | kModeSubtract);
     if (fwd_all_modes<B, T>()) return true;
     if (!TMA) return V == 4 && (MODE == 0 || MODE == 2 || MODE == 3);
     return (V == 4 && MODE == 0) || ((V == 4 || V == 6 || V == 8) && (MODE == 2 || MODE == 3));
@@ -523,6 +546,7 @@ cudaError_t launch_fwd_t(const FwdArgs &a, const FwdLaunch &L, int sm_count, cud
     case 1: return launch_fwd_mode<B, T, 1>(a, L, sm_count, s);
     case 2: return launch_fwd_mode<B, T, 2>(a, L, sm_count, s);
     case 3: return launch_fwd_mode<B, T, 3>(a, L, sm_count, s);
+    case kModePackedFma | kModeSubtract: return launch_fwd_mode<B, T, kModePackedFma | kModeSubtract>(a, L, sm_count, s);
     default: return cudaErrorInvalidValue;
     }
 }

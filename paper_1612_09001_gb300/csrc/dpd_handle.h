@@ -35,10 +35,12 @@ struct EstimateWorkspace {
     bool use_inverse = false;     // refinement solves through Linv (problem 0 only)
     // pinned host copies read back by dpd_estimate (single problem)
     int hK = 0;                   // K the host buffers were sized for
-    double2 *h_L = nullptr;       // Cholesky factor, K x K (condition estimate on the host)
-    int *h_info = nullptr;        // its pivot status
+    double2 *h_G = nullptr;       // Gram matrix G, K x K (condition estimate on the host)
+    double2 *h_Linv = nullptr;    // inverse Cholesky factor of D G D, K x K
+    int *h_info = nullptr;        // pivot status of the factorisation
     double *h_norm = nullptr;     // ||t - Psi h||^2, ||t||^2
-    cudaEvent_t ev_L = nullptr;   // h_L and h_info have landed
+    cudaEvent_t ev_G = nullptr;   // h_G has landed
+    cudaEvent_t ev_L = nullptr;   // h_info (and h_Linv) have landed
 };
 
 // Device staging of dpd_apply_host's copy / compute pipeline, created on first use.

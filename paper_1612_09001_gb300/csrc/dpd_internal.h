@@ -41,14 +41,16 @@ struct HostTab {
 
 // Forward compute modes (template bits): coefficients read from the kernel
 // parameter bank instead of shared memory; packed f32x2 fused multiply-adds.
-enum : int { kModeParamCoef = 1, kModePackedFma = 2 };
+// kModeSubtract (internal, least-squares refinement only): the kernel writes
+// sub[n] - y[n] instead of y[n].
+enum : int { kModeParamCoef = 1, kModePackedFma = 2, kModeSubtract = 4 };
 
 // Forward launch shape.
 constexpr int kFwdMaxWarps = 16;   // consumer warps per CTA of the TMA kernel (register budget)
 
 struct FwdLaunch {
     int mode = kModeParamCoef | kModePackedFma;   // compute mode bits
-    int V = 8;            // samples per consumer thread (2, 4 or 8)
+    int V = 8;            // samples per consumer thread (2, 4, 6 or 8)
     int warps = 16;       // consumer warps per CTA (tile = warps * 32 * V samples)
     int stages = 4;       // shared-memory ring depth per group (bulk-copy pipeline)
     int ctas_per_sm = 0;  // 0: as many as fit
@@ -64,6 +66,7 @@ struct FwdArgs {
     int *status;          // device error word
     int vec_store;        // y is 16-byte aligned
     const HostTab *host_tab;   // host copy of the table (param-bank modes), or null
+    const float2 *sub = nullptr;   // kModeSubtract: minuend, n samples, 16-byte aligned
 };
 
 // Floats of the adjoint table: per tap, four polynomials of B coefficients
@@ -110,6 +113,8 @@ cudaError_t launch_fwd_any(int B, int T, const FwdArgs &a, const FwdLaunch &L, i
 
 // Build the forward widely-linear table and the adjoint table from the stacked
 // coefficient vector h (K complex); adj_tab may be null.
+// The forward table straight from FP64 coefficients (rounded to FP32 first).
+cudaError_t launch_wl_table_f64(const double2 *h, int Bp, int Bq, int T, float *tab, cudaStream_t s);
 cudaError_t launch_wl_table(const float2 *h, int Bp, int Bq, int T, float *tab, float *adj_tab,
                             cudaStream_t s);
 

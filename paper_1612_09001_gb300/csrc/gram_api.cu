@@ -52,21 +52,25 @@ dpd_status reserve(dpd_handle h, int nprob, int cpp, int64_t nsamp)
         w.nprob = nprob;
         w.cpp = cpp;
     }
-    if (w.hK != K || !w.h_L) {
-        cudaFreeHost(w.h_L);
+    if (w.hK != K || !w.h_G) {
+        cudaFreeHost(w.h_G);
+        cudaFreeHost(w.h_Linv);
         cudaFreeHost(w.h_info);
         cudaFreeHost(w.h_norm);
-        w.h_L = nullptr;
+        w.h_G = nullptr;
+        w.h_Linv = nullptr;
         w.h_info = nullptr;
         w.h_norm = nullptr;
         w.hK = 0;
-        if (cudaMallocHost(&w.h_L, sizeof(double2) * K * K) != cudaSuccess ||
+        if (cudaMallocHost(&w.h_G, sizeof(double2) * K * K) != cudaSuccess ||
+            cudaMallocHost(&w.h_Linv, sizeof(double2) * K * K) != cudaSuccess ||
             cudaMallocHost(&w.h_info, sizeof(int)) != cudaSuccess ||
             cudaMallocHost(&w.h_norm, 2 * sizeof(double)) != cudaSuccess)
             return DPD_ERR_ALLOC;
         w.hK = K;
     }
     if (!w.ev_L && cudaEventCreateWithFlags(&w.ev_L, cudaEventDisableTiming) != cudaSuccess) return DPD_ERR_CUDA;
+    if (!w.ev_G && cudaEventCreateWithFlags(&w.ev_G, cudaEventDisableTiming) != cudaSuccess) return DPD_ERR_CUDA;
     if (nsamp > w.nsamp) {
         cudaDeviceSynchronize();
         ok = grow(w.y, 0, (size_t)nsamp) && grow(w.e, 0, (size_t)nsamp);
@@ -185,7 +189,8 @@ dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_
 }
 
 // e = t - Psi(u) h for the current FP64 coefficients of problem p (FP32 filter);
-// with `norms`, also ||e||^2 and ||t||^2 into w.norm_part + 2048.
+// with `norms`, only ||e||^2 and ||t||^2 into w.norm_part + 2048 (e itself is
+// not written).
 dpd_status residual_of(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, cudaStream_t s,
                        bool norms = false)
 {
@@ -193,8 +198,7 @@ dpd_status residual_of(dpd_handle h, int p, const float2 *u, const float2 *t, in
     dpd_status st = DPD_OK;
     const double2 *hm = monomial_h(h, p, 1, s, st);
     if (st != DPD_OK) return st;
-    if (dpd::launch_h_to_f32(hm, h->K, w.hf, s) != cudaSuccess) return DPD_ERR_CUDA;
-    if (dpd::launch_wl_table(w.hf, h->Bp, h->Bq, h->T, w.tab, nullptr, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dpd::launch_wl_table_f64(hm, h->Bp, h->Bq, h->T, w.tab, s) != cudaSuccess) return DPD_ERR_CUDA;
     dpd::FwdArgs fa;
     fa.x = u;
     fa.y = w.y;
@@ -203,15 +207,31 @@ dpd_status residual_of(dpd_handle h, int p, const float2 *u, const float2 *t, in
     fa.status = h->d_status;
     fa.vec_store = 1;
     fa.host_tab = nullptr;
-    dpd::FwdLaunch L = h->fwd;
-    L.mode = dpd::kModePackedFma;   // coefficients live on the device
+    // Coefficients live on the device (shared-memory table): 6 samples per
+    // thread, 16 warps in two groups of 8, 4 stages (measured best for these
+    // shapes on GB300: 31.6 us per 2^22 samples at P = Q = 11, M = 7, against
+    // about 42 at the single-stream default of 8 samples per thread).
+    dpd::FwdLaunch L;
+    L.mode = dpd::kModePackedFma;
+    L.V = 6;
+    L.warps = 16;
+    L.group = 8;
+    L.stages = 4;
+    const bool aligned16 = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(t)) & 15u) == 0;
+    if (!norms && aligned16) {
+        // The filter writes e = t - Psi(u) h itself (no separate residual pass).
+        L.mode = dpd::kModePackedFma | dpd::kModeSubtract;
+        fa.y = w.e;
+        fa.sub = t;
+        return dpd::launch_fwd_any(h->B, h->T, fa, L, h->sm_count, s) == cudaSuccess ? DPD_OK : DPD_ERR_CUDA;
+    }
     if ((reinterpret_cast<uintptr_t>(u) & 15u) != 0) {
         L.use_tma = 0;
         L.V = 4;
     }
     if (dpd::launch_fwd_any(h->B, h->T, fa, L, h->sm_count, s) != cudaSuccess) return DPD_ERR_CUDA;
     if (norms)
-        return dpd::launch_residual_norm(t, w.y, n, w.e, w.norm_part, w.norm_part + 2 * 1024, s) == cudaSuccess
+        return dpd::launch_residual_norm(t, w.y, n, nullptr, w.norm_part, w.norm_part + 2 * 1024, s) == cudaSuccess
                    ? DPD_OK
                    : DPD_ERR_CUDA;
     if (dpd::launch_residual(t, w.y, n, w.e, s) != cudaSuccess) return DPD_ERR_CUDA;
@@ -257,152 +277,254 @@ dpd_status refine_once(dpd_handle h, int p, const float2 *u, const float2 *t, in
     return DPD_OK;
 }
 
-// 2-norm condition number of A = L L^H (the equilibrated Gram matrix): the
-// largest eigenvalues of A and of A^{-1} (two triangular solves per product),
-// FP64 on the host.
-double cond_estimate(const double2 *L, int K)
+// Condition number of A = D G D = L L^H (the equilibrated Gram matrix, D =
+// diag(G)^{-1/2}) in the 2-norm: the largest eigenvalue of A (products with A
+// itself, formed from G) times the largest eigenvalue of A^{-1} = L^{-H} L^{-1}
+// (products with the explicit inverse of L that the solves use), FP64 on the
+// host.  Complex vectors and matrices are kept as separate real and imaginary
+// arrays, padded to an even length N with zeros, and processed two elements
+// at a time with GCC vector types (portable across x86-64 and AArch64): every
+// inner product is split over several vector partial sums, so no loop is one
+// long chain of dependent additions.
+namespace cond {
+
+typedef double v2d __attribute__((vector_size(16)));
+
+inline v2d ld2(const double *p) { return *reinterpret_cast<const v2d *>(p); }   // 16-byte aligned
+inline void st2(double *p, v2d v) { *reinterpret_cast<v2d *>(p) = v; }
+inline double hsum(v2d v) { return v[0] + v[1]; }
+
+// Padded split storage: rows of N (even) doubles; the heap blocks of
+// std::vector are 16-byte aligned (the allocator's fundamental alignment on
+// x86-64 and AArch64), so every row starts on a 16-byte boundary.
+struct Split {
+    int N = 0;
+    std::vector<double> re, im;
+    Split(int rows, int n) : N(n), re((size_t)rows * n, 0.0), im((size_t)rows * n, 0.0) {}
+    double *r(int row) { return re.data() + (size_t)row * N; }
+    double *i(int row) { return im.data() + (size_t)row * N; }
+    const double *r(int row) const { return re.data() + (size_t)row * N; }
+    const double *i(int row) const { return im.data() + (size_t)row * N; }
+};
+
+// y = M x for the first `rows` rows of M (row-major, padded width N); with
+// `lower`, row i reads columns < i + 1 rounded up to the block (M is zero above
+// its diagonal).  Four rows at a time, so every x element is loaded once per
+// four rows.
+void matvec(const Split &M, int rows, bool lower, const double *xr, const double *xi, double *yr, double *yi)
 {
-    auto mulL = [&](const std::vector<double2> &x, bool herm) {   // L x or L^H x
-        std::vector<double2> y((size_t)K, make_double2(0, 0));
-        for (int i = 0; i < K; ++i)
-            for (int k = 0; k <= i; ++k) {
-                const double2 l = L[(size_t)i * K + k];
-                if (!herm) {
-                    y[i].x += l.x * x[k].x - l.y * x[k].y;
-                    y[i].y += l.x * x[k].y + l.y * x[k].x;
-                } else {
-                    y[k].x += l.x * x[i].x + l.y * x[i].y;
-                    y[k].y += l.x * x[i].y - l.y * x[i].x;
-                }
-            }
-        return y;
-    };
-    auto solveL = [&](std::vector<double2> b, bool herm) {   // L^{-1} b or L^{-H} b
-        if (!herm) {
-            for (int i = 0; i < K; ++i) {
-                double2 s = b[i];
-                for (int k = 0; k < i; ++k) {
-                    const double2 l = L[(size_t)i * K + k];
-                    s.x -= l.x * b[k].x - l.y * b[k].y;
-                    s.y -= l.x * b[k].y + l.y * b[k].x;
-                }
-                const double d = L[(size_t)i * K + i].x;
-                b[i] = make_double2(s.x / d, s.y / d);
-            }
-        } else {
-            for (int i = K - 1; i >= 0; --i) {
-                double2 s = b[i];
-                for (int k = i + 1; k < K; ++k) {
-                    const double2 l = L[(size_t)k * K + i];
-                    s.x -= l.x * b[k].x + l.y * b[k].y;
-                    s.y -= l.x * b[k].y - l.y * b[k].x;
-                }
-                const double d = L[(size_t)i * K + i].x;
-                b[i] = make_double2(s.x / d, s.y / d);
+    const int N = M.N;
+    int i = 0;
+    for (; i + 4 <= rows; i += 4) {
+        const int kend = lower ? std::min(N, (i + 4 + 1) & ~1) : N;
+        v2d sr[4] = {}, si[4] = {};
+        for (int k = 0; k < kend; k += 2) {
+            const v2d a = ld2(xr + k), b = ld2(xi + k);
+            for (int q = 0; q < 4; ++q) {
+                const v2d mr = ld2(M.r(i + q) + k), mi = ld2(M.i(i + q) + k);
+                sr[q] += mr * a - mi * b;
+                si[q] += mr * b + mi * a;
             }
         }
-        return b;
-    };
-    // Largest eigenvalue of the Hermitian positive definite operator by Lanczos
-    // with full reorthogonalisation (one Gram-Schmidt pass per step), stopped
-    // once the largest Ritz value -- the largest root of the Lanczos
-    // tridiagonal, found by Sturm-sequence bisection -- changes by less than
-    // 1e-12 relative over five steps (checked at steps 10, 15, ..., at most
-    // 40).  On these clustered spectra plain power iterations stay
-    // percent-level low after 100 steps; this converges to about 1e-11 in
-    // 15-30.  The largest Ritz value only grows with the step count, so each
-    // bisection starts from the previous one.
-    auto dotc = [&](const std::vector<double2> &a, const std::vector<double2> &b) {   // a^H b
-        double2 r = make_double2(0, 0);
-        for (int i = 0; i < K; ++i) {
-            r.x += a[i].x * b[i].x + a[i].y * b[i].y;
-            r.y += a[i].x * b[i].y - a[i].y * b[i].x;
+        for (int q = 0; q < 4; ++q) {
+            yr[i + q] = hsum(sr[q]);
+            yi[i + q] = hsum(si[q]);
         }
-        return r;
-    };
-    auto ritz_max = [](const std::vector<double> &al, const std::vector<double> &be, double floor_) {
-        const int n = (int)al.size();
-        double lo = al[0], hi = al[0];
-        for (int i = 0; i < n; ++i) {
-            const double r = (i > 0 ? std::fabs(be[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(be[i]) : 0.0);
-            lo = std::min(lo, al[i] - r);
-            hi = std::max(hi, al[i] + r);
+    }
+    for (; i < rows; ++i) {
+        const int kend = lower ? std::min(N, (i + 1 + 1) & ~1) : N;
+        v2d sr = {0, 0}, si = {0, 0};
+        for (int k = 0; k < kend; k += 2) {
+            const v2d a = ld2(xr + k), b = ld2(xi + k), mr = ld2(M.r(i) + k), mi = ld2(M.i(i) + k);
+            sr += mr * a - mi * b;
+            si += mr * b + mi * a;
         }
-        if (floor_ > lo && floor_ < hi) lo = floor_;
-        auto below = [&](double x) {   // eigenvalues of the tridiagonal below x
-            int c = 0;
-            double d = 1.0;
-            for (int i = 0; i < n; ++i) {
-                d = al[i] - x - (i > 0 ? be[i - 1] * be[i - 1] / d : 0.0);
-                if (d == 0.0) d = -1e-300;
-                if (d < 0.0) ++c;
-            }
-            return c;
-        };
-        for (int it = 0; it < 200 && hi - lo > 1e-15 * std::fabs(hi); ++it) {
-            const double mid = 0.5 * (lo + hi);
-            if (below(mid) >= n)
-                hi = mid;
-            else
-                lo = mid;
-        }
-        return 0.5 * (lo + hi);
-    };
-    auto largest = [&](bool inverse) {
-        const int m = std::min(K, 40);
-        std::vector<std::vector<double2>> q;
-        std::vector<double> al, be;
-        std::vector<double2> v((size_t)K);
-        double nv = 0;
-        for (int i = 0; i < K; ++i) {
-            v[i] = make_double2(1.0 + 0.01 * i, 0.003 * i);
-            nv += v[i].x * v[i].x + v[i].y * v[i].y;
-        }
-        nv = std::sqrt(nv);
-        for (auto &e : v) e = make_double2(e.x / nv, e.y / nv);
-        q.push_back(v);
-        double prev = -1.0, lam = 0.0;
-        for (int j = 0; j < m; ++j) {
-            std::vector<double2> w =
-                inverse ? solveL(solveL(q[j], false), true) : mulL(mulL(q[j], true), false);
-            al.push_back(dotc(q[j], w).x);
-            for (int i = 0; i <= j; ++i) {
-                const double2 c = dotc(q[i], w);
-                for (int k = 0; k < K; ++k) {
-                    w[k].x -= c.x * q[i][k].x - c.y * q[i][k].y;
-                    w[k].y -= c.x * q[i][k].y + c.y * q[i][k].x;
-                }
-            }
-            const bool check = j >= 10 && (j % 5 == 0 || j == m - 1);
-            if (check || j == m - 1) {
-                lam = ritz_max(al, be, prev);
-                if (check && prev > 0 && std::fabs(lam - prev) <= 1e-12 * lam) break;
-                prev = lam * (1.0 - 1e-15);   // bisection floor for the next check
-            }
-            double bn = 0;
-            for (const auto &e : w) bn += e.x * e.x + e.y * e.y;
-            bn = std::sqrt(bn);
-            if (!(bn > 1e-14 * std::fabs(al.back()))) {   // invariant subspace: its Ritz values are exact
-                lam = ritz_max(al, be, prev);
-                break;
-            }
-            be.push_back(bn);
-            for (auto &e : w) e = make_double2(e.x / bn, e.y / bn);
-            q.push_back(w);
-        }
-        return lam;
-    };
-    // The two runs are independent: the inverse one on a second host thread.
-    double linv = 0.0;
-    try {
-        std::thread inv_run([&] { linv = largest(true); });
-        const double lmax = largest(false);
-        inv_run.join();
-        return lmax * linv;
-    } catch (const std::system_error &) {   // no thread available: one after the other
-        return largest(false) * largest(true);
+        yr[i] = hsum(sr);
+        yi[i] = hsum(si);
     }
 }
+
+// y = M^H z for a lower-triangular M (row-major, padded width N): row by row,
+// y[0 .. i] += conj(M_i,0..i) z_i (independent over the columns).
+void matvec_h_lower(const Split &M, int rows, const double *zr, const double *zi, double *yr, double *yi)
+{
+    const int N = M.N;
+    for (int k = 0; k < N; k += 2) {
+        st2(yr + k, v2d{0, 0});
+        st2(yi + k, v2d{0, 0});
+    }
+    for (int i = 0; i < rows; ++i) {
+        const v2d a = v2d{zr[i], zr[i]}, b = v2d{zi[i], zi[i]};
+        const int kend = std::min(N, (i + 1 + 1) & ~1);
+        for (int k = 0; k < kend; k += 2) {
+            const v2d mr = ld2(M.r(i) + k), mi = ld2(M.i(i) + k);
+            st2(yr + k, ld2(yr + k) + mr * a + mi * b);
+            st2(yi + k, ld2(yi + k) + mr * b - mi * a);
+        }
+    }
+}
+
+double2 dotc(int N, const double *a_r, const double *a_i, const double *b_r, const double *b_i)   // a^H b
+{
+    v2d sr[2] = {}, si[2] = {};
+    int k = 0;
+    for (; k + 4 <= N; k += 4)
+        for (int h = 0; h < 2; ++h) {
+            const v2d ar = ld2(a_r + k + 2 * h), ai = ld2(a_i + k + 2 * h), br = ld2(b_r + k + 2 * h),
+                      bi = ld2(b_i + k + 2 * h);
+            sr[h] += ar * br + ai * bi;
+            si[h] += ar * bi - ai * br;
+        }
+    for (; k < N; k += 2) {
+        const v2d ar = ld2(a_r + k), ai = ld2(a_i + k), br = ld2(b_r + k), bi = ld2(b_i + k);
+        sr[0] += ar * br + ai * bi;
+        si[0] += ar * bi - ai * br;
+    }
+    return make_double2(hsum(sr[0] + sr[1]), hsum(si[0] + si[1]));
+}
+
+// Largest root of the Lanczos tridiagonal by Sturm-sequence bisection,
+// starting from `floor_` (the Ritz values only grow with the step count).
+double ritz_max(const std::vector<double> &al, const std::vector<double> &be, double floor_)
+{
+    const int n = (int)al.size();
+    double lo = al[0], hi = al[0];
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? std::fabs(be[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(be[i]) : 0.0);
+        lo = std::min(lo, al[i] - r);
+        hi = std::max(hi, al[i] + r);
+    }
+    if (floor_ > lo && floor_ < hi) lo = floor_;
+    auto below = [&](double x) {   // eigenvalues of the tridiagonal below x
+        int c = 0;
+        double dd = 1.0;
+        for (int i = 0; i < n; ++i) {
+            dd = al[i] - x - (i > 0 ? be[i - 1] * be[i - 1] / dd : 0.0);
+            if (dd == 0.0) dd = -1e-300;
+            if (dd < 0.0) ++c;
+        }
+        return c;
+    };
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * std::fabs(hi); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (below(mid) >= n)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Largest eigenvalue of the Hermitian positive definite operator `op` (w = op
+// v on padded split vectors of length N, K of them significant) by Lanczos
+// with full reorthogonalisation (classical Gram-Schmidt, repeated once when
+// the first pass cancels more than half of the squared norm: without it, a
+// vector formed after the Krylov space has converged keeps rounding-level
+// components along the earlier ones, and the Ritz values of the next steps
+// overshoot the spectrum), stopped once the largest Ritz value changes by
+// less than 1e-12 relative over five steps (checked at steps 10, 15, ..., at
+// most 40).  On these clustered spectra plain power iterations stay
+// percent-level low after 100 steps; this converges to about 1e-11 in 15-40.
+template <class Op>
+double largest(int K, int N, Op op)
+{
+    const int m = std::min(K, 40);
+    Split Q(m + 1, N), W(1, N);
+    std::vector<double> cr(m + 1), ci(m + 1), al, be;
+    double *wr = W.r(0), *wi = W.i(0);
+    double nv = 0;
+    for (int i = 0; i < K; ++i) {
+        Q.r(0)[i] = 1.0 + 0.01 * i;
+        Q.i(0)[i] = 0.003 * i;
+        nv += Q.r(0)[i] * Q.r(0)[i] + Q.i(0)[i] * Q.i(0)[i];
+    }
+    nv = std::sqrt(nv);
+    for (int i = 0; i < K; ++i) {
+        Q.r(0)[i] /= nv;
+        Q.i(0)[i] /= nv;
+    }
+    double prev = -1.0, lam = 0.0;
+    for (int j = 0; j < m; ++j) {
+        op(Q.r(j), Q.i(j), wr, wi);
+        al.push_back(dotc(N, Q.r(j), Q.i(j), wr, wi).x);
+        double before = dotc(N, wr, wi, wr, wi).x;
+        for (int pass = 0; pass < 2; ++pass) {
+            // c = Q^H w over the j + 1 vectors so far (the rows of Q), then w -= Q^T c.
+            for (int i = 0; i <= j; ++i) {
+                const double2 c = dotc(N, Q.r(i), Q.i(i), wr, wi);
+                cr[i] = c.x;
+                ci[i] = c.y;
+            }
+            for (int i = 0; i <= j; ++i) {
+                const v2d a = v2d{cr[i], cr[i]}, b = v2d{ci[i], ci[i]};
+                const double *ur = Q.r(i), *ui = Q.i(i);
+                for (int k = 0; k < N; k += 2) {
+                    const v2d qr2 = ld2(ur + k), qi2 = ld2(ui + k);
+                    st2(wr + k, ld2(wr + k) - (a * qr2 - b * qi2));
+                    st2(wi + k, ld2(wi + k) - (a * qi2 + b * qr2));
+                }
+            }
+            const double after = dotc(N, wr, wi, wr, wi).x;
+            if (after >= 0.5 * before) break;
+            before = after;
+        }
+        const bool check = j >= 10 && (j % 5 == 0 || j == m - 1);
+        if (check || j == m - 1) {
+            lam = ritz_max(al, be, prev);
+            if (check && prev > 0 && std::fabs(lam - prev) <= 1e-12 * lam) break;
+            prev = lam * (1.0 - 1e-15);   // bisection floor for the next check
+        }
+        const double bn = std::sqrt(dotc(N, wr, wi, wr, wi).x);
+        if (!(bn > 1e-14 * std::fabs(al.back()))) {   // invariant subspace: its Ritz values are exact
+            lam = ritz_max(al, be, prev);
+            break;
+        }
+        be.push_back(bn);
+        for (int k = 0; k < N; ++k) {
+            Q.r(j + 1)[k] = wr[k] / bn;
+            Q.i(j + 1)[k] = wi[k] / bn;
+        }
+    }
+    return lam;
+}
+
+// Largest eigenvalue of D G D (D = diag(G)^{-1/2}, as the factorisation forms it).
+double largest_dgd(const double2 *G, int K)
+{
+    const int N = (K + 1) & ~1;
+    std::vector<double> d(K);
+    for (int i = 0; i < K; ++i) {
+        const double gii = G[(size_t)i * K + i].x;
+        d[i] = gii > 0.0 ? 1.0 / std::sqrt(gii) : 0.0;
+    }
+    Split A(K, N);
+    for (int i = 0; i < K; ++i)
+        for (int k = 0; k < K; ++k) {
+            A.r(i)[k] = G[(size_t)i * K + k].x * d[i] * d[k];
+            A.i(i)[k] = G[(size_t)i * K + k].y * d[i] * d[k];
+        }
+    return largest(K, N, [&](const double *vr, const double *vi, double *wr, double *wi) {
+        matvec(A, K, false, vr, vi, wr, wi);
+    });
+}
+
+// Largest eigenvalue of (L L^H)^{-1} = L^{-H} L^{-1}, from L^{-1} (lower triangle).
+double largest_inverse(const double2 *Linv, int K)
+{
+    const int N = (K + 1) & ~1;
+    Split Li(K, N), T(1, N);
+    for (int i = 0; i < K; ++i)
+        for (int k = 0; k <= i; ++k) {
+            Li.r(i)[k] = Linv[(size_t)i * K + k].x;
+            Li.i(i)[k] = Linv[(size_t)i * K + k].y;
+        }
+    return largest(K, N, [&](const double *vr, const double *vi, double *wr, double *wi) {
+        matvec(Li, K, true, vr, vi, T.r(0), T.i(0));
+        matvec_h_lower(Li, K, T.r(0), T.i(0), wr, wi);
+    });
+}
+
+}  // namespace cond
 
 // Statistics of a problem: ||t - Psi h||^2 and ||t||^2 of the final
 // coefficients (FP32 residual summed in FP64 on the device), queued on s and
@@ -454,10 +576,12 @@ void free_estimate_workspace(EstimateWorkspace &w)
     cudaFree(w.hm64);
     cudaFree(w.Linv);
     cudaFree(w.tmpv);
-    cudaFreeHost(w.h_L);
+    cudaFreeHost(w.h_G);
+    cudaFreeHost(w.h_Linv);
     cudaFreeHost(w.h_info);
     cudaFreeHost(w.h_norm);
     if (w.ev_L) cudaEventDestroy(w.ev_L);
+    if (w.ev_G) cudaEventDestroy(w.ev_G);
     w = EstimateWorkspace();
 }
 
@@ -507,19 +631,25 @@ dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, i
     if (cudaMemcpyAsync(w.probs, &pr, sizeof(pr), cudaMemcpyHostToDevice, s) != cudaSuccess) return DPD_ERR_CUDA;
     if (ortho(h) && (st = compute_basis(h, std::vector<int64_t>{n}, s)) != DPD_OK) return st;
     if ((st = run_gram(h, 1, cpp, precision, s)) != DPD_OK) return st;
-    if (dpd::launch_chol(w.G, 1, h->K, w.L, w.d, w.info, s) != cudaSuccess) return DPD_ERR_CUDA;
-    // The factor and its pivot status go to pinned host memory while the
-    // device carries on: the solves skip a failed factorisation on the device,
-    // and the host condition estimate (Lanczos on L) runs during the
-    // refinement instead of after it.
+    // For the statistics, G and (after the factorisation) the inverse factor go
+    // to pinned host memory while the device carries on, and so does the pivot
+    // status: the host condition estimate (Lanczos on D G D from G, and on its
+    // inverse) runs during the factorisation and the refinement instead of
+    // after them, and the solves skip a failed factorisation on the device.
     const int K = h->K;
-    if (cudaMemcpyAsync(w.h_info, w.info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        (stats && cudaMemcpyAsync(w.h_L, w.L, sizeof(double2) * K * K, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
-        cudaEventRecord(w.ev_L, s) != cudaSuccess)
+    if (stats && (cudaMemcpyAsync(w.h_G, w.G, sizeof(double2) * K * K, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                  cudaEventRecord(w.ev_G, s) != cudaSuccess))
+        return DPD_ERR_CUDA;
+    if (dpd::launch_chol(w.G, 1, h->K, w.L, w.d, w.info, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (cudaMemcpyAsync(w.h_info, w.info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return DPD_ERR_CUDA;
     // The solves go through the explicit inverse of L: two parallel
     // matrix-vector products instead of two K-step sequential chains each.
     if (dpd::launch_chol_invert(w.L, w.info, K, w.Linv, s) != cudaSuccess) return DPD_ERR_CUDA;
+    if ((stats && cudaMemcpyAsync(w.h_Linv, w.Linv, sizeof(double2) * K * K, cudaMemcpyDeviceToHost, s) !=
+                      cudaSuccess) ||
+        cudaEventRecord(w.ev_L, s) != cudaSuccess)
+        return DPD_ERR_CUDA;
     w.use_inverse = true;
     if (dpd::launch_solve_inverse(w.Linv, w.d, w.info, w.g, K, w.tmpv, w.h64, 0, s) != cudaSuccess)
         return DPD_ERR_CUDA;
@@ -529,10 +659,27 @@ dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, i
     if (st != DPD_OK) return st;
     if (dpd::launch_h_to_f32(hm, K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
     if (stats && (st = queue_norms(h, 0, pr.u, pr.t, n, s)) != DPD_OK) return st;
-    double cond = 0.0;
-    if (cudaEventSynchronize(w.ev_L) != cudaSuccess) return DPD_ERR_CUDA;
-    const int info = *w.h_info;
-    if (stats && info == 0) cond = cond_estimate(w.h_L, K);   // overlaps the queued device work
+    // The two Lanczos runs overlap the queued device work: the one on D G D
+    // (a second host thread) as soon as G has landed, the one on the inverse
+    // once the inverse factor has.
+    double lmax = 0.0, linv = 0.0;
+    std::thread dgd_run;
+    bool threaded = false;
+    if (stats) {
+        if (cudaEventSynchronize(w.ev_G) != cudaSuccess) return DPD_ERR_CUDA;
+        try {
+            dgd_run = std::thread([&] { lmax = cond::largest_dgd(w.h_G, K); });
+            threaded = true;
+        } catch (const std::system_error &) {   // no thread available: on this one, below
+        }
+    }
+    const bool synced = cudaEventSynchronize(w.ev_L) == cudaSuccess;
+    const int info = synced ? *w.h_info : 0;
+    if (synced && stats && info == 0) linv = cond::largest_inverse(w.h_Linv, K);
+    if (threaded) dgd_run.join();
+    if (!synced) return DPD_ERR_CUDA;
+    if (stats && !threaded) lmax = cond::largest_dgd(w.h_G, K);
+    const double cond = lmax * linv;
     if (cudaStreamSynchronize(s) != cudaSuccess) return DPD_ERR_CUDA;
     if (info != 0) return DPD_ERR_NOT_SPD;
     if (stats) {

@@ -10,32 +10,44 @@ namespace dpd {
 
 // Column sums over the problem's CTAs of the partial P and Q blocks (rows and
 // columns < D), in FP64 and a fixed order: SPQ[i][c] for c < 2 kGramS.
-__global__ void gram_reduce_kernel(const float *__restrict__ partials, int cpp, int D, double *__restrict__ SPQ)
+constexpr int kReduceGroups = 8;   // partial groups per column, summed by separate warps
+
+__global__ void __launch_bounds__(32 * kReduceGroups) gram_reduce_kernel(const float *__restrict__ partials, int cpp,
+                                                                         int D, double *__restrict__ SPQ)
 {
+    // Lane l of warp g sums partials g, g + 8, g + 16, ... of entry idx in
+    // FP64 (four interleaved sums), then warp 0 adds the eight group sums in
+    // group order: a fixed order, with up to 19 loads in flight per thread
+    // instead of one chain over all partials.
+    __shared__ double grp[kReduceGroups][32];
     const int p = blockIdx.y;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // i * kGramPartCols + c
-    if (idx >= kGramS * kGramPartCols) return;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int idx = blockIdx.x * 32 + lane;   // i * kGramPartCols + c
+    const bool in = idx < kGramS * kGramPartCols;
     const int i = idx / kGramPartCols, c = idx % kGramPartCols, j = c % kGramS;
     double s = 0.0;
-    if (i < D && j < D) {
+    if (in && i < D && j < D) {
         const size_t part = (size_t)kGramRows * kGramPartCols;
         const float *base = partials + (size_t)p * cpp * part + (size_t)i * kGramPartCols + c;
         double s4[4] = {0.0, 0.0, 0.0, 0.0};
-        int k = 0;
-        for (; k + 4 <= cpp; k += 4) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) s4[q] += (double)base[(size_t)(k + q) * part];
-        }
-        for (; k < cpp; ++k) s4[0] += (double)base[(size_t)k * part];
+        int k = g, q = 0;
+        for (; k < cpp; k += kReduceGroups, q = (q + 1) & 3) s4[q] += (double)base[(size_t)k * part];
         s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
-    SPQ[(size_t)p * kGramS * kGramPartCols + idx] = s;
+    grp[g][lane] = s;
+    __syncthreads();
+    if (g == 0 && in) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < kReduceGroups; ++q) t += grp[q][lane];
+        SPQ[(size_t)p * kGramS * kGramPartCols + idx] = t;
+    }
 }
 
 cudaError_t launch_gram_reduce(const float *partials, int nprob, int cpp, int D, double *S, cudaStream_t s)
 {
-    dim3 grid((kGramS * kGramPartCols + 255) / 256, nprob);
-    gram_reduce_kernel<<<grid, 256, 0, s>>>(partials, cpp, D, S);
+    dim3 grid((kGramS * kGramPartCols + 31) / 32, nprob);
+    gram_reduce_kernel<<<grid, 32 * kReduceGroups, 0, s>>>(partials, cpp, D, S);
     count_launch();
     return cudaGetLastError();
 }
@@ -599,23 +611,26 @@ cudaError_t launch_chol_solve(const double2 *L, const double *d, const int *info
 
 // Column j of L^{-1} per CTA: L x = e_j by column-oriented forward
 // substitution.  The CTA first stages the strictly lower triangle of the
-// trailing block L[j:, j:] in shared memory (packed by rows), then one warp
-// runs the K - j steps, lane l holding rows j + l, j + l + 32, ...: step k, the
-// lane of row k finishes x_k = r_k / L_kk and broadcasts it, and every lane
-// subtracts L_ik x_k from its rows i > k.  The columns are independent, so the
-// K CTAs spread the FP64 work of the inverse (K^3/6 complex updates) over as
-// many SMs instead of one; column 0, the longest, bounds the kernel.
-constexpr int kInvRows = 4;   // rows per lane: K <= 128
-constexpr int kInvThreads = 128;
+// trailing block L[j:, j:] in shared memory (packed by rows); thread t then
+// owns row j + t.  Step k: the thread of row k finishes x_k = r_k / L_kk and
+// publishes it, and after one barrier every thread of a row i > k subtracts
+// L_ik x_k.  The rows are spread over four warps, so the FP64 updates of a
+// step (about 2 fused multiply-adds per clock per SM on this GPU, i.e. one
+// warp instruction per 64 clocks in each SM sub-partition) run on all four
+// sub-partitions instead of one.  The columns are independent, so the K CTAs
+// spread the inverse (K^3/6 complex updates) over as many SMs; column 0, the
+// longest, bounds the kernel.
+constexpr int kInvThreads = 128;   // one row per thread: K <= 128
 
 __global__ void __launch_bounds__(kInvThreads) chol_invert_kernel(const double2 *__restrict__ L,
                                                                   const int *__restrict__ info, int K,
                                                                   double2 *__restrict__ Linv)
 {
-    extern __shared__ double2 tri[];   // row i' (i' = i - j) of L[j:, j:] at i'(i'-1)/2, i' entries
+    extern __shared__ double2 tri[];   // row i' (i' = i - j) of L[j:, j:] at i'(i'-1)/2, i' entries; then x
     if (info[0] != 0) return;
-    const int j = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int j = blockIdx.x, tid = threadIdx.x;
     const int m_ = K - j;
+    double2 *xs = tri + (size_t)m_ * (m_ - 1) / 2;   // x_k, published at step k
     for (int e = tid; e < m_ * (m_ - 1) / 2; e += kInvThreads) {
         int ip = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);   // row of packed element e
         while (ip * (ip - 1) / 2 > e) --ip;
@@ -623,43 +638,25 @@ __global__ void __launch_bounds__(kInvThreads) chol_invert_kernel(const double2 
         const int kp = e - ip * (ip - 1) / 2;
         tri[e] = L[(size_t)(j + ip) * K + j + kp];
     }
+    const bool mine = tid < m_;
+    double2 r = make_double2(tid == 0 ? 1.0 : 0.0, 0.0);
+    const double inv_own = mine ? 1.0 / L[(size_t)(j + tid) * K + j + tid].x : 0.0;
+    const double2 *lrow = tri + (size_t)tid * (tid - 1) / 2;   // row tid of the staged triangle
     __syncthreads();
-    if (tid >= 32) return;
-    double2 r[kInvRows];
-    double inv_own[kInvRows];
-#pragma unroll
-    for (int m = 0; m < kInvRows; ++m) {
-        const int ip = lane + 32 * m;
-        r[m] = make_double2(ip == 0 ? 1.0 : 0.0, 0.0);
-        inv_own[m] = ip < m_ ? 1.0 / L[(size_t)(j + ip) * K + j + ip].x : 0.0;
-    }
     for (int kp = 0; kp < m_; ++kp) {
-        const int owner = kp & 31, mo = kp >> 5;
-        double2 xk = make_double2(0.0, 0.0);
-#pragma unroll
-        for (int m = 0; m < kInvRows; ++m)
-            if (m == mo && lane == owner) {   // row k is final: x_k = r_k / L_kk (real diagonal)
-                xk = make_double2(r[m].x * inv_own[m], r[m].y * inv_own[m]);
-                r[m] = xk;
-            }
-        xk.x = __shfl_sync(0xffffffffu, xk.x, owner);
-        xk.y = __shfl_sync(0xffffffffu, xk.y, owner);
-#pragma unroll
-        for (int m = 0; m < kInvRows; ++m) {
-            const int ip = lane + 32 * m;
-            if (ip > kp && ip < m_) {
-                const double2 l = tri[ip * (ip - 1) / 2 + kp];
-                r[m].x = fma(-l.x, xk.x, fma(l.y, xk.y, r[m].x));
-                r[m].y = fma(-l.x, xk.y, fma(-l.y, xk.x, r[m].y));
-            }
+        if (tid == kp) {   // row k is final: x_k = r_k / L_kk (real diagonal)
+            r = make_double2(r.x * inv_own, r.y * inv_own);
+            xs[kp] = r;
+        }
+        __syncthreads();
+        if (mine && tid > kp) {
+            const double2 l = lrow[kp], xk = xs[kp];
+            r.x = fma(-l.x, xk.x, fma(l.y, xk.y, r.x));
+            r.y = fma(-l.x, xk.y, fma(-l.y, xk.x, r.y));
         }
     }
-#pragma unroll
-    for (int m = 0; m < kInvRows; ++m) {   // column j, rows >= j
-        const int ip = lane + 32 * m;
-        if (ip < m_) Linv[(size_t)(j + ip) * K + j] = r[m];
-    }
-    for (int i = lane; i < j; i += 32) Linv[(size_t)i * K + j] = make_double2(0.0, 0.0);
+    if (mine) Linv[(size_t)(j + tid) * K + j] = r;   // column j, rows >= j
+    for (int i = tid; i < j; i += kInvThreads) Linv[(size_t)i * K + j] = make_double2(0.0, 0.0);
 }
 
 // One warp per output element: tmp_i = sum_{k <= i} Linv[i][k] d_k rhs_k
@@ -704,8 +701,8 @@ __global__ void __launch_bounds__(128) inv_matvec_kernel(const double2 *__restri
 
 cudaError_t launch_chol_invert(const double2 *L, const int *info, int K, double2 *Linv, cudaStream_t s)
 {
-    if (K > 32 * kInvRows) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(double2) * (size_t)K * (K - 1) / 2;
+    if (K > kInvThreads) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double2) * ((size_t)K * (K - 1) / 2 + (size_t)K);
     static SmemAttr smem_rec;
     const cudaError_t e = ensure_smem(smem_rec, (const void *)chol_invert_kernel, smem > 0 ? smem : 16);
     if (e != cudaSuccess) return e;
@@ -785,34 +782,39 @@ __global__ void sum_pairs_kernel(const double *__restrict__ part, int nb, double
     }
 }
 
-// Residual and both sums of squares in one pass: e = t - y, and per block
-// sum |e|^2 and sum |t|^2, then one fixed-order final sum (sum_pairs_kernel).
-// The squares of the FP32 samples are formed and summed in FP32 over runs of
-// 32 samples per thread, and the runs are added in FP64 (FP64 arithmetic on
-// this GPU is a small fraction of the FP32 rate); a run's FP32 sum carries at
-// most about 2e-6 relative error, well below what the reported ratio needs.
+// Residual and both sums of squares in one pass: e = t - y (when e is not
+// null), and per block sum |e|^2 and sum |t|^2, then one fixed-order final sum
+// (sum_pairs_kernel).  The squares of the FP32 samples are formed and summed
+// in FP32 over the four samples of a pass, and the passes are added in FP64
+// (FP64 arithmetic on this GPU is a small fraction of the FP32 rate).
 __global__ void residual_norm_kernel(const float2 *__restrict__ t, const float2 *__restrict__ y, int64_t n,
                                      float2 *__restrict__ e, double *__restrict__ part)
 {
+    // Four samples per thread and pass (all loads issued before any use);
+    // e is written only when requested.
     __shared__ double se[256], st[256];
     double a = 0.0, b = 0.0;
-    float a32 = 0.f, b32 = 0.f;
-    int run = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 tv = t[i], yv = y[i];
-        const float2 ev = make_float2(tv.x - yv.x, tv.y - yv.y);
-        e[i] = ev;
-        a32 = fmaf(ev.x, ev.x, fmaf(ev.y, ev.y, a32));
-        b32 = fmaf(tv.x, tv.x, fmaf(tv.y, tv.y, b32));
-        if (++run == 32) {
-            a += (double)a32;
-            b += (double)b32;
-            a32 = b32 = 0.f;
-            run = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        float2 tv[4], yv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t i = i0 + q * stride;
+            tv[q] = i < n ? t[i] : make_float2(0.f, 0.f);
+            yv[q] = i < n ? y[i] : make_float2(0.f, 0.f);
         }
+        float a32 = 0.f, b32 = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 ev = make_float2(tv[q].x - yv[q].x, tv[q].y - yv[q].y);
+            const int64_t i = i0 + q * stride;
+            if (e && i < n) e[i] = ev;
+            a32 = fmaf(ev.x, ev.x, fmaf(ev.y, ev.y, a32));
+            b32 = fmaf(tv[q].x, tv[q].x, fmaf(tv[q].y, tv[q].y, b32));
+        }
+        a += (double)a32;
+        b += (double)b32;
     }
-    a += (double)a32;
-    b += (double)b32;
     se[threadIdx.x] = a;
     st[threadIdx.x] = b;
     __syncthreads();
