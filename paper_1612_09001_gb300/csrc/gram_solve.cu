@@ -699,6 +699,65 @@ __global__ void __launch_bounds__(128) inv_matvec_kernel(const double2 *__restri
     }
 }
 
+// Both products of a solve in one launch: a cluster of kSolveCluster CTAs,
+// warp w of the cluster taking rows w, w + 64, ...  Phase 1: tmp_i =
+// sum_{k <= i} Linv[i][k] d_k rhs_k, each finished element written into every
+// CTA's copy of tmp (distributed shared memory); after the cluster barrier,
+// phase 2: h_k (+)= d_k sum_{i >= k} conj(Linv[i][k]) tmp_i.  The same
+// arithmetic and summation order per element as inv_matvec_kernel.
+constexpr int kSolveCluster = 8;
+constexpr int kSolveThreads = 256;
+
+__global__ void __launch_bounds__(kSolveThreads) solve_inverse_cluster_kernel(const double2 *__restrict__ Linv,
+                                                                              const double *__restrict__ d,
+                                                                              const int *__restrict__ info,
+                                                                              const double2 *__restrict__ rhs, int K,
+                                                                              double2 *__restrict__ h, int accumulate)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ double2 tmp[kCholMaxK];
+    if (info[0] != 0) return;   // the same value for every CTA of the cluster: none reaches the barrier
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)cluster.block_rank() * (kSolveThreads / 32) + (threadIdx.x >> 5);
+    constexpr int NW = kSolveCluster * (kSolveThreads / 32);
+    for (int row = gw; row < K; row += NW) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = lane; k <= row; k += 32) {
+            const double2 l = Linv[(size_t)row * K + k];
+            const double2 b = make_double2(rhs[k].x * d[k], rhs[k].y * d[k]);
+            acc.x = fma(l.x, b.x, fma(-l.y, b.y, acc.x));
+            acc.y = fma(l.x, b.y, fma(l.y, b.x, acc.y));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane < kSolveCluster) *cluster.map_shared_rank(&tmp[row], lane) = acc;
+    }
+    cluster.sync();
+    for (int row = gw; row < K; row += NW) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int i = row + lane; i < K; i += 32) {
+            const double2 l = Linv[(size_t)i * K + row];
+            const double2 b = tmp[i];
+            acc.x = fma(l.x, b.x, fma(l.y, b.y, acc.x));
+            acc.y = fma(l.x, b.y, fma(-l.y, b.x, acc.y));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0) {
+            acc = make_double2(acc.x * d[row], acc.y * d[row]);
+            if (accumulate) acc = make_double2(h[row].x + acc.x, h[row].y + acc.y);
+            h[row] = acc;
+        }
+    }
+}
+
 cudaError_t launch_chol_invert(const double2 *L, const int *info, int K, double2 *Linv, cudaStream_t s)
 {
     if (K > kInvThreads) return cudaErrorInvalidValue;
@@ -715,6 +774,24 @@ cudaError_t launch_solve_inverse(const double2 *Linv, const double *d, const int
                                  double2 *tmp, double2 *h, int accumulate, cudaStream_t s)
 {
     const int grid = (K + 3) / 4;
+    if (K <= kCholMaxK) {   // one cluster launch (see solve_inverse_cluster_kernel)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kSolveCluster);
+        cfg.blockDim = dim3(kSolveThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kSolveCluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, solve_inverse_cluster_kernel, Linv, d, info, rhs, K, h,
+                                                 accumulate);
+        count_launch();
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     inv_matvec_kernel<<<grid, 128, 0, s>>>(Linv, d, info, rhs, K, 0, tmp, 0);
     count_launch();
     cudaError_t e = cudaGetLastError();
