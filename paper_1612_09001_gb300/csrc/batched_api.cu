@@ -62,8 +62,13 @@ dpd_status build_items(dpd_plan p, int V, int warps)
     const int S = warps * 32 * V;
     std::vector<int> order(p->streams.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    // Costliest models first (B T per sample), and streams of the same model
+    // next to each other, so that the items a CTA takes one after another
+    // mostly run the same (B, T) code path.
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return p->streams[a].B * p->streams[a].T > p->streams[b].B * p->streams[b].T;
+        const int ca = p->streams[a].B * p->streams[a].T, cb = p->streams[b].B * p->streams[b].T;
+        if (ca != cb) return ca > cb;
+        return p->streams[a].B > p->streams[b].B;
     });
     std::vector<dpd::BatchItem> items;
     for (int si : order) {
