@@ -11,13 +11,6 @@
 #include "dpd_model.h"
 #include "dpd_batched.cuh"
 
-namespace dpd {
-cudaError_t launch_batched_57(const BatchArgs &a, int V, int warps, int stages, int cps, int sm_count,
-                              cudaStream_t s);
-cudaError_t launch_batched_68(const BatchArgs &a, int V, int warps, int stages, int cps, int sm_count,
-                              cudaStream_t s);
-}  // namespace dpd
-
 struct dpd_plan_s {
     int device = 0, sm_count = 0;
     std::vector<dpd::BatchStream> streams;   // host copy (device pointers, sizes, table offsets)

@@ -14,10 +14,14 @@ __device__ __forceinline__ float2 coef_f32(const double2 *h, int i)
     return make_float2((float)h[i].x, (float)h[i].y);
 }
 
+// blockIdx.x selects a problem of a batch: coefficients hin + x * hstride,
+// table tab + x * tstride (0 for a single table).
 template <typename H>
 __global__ void wl_table_kernel(const H *__restrict__ hin, int Bp, int Bq, int T, int B, float *__restrict__ tab,
-                                float *__restrict__ adj)
+                                float *__restrict__ adj, int hstride = 0, int tstride = 0)
 {
+    hin += (size_t)blockIdx.x * hstride;
+    tab += (size_t)blockIdx.x * tstride;
     auto h = [hin](int i) { return coef_f32(hin, i); };
     const int i = threadIdx.x;   // one thread per (tap k, order index m)
     if (i < T * B) {
@@ -80,12 +84,26 @@ cudaError_t launch_wl_table_f64(const double2 *h, int Bp, int Bq, int T, float *
     return cudaGetLastError();
 }
 
+cudaError_t launch_wl_table_f64_many(const double2 *h, int count, int hstride, int Bp, int Bq, int T, float *tab,
+                                     int tstride, cudaStream_t s)
+{
+    const int B = Bp > Bq ? Bp : Bq;
+    wl_table_kernel<double2><<<count, 64, 0, s>>>(h, Bp, Bq, T, B, tab, nullptr, hstride, tstride);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // One block per coefficient: thread t sums rows t, t + 256, ... in order, then a
 // fixed shared-memory tree combines the 256 sums (deterministic, FP64).
+// blockIdx.y selects a problem of a batch (its rows and outputs follow the
+// previous problem's).
 __global__ void adj_finalize_kernel(const float2 *__restrict__ partials, int rows, int K,
                                     float2 *__restrict__ gh, double2 *__restrict__ gh64)
 {
     const int i = blockIdx.x, t = threadIdx.x;
+    partials += (size_t)blockIdx.y * rows * K;
+    if (gh) gh += (size_t)blockIdx.y * K;
+    if (gh64) gh64 += (size_t)blockIdx.y * K;
     double re = 0.0, im = 0.0;
     for (int r = t; r < rows; r += 256) {
         const float2 v = partials[(size_t)r * K + i];
@@ -119,6 +137,14 @@ cudaError_t launch_adj_finalize(const float2 *partials, int rows, int K, float2 
 cudaError_t launch_adj_finalize64(const float2 *partials, int rows, int K, double2 *out, cudaStream_t s)
 {
     adj_finalize_kernel<<<K, 256, 0, s>>>(partials, rows, K, nullptr, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_finalize64_many(const float2 *partials, int rows, int K, int count, double2 *out,
+                                       cudaStream_t s)
+{
+    adj_finalize_kernel<<<dim3((unsigned)K, (unsigned)count), 256, 0, s>>>(partials, rows, K, nullptr, out);
     count_launch();
     return cudaGetLastError();
 }

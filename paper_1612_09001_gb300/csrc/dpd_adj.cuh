@@ -531,8 +531,8 @@ __global__ void __launch_bounds__(256) adj_gh_kernel(AdjArgs a, int T, int Bp, i
 // released it) with tile i - 1 + stages; the whole warp waits, so that its
 // lanes stay converged.
 template <int B, int TG, int V>
-__global__ void __launch_bounds__(32 * kAdjGhWarps, 1)
-    adj_gh_tma_kernel(AdjArgs a, int stages, int64_t ntiles, int T, int Bp, int Bq, int K)
+__device__ __forceinline__ void adj_gh_tma_body(const AdjArgs &a, int stages, int64_t ntiles, int T, int Bp, int Bq,
+                                                int K)
 {
     constexpr int NA = 4 * B * TG + 2;
     constexpr int NP = NA / 2;
@@ -640,6 +640,26 @@ __global__ void __launch_bounds__(32 * kAdjGhWarps, 1)
                                 a.partials + (size_t)blockIdx.x * K);
 }
 
+template <int B, int TG, int V>
+__global__ void __launch_bounds__(32 * kAdjGhWarps, 1)
+    adj_gh_tma_kernel(AdjArgs a, int stages, int64_t ntiles, int T, int Bp, int Bq, int K)
+{
+    adj_gh_tma_body<B, TG, V>(a, stages, ntiles, T, Bp, Bq, K);
+}
+
+// Many independent problems in one launch (the least-squares refinement of a
+// batch): grid (CTAs per problem, tap groups, problems); problem z's
+// arguments (x, gy, n, its own partials rows, 16-byte aligned buffers) come
+// from args[z].
+template <int B, int TG, int V>
+__global__ void __launch_bounds__(32 * kAdjGhWarps, 1)
+    adj_gh_tma_batched_kernel(const AdjArgs *__restrict__ args, int stages, int T, int Bp, int Bq, int K)
+{
+    constexpr int S = kAdjGhWarps * 32 * V * kAdjGhSub;
+    const AdjArgs a = args[blockIdx.z];
+    adj_gh_tma_body<B, TG, V>(a, stages, (a.n + S - 1) / S, T, Bp, Bq, K);
+}
+
 // ---------------------------------------------------------------- launches
 inline bool adj_staged_ok(const AdjArgs &a)
 {
@@ -733,6 +753,37 @@ cudaError_t launch_adj_gh(const AdjArgs &a, const AdjLaunch &L, int T, int Bp, i
     }
 }
 
+template <int B, int TG>
+cudaError_t launch_adj_gh_batched_tg(const AdjArgs *args, int count, int blocks, int T, int Bp, int Bq, int K,
+                                     cudaStream_t s)
+{
+    constexpr int V = kAdjGhV;
+    constexpr int S = kAdjGhWarps * 32 * V * kAdjGhSub;
+    constexpr int NA = 4 * B * TG + 2;
+    const size_t smem = adj_staged_smem(S, kAdjGhStages, kAdjGhWarps * NA, kAdjGhHalo);
+    static SmemAttr smem_rec;
+    const cudaError_t attr = ensure_smem(smem_rec, (const void *)adj_gh_tma_batched_kernel<B, TG, V>, smem);
+    if (attr != cudaSuccess) return attr;
+    dim3 grid((unsigned)blocks, (unsigned)((T + TG - 1) / TG), (unsigned)count);
+    adj_gh_tma_batched_kernel<B, TG, V><<<grid, 32 * kAdjGhWarps, smem, s>>>(args, kAdjGhStages, T, Bp, Bq, K);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int B>
+cudaError_t launch_adj_gh_batched(const AdjArgs *args, int count, int blocks, int tap_group, int T, int Bp, int Bq,
+                                  int K, cudaStream_t s)
+{
+    switch (tap_group) {
+    case 1: return launch_adj_gh_batched_tg<B, 1>(args, count, blocks, T, Bp, Bq, K, s);
+    case 2: return launch_adj_gh_batched_tg<B, 2>(args, count, blocks, T, Bp, Bq, K, s);
+    case 3: return launch_adj_gh_batched_tg<B, 3>(args, count, blocks, T, Bp, Bq, K, s);
+    case 4: return launch_adj_gh_batched_tg<B, 4>(args, count, blocks, T, Bp, Bq, K, s);
+    case 5: return launch_adj_gh_batched_tg<B, 5>(args, count, blocks, T, Bp, Bq, K, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int B>
 cudaError_t launch_adj_gx(const AdjArgs &a, int T, int sm_count, cudaStream_t s)
 {
@@ -760,6 +811,12 @@ cudaError_t launch_adj_gx(const AdjArgs &a, int T, int sm_count, cudaStream_t s)
         }                                                                                          \
         if (a.partials) return launch_adj_gh<BB>(a, L, T, Bp, Bq, K, s);                           \
         return cudaSuccess;                                                                        \
+    }                                                                                              \
+    template <>                                                                                    \
+    cudaError_t launch_adj_gh_many<BB>(const AdjArgs *args, int count, int blocks, int tap_group,  \
+                                       int T, int Bp, int Bq, int K, cudaStream_t s)               \
+    {                                                                                              \
+        return launch_adj_gh_batched<BB>(args, count, blocks, tap_group, T, Bp, Bq, K, s);          \
     }
 
 }  // namespace dpd

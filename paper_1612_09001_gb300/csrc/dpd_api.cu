@@ -36,6 +36,20 @@ cudaError_t launch_adj_any(int B, const AdjArgs &a, const AdjLaunch &L, int T, i
     }
 }
 
+cudaError_t launch_adj_gh_many_any(int B, const AdjArgs *args, int count, int blocks, int tap_group, int T, int Bp,
+                                   int Bq, int K, cudaStream_t s)
+{
+    switch (B) {
+    case 1: return launch_adj_gh_many<1>(args, count, blocks, tap_group, T, Bp, Bq, K, s);
+    case 2: return launch_adj_gh_many<2>(args, count, blocks, tap_group, T, Bp, Bq, K, s);
+    case 3: return launch_adj_gh_many<3>(args, count, blocks, tap_group, T, Bp, Bq, K, s);
+    case 4: return launch_adj_gh_many<4>(args, count, blocks, tap_group, T, Bp, Bq, K, s);
+    case 5: return launch_adj_gh_many<5>(args, count, blocks, tap_group, T, Bp, Bq, K, s);
+    case 6: return launch_adj_gh_many<6>(args, count, blocks, tap_group, T, Bp, Bq, K, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_zc_any(int B, int T, const FwdArgs &a, bool param_coef, cudaStream_t s)
 {
     switch (B) {

@@ -239,6 +239,13 @@ __host__ __device__ constexpr size_t batch_smem(int warps, int gw, int stages, i
            (size_t)(warps / gw) * stages * batch_slot_bytes(gw * 32 * V);
 }
 
+// One persistent launch over the work items: orders up to 9 (B <= 5) and up
+// to 7 taps (batched_57.cu), or up to 11 and 8 (batched_68.cu).
+cudaError_t launch_batched_57(const BatchArgs &a, int V, int warps, int stages, int cps, int sm_count,
+                              cudaStream_t s);
+cudaError_t launch_batched_68(const BatchArgs &a, int V, int warps, int stages, int cps, int sm_count,
+                              cudaStream_t s);
+
 template <int BMAX, int TMAX, int V>
 cudaError_t launch_batched_impl(const BatchArgs &a, int warps, int stages, int ctas_per_sm, int sm_count,
                                 cudaStream_t s)

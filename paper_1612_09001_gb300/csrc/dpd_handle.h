@@ -40,6 +40,15 @@ struct EstimateWorkspace {
     int *h_info = nullptr;        // pivot status of the factorisation
     double *h_norm = nullptr;     // ||t - Psi h||^2, ||t||^2
     cudaEvent_t ev_G = nullptr;   // h_G has landed
+    // batched refinement (dpd_estimate_batched): per-problem forward tables,
+    // work lists of the batched forward and coefficient-gradient launches
+    float *tabb = nullptr;        // [problems][tstride]
+    size_t tabb_cap = 0;
+    void *bstreams = nullptr;     // dpd::BatchStream [problems]
+    void *bitems = nullptr;       // dpd::BatchItem [items]
+    void *badj = nullptr;         // dpd::AdjArgs [problems]
+    float2 *bpart = nullptr;      // coefficient-gradient partials, [problems][K]
+    size_t bprob_cap = 0, bitems_cap = 0;
     cudaEvent_t ev_L = nullptr;   // h_info (and h_Linv) have landed
 };
 

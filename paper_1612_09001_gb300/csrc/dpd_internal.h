@@ -98,6 +98,14 @@ struct AdjLaunch {
 template <int B>
 cudaError_t launch_adj(const AdjArgs &a, const AdjLaunch &L, int T, int Bp, int Bq, int K, int sm_count,
                        cudaStream_t s);
+// Coefficient gradients of `count` independent problems in one launch (staged
+// kernel; args[z] on the device, 16-byte aligned x and gy, one partials row
+// per CTA of each problem).
+template <int B>
+cudaError_t launch_adj_gh_many(const AdjArgs *args, int count, int blocks, int tap_group, int T, int Bp, int Bq,
+                               int K, cudaStream_t s);
+cudaError_t launch_adj_gh_many_any(int B, const AdjArgs *args, int count, int blocks, int tap_group, int T, int Bp,
+                                   int Bq, int K, cudaStream_t s);
 cudaError_t launch_adj_any(int B, const AdjArgs &a, const AdjLaunch &L, int T, int Bp, int Bq, int K,
                            int sm_count, cudaStream_t s);
 // gh[i] = sum over `rows` rows of partials[row * K + i], accumulated in FP64 in row order.
@@ -113,8 +121,11 @@ cudaError_t launch_fwd_any(int B, int T, const FwdArgs &a, const FwdLaunch &L, i
 
 // Build the forward widely-linear table and the adjoint table from the stacked
 // coefficient vector h (K complex); adj_tab may be null.
-// The forward table straight from FP64 coefficients (rounded to FP32 first).
+// The forward table straight from FP64 coefficients (rounded to FP32 first);
+// _many: `count` problems, coefficients hstride and tables tstride apart.
 cudaError_t launch_wl_table_f64(const double2 *h, int Bp, int Bq, int T, float *tab, cudaStream_t s);
+cudaError_t launch_wl_table_f64_many(const double2 *h, int count, int hstride, int Bp, int Bq, int T, float *tab,
+                                     int tstride, cudaStream_t s);
 cudaError_t launch_wl_table(const float2 *h, int Bp, int Bq, int T, float *tab, float *adj_tab,
                             cudaStream_t s);
 

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/dpd.h"
+#include "dpd_batched.cuh"
 #include "dpd_gram.cuh"
 #include "dpd_handle.h"
 
@@ -273,6 +274,108 @@ dpd_status refine_once(dpd_handle h, int p, const float2 *u, const float2 *t, in
     } else if (dpd::launch_chol_solve(w.L + (size_t)p * K * K, w.d + (size_t)p * K, w.info + p, rhs, 1, K,
                                       w.h64 + (size_t)p * K, 1, s) != cudaSuccess) {
         return DPD_ERR_CUDA;
+    }
+    return DPD_OK;
+}
+
+// Refinement of all problems of a batch together, each step one launch per
+// kernel: the per-problem forward tables, the batched forward filter (6
+// samples per thread, 16 warps in groups of 8, 4 stages) into the residual
+// buffers, e = t - Psi h in place, the coefficient gradients of all problems
+// (one CTA per problem and tap group), their FP64 sums, the basis transform
+// (orthogonal basis) and the batched Cholesky solve.  Needs 16-byte aligned
+// inputs u (the bulk-copy pipelines); the caller checks that.
+dpd_status refine_batched(dpd_handle h, const std::vector<dpd::GramProblem> &probs, int64_t nmax, int iters,
+                          cudaStream_t s)
+{
+    EstimateWorkspace &w = h->est;
+    const int K = h->K, count = (int)probs.size();
+    const int64_t stride = (nmax + 1) & ~int64_t(1);   // keeps every e_p 16-byte aligned
+    const int tfl = dpd::wl_table_floats(h->B, h->T), tstride = (tfl + 3) & ~3;
+    constexpr int V = 6, warps = 16, group = 8, stages = 4;
+    const int S = warps * 32 * V;
+    std::vector<dpd::BatchStream> st((size_t)count);
+    std::vector<dpd::BatchItem> items;
+    std::vector<dpd::AdjArgs> adj((size_t)count);
+    for (int p = 0; p < count; ++p) {
+        float2 *ep = w.e + (size_t)p * stride;
+        st[p] = {probs[p].u, ep, probs[p].n, h->B, h->T, p * tstride, tstride * 4};
+        for (int64_t t = 0; t * S < probs[p].n; ++t) items.push_back({p, (int)t});
+        dpd::AdjArgs &a = adj[p];
+        a.x = probs[p].u;
+        a.gy = ep;
+        a.n = probs[p].n;
+        a.gx = nullptr;
+        a.adj_tab = nullptr;
+        a.host_adj_tab = nullptr;
+        a.status = h->d_status;
+    }
+    if ((size_t)count > w.bprob_cap) {
+        cudaDeviceSynchronize();
+        cudaFree(w.bstreams);
+        cudaFree(w.badj);
+        cudaFree(w.bpart);
+        cudaFree(w.tabb);
+        w.bstreams = w.badj = nullptr;
+        w.bpart = nullptr;
+        w.tabb = nullptr;
+        w.bprob_cap = 0;
+        if (cudaMalloc(&w.bstreams, sizeof(dpd::BatchStream) * count) != cudaSuccess ||
+            cudaMalloc(&w.badj, sizeof(dpd::AdjArgs) * count) != cudaSuccess ||
+            cudaMalloc(&w.bpart, sizeof(float2) * (size_t)count * K) != cudaSuccess ||
+            cudaMalloc(&w.tabb, sizeof(float) * (size_t)count * tstride) != cudaSuccess)
+            return DPD_ERR_ALLOC;
+        w.bprob_cap = (size_t)count;
+    }
+    if (items.size() > w.bitems_cap) {
+        cudaDeviceSynchronize();
+        cudaFree(w.bitems);
+        w.bitems = nullptr;
+        w.bitems_cap = 0;
+        if (cudaMalloc(&w.bitems, sizeof(dpd::BatchItem) * items.size()) != cudaSuccess) return DPD_ERR_ALLOC;
+        w.bitems_cap = items.size();
+    }
+    for (int p = 0; p < count; ++p) adj[p].partials = w.bpart + (size_t)p * K;   // one row per problem
+    // The host vectors are copied before this function returns (synchronous copies).
+    if (cudaMemcpy(w.bstreams, st.data(), sizeof(dpd::BatchStream) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(w.bitems, items.data(), sizeof(dpd::BatchItem) * items.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(w.badj, adj.data(), sizeof(dpd::AdjArgs) * count, cudaMemcpyHostToDevice) != cudaSuccess)
+        return DPD_ERR_CUDA;
+    dpd::BatchArgs ba;
+    ba.streams = static_cast<const dpd::BatchStream *>(w.bstreams);
+    ba.items = static_cast<const dpd::BatchItem *>(w.bitems);
+    ba.nitems = (int)items.size();
+    ba.nstreams = count;
+    ba.tabs = w.tabb;
+    ba.tab_floats = (int64_t)count * tstride;
+    ba.status = h->d_status;
+    ba.gw = group;
+    const bool small = h->B <= 5 && h->T <= 7;
+    dpd_status stt = DPD_OK;
+    for (int it = 0; it < iters; ++it) {
+        const double2 *hm = monomial_h(h, 0, count, s, stt);
+        if (stt != DPD_OK) return stt;
+        if (dpd::launch_wl_table_f64_many(hm, count, K, h->Bp, h->Bq, h->T, w.tabb, tstride, s) != cudaSuccess)
+            return DPD_ERR_CUDA;
+        const cudaError_t fe = small ? dpd::launch_batched_57(ba, V, warps, stages, 0, h->sm_count, s)
+                                     : dpd::launch_batched_68(ba, V, warps, stages, 0, h->sm_count, s);
+        if (fe != cudaSuccess) return DPD_ERR_CUDA;
+        if (dpd::launch_residual_many(static_cast<const dpd::GramProblem *>(w.probs), count, nmax, stride, w.e, s) !=
+            cudaSuccess)
+            return DPD_ERR_CUDA;
+        if (dpd::launch_adj_gh_many_any(h->B, static_cast<const dpd::AdjArgs *>(w.badj), count, 1, h->adj.tap_group,
+                                        h->T, h->Bp, h->Bq, K, s) != cudaSuccess)
+            return DPD_ERR_CUDA;
+        if (dpd::launch_adj_finalize64_many(w.bpart, 1, K, count, w.delta, s) != cudaSuccess) return DPD_ERR_CUDA;
+        const double2 *rhs = w.delta;   // Psi^H (t - Psi h) in the monomial basis
+        if (ortho(h)) {                 // W^T of it, the right-hand sides in the working basis
+            if (dpd::launch_basis_transform(w.delta, w.hm64, w.ubasis64, count, K, h->Bp, h->Bq, h->T, 0, s) !=
+                cudaSuccess)
+                return DPD_ERR_CUDA;
+            rhs = w.hm64;
+        }
+        if (dpd::launch_chol_solve(w.L, w.d, w.info, rhs, count, K, w.h64, 1, s) != cudaSuccess) return DPD_ERR_CUDA;
     }
     return DPD_OK;
 }
@@ -576,6 +679,11 @@ void free_estimate_workspace(EstimateWorkspace &w)
     cudaFree(w.hm64);
     cudaFree(w.Linv);
     cudaFree(w.tmpv);
+    cudaFree(w.tabb);
+    cudaFree(w.bstreams);
+    cudaFree(w.bitems);
+    cudaFree(w.badj);
+    cudaFree(w.bpart);
     cudaFreeHost(w.h_G);
     cudaFreeHost(w.h_Linv);
     cudaFreeHost(w.h_info);
@@ -704,7 +812,12 @@ dpd_status dpd_estimate_batched(dpd_handle h, const void *const *u, const void *
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int cpp = gram_cpp(h, count, nmax, precision);
-    dpd_status st = reserve(h, count, cpp, refine_iters > 0 ? nmax : 0);
+    // Refinement of all problems together needs 16-byte aligned inputs and one
+    // residual buffer per problem; otherwise the problems are refined one by one.
+    bool together = refine_iters > 0 && count > 1;
+    for (int i = 0; i < count && together; ++i) together = (reinterpret_cast<uintptr_t>(u[i]) & 15u) == 0;
+    const int64_t nsamp = refine_iters > 0 ? (together ? ((nmax + 1) & ~int64_t(1)) * count : nmax) : 0;
+    dpd_status st = reserve(h, count, cpp, nsamp);
     if (st != DPD_OK) return st;
     EstimateWorkspace &w = h->est;
     if (cudaMemcpy(w.probs, probs.data(), sizeof(dpd::GramProblem) * count, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -720,9 +833,14 @@ dpd_status dpd_estimate_batched(dpd_handle h, const void *const *u, const void *
         return DPD_ERR_CUDA;
     bool any_bad = false;
     for (int i = 0; i < count; ++i) any_bad |= info[i] != 0;
-    for (int it = 0; it < refine_iters; ++it)
-        for (int p = 0; p < count; ++p)
-            if (info[p] == 0 && (st = refine_once(h, p, probs[p].u, probs[p].t, probs[p].n, s)) != DPD_OK) return st;
+    if (together) {   // problems that did not factor keep unspecified coefficients
+        if ((st = refine_batched(h, probs, nmax, refine_iters, s)) != DPD_OK) return st;
+    } else {
+        for (int it = 0; it < refine_iters; ++it)
+            for (int p = 0; p < count; ++p)
+                if (info[p] == 0 && (st = refine_once(h, p, probs[p].u, probs[p].t, probs[p].n, s)) != DPD_OK)
+                    return st;
+    }
     const double2 *hm = monomial_h(h, 0, count, s, st);
     if (st != DPD_OK) return st;
     if (dpd::launch_h_to_f32(hm, count * h->K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
