@@ -469,6 +469,23 @@ def measure_grad(dev, log2_n=24, reps=20):
             torch.cuda.synchronize(dev)
             us = e0.elapsed_time(e1) * 1e3 / reps
             row[name] = {"us": us, "gsamples_per_s": n / us / 1e3}
+        # Coefficients set from device memory: the derived tables are copied
+        # back to host memory behind the set, and once that copy has landed the
+        # input gradient takes them by value as well.
+        f.set_coeffs(torch.from_numpy(synth.coeffs(Pm, Qm, Mm, key=(0, 1)).astype("complex64")).to(dev))
+        torch.cuda.synchronize(dev)
+        for _ in range(3):
+            f.grad(x, gy, gx=gx)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            f.grad(x, gy, gx=gx)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        us = e0.elapsed_time(e1) * 1e3 / reps
+        row["gx_device_set_coeffs"] = {"us": us, "gsamples_per_s": n / us / 1e3}
         f.sync_status()
         f.close()
         # The allocation-free entry point (no handle: plain-load kernel) on the

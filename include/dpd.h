@@ -88,6 +88,13 @@ dpd_status dpd_num_coeffs(dpd_handle h, int *K);
  * so it must not be captured in a CUDA graph); device buffers are read by a
  * kernel on `stream` without synchronising (capturable), so they must stay
  * valid until that kernel has run.  The caller keeps ownership.
+ * The kernels take the prepared tables as launch arguments when a host copy
+ * exists, else read them from device memory (same results, bit for bit).  After
+ * a device-side set outside graph capture the tables are copied back to pinned
+ * host memory behind the set, without waiting; calls made once that copy has
+ * landed (checked without blocking) take them as arguments.  A CUDA graph
+ * captured after a host-side set keeps those coefficients; one captured after
+ * a device-side set reads the tables on the device at every replay.
  * K must equal dpd_num_coeffs.  Work is ordered on `stream`: later calls on
  * the same stream see the new coefficients.
  */

@@ -166,6 +166,12 @@ dpd_status dpd_create(int P, int Q, int M, dpd_handle *out)
         dpd_destroy(f);
         return DPD_ERR_ALLOC;
     }
+    if (cudaMallocHost(&f->h_tab_pin, sizeof(float) * dpd::wl_table_floats(f->B, f->T)) != cudaSuccess ||
+        cudaMallocHost(&f->h_adj_pin, sizeof(float) * dpd::adj_table_floats(f->B, f->T)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f->ev_tab, cudaEventDisableTiming) != cudaSuccess) {
+        dpd_destroy(f);
+        return DPD_ERR_ALLOC;
+    }
     if (cudaMemset(f->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(f->d_hist, 0, sizeof(float2) * dpd::kHalo) != cudaSuccess) {
         dpd_destroy(f);
@@ -185,11 +191,48 @@ dpd_status dpd_destroy(dpd_handle h)
     cudaFree(h->d_status);
     cudaFree(h->d_hist);
     cudaFree(h->d_loss_part);
+    cudaFreeHost(h->h_tab_pin);
+    cudaFreeHost(h->h_adj_pin);
+    if (h->ev_tab) cudaEventDestroy(h->ev_tab);
     free_estimate_workspace(h->est);
     free_host_pipeline(h->host);
     delete h;
     return DPD_OK;
 }
+
+namespace {
+
+bool capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+}
+
+// Whether launches on `s` may pass the coefficient tables by value (kernel
+// parameter bank).  Coefficients set from host memory: always.  Coefficients
+// set from device memory: once the queued copy of the derived tables back to
+// host memory has landed, and not while `s` is being captured -- a captured
+// graph then keeps reading the tables on the device at every replay, as it
+// did before the copy existed.
+bool param_tables(dpd_handle h, cudaStream_t s)
+{
+    if (h->tab_pending && !capturing(s)) {
+        const cudaError_t q = cudaEventQuery(h->ev_tab);
+        if (q == cudaSuccess) {
+            std::memcpy(h->h_tab.v, h->h_tab_pin, sizeof(float) * dpd::wl_table_floats(h->B, h->T));
+            std::memcpy(h->h_adj_tab, h->h_adj_pin, sizeof(float) * dpd::adj_table_floats(h->B, h->T));
+            h->host_tab_valid = true;
+            h->tab_from_device = true;
+            h->tab_pending = false;
+        } else if (q != cudaErrorNotReady) {
+            (void)cudaGetLastError();   // the copy failed: keep reading the device tables
+            h->tab_pending = false;
+        }
+    }
+    return h->host_tab_valid && !(h->tab_from_device && capturing(s));
+}
+
+}  // namespace
 
 dpd_status dpd_num_coeffs(dpd_handle h, int *K)
 {
@@ -217,8 +260,22 @@ dpd_status dpd_set_coeffs(dpd_handle h, const void *coeffs, int K, int where, vo
         src = h->d_h;
     }
     h->host_tab_valid = false;
+    h->tab_from_device = false;
+    h->tab_pending = false;
     cudaError_t e = dpd::launch_wl_table(src, h->Bp, h->Bq, h->T, h->d_tab, h->d_adj_tab, s);
     if (e != cudaSuccess) return DPD_ERR_CUDA;
+    if (where == DPD_DEVICE && !capturing(s)) {
+        // Copy the derived tables back to pinned host memory without waiting:
+        // later calls pass them by value once the copy has landed.
+        if (cudaMemcpyAsync(h->h_tab_pin, h->d_tab, sizeof(float) * dpd::wl_table_floats(h->B, h->T),
+                            cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+            cudaMemcpyAsync(h->h_adj_pin, h->d_adj_tab, sizeof(float) * dpd::adj_table_floats(h->B, h->T),
+                            cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+            cudaEventRecord(h->ev_tab, s) == cudaSuccess)
+            h->tab_pending = true;
+        else
+            return DPD_ERR_CUDA;
+    }
     if (where == DPD_HOST) {
         // Keep host copies of the tables so that dpd_apply and dpd_grad can pass
         // them by value.
@@ -239,10 +296,10 @@ dpd_status dpd_set_coeffs(dpd_handle h, const void *coeffs, int K, int where, vo
 // give every SM a few tiles gets 4 samples per thread and fewer warps per tile
 // (tiles of 128 to 512 samples): such calls are bound by latency, and more,
 // smaller tiles spread them over more SMs.
-static dpd::FwdLaunch launch_for(dpd_handle h, int64_t n)
+static dpd::FwdLaunch launch_for(dpd_handle h, int64_t n, bool param_tab)
 {
     dpd::FwdLaunch L = h->fwd;
-    if (!h->host_tab_valid) L.mode &= ~dpd::kModeParamCoef;
+    if (!param_tab) L.mode &= ~dpd::kModeParamCoef;
     const int64_t tile = (int64_t)L.warps * 32 * L.V;
     if (h->fwd_auto && (n + tile - 1) / tile < 4 * (int64_t)h->sm_count) {
         L.V = 4;
@@ -274,8 +331,9 @@ dpd_status dpd_apply(dpd_handle h, const void *x, void *y, int64_t n, void *stre
     a.tab = h->d_tab;
     a.status = h->d_status;
     a.vec_store = aligned(y, 16) ? 1 : 0;
-    a.host_tab = h->host_tab_valid ? &h->h_tab : nullptr;
-    dpd::FwdLaunch L = launch_for(h, n);
+    const bool pt = param_tables(h, static_cast<cudaStream_t>(stream));
+    a.host_tab = pt ? &h->h_tab : nullptr;
+    dpd::FwdLaunch L = launch_for(h, n, pt);
     if (!aligned(x, 16)) {
         // 8-byte aligned input: plain-load kernel (built for V = 4)
         L.use_tma = 0;
@@ -314,7 +372,7 @@ dpd_status dpd_grad(dpd_handle h, const void *x, const void *gy, int64_t n, void
     a.partials = gh ? h->d_partials : nullptr;
     a.adj_tab = h->d_adj_tab;
     a.status = h->d_status;
-    a.host_adj_tab = h->host_tab_valid ? h->h_adj_tab : nullptr;
+    a.host_adj_tab = param_tables(h, s) ? h->h_adj_tab : nullptr;
     dpd::AdjLaunch L = h->adj;
     int64_t need = (n + 1023) / 1024;
     if (L.gh_blocks > need) L.gh_blocks = (int)need;
@@ -405,13 +463,14 @@ dpd_status apply_zero_copy(dpd_handle h, const void *x, void *y, int64_t n, cuda
     a.tab = h->d_tab;
     a.status = h->d_status;
     a.vec_store = 0;
-    a.host_tab = h->host_tab_valid ? &h->h_tab : nullptr;
+    const bool pt = param_tables(h, stream);
+    a.host_tab = pt ? &h->h_tab : nullptr;
     if (aligned(a.x, 16) && aligned(a.y, 16))   // staged, coalesced 16-byte accesses
-        return cuda_status(dpd::launch_zc_any(h->B, h->T, a, h->host_tab_valid, stream));
+        return cuda_status(dpd::launch_zc_any(h->B, h->T, a, pt, stream));
     dpd::FwdLaunch L = h->fwd;
     L.use_tma = 0;   // 8-byte aligned buffers: plain loads and stores straight to host memory
     L.V = 4;
-    L.mode &= dpd::kModePackedFma | (h->host_tab_valid ? dpd::kModeParamCoef : 0);
+    L.mode &= dpd::kModePackedFma | (pt ? dpd::kModeParamCoef : 0);
     return cuda_status(dpd::launch_fwd_any(h->B, h->T, a, L, h->sm_count, stream));
 }
 
@@ -450,6 +509,7 @@ dpd_status apply_pipelined(dpd_handle h, const void *x, void *y, int64_t n, cuda
     dpd_status st = ensure_pipeline(h);
     if (st != DPD_OK) return st;
     HostPipeline &P = h->host;
+    const bool pt = param_tables(h, stream);
     if (cudaEventRecord(P.start, stream) != cudaSuccess) return DPD_ERR_CUDA;
     for (int i = 0; i < kHostSlots; ++i)
         if (cudaStreamWaitEvent(P.streams[i], P.start, 0) != cudaSuccess) return DPD_ERR_CUDA;
@@ -471,9 +531,9 @@ dpd_status apply_pipelined(dpd_handle h, const void *x, void *y, int64_t n, cuda
         a.tab = h->d_tab;
         a.status = h->d_status;
         a.vec_store = 1;
-        a.host_tab = h->host_tab_valid ? &h->h_tab : nullptr;
+        a.host_tab = pt ? &h->h_tab : nullptr;
         dpd::FwdLaunch L = h->fwd;
-        if (!h->host_tab_valid) L.mode &= ~dpd::kModeParamCoef;
+        if (!pt) L.mode &= ~dpd::kModeParamCoef;
         if (dpd::launch_fwd_any(h->B, h->T, a, L, h->sm_count, s) != cudaSuccess) return DPD_ERR_CUDA;
         if (cudaMemcpyAsync(ys + c0, P.out[slot] + hs, sizeof(float2) * len, cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return DPD_ERR_CUDA;

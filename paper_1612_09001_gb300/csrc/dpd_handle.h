@@ -77,9 +77,14 @@ struct dpd_filter {
     float2 *d_partials;  // coefficient-gradient workspace: rows_max x K complex
     int rows_max;
     bool has_coeffs;
-    bool host_tab_valid;  // h_tab / h_adj_tab mirror d_tab / d_adj_tab (coefficients set from host memory)
+    bool host_tab_valid;  // h_tab / h_adj_tab mirror d_tab / d_adj_tab
+    bool tab_from_device = false;   // ... copied back after a device-side dpd_set_coeffs
+    bool tab_pending = false;       // a copy back is queued (ev_tab marks its end)
     dpd::HostTab h_tab;
     float h_adj_tab[dpd::kMaxAdjTabFloats];
+    float *h_tab_pin = nullptr;     // pinned landing buffers of the copy back
+    float *h_adj_pin = nullptr;
+    cudaEvent_t ev_tab = nullptr;
     dpd::FwdLaunch fwd;
     bool fwd_auto = true;
     int est_basis = 0;      // DPD_BASIS_MONOMIAL or DPD_BASIS_ORTHOGONAL (least-squares estimates)   // default launch shape: shrink the tile for short inputs (off once set explicitly)

@@ -230,3 +230,35 @@ def test_autograd_function_matches_torch_autograd(P, Q, M):
     assert rel_err(yd.detach().cpu().numpy(), yc.detach().numpy()) < 1e-5
     assert rel_err(xd.grad.cpu().numpy(), xc.grad.numpy()) < 1e-5
     assert rel_err(hd.grad.cpu().numpy(), hc.grad.numpy()) < 1e-5
+
+
+def test_device_set_coefficients_use_the_same_tables():
+    """Coefficients set from device memory: the tables are copied back behind
+    the set; gradients before the copy has landed (tables read on the device)
+    and after (tables passed by value) are bitwise equal, and equal to those of
+    the same coefficients set from host memory."""
+    P, Q, M = 9, 9, 4
+    n = 100003
+    x = torch.from_numpy(synth.ofdm2(n, key=(95, 0))).cuda()
+    gy = torch.from_numpy(synth.ofdm2(n, key=(95, 1))).cuda()
+    h = synth.coeffs(P, Q, M, key=(95, 2)).astype(np.complex64)
+    f = dpd.DPD(P, Q, M)
+    f.set_coeffs(torch.from_numpy(h).cuda())
+    gh0 = torch.empty(f.K, dtype=torch.complex64, device="cuda")
+    gx0 = torch.empty_like(x)
+    f.grad(x, gy, gh=gh0, gx=gx0)          # queued right behind the set
+    torch.cuda.synchronize()
+    gh1 = torch.empty_like(gh0)
+    gx1 = torch.empty_like(x)
+    f.grad(x, gy, gh=gh1, gx=gx1)          # the copy back has landed
+    f.sync_status()
+    g = dpd.DPD(P, Q, M)
+    g.set_coeffs(h)                        # host memory
+    gh2 = torch.empty_like(gh0)
+    gx2 = torch.empty_like(x)
+    g.grad(x, gy, gh=gh2, gx=gx2)
+    g.sync_status()
+    for a, b in ((gx0, gx1), (gx1, gx2), (gh0, gh1), (gh1, gh2)):
+        assert torch.equal(a, b)
+    f.close()
+    g.close()
