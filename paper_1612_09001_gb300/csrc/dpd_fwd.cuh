@@ -236,7 +236,7 @@ __host__ __device__ constexpr size_t fwd_tma_smem(int warps, int gw, int stages)
 struct FwdShape {
     int warps, gw, stages;
 };
-constexpr FwdShape kFwdShapes[] = {{0, 0, 0}, {16, 4, 4}, {12, 3, 3}, {12, 2, 4}};
+constexpr FwdShape kFwdShapes[] = {{0, 0, 0}, {16, 4, 4}, {12, 3, 3}, {12, 2, 4}, {16, 8, 4}};
 constexpr int kFwdNumShapes = sizeof(kFwdShapes) / sizeof(kFwdShapes[0]);
 
 template <int SH>
@@ -478,6 +478,7 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
                 if (sh == 1) kern = fwd_tma_kernel<B, T, V, MODE, 1>;
                 if (sh == 2) kern = fwd_tma_kernel<B, T, V, MODE, 2>;
                 if (sh == 3) kern = fwd_tma_kernel<B, T, V, MODE, 3>;
+                if (sh == 4) kern = fwd_tma_kernel<B, T, V, MODE, 4>;
             }
             static SmemAttr smem_rec[kFwdNumShapes];   // per instantiation
             cudaError_t ae = ensure_smem(smem_rec[sh], (const void *)kern, smem);

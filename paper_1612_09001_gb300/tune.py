@@ -32,6 +32,7 @@ FWD_CANDIDATES = ([dict(mode=m, V=V, warps=w, stages=s, ctas_per_sm=0, use_tma=1
                    for m in (3, 2) for V in (8, 4) for (w, g) in ((12, 1), (12, 2), (12, 3), (12, 4), (12, 6),
                                                                  (16, 1), (16, 2), (16, 4), (16, 8))
                    for s in (3, 4)] +
+
                   [dict(mode=3, V=6, warps=w, stages=s, ctas_per_sm=0, use_tma=1, group=g)
                    for (w, g) in ((8, 0), (12, 0), (12, 2), (12, 3), (12, 4), (16, 2), (16, 4), (16, 8))
                    for s in (3, 4)])

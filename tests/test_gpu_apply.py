@@ -133,10 +133,10 @@ def test_compute_modes(P, Q, M, mode, V, use_tma, host_coeffs):
 
 
 @pytest.mark.parametrize("P,Q,M", [(9, 9, 4), (5, 5, 2), (7, 7, 3), (11, 11, 7)])
-@pytest.mark.parametrize("warps,group,stages", [(16, 4, 4), (12, 3, 3), (12, 2, 4), (16, 2, 3)])
+@pytest.mark.parametrize("warps,group,stages", [(16, 4, 4), (12, 3, 3), (12, 2, 4), (16, 8, 4), (16, 2, 3)])
 def test_grouped_shapes(P, Q, M, warps, group, stages):
     """The grouped ring at the shapes the library builds with compile-time
-    tile arithmetic (16/4/4, 12/3/3, 12/2/4 for the benchmarked models) and a
+    tile arithmetic (16/4/4, 12/3/3, 12/2/4, 16/8/4 for the benchmarked models) and a
     runtime one (16/2/3), with parameter-bank coefficients (mode 3), on sizes
     that end inside a group's sub-tile, on a group boundary and past one."""
     h = synth.coeffs(P, Q, M, key=(9, 1), f_std=0.3, g_std=0.3)
