@@ -14,18 +14,20 @@
 //   d = B T + b T + k    Im psi_b(u_{n-k})
 //   d = 2 B T            1
 //   d = 2 B T + 1, + 2   Re t, Im t
-// and S = X^T X (D x D, D <= 99) holds all of A^T A up to signs.  S is a dense
-// contraction over the n rows, so it runs on the tensor cores: each CTA
-// generates R rows of X at a time (the basis, recomputed from u, never stored
-// in global memory) into shared memory as operand rows (one per distinct
-// column, K-major, 128-byte swizzle), split into a high and a low part (BF16
-// or TF32), X = hi + lo.  The split product hi^T hi + hi^T lo + lo^T hi is
-// P + Q + Q^T with P = hi^T hi and Q = hi^T lo, and one MMA with A = hi
-// (128 rows) and B = [hi; lo] (256 rows) yields [P | Q]: one 128 x 256 tcgen05
-// MMA per K step, accumulating in tensor memory (FP32).  Each CTA writes its
-// partial P and Q; S = P + Q + Q^T is summed in FP64 in a fixed order.  The K x K system is then equilibrated and factored in FP64
-// (Cholesky), and refined against the FP32 residual t - Psi h computed by the
-// filter and adjoint kernels.
+// and S = X^T X (D x D, D <= 99) holds all of A^T A up to signs.
+//
+// S is a contraction over the n rows, run on the tensor cores.  Every distinct
+// column is one of 15 signals (Re / Im psi_b, Re / Im t, the constant) read at
+// a tap, so an entry of S is a lagged correlation of two signals, less the
+// products that fall off the end of the record; the tensor kernel computes the
+// 15 x 14 x 8 lagged correlations (the basis recomputed from u, never stored
+// in global memory), as a polyphase product whose operands hold each signal
+// once per sample, split into a high and a low part (BF16 or TF32), X = hi +
+// lo, with hi hi + hi lo + lo hi summed in FP32 in tensor memory.  Per-CTA
+// partial sums are added in FP64 in a fixed order and S is filled from them
+// and the last samples of the record.  The K x K system is then equilibrated
+// and factored in FP64 (Cholesky), and refined against the FP32 residual
+// t - Psi h computed by the filter and adjoint kernels.
 #pragma once
 
 #include "dpd_internal.h"
@@ -68,7 +70,8 @@ struct GramArgs {
     int nprob;
     int cpp;               // CTAs per problem (row chunks)
     int Bp, Bq, T, K;
-    float *partials;       // [nprob * cpp][kGramRows][kGramPartCols]
+    float *partials;       // FP32 kernel: [nprob * cpp][kGramRows][kGramPartCols] floats;
+                           // tensor kernel: [nprob * cpp][kLagEntries] doubles
     int *status;
     // Basis of the psi columns: per problem a kMaxB x kMaxB matrix U (row-major,
     // U[a][b] multiplies |u|^{2a} u in basis function b, upper triangular), or
@@ -84,6 +87,12 @@ cudaError_t launch_gram(int precision, const GramArgs &a, cudaStream_t s);
 // S[p][i][c] (i < D, c < 2 kGramS) = sum over the problem's CTAs of the partial P and Q
 // blocks, in FP64 and a fixed order (S = P + Q + Q^T is formed by the assembly).
 cudaError_t launch_gram_reduce(const float *partials, int nprob, int cpp, int D, double *S, cudaStream_t s);
+// Tensor-core precisions: each CTA's partial is kLagEntries FP64 lag sums
+// C[a][b][d] (a < 15, b < 14, d < kMaxT); this sums them per problem into C (FP64, fixed
+// order) and fills S (P block, Q = 0) from them and the end of each record.
+constexpr int kLagEntries = 15 * 14 * kMaxT;
+cudaError_t launch_gram_lag_finish(const float *partials, const GramProblem *probs, const float *ubasis, int nprob,
+                                   int cpp, int B, int T, double *C, double *S, cudaStream_t s);
 // G (K x K, row-major), g (K) and t^H t per problem from S.
 cudaError_t launch_gram_assemble(const double *S, int nprob, int K, int Bp, int B, int T, double2 *G, double2 *g,
                                  double *tt, cudaStream_t s);

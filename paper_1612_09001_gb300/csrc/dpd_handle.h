@@ -16,6 +16,7 @@ struct EstimateWorkspace {
     void *probs = nullptr;        // GramProblem[nprob]
     float *partials = nullptr;    // [nprob * cpp][kGramRows][kGramPartCols]
     double *S = nullptr;          // [nprob][kGramS][kGramPartCols]: summed P and Q blocks
+    double *Clag = nullptr;       // [nprob][kLagEntries]: summed lag sums (tensor-core Gram)
     double2 *G = nullptr, *g = nullptr, *L = nullptr, *h64 = nullptr, *delta = nullptr;
     double *d = nullptr, *tt = nullptr;
     int *info = nullptr;

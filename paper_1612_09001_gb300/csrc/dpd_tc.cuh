@@ -54,6 +54,20 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t smem_addr)
     return d;
 }
 
+// Shared-memory matrix descriptor, K-major operand without swizzle: core
+// matrices of 8 rows x 16 bytes (128 contiguous bytes, row i at 16 i), `lbo`
+// bytes apart along K and `sbo` bytes apart from one 8-row group to the next.
+// Same fields as above, layout 0.
+__device__ __forceinline__ uint64_t umma_desc_kmajor(uint32_t smem_addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // version; layout bits 61-63 stay 0 (no swizzle)
+    return d;
+}
+
 // Byte offset of the 16-byte chunk `ch` (0..7) of row `row` inside a K-major
 // 128-byte-swizzled tile whose rows are 128 bytes.
 __device__ __forceinline__ uint32_t sw128_offset(int row, int ch)

@@ -39,7 +39,7 @@ dpd_status reserve(dpd_handle h, int nprob, int cpp, int64_t nsamp)
         const size_t np = (size_t)nprob, parts = (size_t)nprob * cpp;
         ok = ok && grow(reinterpret_cast<dpd::GramProblem *&>(w.probs), 0, np);
         ok = ok && grow(w.partials, 0, parts * dpd::kGramRows * dpd::kGramPartCols);
-        ok = ok && grow(w.S, 0, np * dpd::kGramS * dpd::kGramPartCols);
+        ok = ok && grow(w.S, 0, np * dpd::kGramS * dpd::kGramPartCols) && grow(w.Clag, 0, np * dpd::kLagEntries);
         ok = ok && grow(w.G, 0, np * K * K) && grow(w.L, 0, np * K * K);
         ok = ok && grow(w.g, 0, np * K) && grow(w.h64, 0, np * K) && grow(w.delta, 0, np * K);
         ok = ok && grow(w.d, 0, np * K) && grow(w.tt, 0, np) && grow(w.info, 0, np);
@@ -183,7 +183,11 @@ dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_
     a.ubasis = ortho(h) ? w.ubasis : nullptr;
     if (dpd::launch_gram(precision, a, s) != cudaSuccess) return DPD_ERR_CUDA;
     const int D = dpd::gram_distinct(h->B, h->T);
-    if (dpd::launch_gram_reduce(w.partials, nprob, cpp, D, w.S, s) != cudaSuccess) return DPD_ERR_CUDA;
+    const cudaError_t e = precision == dpd::kPrecFP32
+                              ? dpd::launch_gram_reduce(w.partials, nprob, cpp, D, w.S, s)
+                              : dpd::launch_gram_lag_finish(w.partials, a.probs, a.ubasis, nprob, cpp, h->B, h->T,
+                                                            w.Clag, w.S, s);
+    if (e != cudaSuccess) return DPD_ERR_CUDA;
     if (dpd::launch_gram_assemble(w.S, nprob, h->K, h->Bp, h->B, h->T, w.G, w.g, w.tt, s) != cudaSuccess)
         return DPD_ERR_CUDA;
     return DPD_OK;
@@ -658,6 +662,7 @@ void free_estimate_workspace(EstimateWorkspace &w)
 {
     cudaFree(w.probs);
     cudaFree(w.partials);
+    cudaFree(w.Clag);
     cudaFree(w.S);
     cudaFree(w.G);
     cudaFree(w.g);

@@ -1,6 +1,8 @@
 // Gram contraction S = X^T X of the distinct real columns of the basis (see
-// dpd_gram.cuh): tcgen05 tensor-core kernel with split BF16 / TF32 operands,
-// and the plain FP32 CUDA-core form it is compared against.
+// dpd_gram.cuh): the tcgen05 tensor-core kernel (lagged correlations of the
+// basis and target signals, split BF16 / TF32 operands) with the kernels that
+// turn its sums into S, and the plain FP32 CUDA-core form it is compared
+// against.
 #include <cuda_bf16.h>
 
 #include "dpd_gram.cuh"
@@ -10,48 +12,7 @@ namespace dpd {
 
 namespace {
 
-// ------------------------------------------------------------------ the basis
-// Every distinct column is one of 15 "series" -- Re / Im of psi_b(u_j) for
-// b < 6, Re / Im of t, or the constant 1 -- read at stage row rr from element
-// w = rr + off, off = T-1-k for a tap-k column and T-1 for the others.
-// Element w of a stage is sample n0 - (T-1) + w.
-constexpr int kSeries = 15;
-constexpr int kSerT = 12;      // Re t = 12, Im t = 13
-constexpr int kSerOne = 14;
-constexpr int kSerLen = 72;    // elements per series (>= 64 + kMaxT - 1, even)
-// Per series: BF16: hi, hi shifted by one, lo, lo shifted by one (16-bit each);
-// TF32: hi, lo (32-bit each).  Both 4 * kSerLen * 2 bytes.
-constexpr int kSerBytes = 4 * kSerLen * 2;
-constexpr int kStagingBytes = kSeries * kSerBytes;
-constexpr int kPsiStride = 64 + kMaxT - 1;
-
-__device__ __forceinline__ void distinct_source(int d, int B, int T, int &series, int &off)
-{
-    const int BT = B * T;
-    if (d < 2 * BT) {
-        const int im = d >= BT ? 1 : 0, dd = im ? d - BT : d;
-        series = 2 * (dd / T) + im;
-        off = T - 1 - dd % T;
-    } else {
-        series = d == 2 * BT ? kSerOne : kSerT + (d - 2 * BT - 1);
-        off = T - 1;
-    }
-}
-
-// Series work of a stage is spread over the 512 threads: threads
-// 0 .. 6 kSerLen - 1 own element w = tid % kSerLen of the psi series of order
-// b = tid / kSerLen (Re and Im); threads 6 kSerLen .. 511 own target row
-// rr = tid - 6 kSerLen (Re t, Im t and the constant).
-constexpr int kPsiThreads = kMaxB * kSerLen;   // 432
-static_assert(512 - kPsiThreads >= 64, "a target row per remaining thread");
-
-// The raw samples of a stage (kSerLen basis samples from n0 - (T-1), then up
-// to 64 target samples from n0) are fetched kAhead stages in advance with
-// asynchronous 8-byte copies into a ring of shared-memory slots (zero-filled
-// outside the problem), one copy group per stage and thread.
-constexpr int kAhead = 3;
-constexpr int kRawSlots = kAhead + 1;
-constexpr int kRawLen = kSerLen + 64;
+constexpr int kPsiStride = 64 + kMaxT - 1;   // basis samples staged per FP32 tile (64 rows + taps)
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, uint32_t src_bytes)
 {
@@ -61,248 +22,316 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// This thread's copies of the stage starting at row n0 into `slot`; `active`
-// false commits an empty group (keeps the per-thread group count uniform).
-template <int R>
-__device__ __forceinline__ void fetch_stage(float2 *slot, const GramProblem &pr, int64_t n0, int T, bool active)
+}  // namespace
+
+constexpr int kThreads = 512;
+
+// ------------------------------------------------------------------ lag-correlation form
+// Every distinct column is a signal read at a delay: tap k of signal s is
+// x_s(n - k), zero before the record starts.  An entry of S that pairs taps
+// m >= m' of signals a and b is therefore a lagged correlation of the two
+// signals, less the products that fall off the end of the record:
+//   S[(a, m), (b, m')] = C_ab(d) - sum_{k = N-m}^{N-1-d} x_a(k) x_b(k + d),  d = m - m',
+//   C_ab(d) = sum_{k >= 0} x_a(k) x_b(k + d)   (x = 0 outside [0, N)).
+// The tensor kernel below computes C for the 15 signals (Re / Im psi_b, b < 6;
+// Re / Im t; the constant) against the 14 non-constant ones at lags 0 .. 7;
+// the finishing kernels subtract the end products (at most T - 1 per entry,
+// from the last samples of the record) and fill S.  The operands hold each
+// signal once per sample instead of once per tap.
+//
+// Polyphase contraction.  With n = 8 q + r (phase r < 8),
+//   D[(a, r), (b, j)] = sum_q x_a(8 q + r) x_b(8 q + j),   j < 16,
+// and C_ab(d) = sum_r D[(a, r), (b, r + d)].  Rows (a, r) form the A operand
+// (15 signals x 8 phases, padded to M = 128), rows (b, j) the B operand
+// (14 signals x 16 = N = 224), q is the contraction index.  In the K-major
+// layout without swizzle a core matrix is 8 rows x 16 bytes, so the 8 rows of
+// one signal's phases r form one core-matrix row group; row (b, j + 8) is row
+// (b, j) advanced by one q and is written as a second group right behind it.
+// A signal's slot in a stage is [phases 0-7 | phases 8-15], 1 KB each (8 rows
+// x 128 bytes: 8 core matrices along K); the A descriptor steps over slots
+// (2 KB per 8 rows: first halves only, slot 15 stays zero), the B descriptor
+// over halves (1 KB).
+//
+// Products.  X = hi + lo (BF16 or TF32) and hi hi + hi lo + lo hi are summed
+// into one FP32 accumulator: three MMAs per K step, four K steps per stage.
+//
+// Generation.  One task per thread and stage: a core-matrix row (c, r) of one
+// signal pair (Re / Im psi_b, or Re / Im t), i.e. E + 1 raw samples 8 apart
+// (E = 8 BF16 / 4 TF32 values per 16-byte row, and the one that follows for
+// the advanced row), or a row of the constant.  The raw ring is padded by 8
+// samples per 8 E so that the 16 lanes of a half warp (two core matrices c)
+// load from distinct banks.
+constexpr int kLagSigA = 15;                 // A side: 12 basis, 2 target, the constant
+constexpr int kLagSigB = 14;                 // B side: all but the constant
+constexpr int kLagSerT = 12, kLagSerOne = 14;
+constexpr int kLagHalfBytes = 1024;          // 8 rows x 128 bytes (8 core matrices along K)
+constexpr int kLagSlotBytes = 2 * kLagHalfBytes;
+constexpr int kLagPart = 16 * kLagSlotBytes; // hi (then lo) part of a stage
+constexpr int kLagStageBytes = 2 * kLagPart;
+constexpr int kLagStages = 3;
+constexpr int kLagAhead = 2;                 // raw stages fetched ahead
+constexpr int kLagRawSlots = kLagAhead + 1;
+constexpr int kLagKSteps = 4;                // MMA K steps per stage (16 BF16 / 8 TF32 values each)
+constexpr int kLagN = 16 * kLagSigB;         // 224 accumulator columns
+constexpr int kLagAccCols = 256;             // column spacing of the two accumulators
+constexpr int kLagChunk = 4;                 // stages per accumulation chunk
+constexpr int kLagDStride = 257;             // row stride of the final D in shared memory (floats)
+static_assert(kLagStages <= kLagChunk + 1, "drain must precede the reuse of an accumulator");
+static_assert(kLagEntries == kLagSigA * kLagSigB * kMaxT, "lag partial size");
+
+template <int FMT>
+struct LagGeom {
+    static constexpr int E = FMT == kFmtBF16 ? 8 : 4;      // values per 16-byte core-matrix row
+    static constexpr int R = 8 * 8 * E;                    // samples per stage: 8 phases x 8 core matrices x E
+    __host__ __device__ static constexpr int pidx(int j) { return j + 8 * (j / (8 * E)); }
+    static constexpr int RawSig = R + 8 + 8 * ((R + 7) / (8 * E));   // padded samples per raw signal
+    static constexpr int Raw = 2 * RawSig;                 // float2 per raw slot: u, then t
+};
+
+// psi_b = w_b(|u|^2) u: w_b(r) = r^b, or sum_{a <= b} U[a][b] r^a (Horner).
+__device__ __forceinline__ float psi_weight(int b, float r, const float *su)
 {
-    const int tid = threadIdx.x;
+    float p = 1.f;
+    if (su) {
+        p = su[b * kMaxB + b];
+        for (int a = b - 1; a >= 0; --a) p = fmaf(p, r, su[a * kMaxB + b]);
+    } else {
+        for (int e = 0; e < b; ++e) p *= r;   // low order first, as in the filter
+    }
+    return p;
+}
+
+// Raw samples of a stage: u and t from n0, R + 8 of each (the last 8 feed the
+// advanced rows), zero outside the problem.  One copy group per thread and stage.
+template <int FMT>
+__device__ __forceinline__ void lag_fetch(float2 *slot, const GramProblem &pr, int64_t n0, bool active)
+{
+    using G = LagGeom<FMT>;
     if (active) {
-        if (tid < kSerLen) {
-            const int64_t j = n0 - (T - 1) + tid;
-            const bool v = tid < R + T - 1 && j >= 0 && j < pr.n;
-            cp_async8(smem_addr(slot + tid), v ? pr.u + j : pr.u, v ? 8u : 0u);
-        } else if (tid >= kPsiThreads && tid - kPsiThreads < R) {
-            const int r = tid - kPsiThreads;
-            const int64_t j = n0 + r;
-            const bool v = pr.t != nullptr && j < pr.n;
-            cp_async8(smem_addr(slot + kSerLen + r), v ? pr.t + j : pr.u, v ? 8u : 0u);
+        for (int i = threadIdx.x; i < G::R + 8; i += kThreads) {
+            const int64_t j = n0 + i;
+            const bool vu = j < pr.n, vt = pr.t != nullptr && j < pr.n;
+            const int o = G::pidx(i);
+            cp_async8(smem_addr(slot + o), vu ? pr.u + j : pr.u, vu ? 8u : 0u);
+            cp_async8(smem_addr(slot + G::RawSig + o), vt ? pr.t + j : pr.u, vt ? 8u : 0u);
         }
     }
     cp_async_commit();
 }
 
-template <int FMT>
-__device__ __forceinline__ void put_series(unsigned char *stg, int series, int w, float v)
+// One core-matrix row (16 bytes) of a signal and its advanced copy, hi and lo:
+// v[i] is the value at K index i of the row, v[E] the next one.
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo_elem, float hi_elem)
 {
-    unsigned char *base = stg + series * kSerBytes;
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo_elem, hi_elem);   // lo_elem in the low half
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+template <int FMT, int E>
+__device__ __forceinline__ void lag_put(unsigned char *p, const float (&v)[E + 1])
+{
+    uint32_t h[4], hs[4], l[4], ls[4];
     if constexpr (FMT == kFmtBF16) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-        uint16_t *hi0 = reinterpret_cast<uint16_t *>(base);   // element i at i
-        uint16_t *hi1 = hi0 + kSerLen;                         // element i at i - 1
-        uint16_t *lo0 = hi0 + 2 * kSerLen;
-        uint16_t *lo1 = hi0 + 3 * kSerLen;
-        const uint16_t hb = *reinterpret_cast<const uint16_t *>(&h), lb = *reinterpret_cast<const uint16_t *>(&l);
-        hi0[w] = hb;
-        lo0[w] = lb;
-        if (w >= 1) {
-            hi1[w - 1] = hb;
-            lo1[w - 1] = lb;
+        uint32_t H[5], L[5];
+        float lo[E + 1];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            H[k] = bf16x2_bits(v[2 * k], v[2 * k + 1]);
+            lo[2 * k] = v[2 * k] - __uint_as_float(H[k] << 16);
+            lo[2 * k + 1] = v[2 * k + 1] - __uint_as_float(H[k] & 0xFFFF0000u);
+        }
+        H[4] = bf16x2_bits(v[8], 0.f);
+        lo[8] = v[8] - __uint_as_float(H[4] << 16);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) L[k] = bf16x2_bits(lo[2 * k], lo[2 * k + 1]);
+        L[4] = bf16x2_bits(lo[8], 0.f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {   // advanced by one: elements 2k + 1, 2k + 2
+            h[k] = H[k];
+            l[k] = L[k];
+            hs[k] = __byte_perm(H[k], H[k + 1], 0x5432);
+            ls[k] = __byte_perm(L[k], L[k + 1], 0x5432);
         }
     } else {
-        uint32_t *hi = reinterpret_cast<uint32_t *>(base);
-        uint32_t *lo = hi + kSerLen;
-        const float h = to_tf32(v);
-        hi[w] = __float_as_uint(h);
-        lo[w] = __float_as_uint(to_tf32(v - h));
-    }
-}
-
-// Convert the raw samples of a stage (rows from n0) into the series arrays.
-template <int FMT, int R>
-__device__ __forceinline__ void stage_series(unsigned char *stg, const float2 *slot, int64_t n0, int64_t n, int B,
-                                             int T, const float *su)
-{
-    const int tid = threadIdx.x;
-    if (tid < kPsiThreads) {
-        const int w = tid % kSerLen, b = tid / kSerLen;
-        if (b < B) {
-            const float2 u = slot[w];   // zero outside the problem
-            const float r = fmaf(u.x, u.x, u.y * u.y);
-            float p = 1.f;
-            if (su) {   // sum_{a <= b} U[a][b] r^a by Horner's rule
-                p = su[b * kMaxB + b];
-                for (int a = b - 1; a >= 0; --a) p = fmaf(p, r, su[a * kMaxB + b]);
-            } else {
-                for (int e = 0; e < b; ++e) p *= r;   // r^b, low order first as in the filter
-            }
-            put_series<FMT>(stg, 2 * b, w, p * u.x);   // psi_b = |u|^{2b} u (or its combination)
-            put_series<FMT>(stg, 2 * b + 1, w, p * u.y);
+        uint32_t hw[E + 1], lw[E + 1];
+#pragma unroll
+        for (int i = 0; i <= E; ++i) {
+            const float a = to_tf32(v[i]);
+            hw[i] = __float_as_uint(a);
+            lw[i] = __float_as_uint(to_tf32(v[i] - a));
         }
-    } else {
-        const int rr = tid - kPsiThreads;
-        if (rr < R) {
-            const int w = rr + T - 1;
-            const float2 t = slot[kSerLen + rr];
-            put_series<FMT>(stg, kSerT, w, t.x);
-            put_series<FMT>(stg, kSerT + 1, w, t.y);
-            put_series<FMT>(stg, kSerOne, w, n0 + rr < n ? 1.f : 0.f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            h[k] = hw[k];
+            hs[k] = hw[k + 1];
+            l[k] = lw[k];
+            ls[k] = lw[k + 1];
         }
     }
+    *reinterpret_cast<uint4 *>(p) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(p + kLagHalfBytes) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
+    *reinterpret_cast<uint4 *>(p + kLagPart) = make_uint4(l[0], l[1], l[2], l[3]);
+    *reinterpret_cast<uint4 *>(p + kLagPart + kLagHalfBytes) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
 }
 
-}  // namespace
-
-// ------------------------------------------------------------------ tensor cores
-// Operand generation.  Each stage converts every basis value to its hi / lo
-// pair once, into a series array in shared memory; an operand chunk (8 BF16 or
-// 4 TF32 rows of one distinct column) is then four 32-bit shared loads per
-// half and two 16-byte stores.  BF16 series are kept twice, as 16-bit arrays
-// starting at element 0 and at element 1, so a chunk at any offset reads whole
-// aligned words.  Every generator thread owns up to four fixed chunks (the
-// addresses are computed once); the global loads of the next stage are issued
-// before the current stage is generated.
-//
-// Products.  X = hi + lo; the split product hi^T hi + hi^T lo + lo^T hi is
-// P + Q + Q^T with P = hi^T hi, Q = hi^T lo.  The hi and lo tiles of a stage
-// are adjacent in shared memory, so one MMA with A = hi (128 operand rows) and
-// B = [hi; lo] (256 rows) produces [P | Q] in a 128 x 256 accumulator: one
-// MMA per K step (a tcgen05 MMA with M = 128 takes the same time for any N up
-// to 256, so the full width is used).
-//
-// Accumulation.  The tensor core's FP32 accumulator drops low-order bits on
-// every MMA step, a bias that grows with the number of steps summed into one
-// accumulator.  So each accumulation covers a chunk of kChunk stages only and
-// is then added, with round-to-nearest, into FP32 running sums in registers:
-// every thread owns one tensor-memory lane (a distinct column) and one piece
-// of its columns -- P [0, 64), P [64, 112), Q [128, 192) or Q [192, 240) --
-// read as 64 columns with one wait (the 48-column pieces read 16 unused ones).  Two accumulators in tensor memory
-// (2 x 256 columns) alternate between chunks, so the MMAs of one chunk run
-// while the previous one is drained.
-//
-// Roles.  All sixteen warps generate operands and drain accumulators; thread 0
-// also issues the MMAs of a stage once the barrier at the top of the next
-// iteration has shown that every thread has written it.  Sixteen warps (four
-// per SM sub-partition) at 128 registers each fill the register file.
-constexpr int kThreads = 512;
-constexpr int kOpTile = 16384;            // 128 operand rows x 128 bytes
-constexpr int kStageBytes = 2 * kOpTile;  // hi tile, then lo tile
-constexpr int kStages = 4;
-constexpr int kChunk = 8;
-// A chunk is drained kStages stages after its last one was generated, and its
-// accumulator is reused by the chunk two later, whose first stage is issued
-// kChunk + 1 stages after that last one.
-static_assert(kStages <= kChunk + 1, "drain must precede the reuse of an accumulator");
-constexpr int kAccN = 256;                // accumulator columns: P in [0, 128), Q in [128, 256)
-constexpr int kAccPer = 64;               // sums per thread (a piece of 64 or 48 columns)
-constexpr int kTasks = 2;                 // operand chunks per thread (8 D <= 792 <= 2 x 512)
-constexpr int kTmemCols = 2 * kAccN;
-
-// Barriers: empty[s] (MMA commit: stage s consumed), acc_full[b] (MMA commit:
-// a chunk's sum is complete in accumulator b), fin (MMA commit: everything
-// issued has completed, before tensor memory is released).
+// Operands of the stage starting at sample n0 from its raw slot.  Warp w:
+// w < 12: Re / Im psi_{w/2}; 12, 13: Re / Im t; 14, 15: the constant; core
+// matrices c = 4 (w & 1) .. + 3, lane (c, r).
 template <int FMT>
-__global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a)
+__device__ __forceinline__ void lag_generate(unsigned char *st, const float2 *slot, int64_t n0, int64_t n,
+                                             const float *su)
 {
-    constexpr int R = (FMT == kFmtBF16) ? 64 : 32;   // rows per stage: 128 bytes per operand row
-    constexpr int NK = 4;                            // MMAs along K per stage (K = 16 bf16 / 8 tf32)
+    using G = LagGeom<FMT>;
+    constexpr int E = G::E;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = 4 * (w & 1) + (lane >> 3), r = lane & 7;
+    const int cr = c * 128 + r * 16;
+    if (w >= 14) {   // 1 inside the record (hi only; lo and the advanced rows stay zero)
+        uint32_t q[4];
+        if constexpr (FMT == kFmtBF16) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t s0 = n0 + 8 * (E * c + 2 * k) + r;
+                q[k] = (s0 < n ? 0x3F80u : 0u) | (s0 + 8 < n ? 0x3F800000u : 0u);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = n0 + 8 * (E * c + k) + r < n ? 0x3F800000u : 0u;
+        }
+        *reinterpret_cast<uint4 *>(st + kLagSerOne * kLagSlotBytes + cr) = make_uint4(q[0], q[1], q[2], q[3]);
+        return;
+    }
+    const bool target = w >= 12;
+    const float2 *src = slot + (target ? G::RawSig : 0);
+    float re[E + 1], im[E + 1];
+#pragma unroll
+    for (int i = 0; i <= E; ++i) {
+        const float2 x = src[G::pidx(8 * (E * c + i) + r)];
+        re[i] = x.x;
+        im[i] = x.y;
+    }
+    int sig = kLagSerT;
+    if (!target) {
+        const int b = w >> 1;
+        sig = 2 * b;
+        float rr[E + 1], pw[E + 1];
+#pragma unroll
+        for (int i = 0; i <= E; ++i) rr[i] = fmaf(re[i], re[i], im[i] * im[i]);
+        // w_b(r) exactly as psi_weight evaluates it
+        if (su) {
+            const float top = su[b * kMaxB + b];
+#pragma unroll
+            for (int i = 0; i <= E; ++i) pw[i] = top;
+            for (int a = b - 1; a >= 0; --a) {
+                const float cf = su[a * kMaxB + b];
+#pragma unroll
+                for (int i = 0; i <= E; ++i) pw[i] = fmaf(pw[i], rr[i], cf);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i <= E; ++i) pw[i] = 1.f;
+            for (int e = 0; e < b; ++e)
+#pragma unroll
+                for (int i = 0; i <= E; ++i) pw[i] *= rr[i];
+        }
+#pragma unroll
+        for (int i = 0; i <= E; ++i) {
+            re[i] *= pw[i];
+            im[i] *= pw[i];
+        }
+    }
+    unsigned char *p = st + sig * kLagSlotBytes + cr;
+    lag_put<FMT, E>(p, re);
+    lag_put<FMT, E>(p + kLagSlotBytes, im);
+}
+
+// Barriers: empty[s] (MMA commit: stage s consumed), acc_full[b] (a chunk's
+// sum is complete in accumulator b), fin (everything issued has completed).
+// Roles: every thread generates one task per stage and drains, thread 0
+// issues a stage's MMAs after the barrier that follows its generation.
+template <int FMT>
+__global__ void __launch_bounds__(kThreads, 1) gram_lag_kernel(GramArgs a)
+{
+    using G = LagGeom<FMT>;
+    constexpr int R = G::R;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *stages = smem;
-    unsigned char *staging = smem + kStages * kStageBytes;   // 2 x kStagingBytes
-    float2 *raw = reinterpret_cast<float2 *>(staging + 2 * kStagingBytes);   // kRawSlots x kRawLen
-    uint64_t *empty = reinterpret_cast<uint64_t *>(raw + kRawSlots * kRawLen);
-    uint64_t *acc_full = empty + kStages;
+    float2 *raw = reinterpret_cast<float2 *>(stages + kLagStages * kLagStageBytes);
+    uint64_t *empty = reinterpret_cast<uint64_t *>(raw + kLagRawSlots * G::Raw);
+    uint64_t *acc_full = empty + kLagStages;
     uint64_t *fin = acc_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
-    float *su_buf = reinterpret_cast<float *>(tmem_slot + 4);   // basis coefficients U (kUSize)
+    float *su_buf = reinterpret_cast<float *>(tmem_slot + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int prob = blockIdx.x / a.cpp, chunk = blockIdx.x % a.cpp;
     const GramProblem pr = a.probs[prob];
-    const int T = a.T, B = a.Bp > a.Bq ? a.Bp : a.Bq;
-    const int D = gram_distinct(B, T);
     const int64_t nblk = (pr.n + R - 1) / R;
     const int64_t b0 = nblk * chunk / a.cpp, b1 = nblk * (chunk + 1) / a.cpp;
     const int nits = (int)(b1 - b0);
-    const int nchunks = (nits + kChunk - 1) / kChunk;
+    const int nchunks = (nits + kLagChunk - 1) / kLagChunk;
 
     const float *su = nullptr;
     if (a.ubasis) {
         if (tid < kUSize) su_buf[tid] = a.ubasis[(size_t)prob * kUSize + tid];
         su = su_buf;
     }
-    // Operand rows >= D are never written and stay zero.
-    for (int i = tid; i < kStages * kStageBytes / 16; i += kThreads)
+    // Slot 15, the constant's lo and advanced rows are never written and stay zero.
+    for (int i = tid; i < kLagStages * kLagStageBytes / 16; i += kThreads)
         reinterpret_cast<uint4 *>(stages)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&empty[s]), 1);
+        for (int s = 0; s < kLagStages; ++s) mbar_init(smem_addr(&empty[s]), 1);
         for (int b = 0; b < 2; ++b) mbar_init(smem_addr(&acc_full[b]), 1);
         mbar_init(smem_addr(fin), 1);
         fence_barrier_init();
     }
     if (warp == 0) {
-        tmem_alloc(smem_addr(tmem_slot), kTmemCols);
+        tmem_alloc(smem_addr(tmem_slot), 2 * kLagAccCols);
         tmem_relinquish();
     }
 #pragma unroll
-    for (int j = 0; j <= kAhead; ++j) fetch_stage<R>(raw + j * kRawLen, pr, (b0 + j) * R, T, j < nits);
-    cp_async_wait<kAhead>();   // stage 0 has landed (this thread's copies)
-    __syncthreads();
-    if (nits > 0) stage_series<FMT, R>(staging, raw, b0 * R, pr.n, B, T, su);
-    fence_async_shared();
+    for (int j = 0; j < kLagAhead; ++j) lag_fetch<FMT>(raw + j * G::Raw, pr, (b0 + j) * R, j < nits);
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
     const int quarter = warp & 3, piece = warp >> 2;
-    const int row = 32 * quarter + lane;   // tensor-memory lane = distinct column
-    // piece 0: P [0, 64), 1: P [64, 112), 2: Q [128, 192), 3: Q [192, 240)
-    const int pcol = (piece >> 1) * 128 + (piece & 1) * 64;
-    const bool wide = (piece & 1) == 0;   // 64 columns, else 48
-    const uint32_t lane_taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)pcol;
-    float acc[kAccPer];
+    const int row = 32 * quarter + lane;   // tensor-memory lane = A row (signal, phase)
+    const uint32_t lane_taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(64 * piece);
+    float acc[64];
 #pragma unroll
-    for (int i = 0; i < kAccPer; ++i) acc[i] = 0.f;
+    for (int i = 0; i < 64; ++i) acc[i] = 0.f;
 
-    // This thread's operand chunks: task tid + 256 q = (column << 3) | chunk.
-    int src[kTasks], dst[kTasks], chk[kTasks];
-#pragma unroll
-    for (int q = 0; q < kTasks; ++q) {
-        const int task = tid + kThreads * q;
-        src[q] = -1;
-        dst[q] = 0;
-        chk[q] = 0;
-        if (task < 8 * D) {
-            const int d = task >> 3, ch = task & 7;
-            int series, off;
-            distinct_source(d, B, T, series, off);
-            int word;
-            if constexpr (FMT == kFmtBF16) {
-                const int o = ch * 8 + off;
-                word = (o & 1) ? kSerLen / 2 + (o - 1) / 2 : o / 2;
-            } else {
-                word = ch * 4 + off;
-            }
-            src[q] = series * (kSerBytes / 4) + word;
-            dst[q] = (int)sw128_offset(d, ch);
-            chk[q] = ch;
-        }
-    }
-
-    // MMAs of stage j (thread 0, after a barrier that followed every thread's
-    // writes of that stage and every drain of the accumulator it reuses).
-    const uint32_t idesc = umma_idesc(FMT, 128, kAccN);   // M = 128, N = 256
+    const uint32_t idesc = umma_idesc(FMT, 128, kLagN);
     int issued = 0;
     auto issue = [&](int j) {
-        const int s = j % kStages, c = j / kChunk, buf = c & 1;
+        const int s = j % kLagStages, c = j / kLagChunk, buf = c & 1;
         tc_fence_after_sync();
-        const uint32_t hb = smem_addr(stages + s * kStageBytes);   // hi rows 0-127, lo rows 128-255
-        const uint32_t dacc = tmem + (uint32_t)(buf * kAccN);
+        const uint32_t hb = smem_addr(stages + s * kLagStageBytes), lb = hb + kLagPart;
+        const uint32_t dacc = tmem + (uint32_t)(buf * kLagAccCols);
 #pragma unroll
-        for (int kk = 0; kk < NK; ++kk) {
-            const uint64_t desc = umma_desc_sw128(hb + kk * 32);
-            const uint32_t accumulate = (j % kChunk == 0 && kk == 0) ? 0u : 1u;
-            if constexpr (FMT == kFmtBF16)
-                umma_bf16(dacc, desc, desc, idesc, accumulate);
-            else
-                umma_tf32(dacc, desc, desc, idesc, accumulate);
+        for (int kk = 0; kk < kLagKSteps; ++kk) {
+            const uint32_t o = (uint32_t)kk * 256u;   // two core matrices along K per step
+            const uint64_t ah = umma_desc_kmajor(hb + o, 128u, kLagSlotBytes);
+            const uint64_t al = umma_desc_kmajor(lb + o, 128u, kLagSlotBytes);
+            const uint64_t bh = umma_desc_kmajor(hb + o, 128u, kLagHalfBytes);
+            const uint64_t bl = umma_desc_kmajor(lb + o, 128u, kLagHalfBytes);
+            const uint32_t first = (j % kLagChunk == 0 && kk == 0) ? 0u : 1u;
+            if constexpr (FMT == kFmtBF16) {
+                umma_bf16(dacc, ah, bh, idesc, first);
+                umma_bf16(dacc, ah, bl, idesc, 1u);
+                umma_bf16(dacc, al, bh, idesc, 1u);
+            } else {
+                umma_tf32(dacc, ah, bh, idesc, first);
+                umma_tf32(dacc, ah, bl, idesc, 1u);
+                umma_tf32(dacc, al, bh, idesc, 1u);
+            }
         }
         ++issued;
         umma_commit(smem_addr(&empty[s]));
-        if ((j + 1) % kChunk == 0 || j + 1 == nits) umma_commit(smem_addr(&acc_full[buf]));
+        if ((j + 1) % kLagChunk == 0 || j + 1 == nits) umma_commit(smem_addr(&acc_full[buf]));
     };
 
     auto drain = [&](int c) -> bool {
@@ -311,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a)
         tc_fence_after_sync();
         if (ok) {
             float v[64];
-            tmem_ld64(lane_taddr + (uint32_t)(buf * kAccN), v);
+            tmem_ld64(lane_taddr + (uint32_t)(buf * kLagAccCols), v);
 #pragma unroll
             for (int i = 0; i < 64; ++i) acc[i] += v[i];
         }
@@ -321,67 +350,27 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a)
 
     bool failed = false;
     int next_drain = 0;
-    bool drained_ok = true;   // drains of the previous iteration
+    bool drained_ok = true;
     for (int it = 0; it < nits; ++it) {
-        const int s = it % kStages;
+        const int s = it % kLagStages;
         bool ok = drained_ok;
-        if (it >= kStages)
-            ok = mbar_wait(smem_addr(&empty[s]), (uint32_t)(((it / kStages) - 1) & 1), a.status) && ok;
-        cp_async_wait<kAhead - 1>();   // this thread's copies of stage it + 1 have landed
-        // every thread has written stage it - 1, drained what it had to, and
-        // its copies of stage it + 1 are visible
+        if (it >= kLagStages)
+            ok = mbar_wait(smem_addr(&empty[s]), (uint32_t)(((it / kLagStages) - 1) & 1), a.status) && ok;
+        cp_async_wait<kLagAhead - 1>();   // this thread's copies of stage it have landed
+        // every thread has written stage it - 1 and its copies of stage it are visible
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
         }
         if (tid == 0 && it > 0) issue(it - 1);
-        const int64_t n0 = (b0 + it) * R;
-        // the slot of stage it (read in the previous iteration) receives stage it + kAhead + 1
-        fetch_stage<R>(raw + (it % kRawSlots) * kRawLen, pr, n0 + (int64_t)(kAhead + 1) * R, T,
-                       it + kAhead + 1 < nits);
-        const uint32_t *stw = reinterpret_cast<const uint32_t *>(staging + (it & 1) * kStagingBytes);
-        unsigned char *hi = stages + s * kStageBytes;
-        unsigned char *lo = hi + kOpTile;
-        const int64_t rem = pr.n - n0;
-        const int nvalid = rem < R ? (int)rem : R;
-#pragma unroll
-        for (int q = 0; q < kTasks; ++q) {
-            if (src[q] < 0) continue;
-            const uint32_t *hw = stw + src[q];
-            const uint32_t *lw = hw + kSerLen;   // lo arrays follow the hi arrays
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                h[k] = hw[k];
-                l[k] = lw[k];
-            }
-            if (nvalid < R) {   // last stage of the problem: rows past the end are zero
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    uint32_t m;
-                    if constexpr (FMT == kFmtBF16) {
-                        const int r0 = chk[q] * 8 + 2 * k;
-                        m = (r0 < nvalid ? 0x0000FFFFu : 0u) | (r0 + 1 < nvalid ? 0xFFFF0000u : 0u);
-                    } else {
-                        m = chk[q] * 4 + k < nvalid ? 0xFFFFFFFFu : 0u;
-                    }
-                    h[k] &= m;
-                    l[k] &= m;
-                }
-            }
-            *reinterpret_cast<uint4 *>(hi + dst[q]) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4 *>(lo + dst[q]) = make_uint4(l[0], l[1], l[2], l[3]);
-        }
-        if (it + 1 < nits)
-            stage_series<FMT, R>(staging + ((it + 1) & 1) * kStagingBytes, raw + ((it + 1) % kRawSlots) * kRawLen,
-                                 n0 + R, pr.n, B, T, su);
+        // the slot of stage it - 1 (read in the previous iteration) receives stage it + kLagAhead
+        lag_fetch<FMT>(raw + ((it + kLagAhead) % kLagRawSlots) * G::Raw, pr, (b0 + it + kLagAhead) * R,
+                       it + kLagAhead < nits);
+        lag_generate<FMT>(stages + s * kLagStageBytes, raw + (it % kLagRawSlots) * G::Raw, (b0 + it) * R, pr.n, su);
         fence_async_shared();
-        // Drain every chunk whose last stage was consumed kStages stages ago:
-        // its MMAs are complete (this stage's empty wait saw them).  A failed
-        // drain is voted on at the top of the next iteration.
         while (next_drain < nchunks) {
-            const int last = min((next_drain + 1) * kChunk, nits) - 1;
-            if (last + kStages > it) break;
+            const int last = min((next_drain + 1) * kLagChunk, nits) - 1;
+            if (last + kLagStages > it) break;
             drained_ok = drain(next_drain++) && drained_ok;
         }
     }
@@ -394,31 +383,197 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a)
             failed = __syncthreads_or(!drained_ok);
         }
     }
-    cp_async_wait<0>();   // no copy into this CTA's shared memory outlives it
-    // Every MMA issued must be complete before tensor memory is released.
+    cp_async_wait<0>();
     if (tid == 0 && issued > 0) {
         umma_commit(smem_addr(fin));
         mbar_wait(smem_addr(fin), 0u, a.status);
     }
+    tc_fence_before_sync();
+    __syncthreads();   // every MMA has completed: the stage buffers are free
 
-    float *part = a.partials + (size_t)blockIdx.x * kGramRows * kGramPartCols;
+    // C[a][b][d] = sum_r D[(a, r), (b, r + d)] through shared memory, FP64.
+    float *Dsm = reinterpret_cast<float *>(stages);
     const bool zero = failed || nits == 0;
 #pragma unroll
-    for (int i = 0; i < kAccPer; ++i)   // P -> partial columns [0, 112), Q -> [112, 224)
-        if (wide || i < 48) part[(size_t)row * kGramPartCols + (piece >> 1) * kGramS + (piece & 1) * 64 + i] = zero ? 0.f : acc[i];
+    for (int i = 0; i < 64; ++i)
+        if (64 * piece + i < kLagN) Dsm[row * kLagDStride + 64 * piece + i] = zero ? 0.f : acc[i];
+    __syncthreads();
+    double *part = reinterpret_cast<double *>(a.partials) + (size_t)blockIdx.x * kLagEntries;
+    for (int e = tid; e < kLagEntries; e += kThreads) {
+        const int sa = e / (kLagSigB * kMaxT), sb = (e / kMaxT) % kLagSigB, d = e % kMaxT;
+        const float *dp = Dsm + (8 * sa) * kLagDStride + 16 * sb + d;
+        double v = 0.0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v += (double)dp[r * (kLagDStride + 1)];
+        part[e] = v;
+    }
 
     tc_fence_before_sync();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after_sync();
-        tmem_dealloc(tmem, kTmemCols);
+        tmem_dealloc(tmem, 2 * kLagAccCols);
     }
 }
 
-size_t gram_tc_smem()
+size_t gram_lag_smem(int fmt)
 {
-    return 1024 + (size_t)kStages * kStageBytes + 2 * (size_t)kStagingBytes + (size_t)kRawSlots * kRawLen * 8 +
-           (kStages + 3) * 8 + 16 + kUSize * 4;
+    const int raw = fmt == kFmtBF16 ? LagGeom<kFmtBF16>::Raw : LagGeom<kFmtTF32>::Raw;
+    const size_t body = (size_t)kLagStages * kLagStageBytes + (size_t)kLagRawSlots * raw * 8 +
+                        (kLagStages + 3) * 8 + 16 + kUSize * 4;
+    const size_t dfinal = (size_t)128 * kLagDStride * 4;
+    return 1024 + (body > dfinal ? body : dfinal);
+}
+
+// ---- finishing: partial lag sums -> S
+// C[p][e] = sum over the problem's CTAs of the FP64 partials, in a fixed order.
+__global__ void __launch_bounds__(256) gram_lag_reduce_kernel(const double *__restrict__ partials, int cpp,
+                                                              double *__restrict__ C)
+{
+    __shared__ double grp[8][32];
+    const int p = blockIdx.y, lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (e < kLagEntries) {
+        const double *base = partials + (size_t)p * cpp * kLagEntries + e;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // partials g, g + 8, g + 16, g + 24, g + 32, ...
+        int k = g;
+        for (; k + 24 < cpp; k += 32) {
+            s0 += base[(size_t)k * kLagEntries];
+            s1 += base[(size_t)(k + 8) * kLagEntries];
+            s2 += base[(size_t)(k + 16) * kLagEntries];
+            s3 += base[(size_t)(k + 24) * kLagEntries];
+        }
+        for (; k < cpp; k += 8) s0 += base[(size_t)k * kLagEntries];
+        s = (s0 + s1) + (s2 + s3);
+    }
+    grp[g][lane] = s;
+    __syncthreads();
+    if (g == 0 && e < kLagEntries) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += grp[q][lane];
+        C[(size_t)p * kLagEntries + e] = t;
+    }
+}
+
+// Signal and tap of distinct column d (the order of dpd_gram.cuh).
+__device__ __forceinline__ void lag_source(int d, int B, int T, int &sig, int &tap)
+{
+    const int BT = B * T;
+    if (d < 2 * BT) {
+        const int im = d >= BT ? 1 : 0, dd = im ? d - BT : d;
+        sig = 2 * (dd / T) + im;
+        tap = dd % T;
+    } else {
+        sig = d == 2 * BT ? kLagSerOne : kLagSerT + (d - 2 * BT - 1);
+        tap = 0;
+    }
+}
+
+// S (P block, Q = 0: the layout the assembly reads) from the lag sums; grid
+// (entries / 256, problems).  The last T - 1 samples of every signal,
+// evaluated as the tensor kernel evaluates them, give the end products.
+__global__ void __launch_bounds__(256) gram_lag_spq_kernel(const double *__restrict__ Call,
+                                                           const GramProblem *__restrict__ probs,
+                                                           const float *__restrict__ ubasis, int B, int T,
+                                                           double *__restrict__ SPQall)
+{
+    __shared__ double xt[kLagSigA][kMaxT];   // x_s(N - 8 + i), zero before the record
+    __shared__ float su_buf[kUSize];
+    __shared__ int2 src[kGramS];              // (signal, tap) of each distinct column
+    const int p = blockIdx.y, tid = threadIdx.x;
+    const GramProblem pr = probs[p];
+    const int64_t N = pr.n;
+    const int D = gram_distinct(B, T);
+    const double *C = Call + (size_t)p * kLagEntries;
+    double *SPQ = SPQall + (size_t)p * kGramS * kGramPartCols;
+    const float *su = nullptr;
+    if (ubasis) {
+        if (tid < kUSize) su_buf[tid] = ubasis[(size_t)p * kUSize + tid];
+        su = su_buf;
+    }
+    if (tid < D) {
+        int sig, tap;
+        lag_source(tid, B, T, sig, tap);
+        src[tid] = make_int2(sig, tap);
+    }
+    __syncthreads();
+    if (tid < kMaxT * 8) {
+        const int i = tid / 8, g = tid % 8;   // sample N - 8 + i; g < 6 basis, 6 target, 7 constant
+        const int64_t k = N - kMaxT + i;
+        double v0 = 0.0, v1 = 0.0;
+        if (k >= 0) {
+            if (g < 6) {
+                const float2 x = pr.u[k];
+                const float w = psi_weight(g, fmaf(x.x, x.x, x.y * x.y), su);
+                v0 = (double)(w * x.x);
+                v1 = (double)(w * x.y);
+            } else if (g == 6) {
+                if (pr.t) {
+                    const float2 x = pr.t[k];
+                    v0 = x.x;
+                    v1 = x.y;
+                }
+            } else {
+                v0 = 1.0;
+            }
+        }
+        if (g < 6) {
+            xt[2 * g][i] = v0;
+            xt[2 * g + 1][i] = v1;
+        } else if (g == 6) {
+            xt[kLagSerT][i] = v0;
+            xt[kLagSerT + 1][i] = v1;
+        } else {
+            xt[kLagSerOne][i] = v0;
+        }
+    }
+    __syncthreads();
+    const int e = blockIdx.x * blockDim.x + tid;
+    if (e >= D * D) return;
+    const int i = e / D, j = e % D;
+    SPQ[(size_t)i * kGramPartCols + kGramS + j] = 0.0;
+    if (j < i) return;
+    int sa = src[i].x, ma = src[i].y, sb = src[j].x, mb = src[j].y;
+    // (sa, ma): the larger tap; at equal taps the constant on the A side
+    if (mb > ma || (mb == ma && sb == kLagSerOne)) {
+        const int s0 = sa, m0 = ma;
+        sa = sb;
+        ma = mb;
+        sb = s0;
+        mb = m0;
+    }
+    const int dl = ma - mb;
+    double v;
+    if ((int64_t)ma >= N) {
+        v = 0.0;   // column (sa, ma) is zero on every row
+    } else if (sb == kLagSerOne) {
+        // against the constant at tap 0: sum_{k < N - ma} x_sa(k) = C[one][sa][0] less the last ma samples
+        if (sa == kLagSerOne) {
+            v = (double)N;
+        } else {
+            v = C[(kLagSerOne * kLagSigB + sa) * kMaxT];
+            for (int k = 0; k < ma; ++k) v -= xt[sa][kMaxT - 1 - k];
+        }
+    } else {
+        v = C[(sa * kLagSigB + sb) * kMaxT + dl];
+        // samples N - ma .. N - 1 - dl: xt index k = sample - (N - 8)
+        for (int k = kMaxT - ma; k <= kMaxT - 1 - dl; ++k) v -= xt[sa][k] * xt[sb][k + dl];
+    }
+    SPQ[(size_t)i * kGramPartCols + j] = v;
+}
+
+cudaError_t launch_gram_lag_finish(const float *partials, const GramProblem *probs, const float *ubasis, int nprob,
+                                   int cpp, int B, int T, double *C, double *S, cudaStream_t s)
+{
+    gram_lag_reduce_kernel<<<dim3((kLagEntries + 31) / 32, nprob), 256, 0, s>>>(
+        reinterpret_cast<const double *>(partials), cpp, C);
+    count_launch();
+    const int D = gram_distinct(B, T);
+    gram_lag_spq_kernel<<<dim3((D * D + 255) / 256, nprob), 256, 0, s>>>(C, probs, ubasis, B, T, S);
+    count_launch();
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ FP32 CUDA cores
@@ -441,14 +596,7 @@ __device__ __forceinline__ void stage_basis(const GramProblem &pr, int64_t n0, i
         float2 v = make_float2(0.f, 0.f);
         if (j >= 0 && j < pr.n) {
             const float2 x = pr.u[j];
-            const float r = fmaf(x.x, x.x, x.y * x.y);
-            float p = 1.f;
-            if (su) {   // sum_{a <= bb} U[a][bb] r^a by Horner's rule
-                p = su[bb * kMaxB + bb];
-                for (int a2 = bb - 1; a2 >= 0; --a2) p = fmaf(p, r, su[a2 * kMaxB + bb]);
-            } else {
-                for (int e = 0; e < bb; ++e) p *= r;
-            }
+            const float p = psi_weight(bb, fmaf(x.x, x.x, x.y * x.y), su);
             v = make_float2(p * x.x, p * x.y);
         }
         psi[bb * kPsiStride + w] = v;
@@ -563,7 +711,10 @@ int gram_ctas_per_problem(int precision, int sm_count, int nprob, int64_t n)
     const int total = precision == kPrecFP32 ? 4 * sm_count : sm_count;
     int cpp = total / (nprob > 0 ? nprob : 1);
     if (cpp < 1) cpp = 1;
-    const int64_t blocks = (n + 63) / 64;
+    const int rows = precision == kPrecFP32   ? kF32Rows
+                     : precision == kPrecBF16x3 ? LagGeom<kFmtBF16>::R
+                                                : LagGeom<kFmtTF32>::R;   // samples per stage
+    const int64_t blocks = (n + rows - 1) / rows;
     if (cpp > blocks) cpp = (int)(blocks > 1 ? blocks : 1);
     return cpp;
 }
@@ -580,12 +731,13 @@ cudaError_t launch_gram(int precision, const GramArgs &a, cudaStream_t s)
         count_launch();
         return cudaGetLastError();
     }
-    auto kern = precision == kPrecBF16x3 ? gram_tc_kernel<kFmtBF16> : gram_tc_kernel<kFmtTF32>;
+    const int fmt = precision == kPrecBF16x3 ? kFmtBF16 : kFmtTF32;
+    auto kern = fmt == kFmtBF16 ? gram_lag_kernel<kFmtBF16> : gram_lag_kernel<kFmtTF32>;
     static SmemAttr smem_rec[2];
-    const int ai = precision == kPrecBF16x3 ? 0 : 1;
-    const cudaError_t e = ensure_smem(smem_rec[ai], (const void *)kern, gram_tc_smem());
+    const int ai = fmt == kFmtBF16 ? 0 : 1;
+    const cudaError_t e = ensure_smem(smem_rec[ai], (const void *)kern, gram_lag_smem(fmt));
     if (e != cudaSuccess) return e;
-    kern<<<grid, kThreads, gram_tc_smem(), s>>>(a);
+    kern<<<grid, kThreads, gram_lag_smem(fmt), s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
