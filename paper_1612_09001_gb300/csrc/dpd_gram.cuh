@@ -66,12 +66,13 @@ __host__ __device__ inline void psi_column_refs(int j, int K, int Bp, int B, int
 }
 
 struct GramArgs {
-    const GramProblem *probs;
+    const GramProblem *probs;   // device array of nprob problems, or null: the one problem below
+    GramProblem one;
     int nprob;
     int cpp;               // CTAs per problem (row chunks)
     int Bp, Bq, T, K;
     float *partials;       // FP32 kernel: [nprob * cpp][kGramRows][kGramPartCols] floats;
-                           // tensor kernel: [nprob * cpp][kLagEntries] doubles
+                           // tensor kernel: [nprob * cpp][kLagEntries] float pairs
     int *status;
     // Basis of the psi columns: per problem a kMaxB x kMaxB matrix U (row-major,
     // U[a][b] multiplies |u|^{2a} u in basis function b, upper triangular), or
@@ -87,12 +88,15 @@ cudaError_t launch_gram(int precision, const GramArgs &a, cudaStream_t s);
 // S[p][i][c] (i < D, c < 2 kGramS) = sum over the problem's CTAs of the partial P and Q
 // blocks, in FP64 and a fixed order (S = P + Q + Q^T is formed by the assembly).
 cudaError_t launch_gram_reduce(const float *partials, int nprob, int cpp, int D, double *S, cudaStream_t s);
-// Tensor-core precisions: each CTA's partial is kLagEntries FP64 lag sums
-// C[a][b][d] (a < 15, b < 14, d < kMaxT); this sums them per problem into C (FP64, fixed
-// order) and fills S (P block, Q = 0) from them and the end of each record.
+// Tensor-core precisions: each CTA's partial is kLagEntries lag sums C[a][b][d]
+// (a < 15, b < 14, d < kMaxT), each an FP32 pair (sum, rounding error); this sums them per
+// problem into C (FP64, fixed order).
+// G, g and t^H t are assembled from C directly (the entries of S on the fly), into G / g
+// / tt at K x K, K, 1 per problem; probs may be null for one problem passed as `one`.
 constexpr int kLagEntries = 15 * 14 * kMaxT;
-cudaError_t launch_gram_lag_finish(const float *partials, const GramProblem *probs, const float *ubasis, int nprob,
-                                   int cpp, int B, int T, double *C, double *S, cudaStream_t s);
+cudaError_t launch_gram_lag_finish(const float *partials, const GramProblem *probs, GramProblem one,
+                                   const float *ubasis, int nprob, int cpp, int K, int Bp, int B, int T, double *C,
+                                   double2 *G, double2 *g, double *tt, cudaStream_t s);
 // G (K x K, row-major), g (K) and t^H t per problem from S.
 cudaError_t launch_gram_assemble(const double *S, int nprob, int K, int Bp, int B, int T, double2 *G, double2 *g,
                                  double *tt, cudaStream_t s);

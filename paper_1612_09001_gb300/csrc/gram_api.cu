@@ -166,12 +166,18 @@ int gram_cpp(dpd_handle h, int nprob, int64_t n, int precision)
     return dpd::gram_ctas_per_problem(precision, h->sm_count, nprob, n);
 }
 
-// Gram (+ reduction + assembly) of nprob problems already described in w.probs.
-dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_t s)
+// Gram (+ reduction + assembly) of nprob problems described in w.probs, or of
+// the single problem *one (passed by value to the kernels, no copy); G and g
+// go to G_out / g_out when given, else to the workspace.  The basis is the
+// handle's estimate basis, or the monomials of Eq. 2 with `monomial`.
+dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_t s,
+                    const dpd::GramProblem *one = nullptr, double2 *G_out = nullptr, double2 *g_out = nullptr,
+                    bool monomial = false)
 {
     EstimateWorkspace &w = h->est;
     dpd::GramArgs a;
-    a.probs = static_cast<const dpd::GramProblem *>(w.probs);
+    a.probs = one ? nullptr : static_cast<const dpd::GramProblem *>(w.probs);
+    a.one = one ? *one : dpd::GramProblem{nullptr, nullptr, 0};
     a.nprob = nprob;
     a.cpp = cpp;
     a.Bp = h->Bp;
@@ -180,16 +186,18 @@ dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_
     a.K = h->K;
     a.partials = w.partials;
     a.status = h->d_status;
-    a.ubasis = ortho(h) ? w.ubasis : nullptr;
+    a.ubasis = ortho(h) && !monomial ? w.ubasis : nullptr;
+    double2 *G = G_out ? G_out : w.G, *g = G_out ? g_out : w.g;
     if (dpd::launch_gram(precision, a, s) != cudaSuccess) return DPD_ERR_CUDA;
     const int D = dpd::gram_distinct(h->B, h->T);
-    const cudaError_t e = precision == dpd::kPrecFP32
-                              ? dpd::launch_gram_reduce(w.partials, nprob, cpp, D, w.S, s)
-                              : dpd::launch_gram_lag_finish(w.partials, a.probs, a.ubasis, nprob, cpp, h->B, h->T,
-                                                            w.Clag, w.S, s);
-    if (e != cudaSuccess) return DPD_ERR_CUDA;
-    if (dpd::launch_gram_assemble(w.S, nprob, h->K, h->Bp, h->B, h->T, w.G, w.g, w.tt, s) != cudaSuccess)
+    if (precision == dpd::kPrecFP32) {
+        if (dpd::launch_gram_reduce(w.partials, nprob, cpp, D, w.S, s) != cudaSuccess ||
+            dpd::launch_gram_assemble(w.S, nprob, h->K, h->Bp, h->B, h->T, G, g, w.tt, s) != cudaSuccess)
+            return DPD_ERR_CUDA;
+    } else if (dpd::launch_gram_lag_finish(w.partials, a.probs, a.one, a.ubasis, nprob, cpp, h->K, h->Bp, h->B, h->T,
+                                           w.Clag, G, g, w.tt, s) != cudaSuccess) {
         return DPD_ERR_CUDA;
+    }
     return DPD_OK;
 }
 
@@ -716,14 +724,12 @@ dpd_status dpd_gram(dpd_handle h, const void *u, const void *t, int64_t n, int p
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int cpp = gram_cpp(h, 1, n, precision);
     if ((st = reserve(h, 1, cpp, 0)) != DPD_OK) return st;
+    // Psi of Eq. 2 (the monomial basis, whatever the handle's estimate basis);
+    // the problem travels by value in the kernel arguments.
     const dpd::GramProblem pr{static_cast<const float2 *>(u), static_cast<const float2 *>(t), n};
-    if (cudaMemcpyAsync(h->est.probs, &pr, sizeof(pr), cudaMemcpyHostToDevice, s) != cudaSuccess) return DPD_ERR_CUDA;
-    if ((st = run_gram(h, 1, cpp, precision, s)) != DPD_OK) return st;
-    const size_t KK = (size_t)h->K * h->K;
-    if (cudaMemcpyAsync(G, h->est.G, sizeof(double2) * KK, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return DPD_ERR_CUDA;
-    if (g && cudaMemcpyAsync(g, h->est.g, sizeof(double2) * h->K, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return DPD_ERR_CUDA;
+    if ((st = run_gram(h, 1, cpp, precision, s, &pr, static_cast<double2 *>(G), static_cast<double2 *>(g), true)) !=
+        DPD_OK)
+        return st;
     if (tt && t && (cudaMemcpyAsync(tt, h->est.tt, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                     cudaStreamSynchronize(s) != cudaSuccess))
         return DPD_ERR_CUDA;
@@ -741,9 +747,11 @@ dpd_status dpd_estimate(dpd_handle h, const void *u, const void *t, int64_t n, i
     if ((st = reserve(h, 1, cpp, (refine_iters > 0 || stats) ? n : 0)) != DPD_OK) return st;
     EstimateWorkspace &w = h->est;
     const dpd::GramProblem pr{static_cast<const float2 *>(u), static_cast<const float2 *>(t), n};
-    if (cudaMemcpyAsync(w.probs, &pr, sizeof(pr), cudaMemcpyHostToDevice, s) != cudaSuccess) return DPD_ERR_CUDA;
-    if (ortho(h) && (st = compute_basis(h, std::vector<int64_t>{n}, s)) != DPD_OK) return st;
-    if ((st = run_gram(h, 1, cpp, precision, s)) != DPD_OK) return st;
+    if (ortho(h)) {
+        if (cudaMemcpyAsync(w.probs, &pr, sizeof(pr), cudaMemcpyHostToDevice, s) != cudaSuccess) return DPD_ERR_CUDA;
+        if ((st = compute_basis(h, std::vector<int64_t>{n}, s)) != DPD_OK) return st;
+    }
+    if ((st = run_gram(h, 1, cpp, precision, s, ortho(h) ? nullptr : &pr)) != DPD_OK) return st;
     // For the statistics, G and (after the factorisation) the inverse factor go
     // to pinned host memory while the device carries on, and so does the pivot
     // status: the host condition estimate (Lanczos on D G D from G, and on its

@@ -76,6 +76,8 @@ constexpr int kLagN = 16 * kLagSigB;         // 224 accumulator columns
 constexpr int kLagAccCols = 256;             // column spacing of the two accumulators
 constexpr int kLagChunk = 4;                 // stages per accumulation chunk
 constexpr int kLagDStride = 257;             // row stride of the final D in shared memory (floats)
+constexpr int kLagGenWarps = 15;             // operand generators; warp 15 issues the MMAs
+constexpr int kLagGenThreads = 32 * kLagGenWarps;
 static_assert(kLagStages <= kLagChunk + 1, "drain must precede the reuse of an accumulator");
 static_assert(kLagEntries == kLagSigA * kLagSigB * kMaxT, "lag partial size");
 
@@ -102,13 +104,14 @@ __device__ __forceinline__ float psi_weight(int b, float r, const float *su)
 }
 
 // Raw samples of a stage: u and t from n0, R + 8 of each (the last 8 feed the
-// advanced rows), zero outside the problem.  One copy group per thread and stage.
+// advanced rows), zero outside the problem.  One copy group per generator
+// thread and stage.
 template <int FMT>
 __device__ __forceinline__ void lag_fetch(float2 *slot, const GramProblem &pr, int64_t n0, bool active)
 {
     using G = LagGeom<FMT>;
     if (active) {
-        for (int i = threadIdx.x; i < G::R + 8; i += kThreads) {
+        for (int i = threadIdx.x; i < G::R + 8; i += kLagGenThreads) {
             const int64_t j = n0 + i;
             const bool vu = j < pr.n, vt = pr.t != nullptr && j < pr.n;
             const int o = G::pidx(i);
@@ -133,18 +136,14 @@ __device__ __forceinline__ void lag_put(unsigned char *p, const float (&v)[E + 1
     uint32_t h[4], hs[4], l[4], ls[4];
     if constexpr (FMT == kFmtBF16) {
         uint32_t H[5], L[5];
-        float lo[E + 1];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             H[k] = bf16x2_bits(v[2 * k], v[2 * k + 1]);
-            lo[2 * k] = v[2 * k] - __uint_as_float(H[k] << 16);
-            lo[2 * k + 1] = v[2 * k + 1] - __uint_as_float(H[k] & 0xFFFF0000u);
+            L[k] = bf16x2_bits(v[2 * k] - __uint_as_float(H[k] << 16),
+                               v[2 * k + 1] - __uint_as_float(H[k] & 0xFFFF0000u));
         }
         H[4] = bf16x2_bits(v[8], 0.f);
-        lo[8] = v[8] - __uint_as_float(H[4] << 16);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) L[k] = bf16x2_bits(lo[2 * k], lo[2 * k + 1]);
-        L[4] = bf16x2_bits(lo[8], 0.f);
+        L[4] = bf16x2_bits(v[8] - __uint_as_float(H[4] << 16), 0.f);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {   // advanced by one: elements 2k + 1, 2k + 2
             h[k] = H[k];
@@ -153,17 +152,17 @@ __device__ __forceinline__ void lag_put(unsigned char *p, const float (&v)[E + 1
             ls[k] = __byte_perm(L[k], L[k + 1], 0x5432);
         }
     } else {
-        uint32_t hw[E + 1], lw[E + 1];
+        float hf[E + 1];
+        uint32_t lw[E + 1];
 #pragma unroll
         for (int i = 0; i <= E; ++i) {
-            const float a = to_tf32(v[i]);
-            hw[i] = __float_as_uint(a);
-            lw[i] = __float_as_uint(to_tf32(v[i] - a));
+            hf[i] = to_tf32(v[i]);
+            lw[i] = __float_as_uint(to_tf32(v[i] - hf[i]));
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            h[k] = hw[k];
-            hs[k] = hw[k + 1];
+            h[k] = __float_as_uint(hf[k]);
+            hs[k] = __float_as_uint(hf[k + 1]);
             l[k] = lw[k];
             ls[k] = lw[k + 1];
         }
@@ -175,8 +174,8 @@ __device__ __forceinline__ void lag_put(unsigned char *p, const float (&v)[E + 1
 }
 
 // Operands of the stage starting at sample n0 from its raw slot.  Warp w:
-// w < 12: Re / Im psi_{w/2}; 12, 13: Re / Im t; 14, 15: the constant; core
-// matrices c = 4 (w & 1) .. + 3, lane (c, r).
+// w < 12: Re / Im psi_{w/2}; 12, 13: Re / Im t, core matrices c = 4 (w & 1)
+// .. + 3, lane (c, r); 14: the constant, all 64 rows.
 template <int FMT>
 __device__ __forceinline__ void lag_generate(unsigned char *st, const float2 *slot, int64_t n0, int64_t n,
                                              const float *su)
@@ -184,29 +183,35 @@ __device__ __forceinline__ void lag_generate(unsigned char *st, const float2 *sl
     using G = LagGeom<FMT>;
     constexpr int E = G::E;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = 4 * (w & 1) + (lane >> 3), r = lane & 7;
-    const int cr = c * 128 + r * 16;
-    if (w >= 14) {   // 1 inside the record (hi only; lo and the advanced rows stay zero)
-        uint32_t q[4];
-        if constexpr (FMT == kFmtBF16) {
+    if (w == 14) {   // 1 inside the record (hi only; lo and the advanced rows stay zero)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t s0 = n0 + 8 * (E * c + 2 * k) + r;
-                q[k] = (s0 < n ? 0x3F80u : 0u) | (s0 + 8 < n ? 0x3F800000u : 0u);
+        for (int hh = 0; hh < 2; ++hh) {
+            const int c = 4 * hh + (lane >> 3), r = lane & 7;
+            uint32_t q[4];
+            if constexpr (FMT == kFmtBF16) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int64_t s0 = n0 + 8 * (E * c + 2 * k) + r;
+                    q[k] = (s0 < n ? 0x3F80u : 0u) | (s0 + 8 < n ? 0x3F800000u : 0u);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) q[k] = n0 + 8 * (E * c + k) + r < n ? 0x3F800000u : 0u;
             }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) q[k] = n0 + 8 * (E * c + k) + r < n ? 0x3F800000u : 0u;
+            *reinterpret_cast<uint4 *>(st + kLagSerOne * kLagSlotBytes + c * 128 + r * 16) =
+                make_uint4(q[0], q[1], q[2], q[3]);
         }
-        *reinterpret_cast<uint4 *>(st + kLagSerOne * kLagSlotBytes + cr) = make_uint4(q[0], q[1], q[2], q[3]);
         return;
     }
+    const int c = 4 * (w & 1) + (lane >> 3), r = lane & 7;
     const bool target = w >= 12;
-    const float2 *src = slot + (target ? G::RawSig : 0);
+    // sample 8 (E c + i) + r of the slot sits at pidx = (8 E + 8) c + 8 i + r for
+    // i < E, and sample E (the next core matrix) 8 further
+    const float2 *src = slot + (target ? G::RawSig : 0) + (8 * E + 8) * c + r;
     float re[E + 1], im[E + 1];
 #pragma unroll
     for (int i = 0; i <= E; ++i) {
-        const float2 x = src[G::pidx(8 * (E * c + i) + r)];
+        const float2 x = src[i < E ? 8 * i : 8 * E + 8];
         re[i] = x.x;
         im[i] = x.y;
     }
@@ -240,15 +245,32 @@ __device__ __forceinline__ void lag_generate(unsigned char *st, const float2 *sl
             im[i] *= pw[i];
         }
     }
-    unsigned char *p = st + sig * kLagSlotBytes + cr;
+    unsigned char *p = st + sig * kLagSlotBytes + c * 128 + r * 16;
     lag_put<FMT, E>(p, re);
     lag_put<FMT, E>(p + kLagSlotBytes, im);
 }
 
-// Barriers: empty[s] (MMA commit: stage s consumed), acc_full[b] (a chunk's
-// sum is complete in accumulator b), fin (everything issued has completed).
-// Roles: every thread generates one task per stage and drains, thread 0
-// issues a stage's MMAs after the barrier that follows its generation.
+// Named barrier over the generator warps, OR-reducing a flag.
+__device__ __forceinline__ bool gen_barrier_or(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+        "barrier.cta.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kLagGenThreads)
+        : "memory");
+    return r != 0;
+}
+
+// Barriers: full[s] (the 15 generator warps have written stage buffer s),
+// empty[s] (MMA commit: stage buffer s consumed), acc_full[b] (a chunk's sum is
+// complete in accumulator b), fin (everything issued has completed).
+// Roles: warps 0 .. 14 fetch and generate, warp 15 issues the MMAs (lane 0),
+// all sixteen drain.  An MMA issue blocks while the tensor core's queue is
+// full, so the issuing warp does nothing else on the way: the generators run
+// up to kLagStages stages ahead of it, synchronised only among themselves
+// (raw-slot reuse) and through full / empty.
 template <int FMT>
 __global__ void __launch_bounds__(kThreads, 1) gram_lag_kernel(GramArgs a)
 {
@@ -259,14 +281,15 @@ __global__ void __launch_bounds__(kThreads, 1) gram_lag_kernel(GramArgs a)
     unsigned char *stages = smem;
     float2 *raw = reinterpret_cast<float2 *>(stages + kLagStages * kLagStageBytes);
     uint64_t *empty = reinterpret_cast<uint64_t *>(raw + kLagRawSlots * G::Raw);
-    uint64_t *acc_full = empty + kLagStages;
+    uint64_t *full = empty + kLagStages;
+    uint64_t *acc_full = full + kLagStages;
     uint64_t *fin = acc_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
     float *su_buf = reinterpret_cast<float *>(tmem_slot + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int prob = blockIdx.x / a.cpp, chunk = blockIdx.x % a.cpp;
-    const GramProblem pr = a.probs[prob];
+    const GramProblem pr = a.probs ? a.probs[prob] : a.one;
     const int64_t nblk = (pr.n + R - 1) / R;
     const int64_t b0 = nblk * chunk / a.cpp, b1 = nblk * (chunk + 1) / a.cpp;
     const int nits = (int)(b1 - b0);
@@ -281,7 +304,10 @@ __global__ void __launch_bounds__(kThreads, 1) gram_lag_kernel(GramArgs a)
     for (int i = tid; i < kLagStages * kLagStageBytes / 16; i += kThreads)
         reinterpret_cast<uint4 *>(stages)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
-        for (int s = 0; s < kLagStages; ++s) mbar_init(smem_addr(&empty[s]), 1);
+        for (int s = 0; s < kLagStages; ++s) {
+            mbar_init(smem_addr(&empty[s]), 1);
+            mbar_init(smem_addr(&full[s]), kLagGenWarps);
+        }
         for (int b = 0; b < 2; ++b) mbar_init(smem_addr(&acc_full[b]), 1);
         mbar_init(smem_addr(fin), 1);
         fence_barrier_init();
@@ -290,8 +316,11 @@ __global__ void __launch_bounds__(kThreads, 1) gram_lag_kernel(GramArgs a)
         tmem_alloc(smem_addr(tmem_slot), 2 * kLagAccCols);
         tmem_relinquish();
     }
+    const bool generator = warp < kLagGenWarps;
+    if (generator) {
 #pragma unroll
-    for (int j = 0; j < kLagAhead; ++j) lag_fetch<FMT>(raw + j * G::Raw, pr, (b0 + j) * R, j < nits);
+        for (int j = 0; j < kLagAhead; ++j) lag_fetch<FMT>(raw + j * G::Raw, pr, (b0 + j) * R, j < nits);
+    }
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
@@ -351,61 +380,85 @@ __global__ void __launch_bounds__(kThreads, 1) gram_lag_kernel(GramArgs a)
     bool failed = false;
     int next_drain = 0;
     bool drained_ok = true;
-    for (int it = 0; it < nits; ++it) {
-        const int s = it % kLagStages;
-        bool ok = drained_ok;
-        if (it >= kLagStages)
-            ok = mbar_wait(smem_addr(&empty[s]), (uint32_t)(((it / kLagStages) - 1) & 1), a.status) && ok;
-        cp_async_wait<kLagAhead - 1>();   // this thread's copies of stage it have landed
-        // every thread has written stage it - 1 and its copies of stage it are visible
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
+    if (generator) {
+        for (int it = 0; it < nits; ++it) {
+            const int s = it % kLagStages;
+            bool ok = drained_ok;
+            if (it >= kLagStages)
+                ok = mbar_wait(smem_addr(&empty[s]), (uint32_t)(((it / kLagStages) - 1) & 1), a.status) && ok;
+            cp_async_wait<kLagAhead - 1>();   // this thread's copies of stage it have landed
+            // every generator has finished stage it - 1 and its copies of stage it are visible
+            if (gen_barrier_or(!ok)) {
+                failed = true;
+                break;
+            }
+            // the slot of stage it - 1 (read in the previous iteration) receives stage it + kLagAhead
+            lag_fetch<FMT>(raw + ((it + kLagAhead) % kLagRawSlots) * G::Raw, pr, (b0 + it + kLagAhead) * R,
+                           it + kLagAhead < nits);
+            lag_generate<FMT>(stages + s * kLagStageBytes, raw + (it % kLagRawSlots) * G::Raw, (b0 + it) * R, pr.n,
+                              su);
+            fence_async_shared();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&full[s]));
+            while (next_drain < nchunks) {
+                const int last = min((next_drain + 1) * kLagChunk, nits) - 1;
+                if (last + kLagStages > it) break;
+                drained_ok = drain(next_drain++) && drained_ok;
+            }
         }
-        if (tid == 0 && it > 0) issue(it - 1);
-        // the slot of stage it - 1 (read in the previous iteration) receives stage it + kLagAhead
-        lag_fetch<FMT>(raw + ((it + kLagAhead) % kLagRawSlots) * G::Raw, pr, (b0 + it + kLagAhead) * R,
-                       it + kLagAhead < nits);
-        lag_generate<FMT>(stages + s * kLagStageBytes, raw + (it % kLagRawSlots) * G::Raw, (b0 + it) * R, pr.n, su);
-        fence_async_shared();
-        while (next_drain < nchunks) {
-            const int last = min((next_drain + 1) * kLagChunk, nits) - 1;
-            if (last + kLagStages > it) break;
-            drained_ok = drain(next_drain++) && drained_ok;
-        }
-    }
-    if (!failed && nits > 0) {
-        if (__syncthreads_or(!drained_ok)) {
-            failed = true;
-        } else {
-            if (tid == 0) issue(nits - 1);
+        if (!failed)
             while (next_drain < nchunks) drained_ok = drain(next_drain++) && drained_ok;
-            failed = __syncthreads_or(!drained_ok);
+    } else {
+        // The issuer drains chunk c once the first stage after it is queued
+        // (the tensor core stays busy while it waits).
+        for (int j = 0; j < nits; ++j) {
+            const int s = j % kLagStages;
+            bool ok = mbar_wait(smem_addr(&full[s]), (uint32_t)((j / kLagStages) & 1), a.status);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            if (lane == 0) issue(j);
+            __syncwarp();
+            while (next_drain < nchunks && min((next_drain + 1) * kLagChunk, nits) <= j)
+                drained_ok = drain(next_drain++) && drained_ok;
         }
+        if (!failed)
+            while (next_drain < nchunks) drained_ok = drain(next_drain++) && drained_ok;
     }
+    failed = failed || !drained_ok;
     cp_async_wait<0>();
-    if (tid == 0 && issued > 0) {
+    if (warp == kLagGenWarps && lane == 0 && issued > 0) {
         umma_commit(smem_addr(fin));
         mbar_wait(smem_addr(fin), 0u, a.status);
     }
     tc_fence_before_sync();
-    __syncthreads();   // every MMA has completed: the stage buffers are free
+    failed = __syncthreads_or(failed);   // every MMA has completed: the stage buffers are free
 
-    // C[a][b][d] = sum_r D[(a, r), (b, r + d)] through shared memory, FP64.
+    // C[a][b][d] = sum_r D[(a, r), (b, r + d)] through shared memory: an FP32
+    // sum with its rounding error carried exactly (two-sum), stored as the
+    // pair (sum, error); the FP64 additions (slow on this GPU) are left to the
+    // reduction over CTAs.
     float *Dsm = reinterpret_cast<float *>(stages);
     const bool zero = failed || nits == 0;
 #pragma unroll
     for (int i = 0; i < 64; ++i)
         if (64 * piece + i < kLagN) Dsm[row * kLagDStride + 64 * piece + i] = zero ? 0.f : acc[i];
     __syncthreads();
-    double *part = reinterpret_cast<double *>(a.partials) + (size_t)blockIdx.x * kLagEntries;
+    float2 *part = reinterpret_cast<float2 *>(a.partials) + (size_t)blockIdx.x * kLagEntries;
     for (int e = tid; e < kLagEntries; e += kThreads) {
         const int sa = e / (kLagSigB * kMaxT), sb = (e / kMaxT) % kLagSigB, d = e % kMaxT;
         const float *dp = Dsm + (8 * sa) * kLagDStride + 16 * sb + d;
-        double v = 0.0;
+        float sum = dp[0], err = 0.f;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v += (double)dp[r * (kLagDStride + 1)];
-        part[e] = v;
+        for (int r = 1; r < 8; ++r) {
+            const float x = dp[r * (kLagDStride + 1)];
+            const float t = sum + x, z = t - sum;
+            err += (sum - (t - z)) + (x - z);
+            sum = t;
+        }
+        part[e] = make_float2(sum, err);
     }
 
     tc_fence_before_sync();
@@ -420,14 +473,14 @@ size_t gram_lag_smem(int fmt)
 {
     const int raw = fmt == kFmtBF16 ? LagGeom<kFmtBF16>::Raw : LagGeom<kFmtTF32>::Raw;
     const size_t body = (size_t)kLagStages * kLagStageBytes + (size_t)kLagRawSlots * raw * 8 +
-                        (kLagStages + 3) * 8 + 16 + kUSize * 4;
+                        (2 * kLagStages + 3) * 8 + 16 + kUSize * 4;
     const size_t dfinal = (size_t)128 * kLagDStride * 4;
     return 1024 + (body > dfinal ? body : dfinal);
 }
 
 // ---- finishing: partial lag sums -> S
-// C[p][e] = sum over the problem's CTAs of the FP64 partials, in a fixed order.
-__global__ void __launch_bounds__(256) gram_lag_reduce_kernel(const double *__restrict__ partials, int cpp,
+// C[p][e] = sum over the problem's CTAs of the partial pairs, in FP64 and a fixed order.
+__global__ void __launch_bounds__(256) gram_lag_reduce_kernel(const float2 *__restrict__ partials, int cpp,
                                                               double *__restrict__ C)
 {
     __shared__ double grp[8][32];
@@ -435,16 +488,20 @@ __global__ void __launch_bounds__(256) gram_lag_reduce_kernel(const double *__re
     const int e = blockIdx.x * 32 + lane;
     double s = 0.0;
     if (e < kLagEntries) {
-        const double *base = partials + (size_t)p * cpp * kLagEntries + e;
+        const float2 *base = partials + (size_t)p * cpp * kLagEntries + e;
+        auto val = [&](int k) {
+            const float2 v = base[(size_t)k * kLagEntries];
+            return (double)v.x + (double)v.y;
+        };
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // partials g, g + 8, g + 16, g + 24, g + 32, ...
         int k = g;
         for (; k + 24 < cpp; k += 32) {
-            s0 += base[(size_t)k * kLagEntries];
-            s1 += base[(size_t)(k + 8) * kLagEntries];
-            s2 += base[(size_t)(k + 16) * kLagEntries];
-            s3 += base[(size_t)(k + 24) * kLagEntries];
+            s0 += val(k);
+            s1 += val(k + 8);
+            s2 += val(k + 16);
+            s3 += val(k + 24);
         }
-        for (; k < cpp; k += 8) s0 += base[(size_t)k * kLagEntries];
+        for (; k < cpp; k += 8) s0 += val(k);
         s = (s0 + s1) + (s2 + s3);
     }
     grp[g][lane] = s;
@@ -471,23 +528,25 @@ __device__ __forceinline__ void lag_source(int d, int B, int T, int &sig, int &t
     }
 }
 
-// S (P block, Q = 0: the layout the assembly reads) from the lag sums; grid
-// (entries / 256, problems).  The last T - 1 samples of every signal,
-// evaluated as the tensor kernel evaluates them, give the end products.
-__global__ void __launch_bounds__(256) gram_lag_spq_kernel(const double *__restrict__ Call,
-                                                           const GramProblem *__restrict__ probs,
-                                                           const float *__restrict__ ubasis, int B, int T,
-                                                           double *__restrict__ SPQall)
+// G, g and t^H t of each problem from its lag sums; grid (entries / 256,
+// problems).  An entry of S is C less the end products, which come from the
+// last T - 1 samples of every signal evaluated as the tensor kernel evaluates
+// them; they are a few of the N products of an entry, so they are summed in
+// FP32 and only the difference is formed in FP64.
+__global__ void __launch_bounds__(256) gram_lag_assemble_kernel(const double *__restrict__ Call,
+                                                                const GramProblem *__restrict__ probs,
+                                                                GramProblem one, const float *__restrict__ ubasis,
+                                                                int K, int Bp, int B, int T, double2 *__restrict__ G,
+                                                                double2 *__restrict__ g, double *__restrict__ tt)
 {
-    __shared__ double xt[kLagSigA][kMaxT];   // x_s(N - 8 + i), zero before the record
+    __shared__ float xt[kLagSigA][kMaxT];   // x_s(N - 8 + i), zero before the record
     __shared__ float su_buf[kUSize];
-    __shared__ int2 src[kGramS];              // (signal, tap) of each distinct column
+    __shared__ int2 src[kGramS];             // (signal, tap) of each distinct column
     const int p = blockIdx.y, tid = threadIdx.x;
-    const GramProblem pr = probs[p];
+    const GramProblem pr = probs ? probs[p] : one;
     const int64_t N = pr.n;
     const int D = gram_distinct(B, T);
     const double *C = Call + (size_t)p * kLagEntries;
-    double *SPQ = SPQall + (size_t)p * kGramS * kGramPartCols;
     const float *su = nullptr;
     if (ubasis) {
         if (tid < kUSize) su_buf[tid] = ubasis[(size_t)p * kUSize + tid];
@@ -500,29 +559,29 @@ __global__ void __launch_bounds__(256) gram_lag_spq_kernel(const double *__restr
     }
     __syncthreads();
     if (tid < kMaxT * 8) {
-        const int i = tid / 8, g = tid % 8;   // sample N - 8 + i; g < 6 basis, 6 target, 7 constant
+        const int i = tid / 8, gi = tid % 8;   // sample N - 8 + i; gi < 6 basis, 6 target, 7 constant
         const int64_t k = N - kMaxT + i;
-        double v0 = 0.0, v1 = 0.0;
+        float v0 = 0.f, v1 = 0.f;
         if (k >= 0) {
-            if (g < 6) {
+            if (gi < 6) {
                 const float2 x = pr.u[k];
-                const float w = psi_weight(g, fmaf(x.x, x.x, x.y * x.y), su);
-                v0 = (double)(w * x.x);
-                v1 = (double)(w * x.y);
-            } else if (g == 6) {
+                const float w = psi_weight(gi, fmaf(x.x, x.x, x.y * x.y), su);
+                v0 = w * x.x;
+                v1 = w * x.y;
+            } else if (gi == 6) {
                 if (pr.t) {
                     const float2 x = pr.t[k];
                     v0 = x.x;
                     v1 = x.y;
                 }
             } else {
-                v0 = 1.0;
+                v0 = 1.f;
             }
         }
-        if (g < 6) {
-            xt[2 * g][i] = v0;
-            xt[2 * g + 1][i] = v1;
-        } else if (g == 6) {
+        if (gi < 6) {
+            xt[2 * gi][i] = v0;
+            xt[2 * gi + 1][i] = v1;
+        } else if (gi == 6) {
             xt[kLagSerT][i] = v0;
             xt[kLagSerT + 1][i] = v1;
         } else {
@@ -530,48 +589,66 @@ __global__ void __launch_bounds__(256) gram_lag_spq_kernel(const double *__restr
         }
     }
     __syncthreads();
-    const int e = blockIdx.x * blockDim.x + tid;
-    if (e >= D * D) return;
-    const int i = e / D, j = e % D;
-    SPQ[(size_t)i * kGramPartCols + kGramS + j] = 0.0;
-    if (j < i) return;
-    int sa = src[i].x, ma = src[i].y, sb = src[j].x, mb = src[j].y;
-    // (sa, ma): the larger tap; at equal taps the constant on the A side
-    if (mb > ma || (mb == ma && sb == kLagSerOne)) {
-        const int s0 = sa, m0 = ma;
-        sa = sb;
-        ma = mb;
-        sb = s0;
-        mb = m0;
-    }
-    const int dl = ma - mb;
-    double v;
-    if ((int64_t)ma >= N) {
-        v = 0.0;   // column (sa, ma) is zero on every row
-    } else if (sb == kLagSerOne) {
-        // against the constant at tap 0: sum_{k < N - ma} x_sa(k) = C[one][sa][0] less the last ma samples
-        if (sa == kLagSerOne) {
-            v = (double)N;
-        } else {
-            v = C[(kLagSerOne * kLagSigB + sa) * kMaxT];
-            for (int k = 0; k < ma; ++k) v -= xt[sa][kMaxT - 1 - k];
+    // <x, y> for two signed distinct-column references
+    auto dot = [&](ColRef x, ColRef y) -> double {
+        if (x.sign == 0 || y.sign == 0) return 0.0;
+        int sa = src[x.d].x, ma = src[x.d].y, sb = src[y.d].x, mb = src[y.d].y;
+        // (sa, ma): the larger tap; at equal taps the constant on the A side
+        if (mb > ma || (mb == ma && sb == kLagSerOne)) {
+            const int s0 = sa, m0 = ma;
+            sa = sb;
+            ma = mb;
+            sb = s0;
+            mb = m0;
         }
-    } else {
-        v = C[(sa * kLagSigB + sb) * kMaxT + dl];
-        // samples N - ma .. N - 1 - dl: xt index k = sample - (N - 8)
-        for (int k = kMaxT - ma; k <= kMaxT - 1 - dl; ++k) v -= xt[sa][k] * xt[sb][k + dl];
+        const int dl = ma - mb;
+        double v;
+        if ((int64_t)ma >= N) {
+            v = 0.0;   // column (sa, ma) is zero on every row
+        } else if (sb == kLagSerOne) {
+            // against the constant at tap 0: sum_{k < N - ma} x_sa(k) = C[one][sa][0] less the last ma samples
+            if (sa == kLagSerOne) {
+                v = (double)N;
+            } else {
+                float tl = 0.f;
+                for (int k = 0; k < ma; ++k) tl += xt[sa][kMaxT - 1 - k];
+                v = C[(kLagSerOne * kLagSigB + sa) * kMaxT] - (double)tl;
+            }
+        } else {
+            // samples N - ma .. N - 1 - dl: xt index k = sample - (N - 8)
+            float tl = 0.f;
+            for (int k = kMaxT - ma; k <= kMaxT - 1 - dl; ++k) tl = fmaf(xt[sa][k], xt[sb][k + dl], tl);
+            v = C[(sa * kLagSigB + sb) * kMaxT + dl] - (double)tl;
+        }
+        return x.sign * y.sign > 0 ? v : -v;
+    };
+    const int idx = blockIdx.x * blockDim.x + tid;
+    const ColRef tre{2 * B * T + 1, 1}, tim{2 * B * T + 2, 1};
+    if (idx < K * K) {
+        const int a = idx / K, b = idx % K;
+        ColRef ar, ai, br, bi;
+        psi_column_refs(a, K, Bp, B, T, ar, ai);
+        psi_column_refs(b, K, Bp, B, T, br, bi);
+        G[(size_t)p * K * K + idx] = make_double2(dot(ar, br) + dot(ai, bi), dot(ar, bi) - dot(ai, br));
+    } else if (idx < K * K + K) {
+        const int a = idx - K * K;
+        ColRef ar, ai;
+        psi_column_refs(a, K, Bp, B, T, ar, ai);
+        if (g) g[(size_t)p * K + a] = make_double2(dot(ar, tre) + dot(ai, tim), dot(ar, tim) - dot(ai, tre));
+    } else if (idx == K * K + K) {
+        if (tt) tt[p] = dot(tre, tre) + dot(tim, tim);
     }
-    SPQ[(size_t)i * kGramPartCols + j] = v;
 }
 
-cudaError_t launch_gram_lag_finish(const float *partials, const GramProblem *probs, const float *ubasis, int nprob,
-                                   int cpp, int B, int T, double *C, double *S, cudaStream_t s)
+cudaError_t launch_gram_lag_finish(const float *partials, const GramProblem *probs, GramProblem one,
+                                   const float *ubasis, int nprob, int cpp, int K, int Bp, int B, int T, double *C,
+                                   double2 *G, double2 *g, double *tt, cudaStream_t s)
 {
     gram_lag_reduce_kernel<<<dim3((kLagEntries + 31) / 32, nprob), 256, 0, s>>>(
-        reinterpret_cast<const double *>(partials), cpp, C);
+        reinterpret_cast<const float2 *>(partials), cpp, C);
     count_launch();
-    const int D = gram_distinct(B, T);
-    gram_lag_spq_kernel<<<dim3((D * D + 255) / 256, nprob), 256, 0, s>>>(C, probs, ubasis, B, T, S);
+    gram_lag_assemble_kernel<<<dim3((K * K + K + 1 + 255) / 256, nprob), 256, 0, s>>>(C, probs, one, ubasis, K, Bp,
+                                                                                       B, T, G, g, tt);
     count_launch();
     return cudaGetLastError();
 }
@@ -633,7 +710,7 @@ __global__ void __launch_bounds__(kF32Threads) gram_fp32_kernel(GramArgs a)
 
     const int tid = threadIdx.x;
     const int prob = blockIdx.x / a.cpp, chunk = blockIdx.x % a.cpp;
-    const GramProblem pr = a.probs[prob];
+    const GramProblem pr = a.probs ? a.probs[prob] : a.one;
     const int T = a.T, B = a.Bp > a.Bq ? a.Bp : a.Bq;
     const int D = gram_distinct(B, T);
     const int nb8 = (D + 7) / 8;

@@ -145,6 +145,24 @@ def test_gram_without_host_readback_matches():
     f.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "bf16x3"])
+def test_gram_uses_the_basis_of_eq2_whatever_the_estimate_basis(precision):
+    """dpd_gram returns the Gram of the monomial basis of Eq. 2 also on a handle
+    whose estimates run in the orthogonal basis (set and used first, so that
+    its basis matrix exists on the device), against the FP64 oracle."""
+    P, Q, M, n = 7, 5, 3, 6007
+    u, t, _ = _ls_problem(P, Q, M, n, seed=9)
+    f = dpd.DPD(P, Q, M)
+    ud, td = torch.from_numpy(u).cuda(), torch.from_numpy(t).cuda()
+    f.estimate(ud, td, precision=precision, refine_iters=1, basis="orthogonal")
+    G, g, tt = f.gram(ud, td, precision=precision)
+    Gr, gr = oracle.gram(u, t, P, Q, M)
+    d = np.sqrt(np.abs(np.diag(Gr)))
+    err = np.abs(G.cpu().numpy() - Gr) / np.outer(d, d)
+    assert err.max() <= GRAM_TOL[precision], err.max()
+    f.close()
+
+
 @pytest.mark.parametrize("basis", ["monomial", "orthogonal"])
 def test_estimate_batched_refinement_paths_agree(basis):
     """The batch refined together (16-byte aligned inputs: one launch per
