@@ -23,6 +23,7 @@ struct dpd_plan_s {
     int64_t tab_floats = 0;
     int small = 1;            // every stream has B <= 5 and T <= 7
     int V = 8, warps = 8, stages = 4, ctas_per_sm = 0, group = 0;
+    int nsub = dpd::batch_nsub(8, 8, 4, 8);   // sub-blocks per thread and item (follows the launch shape)
 };
 
 namespace {
@@ -45,14 +46,14 @@ void free_plan(dpd_plan p)
     delete p;
 }
 
-// Work list for tile size S = warps * 32 * V: streams by decreasing per-sample
+// Work list for tile size S = nsub * warps * 32 * V: streams by decreasing per-sample
 // cost (B * T), every tile of a stream in order.  Launched CTAs take items
 // round-robin.  The list goes to a new device buffer that replaces the plan's
 // only once it holds the list, so on failure the plan keeps its previous list
 // (and tiling) unchanged.
-dpd_status build_items(dpd_plan p, int V, int warps)
+dpd_status build_items(dpd_plan p, int V, int warps, int nsub)
 {
-    const int S = warps * 32 * V;
+    const int S = nsub * warps * 32 * V;
     std::vector<int> order(p->streams.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
     // Costliest models first (B T per sample), and streams of the same model
@@ -165,7 +166,7 @@ dpd_status dpd_plan_batched(const dpd_stream_desc *descs, int count, int where, 
         free_plan(p);
         return DPD_ERR_CUDA;
     }
-    dpd_status st = build_items(p, p->V, p->warps);
+    dpd_status st = build_items(p, p->V, p->warps, p->nsub);
     if (st == DPD_OK && cudaDeviceSynchronize() != cudaSuccess) st = DPD_ERR_CUDA;
     if (st != DPD_OK) {
         free_plan(p);
@@ -181,15 +182,18 @@ dpd_status dpd_plan_set_launch(dpd_plan p, int V, int warps, int stages, int cta
     if ((V != 4 && V != 6 && V != 8) || warps < 1 || warps > 16 || stages < 2 || stages > 8 || ctas_per_sm < 0 || group < 0 ||
         (group > 0 && warps % group != 0))
         return DPD_ERR_INVALID_ARGUMENT;
-    if (dpd::batch_smem(warps, group > 0 ? group : warps, stages, V) > (size_t)227 * 1024) return DPD_ERR_UNSUPPORTED;
-    if (V != p->V || warps != p->warps) {
+    const int gw = group > 0 ? group : warps;
+    if (dpd::batch_smem(warps, gw, stages, V) > dpd::kBatchSmemMax) return DPD_ERR_UNSUPPORTED;
+    const int nsub = dpd::batch_nsub(warps, gw, stages, V);
+    if (V != p->V || warps != p->warps || nsub != p->nsub) {
         // Re-tile first: the new shape is kept only once its work list is on
         // the device; on failure the plan runs with its previous shape.
-        const dpd_status st = build_items(p, V, warps);
+        const dpd_status st = build_items(p, V, warps, nsub);
         if (st != DPD_OK) return st;
     }
     p->V = V;
     p->warps = warps;
+    p->nsub = nsub;
     p->stages = stages;
     p->ctas_per_sm = ctas_per_sm;
     p->group = group;
@@ -210,6 +214,7 @@ dpd_status dpd_exec_batched(dpd_plan p, void *stream)
     a.tab_floats = p->tab_floats;
     a.status = p->d_status;
     a.gw = p->group;
+    a.nsub = p->nsub;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = p->small ? dpd::launch_batched_57(a, p->V, p->warps, p->stages, p->ctas_per_sm, p->sm_count, s)
                              : dpd::launch_batched_68(a, p->V, p->warps, p->stages, p->ctas_per_sm, p->sm_count, s);

@@ -42,6 +42,7 @@ struct BatchArgs {
     int64_t tab_floats;   // size of the table pool
     int *status;
     int gw = 0;           // consumer warps per group (0: one group of all warps)
+    int nsub = 1;         // sub-blocks of V samples per thread and item
 };
 
 constexpr int kBatchTabBytes = ((kMaxTabFloats * 4 + 15) / 16) * 16;   // table area of a slot
@@ -97,7 +98,8 @@ __device__ __forceinline__ void batched_item(const unsigned char *slot, const Ba
 #define DPD_BCASE(b, t)                                                                            \
     case (b) * 16 + (t):                                                                           \
         if constexpr ((b) <= BMAX && (t) <= TMAX) {                                                \
-            batched_item<(b), (t), V>(slot, hd, SG, t_in_tile);                                    \
+            for (int sb = 0; sb < a.nsub; ++sb)                                                    \
+                batched_item<(b), (t), V>(slot, hd, SG, sb * gw * 32 + t_in_tile);                 \
             break;                                                                                 \
         }                                                                                          \
         bad = true;                                                                                \
@@ -116,8 +118,8 @@ __global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int s
     // per group g: full[s] at bars[2 stages g + s], empty[s] at bars[2 stages g + stages + s]
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     unsigned char *ring = smem + ((2 * ngroups * stages * 8 + 127) / 128) * 128;
-    const int S = nwarps * 32 * V;    // the item's tile
-    const int SG = gw * 32 * V;       // a group's part of it
+    const int S = a.nsub * nwarps * 32 * V;   // the item's tile
+    const int SG = a.nsub * gw * 32 * V;      // a group's part of it: nsub sub-blocks of gw * 32 * V
     const size_t slot_bytes = batch_slot_bytes(SG);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -233,10 +235,21 @@ __global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int s
 
 // Shared-memory bytes of the batched kernel: barrier pairs of every group and
 // stage, then per group `stages` slots of its sub-tile.
-__host__ __device__ constexpr size_t batch_smem(int warps, int gw, int stages, int V)
+__host__ __device__ constexpr size_t batch_smem(int warps, int gw, int stages, int V, int nsub = 1)
 {
     return (size_t)((2 * (warps / gw) * stages * 8 + 127) / 128) * 128 +
-           (size_t)(warps / gw) * stages * batch_slot_bytes(gw * 32 * V);
+           (size_t)(warps / gw) * stages * batch_slot_bytes(nsub * gw * 32 * V);
+}
+
+// Sub-blocks per thread and item: each item costs a barrier wait, a header read
+// and a dispatch, so an item carries up to 4 sub-blocks of V samples per
+// thread, as many as the ring still fits in shared memory.
+constexpr size_t kBatchSmemMax = 227 * 1024;
+__host__ __device__ constexpr int batch_nsub(int warps, int gw, int stages, int V)
+{
+    return batch_smem(warps, gw, stages, V, 4) <= kBatchSmemMax   ? 4
+           : batch_smem(warps, gw, stages, V, 2) <= kBatchSmemMax ? 2
+                                                                   : 1;
 }
 
 // One persistent launch over the work items: orders up to 9 (B <= 5) and up
@@ -252,7 +265,8 @@ cudaError_t launch_batched_impl(const BatchArgs &a, int warps, int stages, int c
 {
     const int threads = (warps + 1) * 32;
     const int gw = (a.gw > 0 && warps % a.gw == 0) ? a.gw : warps;
-    const size_t smem = batch_smem(warps, gw, stages, V);
+    if (a.nsub < 1 || a.nsub > 4) return cudaErrorInvalidValue;
+    const size_t smem = batch_smem(warps, gw, stages, V, a.nsub);
     auto kern = fwd_batched_kernel<BMAX, TMAX, V>;
     static SmemAttr smem_rec;
     cudaError_t e = ensure_smem(smem_rec, (const void *)kern, smem);

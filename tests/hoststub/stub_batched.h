@@ -7,8 +7,11 @@ enum : int { kFlagTimeout = 1, kFlagBadWork = 2 };
 constexpr int wl_table_floats(int B, int T) { return 4 * B * T + 2; }
 struct BatchStream { const float2 *x; float2 *y; int64_t n; int B, T; int tab_off; int tab_bytes; };
 struct BatchItem { int stream; int tile; };
-struct BatchArgs { const BatchStream *streams; const BatchItem *items; int nitems; int nstreams; const float *tabs; int64_t tab_floats; int *status; int gw = 0; };
-constexpr size_t batch_smem(int warps, int gw, int stages, int V) { return (size_t)(warps / gw) * stages * (64 + 784 + (8 + gw * 32 * V) * 8) + 128; }
+struct BatchArgs { const BatchStream *streams; const BatchItem *items; int nitems; int nstreams; const float *tabs; int64_t tab_floats; int *status; int gw = 0; int nsub = 1; };
+constexpr size_t batch_smem(int warps, int gw, int stages, int V, int nsub = 1) { return (size_t)(warps / gw) * stages * (64 + 784 + (8 + nsub * gw * 32 * V) * 8) + 128; }
+constexpr size_t kBatchSmemMax = 227 * 1024;
+constexpr int batch_nsub(int warps, int gw, int stages, int V) {
+  return batch_smem(warps, gw, stages, V, 4) <= kBatchSmemMax ? 4 : batch_smem(warps, gw, stages, V, 2) <= kBatchSmemMax ? 2 : 1; }
 inline cudaError_t launch_wl_table(const float2 *h, int Bp, int Bq, int T, float *tab, float *adj, cudaStream_t) {
   int B = Bp > Bq ? Bp : Bq; for (int i = 0; i < 4*B*T+2; ++i) tab[i] = h[0].x; return 0; }
 inline cudaError_t launch_batched_57(const BatchArgs &a, int, int, int, int, int, cudaStream_t) { return 0; }
