@@ -44,8 +44,13 @@ constexpr int kAdjGhV = 4;        // samples per thread of the staged gh kernel
 constexpr int kAdjWarps = 8;      // consumer warps of the staged gx kernel
 constexpr int kAdjGhWarps = 12;   // warps of the staged gh kernel (warp 0 also issues the copies)
 constexpr int kAdjStages = 4;     // ring slots of the staged gx kernel
-constexpr int kAdjGhStages = 4;   // ring slots of the staged gh kernel
-constexpr int kAdjGhSub = 2;      // sub-blocks of V samples per thread and staged gh tile
+// Staged gh tile: 4 sub-blocks of V samples per thread (6144 samples), 2 ring
+// slots (197 KB).  Measured on GB300 (2^24 samples, us): 2 x 4 slots 84.8 /
+// 67.6 / 147.5, 3 x 3 83.9 / 62.7 / 142.8, 4 x 2 83.0 / 63.5 / 138.2 at
+// P = Q = 9, M = 4 / P = Q = 7, M = 3 / P = Q = 11, M = 7: a longer tile spreads
+// warp 0's wait for the slot release over more accumulation.
+constexpr int kAdjGhStages = 2;   // ring slots of the staged gh kernel
+constexpr int kAdjGhSub = 4;      // sub-blocks of V samples per thread and staged gh tile
 
 // NS consecutive complex samples p[base .. base+NS-1] (zero past n).  When the
 // buffer is 16-byte aligned, base is even and the rounded-up window lies inside
