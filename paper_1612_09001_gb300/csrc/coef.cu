@@ -141,9 +141,27 @@ cudaError_t launch_adj_finalize64(const float2 *partials, int rows, int K, doubl
     return cudaGetLastError();
 }
 
+// One partial row per problem (the batched refinement): the FP64 sum is the
+// row itself, widened; one thread per coefficient instead of a 256-thread
+// reduction per coefficient.
+__global__ void adj_widen_kernel(const float2 *__restrict__ partials, int64_t n, double2 *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float2 v = partials[i];
+        out[i] = make_double2(v.x, v.y);
+    }
+}
+
 cudaError_t launch_adj_finalize64_many(const float2 *partials, int rows, int K, int count, double2 *out,
                                        cudaStream_t s)
 {
+    if (rows == 1) {
+        const int64_t n = (int64_t)K * count;
+        adj_widen_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(partials, n, out);
+        count_launch();
+        return cudaGetLastError();
+    }
     adj_finalize_kernel<<<dim3((unsigned)K, (unsigned)count), 256, 0, s>>>(partials, rows, K, nullptr, out);
     count_launch();
     return cudaGetLastError();
