@@ -101,7 +101,8 @@ cudaError_t launch_gram_lag_finish(const float *partials, const GramProblem *pro
 cudaError_t launch_gram_assemble(const double *S, int nprob, int K, int Bp, int B, int T, double2 *G, double2 *g,
                                  double *tt, cudaStream_t s);
 // Power sums of r = |u|^2 per problem: mom[p][k - 1] = sum_n r_n^k, k = 1 .. 2 kMaxB - 1,
-// FP64 in a fixed order (part: nprob * kMomBlocks * kMomK doubles of scratch).
+// in a fixed order: per thread as exact FP32 two-sum pairs, then FP64 (part: nprob *
+// kMomBlocks * kMomK doubles of scratch).
 constexpr int kMomK = 2 * kMaxB - 1;
 constexpr int kMomBlocks = 64;
 cudaError_t launch_moments(const GramProblem *probs, int nprob, double *part, double *mom, cudaStream_t s);

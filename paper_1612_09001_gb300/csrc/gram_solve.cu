@@ -52,25 +52,34 @@ cudaError_t launch_gram_reduce(const float *partials, int nprob, int cpp, int D,
     return cudaGetLastError();
 }
 
+// Each thread sums its powers as FP32 pairs (sum, rounding error) with an
+// exact two-sum per addition: FP32 arithmetic, about 2^-48 relative accuracy,
+// where FP64 additions (about two per clock per SM on GB300) bound the kernel.
+// The pairs become FP64 for the block's fixed-order tree.
 __global__ void moments_kernel(const GramProblem *__restrict__ probs, double *__restrict__ part)
 {
     const GramProblem pr = probs[blockIdx.y];
-    double acc[kMomK];
+    float hi[kMomK], lo[kMomK];
 #pragma unroll
-    for (int k = 0; k < kMomK; ++k) acc[k] = 0.0;
+    for (int k = 0; k < kMomK; ++k) {
+        hi[k] = 0.f;
+        lo[k] = 0.f;
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pr.n; i += (int64_t)gridDim.x * blockDim.x) {
         const float2 x = pr.u[i];
         const float r = fmaf(x.x, x.x, x.y * x.y);
         float p = r;
 #pragma unroll
         for (int k = 0; k < kMomK; ++k) {
-            acc[k] += (double)p;
+            const float t = hi[k] + p, z = t - hi[k];
+            lo[k] += (hi[k] - (t - z)) + (p - z);
+            hi[k] = t;
             p *= r;
         }
     }
     __shared__ double red[kMomK][256];
 #pragma unroll
-    for (int k = 0; k < kMomK; ++k) red[k][threadIdx.x] = acc[k];
+    for (int k = 0; k < kMomK; ++k) red[k][threadIdx.x] = (double)hi[k] + (double)lo[k];
     __syncthreads();
     for (int stride = blockDim.x / 2; stride > 0; stride >>= 1) {
         if ((int)threadIdx.x < stride)
