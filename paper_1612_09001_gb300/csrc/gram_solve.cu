@@ -317,16 +317,27 @@ __global__ void __launch_bounds__(256) chol_kernel(const double2 *__restrict__ G
 // each), for few problems: one CTA per problem leaves all but a few SMs idle
 // and is bound by one SM's FP64 rate.  Columns are dealt out cyclically (CTA r
 // owns columns k = r, r + C, ...; its rows i >= k in shared memory).  Step j:
-// the owner of column j has already factored it and written it, with the
-// pivot status, into every CTA's shared column buffer pc[j & 1] (distributed
-// shared memory); after the cluster barrier every CTA updates its own columns
-// k > j with it.  Look-ahead: the owner of column j + 1 first updates that
-// column alone, takes its pivot, scales it and broadcasts it into pc[(j+1) & 1]
-// before its other updates, so the next step's column is ready when the
-// barrier completes.  Double buffering is safe: pc[(j+1) & 1] was last read in
-// step j - 1, which every CTA finished before the barrier of step j.  Every
-// CTA reads the same pivot status after the same barrier, so all of them leave
-// the loop at the same step and pass the same number of cluster barriers.
+// every CTA updates its own columns k > j with column j, which its owner
+// wrote, with the pivot status, into every CTA's shared buffer pc[j % 3]
+// (distributed shared memory) before the cluster barrier that ended step
+// j - 1.  Look-ahead: the owner of column j + 1 first updates that column
+// alone, takes its pivot, scales it and sends it into pc[(j + 1) % 3], then
+// arrives on the barrier and only then updates its other columns, so the next
+// step waits for the column's pivot chain, not for its owner's other updates.
+// The barrier is split (arrive, work, wait); the owner's later reads of
+// pc[j % 3] end before it arrives in step j + 1, and that buffer is written
+// again (column j + 3) only after the barrier of step j + 1: three buffers
+// make the deferral safe.  Every CTA reads the same pivot status after the
+// same barrier, so all of them leave the loop at the same step and pass the
+// same number of barriers.
+// (Measured on GB300, K = 97: 3,750 cycles per column with one barrier per
+// step after all updates; the owner's chain was the critical path.)
+// Split cluster barrier: every thread of every CTA arrives (release: its
+// earlier shared-memory writes, local and remote, are visible to the cluster
+// once the phase completes), then waits (acquire).
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
 constexpr int kCholCluster = 8;
 constexpr int kCholClusterThreads = 256;
 constexpr int kCholMaxK = 2 * kMaxB * kMaxT + 1;   // 97: P = Q = 11, M = 7
@@ -340,8 +351,8 @@ __global__ void __launch_bounds__(kCholClusterThreads) chol_cluster_kernel(const
     cg::cluster_group cluster = cg::this_cluster();
     constexpr int C = kCholCluster;
     extern __shared__ double2 A[];            // [K][ncl]: this CTA's columns
-    __shared__ double2 pc[2][kCholMaxK];      // broadcast pivot columns
-    __shared__ int pbad[2];                   // their pivot status (0 or failing column + 1)
+    __shared__ double2 pc[3][kCholMaxK];      // broadcast pivot columns
+    __shared__ int pbad[3];                   // their pivot status (0 or failing column + 1)
     __shared__ double dsh[kCholMaxK];
     __shared__ double rinv;
     const int rank = (int)cluster.block_rank();
@@ -388,15 +399,15 @@ __global__ void __launch_bounds__(kCholClusterThreads) chol_cluster_kernel(const
         }
         __syncthreads();
         const double ri = rinv;
-        for (int i = k + 1 + tid; i < K; i += nt) {
-            const double2 v = A[(size_t)i * ncl + lc];
-            A[(size_t)i * ncl + lc] = make_double2(v.x * ri, v.y * ri);
-        }
-        __syncthreads();
-        const int m = K - k;
-        for (int e = tid; e < m * C; e += nt) {
-            const int r = e / m, i = k + e % m;
-            *cluster.map_shared_rank(&pc[b][i], r) = A[(size_t)i * ncl + lc];
+        // scale rows below the pivot and send every row >= k (one pass)
+        for (int i = k + tid; i < K; i += nt) {
+            double2 v = A[(size_t)i * ncl + lc];
+            if (i > k) {
+                v = make_double2(v.x * ri, v.y * ri);
+                A[(size_t)i * ncl + lc] = v;
+            }
+#pragma unroll
+            for (int r = 0; r < C; ++r) *cluster.map_shared_rank(&pc[b][i], r) = v;
         }
     };
     // A[i][k] -= pc[i] conj(pc[k]) for rows i >= k of one local column.
@@ -414,7 +425,7 @@ __global__ void __launch_bounds__(kCholClusterThreads) chol_cluster_kernel(const
     if (bad == 0 && rank == 0) factor_and_send(0, 0, 0);
     cluster.sync();
     for (int j = 0; j < K && bad == 0; ++j) {
-        const int b = j & 1;
+        const int b = j % 3;
         if (pbad[b]) {   // the same value in every CTA after the same barrier
             bad = pbad[b];
             break;
@@ -425,7 +436,8 @@ __global__ void __launch_bounds__(kCholClusterThreads) chol_cluster_kernel(const
         if (own_next) {   // look-ahead: column j + 1 first, then its pivot and broadcast
             update_col(col, next, next / C, tid, nt);
             __syncthreads();
-            factor_and_send(next, next / C, next & 1);
+            factor_and_send(next, next / C, next % 3);
+            cluster_arrive();   // column j + 1 is out
         }
         // The rest of this CTA's columns k > j: (local column, row) pairs dealt
         // to the threads, columns in order.
@@ -434,7 +446,8 @@ __global__ void __launch_bounds__(kCholClusterThreads) chol_cluster_kernel(const
             const int k = rank + lc * C;
             if (k < K) update_col(col, k, lc, tid % 32, 32);
         }
-        cluster.sync();
+        if (!own_next) cluster_arrive();
+        cluster_wait();
     }
     cluster.sync();   // no CTA leaves while another may still write into its buffers
 
