@@ -382,24 +382,26 @@ __global__ void __launch_bounds__(kCholClusterThreads) chol_cluster_kernel(const
     }
     __syncthreads();
 
-    // Factor local column lc (global k): pivot, scale, broadcast into buffer b.
-    auto factor_and_send = [&](int k, int lc, int b) {
-        if (tid == 0) {
-            const double piv = A[(size_t)k * ncl + lc].x;
-            int bad = 0;
-            if (!(piv > 1e-30 && piv < 1e30)) {
-                bad = k + 1;
-                rinv = 0.0;
-            } else {
-                const double ri = rsqrt_newton(piv);
-                A[(size_t)k * ncl + lc] = make_double2(piv * ri, 0.0);
-                rinv = ri;
-            }
-            for (int r = 0; r < C; ++r) *cluster.map_shared_rank(&pbad[b], r) = bad;
+    // Pivot of local column lc (global k), by thread 0: the scaled diagonal,
+    // 1/sqrt(pivot) in rinv and the status in sbad (shared).
+    __shared__ int sbad;
+    auto pivot = [&](int k, int lc) {
+        const double piv = A[(size_t)k * ncl + lc].x;
+        if (!(piv > 1e-30 && piv < 1e30)) {
+            sbad = k + 1;
+            rinv = 0.0;
+        } else {
+            const double ri = rsqrt_newton(piv);
+            A[(size_t)k * ncl + lc] = make_double2(piv * ri, 0.0);
+            rinv = ri;
+            sbad = 0;
         }
-        __syncthreads();
+    };
+    // After the pivot and a CTA barrier: status and column (rows below the
+    // pivot scaled, in one pass) into every CTA's buffer b.
+    auto send = [&](int k, int lc, int b) {
+        if (tid < C) *cluster.map_shared_rank(&pbad[b], tid) = sbad;
         const double ri = rinv;
-        // scale rows below the pivot and send every row >= k (one pass)
         for (int i = k + tid; i < K; i += nt) {
             double2 v = A[(size_t)i * ncl + lc];
             if (i > k) {
@@ -422,7 +424,11 @@ __global__ void __launch_bounds__(kCholClusterThreads) chol_cluster_kernel(const
     };
 
     int bad = bad0;
-    if (bad == 0 && rank == 0) factor_and_send(0, 0, 0);
+    if (bad == 0 && rank == 0) {
+        if (tid == 0) pivot(0, 0);
+        __syncthreads();
+        send(0, 0, 0);
+    }
     cluster.sync();
     for (int j = 0; j < K && bad == 0; ++j) {
         const int b = j % 3;
@@ -434,9 +440,10 @@ __global__ void __launch_bounds__(kCholClusterThreads) chol_cluster_kernel(const
         const int next = j + 1;
         const bool own_next = next < K && next % C == rank;
         if (own_next) {   // look-ahead: column j + 1 first, then its pivot and broadcast
-            update_col(col, next, next / C, tid, nt);
+            update_col(col, next, next / C, tid, nt);   // thread 0 takes the diagonal row
+            if (tid == 0) pivot(next, next / C);        // while the other rows are updated
             __syncthreads();
-            factor_and_send(next, next / C, next % 3);
+            send(next, next / C, next % 3);
             cluster_arrive();   // column j + 1 is out
         }
         // The rest of this CTA's columns k > j: (local column, row) pairs dealt
