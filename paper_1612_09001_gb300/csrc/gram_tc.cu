@@ -79,6 +79,7 @@ constexpr int kLagDStride = 257;             // row stride of the final D in sha
 constexpr int kLagGenWarps = 15;             // operand generators; warp 15 issues the MMAs
 constexpr int kLagGenThreads = 32 * kLagGenWarps;
 static_assert(kLagStages <= kLagChunk + 1, "drain must precede the reuse of an accumulator");
+static_assert(kLagN == 3 * 64 + 32, "drain pieces: three of 64 columns and one of 32");
 static_assert(kLagEntries == kLagSigA * kLagSigB * kMaxT, "lag partial size");
 
 template <int FMT>
@@ -368,10 +369,17 @@ __global__ void __launch_bounds__(kThreads, 1) gram_lag_kernel(GramArgs a)
         const bool ok = mbar_wait(smem_addr(&acc_full[buf]), (uint32_t)((c >> 1) & 1), a.status);
         tc_fence_after_sync();
         if (ok) {
-            float v[64];
-            tmem_ld64(lane_taddr + (uint32_t)(buf * kLagAccCols), v);
+            if (piece == 3) {   // columns 192 .. 223: the last 32 of the 256 are unused (N = 224)
+                float v[32];
+                tmem_ld32(lane_taddr + (uint32_t)(buf * kLagAccCols), v);
 #pragma unroll
-            for (int i = 0; i < 64; ++i) acc[i] += v[i];
+                for (int i = 0; i < 32; ++i) acc[i] += v[i];
+            } else {
+                float v[64];
+                tmem_ld64(lane_taddr + (uint32_t)(buf * kLagAccCols), v);
+#pragma unroll
+                for (int i = 0; i < 64; ++i) acc[i] += v[i];
+            }
         }
         tc_fence_before_sync();
         return ok;
