@@ -26,6 +26,7 @@ struct BatchStream {
     int B, T;          // branch pairs, taps
     int tab_off;       // offset of the stream's table in the table pool (floats, 16-byte aligned)
     int tab_bytes;     // bytes copied per item (multiple of 16)
+    const float2 *sub = nullptr;   // if set, y = sub - filter output (a least-squares residual)
 };
 
 struct BatchItem {
@@ -55,6 +56,7 @@ struct BatchSlotHeader {
     int64_t s0;    // first sample of the tile
     int bt;        // B * 16 + T
     int ok;        // item passed item_ok (else skipped by both sides)
+    const float2 *sub;   // the stream's subtrahend or null
 };
 constexpr int kBatchHdrBytes = 64;
 static_assert(sizeof(BatchSlotHeader) <= kBatchHdrBytes, "slot header");
@@ -91,8 +93,17 @@ __device__ __forceinline__ void batched_item(const unsigned char *slot, const Ba
     // table argument is not read in this mode.
     fwd_compute<B, T, V, kModePackedFma>(tab, *reinterpret_cast<const ParamTab<B, T> *>(tab), wr, wi, yr,
                                          yi);
+    const int64_t g0 = hd.s0 + (int64_t)t_in_tile * V;
+    if (hd.sub) {   // residual: y = sub - Psi h
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float2 t = g0 + v < hd.n ? __ldcs(hd.sub + g0 + v) : make_float2(0.f, 0.f);
+            yr[v] = t.x - yr[v];
+            yi[v] = t.y - yi[v];
+        }
+    }
     const bool vec = full && ((reinterpret_cast<uintptr_t>(hd.y) & 15u) == 0);
-    store_outputs<V>(hd.y, hd.s0 + (int64_t)t_in_tile * V, hd.n, vec, yr, yi);
+    store_outputs<V>(hd.y, g0, hd.n, vec, yr, yi);
 }
 
 #define DPD_BCASE(b, t)                                                                            \
@@ -165,6 +176,7 @@ __global__ void __launch_bounds__(32 * 17) fwd_batched_kernel(BatchArgs a, int s
                 hd->s0 = s0;
                 hd->bt = st.B * 16 + st.T;
                 hd->ok = good ? 1 : 0;
+                hd->sub = st.sub;
                 if (!good) {
                     mbar_arrive_expect_tx(fb, 0);   // complete the phase with no copies (releases the header)
                     continue;

@@ -136,9 +136,6 @@ cudaError_t launch_residual_norm(const float2 *t, const float2 *y, int64_t n, fl
                                  cudaStream_t s);
 // Like launch_adj_finalize, summed to FP64.
 cudaError_t launch_adj_finalize64(const float2 *partials, int rows, int K, double2 *out, cudaStream_t s);
-// e_p = t_p - e_p in place for the `count` problems (e_p at e + p * stride, nmax the longest).
-cudaError_t launch_residual_many(const GramProblem *probs, int count, int64_t nmax, int64_t stride, float2 *e,
-                                 cudaStream_t s);
 // The same for `count` problems, each with `rows` rows (outputs K apart).
 cudaError_t launch_adj_finalize64_many(const float2 *partials, int rows, int K, int count, double2 *out,
                                        cudaStream_t s);

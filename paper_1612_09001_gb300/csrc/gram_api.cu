@@ -311,7 +311,7 @@ dpd_status refine_batched(dpd_handle h, const std::vector<dpd::GramProblem> &pro
     std::vector<dpd::AdjArgs> adj((size_t)count);
     for (int p = 0; p < count; ++p) {
         float2 *ep = w.e + (size_t)p * stride;
-        st[p] = {probs[p].u, ep, probs[p].n, h->B, h->T, p * tstride, tstride * 4};
+        st[p] = {probs[p].u, ep, probs[p].n, h->B, h->T, p * tstride, tstride * 4, probs[p].t};   // e = t - Psi h
         for (int64_t t = 0; t * S < probs[p].n; ++t) items.push_back({p, (int)t});
         dpd::AdjArgs &a = adj[p];
         a.x = probs[p].u;
@@ -372,10 +372,7 @@ dpd_status refine_batched(dpd_handle h, const std::vector<dpd::GramProblem> &pro
             return DPD_ERR_CUDA;
         const cudaError_t fe = small ? dpd::launch_batched_57(ba, V, warps, stages, 0, h->sm_count, s)
                                      : dpd::launch_batched_68(ba, V, warps, stages, 0, h->sm_count, s);
-        if (fe != cudaSuccess) return DPD_ERR_CUDA;
-        if (dpd::launch_residual_many(static_cast<const dpd::GramProblem *>(w.probs), count, nmax, stride, w.e, s) !=
-            cudaSuccess)
-            return DPD_ERR_CUDA;
+        if (fe != cudaSuccess) return DPD_ERR_CUDA;   // the filter wrote e_p = t_p - Psi h_p
         if (dpd::launch_adj_gh_many_any(h->B, static_cast<const dpd::AdjArgs *>(w.badj), count, 1, h->adj.tap_group,
                                         h->T, h->Bp, h->Bq, K, s) != cudaSuccess)
             return DPD_ERR_CUDA;

@@ -852,28 +852,6 @@ __global__ void residual_kernel(const float2 *__restrict__ t, const float2 *__re
     }
 }
 
-// e_p = t_p - e_p in place for every problem p of a batch (e_p at e + p * stride).
-__global__ void residual_many_kernel(const GramProblem *__restrict__ probs, int64_t stride, float2 *__restrict__ e)
-{
-    const GramProblem pr = probs[blockIdx.y];
-    float2 *ep = e + (size_t)blockIdx.y * stride;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pr.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 a = pr.t[i], b = ep[i];
-        ep[i] = make_float2(a.x - b.x, a.y - b.y);
-    }
-}
-
-cudaError_t launch_residual_many(const GramProblem *probs, int count, int64_t nmax, int64_t stride, float2 *e,
-                                 cudaStream_t s)
-{
-    int64_t bx = (nmax + 255) / 256;
-    if (bx > 64) bx = 64;
-    if (bx < 1 || count < 1) return cudaSuccess;
-    residual_many_kernel<<<dim3((unsigned)bx, (unsigned)count), 256, 0, s>>>(probs, stride, e);
-    count_launch();
-    return cudaGetLastError();
-}
-
 cudaError_t launch_residual(const float2 *t, const float2 *y, int64_t n, float2 *e, cudaStream_t s)
 {
     int64_t blocks = (n + 255) / 256;

@@ -5,7 +5,7 @@ namespace dpd {
 constexpr int kMaxT = 8; constexpr int kMaxTabFloats = 4*6*8+2;
 enum : int { kFlagTimeout = 1, kFlagBadWork = 2 };
 constexpr int wl_table_floats(int B, int T) { return 4 * B * T + 2; }
-struct BatchStream { const float2 *x; float2 *y; int64_t n; int B, T; int tab_off; int tab_bytes; };
+struct BatchStream { const float2 *x; float2 *y; int64_t n; int B, T; int tab_off; int tab_bytes; const float2 *sub = nullptr; };
 struct BatchItem { int stream; int tile; };
 struct BatchArgs { const BatchStream *streams; const BatchItem *items; int nitems; int nstreams; const float *tabs; int64_t tab_floats; int *status; int gw = 0; int nsub = 1; };
 constexpr size_t batch_smem(int warps, int gw, int stages, int V, int nsub = 1) { return (size_t)(warps / gw) * stages * (64 + 784 + (8 + nsub * gw * 32 * V) * 8) + 128; }
