@@ -19,6 +19,30 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// FP32 (hi, lo) pairs: hi + lo carries a sum to about 2^-48 relative accuracy
+// with FP32 arithmetic only.  two_sum_acc adds x to the pair, keeping the
+// rounding error of the addition exactly (Knuth's two-sum) and summing it into
+// lo; pair_add adds two pairs and renormalises the result.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
+{
+    const float t = hi + x, z = t - hi;
+    lo += (hi - (t - z)) + (x - z);
+    hi = t;
+}
+
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b)
+{
+    const float t = a.x + b.x, z = t - a.x;
+    const float e = ((a.x - (t - z)) + (b.x - z)) + (a.y + b.y);
+    const float s = t + e;
+    return make_float2(s, e - (s - t));
+}
+
+__device__ __forceinline__ float2 shfl_xor_pair(float2 v, int o)
+{
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
 __device__ __forceinline__ uint64_t global_ns()
 {
     uint64_t t;

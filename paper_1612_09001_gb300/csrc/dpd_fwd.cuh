@@ -210,12 +210,14 @@ __device__ __forceinline__ void store_outputs(float2 *__restrict__ y, int64_t g0
 
 // Shared-memory bytes of the TMA kernel for a launch shape: the table area, the
 // barrier pairs of every group and stage, and per group `stages` slots of the
-// group's sub-tile (gw * 32 * V samples) with kHalo history samples each.
+// group's sub-tile (gw * 32 * V samples) with kHalo history samples each;
+// kModeNorms adds as many slots for the minuend's sub-tiles (no history).
 template <int B, int T, int V>
-__host__ __device__ constexpr size_t fwd_tma_smem(int warps, int gw, int stages)
+__host__ __device__ constexpr size_t fwd_tma_smem(int warps, int gw, int stages, bool sub = false)
 {
     return (size_t)tab_bytes<B, T>() + (size_t)((2 * (warps / gw) * stages * 8 + 127) / 128) * 128 +
-           (size_t)(warps / gw) * stages * (size_t)(kHalo + gw * 32 * V) * sizeof(float2);
+           (size_t)(warps / gw) * stages * (size_t)(kHalo + gw * 32 * V) * sizeof(float2) +
+           (sub ? (size_t)(warps / gw) * stages * (size_t)(gw * 32 * V) * sizeof(float2) : 0);
 }
 
 // The consumer warps form groups of gw warps; every group has its own ring of
@@ -269,6 +271,13 @@ __global__ void __launch_bounds__(fwd_lb_threads<SH>(), fwd_lb_blocks<SH>())
     const int S = nwarps * 32 * V;    // tile
     const int SG = gw * 32 * V;       // a group's sub-tile
     const int slot_elems = kHalo + SG;
+    // kModeNorms stages the minuend's sub-tiles through shared memory too (per
+    // group `stages` slots): there its global loads, issued after the filter
+    // arithmetic, would wait in full (measured 39.3 -> 36.4 us per 2^22
+    // samples at P = Q = 11, M = 7).  The plain subtract mode keeps them in
+    // global memory: staging held its slots longer and gained nothing there.
+    constexpr bool STAGE = (MODE & kModeNorms) != 0;
+    const float2 *sring = ring + (size_t)ngroups * stages * slot_elems;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // Prologue that touches no global memory (overlaps the previous grid's tail
@@ -306,14 +315,22 @@ __global__ void __launch_bounds__(fwd_lb_threads<SH>(), fwd_lb_blocks<SH>())
                 }
                 int64_t lo, cnt;
                 int off;
-                tile_copy_range(tile * S + (int64_t)g * SG, SG, a.n, lo, cnt, off);
+                const int64_t s0 = tile * S + (int64_t)g * SG;
+                tile_copy_range(s0, SG, a.n, lo, cnt, off);
                 if (cnt < 0) cnt = 0;   // a group past the end of the input: nothing to copy
                 const uint32_t bytes = (uint32_t)(cnt * (int64_t)sizeof(float2));
+                // STAGE: the minuend's sub-tile when all of it is in the input
+                // (the consumers read a partial one from global memory).  s0 is
+                // even and SG * 8 a multiple of 16: a 16-byte aligned copy.
+                const uint32_t sbytes = (STAGE && s0 + SG <= a.n) ? (uint32_t)SG * (uint32_t)sizeof(float2) : 0u;
                 const uint32_t fb = smem_addr(&gb[s]);
-                mbar_arrive_expect_tx(fb, bytes);
+                mbar_arrive_expect_tx(fb, bytes + sbytes);
                 if (bytes)
                     bulk_copy_g2s_stream(smem_addr(ring + ((size_t)g * stages + s) * slot_elems + off), a.x + lo,
                                          bytes, fb, pol);
+                if (sbytes)
+                    bulk_copy_g2s_stream(smem_addr(sring + ((size_t)g * stages + s) * SG), a.sub + s0, sbytes, fb,
+                                         pol);
             }
             if (gfail < 0 && ++s == stages) {
                 s = 0;
@@ -338,21 +355,32 @@ __global__ void __launch_bounds__(fwd_lb_threads<SH>(), fwd_lb_blocks<SH>())
     const int t_in_tile = (warp - g * gw) * 32 + lane;   // position in the group's sub-tile
     uint64_t *gb = bars + 2 * stages * g;
     const float2 *ring_g = ring + (size_t)g * stages * slot_elems;
+    constexpr bool NORMS = (MODE & kModeNorms) != 0;
     int s = 0;        // slot and parity of the current tile, kept incrementally
     uint32_t ph = 0;
     int64_t it = 0;
+    // NORMS: this thread's sums |sub - y|^2 and |sub|^2 over its tiles as FP32
+    // (hi, lo) pairs; no FP64 arithmetic runs in the kernel (FP64 on this GPU
+    // is a small fraction of the FP32 rate).
+    float2 pe = make_float2(0.f, 0.f), pt = make_float2(0.f, 0.f);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         if constexpr (FIXED) {   // constant ring depth: a cheap modulo
             s = (int)(it % kFwdShapes[SH].stages);
             ph = (uint32_t)((it / kFwdShapes[SH].stages) & 1);
         }
-        if (!mbar_wait(smem_addr(&gb[s]), ph, a.status)) return;
+        if (!mbar_wait(smem_addr(&gb[s]), ph, a.status)) {
+            if constexpr (NORMS) break;   // still take part in the completion count
+            else return;
+        }
         const float2 *slot = ring_g + (size_t)s * slot_elems;
+        const int s_cur = s;
         const int64_t s0 = tile * S + (int64_t)g * SG;
         float wr[W], wi[W];
         const bool full = load_window<T, V>(slot, s0, SG, a.n, a.x, t_in_tile, wr, wi);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&gb[stages + s]));
+        if constexpr (!STAGE) {   // the slot is free once the window is in registers
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&gb[stages + s]));
+        }
         if (!FIXED && ++s == stages) {
             s = 0;
             ph ^= 1u;
@@ -362,15 +390,28 @@ __global__ void __launch_bounds__(fwd_lb_threads<SH>(), fwd_lb_blocks<SH>())
         fwd_compute<B, T, V, MODE & (kModeParamCoef | kModePackedFma)>(tab, ptab, wr, wi, yr, yi);
         const int64_t g0 = s0 + (int64_t)t_in_tile * V;
         if constexpr ((MODE & kModeSubtract) != 0) {   // y <- sub - y
-            if (full) {
-                const float4 *sp = reinterpret_cast<const float4 *>(a.sub + g0);
+            float ea = 0.f, ta = 0.f;   // NORMS: the tile's |sub - y|^2 and |sub|^2 in FP32
+            if (full) {   // STAGE: the minuend's sub-tile is in the slot (full implies s0 + SG <= n)
+                const float4 *sp =
+                    STAGE ? reinterpret_cast<const float4 *>(sring + ((size_t)g * stages + s_cur) * SG + t_in_tile * V)
+                          : reinterpret_cast<const float4 *>(a.sub + g0);
 #pragma unroll
                 for (int i = 0; i < V / 2; ++i) {
-                    const float4 q = __ldcs(sp + i);
+                    float4 q;
+                    if constexpr (STAGE)
+                        q = sp[i];
+                    else
+                        q = __ldcs(sp + i);
                     yr[2 * i] = q.x - yr[2 * i];
                     yi[2 * i] = q.y - yi[2 * i];
                     yr[2 * i + 1] = q.z - yr[2 * i + 1];
                     yi[2 * i + 1] = q.w - yi[2 * i + 1];
+                    if constexpr (NORMS) {
+                        ea = fmaf(yr[2 * i], yr[2 * i], fmaf(yi[2 * i], yi[2 * i], ea));
+                        ea = fmaf(yr[2 * i + 1], yr[2 * i + 1], fmaf(yi[2 * i + 1], yi[2 * i + 1], ea));
+                        ta = fmaf(q.x, q.x, fmaf(q.y, q.y, ta));
+                        ta = fmaf(q.z, q.z, fmaf(q.w, q.w, ta));
+                    }
                 }
             } else {
 #pragma unroll
@@ -379,10 +420,74 @@ __global__ void __launch_bounds__(fwd_lb_threads<SH>(), fwd_lb_blocks<SH>())
                         const float2 q = a.sub[g0 + v];
                         yr[v] = q.x - yr[v];
                         yi[v] = q.y - yi[v];
+                        if constexpr (NORMS) {
+                            ea = fmaf(yr[v], yr[v], fmaf(yi[v], yi[v], ea));
+                            ta = fmaf(q.x, q.x, fmaf(q.y, q.y, ta));
+                        }
                     }
             }
+            if constexpr (NORMS) {
+                two_sum_acc(pe.x, pe.y, ea);
+                two_sum_acc(pt.x, pt.y, ta);
+            }
+            if constexpr (STAGE) {   // both parts of the slot have been read
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&gb[stages + s_cur]));
+            }
         }
-        store_outputs<V>(a.y, g0, a.n, full && a.vec_store, yr, yi);
+        if constexpr (!NORMS) store_outputs<V>(a.y, g0, a.n, full && a.vec_store, yr, yi);
+    }
+    if constexpr (NORMS) {
+        // The consumer warps' pairs meet in shared memory (named barrier 1: the
+        // producer warp has left), warp 0 writes the CTA's pairs as one float4,
+        // and the last CTA of the grid to finish adds those in CTA order
+        // (deterministic), writes the two sums in FP64 and clears the counter
+        // for the next launch.
+        __shared__ float4 red[kFwdMaxWarps];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            pe = pair_add(pe, shfl_xor_pair(pe, o));
+            pt = pair_add(pt, shfl_xor_pair(pt, o));
+        }
+        if (lane == 0) red[warp] = make_float4(pe.x, pe.y, pt.x, pt.y);
+        asm volatile("bar.sync 1, %0;" ::"r"(nwarps * 32) : "memory");
+        if (warp != 0) return;
+        const float4 r = lane < nwarps ? red[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        pe = make_float2(r.x, r.y);
+        pt = make_float2(r.z, r.w);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            pe = pair_add(pe, shfl_xor_pair(pe, o));
+            pt = pair_add(pt, shfl_xor_pair(pt, o));
+        }
+        float4 *part = reinterpret_cast<float4 *>(a.norms);
+        unsigned *count = reinterpret_cast<unsigned *>(a.norms + 2 * kFwdNormSlots + 2);
+        int last = 0;
+        if (lane == 0) {
+            part[blockIdx.x] = make_float4(pe.x, pe.y, pt.x, pt.y);
+            __threadfence();
+            last = atomicAdd(count, 1u) == gridDim.x - 1;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) return;
+        __threadfence();
+        pe = make_float2(0.f, 0.f);
+        pt = make_float2(0.f, 0.f);
+        for (int i = lane; i < (int)gridDim.x; i += 32) {
+            const float4 v = __ldcg(part + i);
+            pe = pair_add(pe, make_float2(v.x, v.y));
+            pt = pair_add(pt, make_float2(v.z, v.w));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            pe = pair_add(pe, shfl_xor_pair(pe, o));
+            pt = pair_add(pt, shfl_xor_pair(pt, o));
+        }
+        if (lane == 0) {
+            a.norms[2 * kFwdNormSlots] = (double)pe.x + (double)pe.y;
+            a.norms[2 * kFwdNormSlots + 1] = (double)pt.x + (double)pt.y;
+            *count = 0u;
+        }
     }
 }
 
@@ -451,7 +556,9 @@ int fwd_shape_index(int warps, int gw, int stages)
 template <int B, int T, int V, int MODE, bool TMA>
 constexpr bool fwd_built()
 {
-    if constexpr ((MODE & kModeSubtract) != 0) return TMA && V == 6 && MODE == (kModePackedFma | kModeSubtract);
+    if constexpr ((MODE & kModeSubtract) != 0)
+        return TMA && V == 6 &&
+               (MODE == (kModePackedFma | kModeSubtract) || MODE == (kModePackedFma | kModeSubtract | kModeNorms));
     if (fwd_all_modes<B, T>()) return true;
     if (!TMA) return V == 4 && (MODE == 0 || MODE == 2 || MODE == 3);
     return (V == 4 && MODE == 0) || ((V == 4 || V == 6 || V == 8) && (MODE == 2 || MODE == 3));
@@ -471,7 +578,7 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
             const int S = L.warps * 32 * V;
             const int gw = (L.group > 0 && L.warps % L.group == 0) ? L.group : L.warps;
             const int64_t ntiles = (a.n + S - 1) / S;
-            const size_t smem = fwd_tma_smem<B, T, V>(L.warps, gw, L.stages);
+            const size_t smem = fwd_tma_smem<B, T, V>(L.warps, gw, L.stages, (MODE & kModeNorms) != 0);
             const int sh = fwd_shape_index<B, T, V, MODE>(L.warps, gw, L.stages);
             void (*kern)(FwdArgs, int, int, int64_t, const ParamTab<B, T>) = fwd_tma_kernel<B, T, V, MODE, 0>;
             if constexpr (fwd_fixed_shapes<B, T, V, MODE>()) {
@@ -491,6 +598,8 @@ cudaError_t launch_fwd_tv(const FwdArgs &a, const FwdLaunch &L, int sm_count, cu
             const int cps = (L.ctas_per_sm > 0 && L.ctas_per_sm < occ) ? L.ctas_per_sm : occ;
             int64_t grid = (int64_t)sm_count * cps;
             if (grid > ntiles) grid = ntiles;
+            if constexpr ((MODE & kModeNorms) != 0)
+                if (!a.norms || grid > kFwdNormSlots || L.warps > kFwdMaxWarps) return cudaErrorInvalidValue;
             // Programmatic dependent launch: this grid may begin launching while
             // the previous one in the stream drains (the kernel waits for it
             // before touching global memory).
@@ -548,6 +657,8 @@ cudaError_t launch_fwd_t(const FwdArgs &a, const FwdLaunch &L, int sm_count, cud
     case 2: return launch_fwd_mode<B, T, 2>(a, L, sm_count, s);
     case 3: return launch_fwd_mode<B, T, 3>(a, L, sm_count, s);
     case kModePackedFma | kModeSubtract: return launch_fwd_mode<B, T, kModePackedFma | kModeSubtract>(a, L, sm_count, s);
+    case kModePackedFma | kModeSubtract | kModeNorms:
+        return launch_fwd_mode<B, T, kModePackedFma | kModeSubtract | kModeNorms>(a, L, sm_count, s);
     default: return cudaErrorInvalidValue;
     }
 }

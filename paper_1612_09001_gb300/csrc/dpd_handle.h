@@ -23,7 +23,7 @@ struct EstimateWorkspace {
     float2 *hf = nullptr;         // coefficients of the refinement pass (complex64)
     float *tab = nullptr;         // their forward table
     float2 *y = nullptr, *e = nullptr;
-    double *norm_part = nullptr;  // 2 * 1024 partial sums + 2 results
+    double *norm_part = nullptr;  // 2 * kFwdNormSlots partial sums, 2 results, a counter
     // orthogonal-polynomial basis (DPD_BASIS_ORTHOGONAL)
     float *ubasis = nullptr;      // [nprob][kUSize] basis coefficients used by the Gram kernels
     double *ubasis64 = nullptr;   // the same values in FP64, for the coefficient transforms

@@ -42,8 +42,13 @@ struct HostTab {
 // Forward compute modes (template bits): coefficients read from the kernel
 // parameter bank instead of shared memory; packed f32x2 fused multiply-adds.
 // kModeSubtract (internal, least-squares refinement only): the kernel writes
-// sub[n] - y[n] instead of y[n].
-enum : int { kModeParamCoef = 1, kModePackedFma = 2, kModeSubtract = 4 };
+// sub[n] - y[n] instead of y[n].  kModeNorms (with kModeSubtract, internal:
+// the statistics of an estimate) writes nothing per sample: it sums
+// |sub - y|^2 and |sub|^2 instead (FwdArgs::norms).
+enum : int { kModeParamCoef = 1, kModePackedFma = 2, kModeSubtract = 4, kModeNorms = 8 };
+
+// Partial-sum slots of kModeNorms: one pair per CTA of the grid.
+constexpr int kFwdNormSlots = 4096;
 
 // Forward launch shape.
 constexpr int kFwdMaxWarps = 16;   // consumer warps per CTA of the TMA kernel (register budget)
@@ -67,6 +72,13 @@ struct FwdArgs {
     int vec_store;        // y is 16-byte aligned
     const HostTab *host_tab;   // host copy of the table (param-bank modes), or null
     const float2 *sub = nullptr;   // kModeSubtract: minuend, n samples, 16-byte aligned
+    // kModeNorms: kFwdNormSlots partial sums (one float4 per CTA: the FP32
+    // (hi, lo) pairs of both sums, the size of two doubles), then the two
+    // results in FP64 (sum |sub - y|^2, sum |sub|^2), then a completion counter
+    // (an unsigned in the next double; zero between launches).  The last CTA to
+    // finish adds the partials in a fixed order, writes the results and clears
+    // the counter.
+    double *norms = nullptr;
 };
 
 // Floats of the adjoint table: per tap, four polynomials of B coefficients

@@ -44,7 +44,9 @@ dpd_status reserve(dpd_handle h, int nprob, int cpp, int64_t nsamp)
         ok = ok && grow(w.g, 0, np * K) && grow(w.h64, 0, np * K) && grow(w.delta, 0, np * K);
         ok = ok && grow(w.d, 0, np * K) && grow(w.tt, 0, np) && grow(w.info, 0, np);
         ok = ok && grow(w.hf, 0, (size_t)K) && grow(w.tab, 0, (size_t)dpd::wl_table_floats(h->B, h->T));
-        ok = ok && grow(w.norm_part, 0, (size_t)2 * 1024 + 2);
+        // partial pairs, the two results, the completion counter (zero)
+        ok = ok && grow(w.norm_part, 0, (size_t)2 * dpd::kFwdNormSlots + 3) &&
+             cudaMemset(w.norm_part, 0, ((size_t)2 * dpd::kFwdNormSlots + 3) * sizeof(double)) == cudaSuccess;
         ok = ok && grow(w.ubasis, 0, np * dpd::kUSize) && grow(w.ubasis64, 0, np * dpd::kUSize);
         ok = ok && grow(w.mom, 0, np * dpd::kMomK) && grow(w.mom_part, 0, np * dpd::kMomBlocks * dpd::kMomK);
         ok = ok && grow(w.hm64, 0, np * K);
@@ -202,8 +204,8 @@ dpd_status run_gram(dpd_handle h, int nprob, int cpp, int precision, cudaStream_
 }
 
 // e = t - Psi(u) h for the current FP64 coefficients of problem p (FP32 filter);
-// with `norms`, only ||e||^2 and ||t||^2 into w.norm_part + 2048 (e itself is
-// not written).
+// with `norms`, only ||e||^2 and ||t||^2 into w.norm_part + 2 kFwdNormSlots
+// (e itself is not written).
 dpd_status residual_of(dpd_handle h, int p, const float2 *u, const float2 *t, int64_t n, cudaStream_t s,
                        bool norms = false)
 {
@@ -231,11 +233,13 @@ dpd_status residual_of(dpd_handle h, int p, const float2 *u, const float2 *t, in
     L.group = 8;
     L.stages = 4;
     const bool aligned16 = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(t)) & 15u) == 0;
-    if (!norms && aligned16) {
-        // The filter writes e = t - Psi(u) h itself (no separate residual pass).
-        L.mode = dpd::kModePackedFma | dpd::kModeSubtract;
+    if (aligned16) {
+        // The filter writes e = t - Psi(u) h itself (no separate residual
+        // pass), or only sums |e|^2 and |t|^2.
+        L.mode = dpd::kModePackedFma | dpd::kModeSubtract | (norms ? dpd::kModeNorms : 0);
         fa.y = w.e;
         fa.sub = t;
+        fa.norms = w.norm_part;
         return dpd::launch_fwd_any(h->B, h->T, fa, L, h->sm_count, s) == cudaSuccess ? DPD_OK : DPD_ERR_CUDA;
     }
     if ((reinterpret_cast<uintptr_t>(u) & 15u) != 0) {
@@ -244,7 +248,8 @@ dpd_status residual_of(dpd_handle h, int p, const float2 *u, const float2 *t, in
     }
     if (dpd::launch_fwd_any(h->B, h->T, fa, L, h->sm_count, s) != cudaSuccess) return DPD_ERR_CUDA;
     if (norms)
-        return dpd::launch_residual_norm(t, w.y, n, nullptr, w.norm_part, w.norm_part + 2 * 1024, s) == cudaSuccess
+        return dpd::launch_residual_norm(t, w.y, n, nullptr, w.norm_part, w.norm_part + 2 * dpd::kFwdNormSlots, s) ==
+                       cudaSuccess
                    ? DPD_OK
                    : DPD_ERR_CUDA;
     if (dpd::launch_residual(t, w.y, n, w.e, s) != cudaSuccess) return DPD_ERR_CUDA;
@@ -646,7 +651,8 @@ dpd_status queue_norms(dpd_handle h, int p, const float2 *u, const float2 *t, in
     EstimateWorkspace &w = h->est;
     dpd_status st = residual_of(h, p, u, t, n, s, true);
     if (st != DPD_OK) return st;
-    if (cudaMemcpyAsync(w.h_norm, w.norm_part + 2 * 1024, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+    if (cudaMemcpyAsync(w.h_norm, w.norm_part + 2 * dpd::kFwdNormSlots, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                        s) !=
         cudaSuccess)
         return DPD_ERR_CUDA;
     return DPD_OK;

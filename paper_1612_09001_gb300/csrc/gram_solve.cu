@@ -863,6 +863,7 @@ cudaError_t launch_residual(const float2 *t, const float2 *y, int64_t n, float2 
 }
 
 constexpr int kNormBlocks = 1024;
+static_assert(kNormBlocks <= kFwdNormSlots, "partial pairs of the statistics pass");
 
 __global__ void sum_pairs_kernel(const double *__restrict__ part, int nb, double *__restrict__ out)
 {

@@ -193,3 +193,38 @@ def test_estimate_batched_refinement_paths_agree(basis):
         ref = oracle.ls(u, t, P, Q, M)
         e = np.linalg.norm(h_tog[i].cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref)
         assert e < 1e-3, (basis, i, e)
+
+
+@pytest.mark.parametrize("aligned", [True, False])
+@pytest.mark.parametrize("n", [1000, 2 * 3072 - 5, 3072 * 152 * 2 + 1237])
+def test_estimate_residual_statistic_against_oracle(n, aligned):
+    """stats["rel_residual"] = ||t - Psi h||^2 / ||t||^2 for the returned
+    coefficients (Sec. 2.2's least-squares residual), with a target that the
+    model does not fit exactly (complex Gaussian noise at 0.3 of the signal's
+    RMS), against the same ratio from the FP64 oracle filter.  A 16-byte
+    aligned input takes the filter pass that sums the squares itself (one
+    partial per warp, 3072-sample tiles: n spans one partial tile, two CTAs
+    and several tiles per CTA with a ragged end); an 8-byte aligned one the
+    filter followed
+    by a separate sum.  The ratio uses the FP64 coefficients on the device and
+    their FP32 copy here: a difference of order 1e-7 relative to ||Psi h||."""
+    P, Q, M = 11, 11, 7
+    u, theta = synth.ls_problem(n, P, Q, M, seed=71)
+    y = oracle.apply(u, theta, P, Q, M)
+    rng = np.random.default_rng([71, 2])
+    rms = np.sqrt(np.mean(np.abs(y) ** 2))
+    t = (y + 0.3 * rms / np.sqrt(2) * (rng.standard_normal(n) + 1j * rng.standard_normal(n))).astype(np.complex64)
+    f = dpd.DPD(P, Q, M)
+    ud, td = torch.from_numpy(u).cuda(), torch.from_numpy(t).cuda()
+    if not aligned:
+        bu = torch.zeros(n + 1, dtype=torch.complex64, device="cuda")
+        bt = torch.zeros(n + 1, dtype=torch.complex64, device="cuda")
+        bu[1:], bt[1:] = ud, td
+        ud, td = bu[1:], bt[1:]
+    h, st = f.estimate(ud, td, precision="tf32x3", refine_iters=1)
+    hc = h.cpu().numpy().astype(np.complex128)
+    e = t.astype(np.complex128) - oracle.apply(u, hc, P, Q, M)
+    ref = np.sum(np.abs(e) ** 2) / np.sum(np.abs(t.astype(np.complex128)) ** 2)
+    assert ref > 1e-3
+    assert abs(st["rel_residual"] - ref) <= 1e-4 * ref, (st["rel_residual"], ref)
+    f.close()
