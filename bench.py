@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--fwd-launch", default=None, metavar="MODE,V,WARPS,STAGES[,GROUP]",
                     help="fix the forward launch shape instead of tuning it (profiling runs)")
     ap.add_argument("--pattern", choices=["small", "batched", "adjoint", "grad", "gram", "gram_one", "ila", "cpu", "sweep",
-                                          "fma", "estimate",
+                                          "fma", "estimate", "estimate_batched",
                                           "oracle"],
                     default=None,
                     help="run only this side measurement (1 GPU) and print its JSON; for profiling")
@@ -761,6 +761,59 @@ def measure_estimate(dev, reps=5, refine_iters=3):
     return out
 
 
+def measure_estimate_batched(dev, reps=5, refine_iters=2):
+    """One batched least-squares estimate of 256 problems of 2^16 rows x K = 97
+    (P = Q = 11, M = 7, BF16x3 and TF32x3, monomial basis, 2 refinements, the
+    per-problem info codes copied to the host): device time (CUDA events
+    around the call, median of `reps` after two warm-up calls), wall time and
+    the library kernel launches the call makes."""
+    import numpy as np
+    import torch
+    import dpd_synth as synth
+    import paper_1612_09001_gb300 as dpd
+    P, Q, M, nb, nr = 11, 11, 7, 256, 1 << 16
+    g = dpd.DPD(P, Q, M)
+    us, ts, thetas = [], [], []
+    for b in range(nb):
+        ub, thb = synth.ls_problem(nr, P, Q, M, seed=b)
+        ubd = torch.from_numpy(ub).to(dev)
+        g.set_coeffs(thb)
+        us.append(ubd)
+        ts.append(g.apply(ubd))
+        thetas.append(thb)
+    us, ts = torch.stack(us), torch.stack(ts)   # equal lengths: one (problems x rows) tensor each
+    f = dpd.DPD(P, Q, M)
+    out = {"workload": f"{nb} LS estimates of {nr} rows x 97 complex columns (P=Q=11, M=7), t = Psi theta, "
+                       f"monomial basis",
+           "refine_iters": refine_iters, "timing": f"median of {reps} calls after 2 warm-up calls"}
+    for prec in ("bf16x3", "tf32x3"):
+        for _ in range(2):
+            f.estimate_batched(us, ts, precision=prec, refine_iters=refine_iters)
+        torch.cuda.synchronize(dev)
+        walls, devs = [], []
+        launches = 0
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            l0 = dpd.kernel_launches()
+            t0 = time.perf_counter()
+            e0.record()
+            hb, info = f.estimate_batched(us, ts, precision=prec, refine_iters=refine_iters)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            walls.append(time.perf_counter() - t0)
+            devs.append(e0.elapsed_time(e1) * 1e-3)
+            launches = dpd.kernel_launches() - l0
+        hb = hb.cpu().numpy()
+        errs = [float(np.linalg.norm(hb[i] - thetas[i]) / np.linalg.norm(thetas[i])) for i in range(nb)]
+        out[prec] = {"wall_ms": statistics.median(walls) * 1e3, "events_ms": statistics.median(devs) * 1e3,
+                     "library_launches": launches, "coef_rel_error_median": float(np.median(errs)),
+                     "not_spd": int(sum(1 for i in info if i))}
+    f.close()
+    g.close()
+    return out
+
+
 def measure_gram_one(dev, precision, reps=10):
     """The Gram contraction alone (dpd_gram: tensor or FP32 kernel, FP64
     reduction and assembly) of 2^22 rows x K = 97 (P = Q = 11, M = 7) in one
@@ -861,6 +914,7 @@ def measure_gram(dev, reps=5):
         us.append(ubd)
         ts.append(g.apply(ubd))
         thetas.append(thb)
+    us, ts = torch.stack(us), torch.stack(ts)   # equal lengths: one (problems x rows) tensor each
     useful_b = 8.0 * nb * nr * K * K
     batch_refine = 2
     out["batch_timing"] = (f"one estimate_batched call over all {nb} problems ((basis,) Gram, FP64 Cholesky, solve, "
@@ -1123,7 +1177,7 @@ def main():
               "gram_one": lambda d: measure_gram_one(d, args.gram_precision),
               "grad": lambda d: measure_grad(d, args.grad_log2n),
               "fma": lambda d: measure_fma_ceiling(d, gpu_index=local),
-              "estimate": measure_estimate}[args.pattern]
+              "estimate": measure_estimate, "estimate_batched": measure_estimate_batched}[args.pattern]
         print(json.dumps({"pattern": args.pattern, "result": fn(dev)}, default=float))
         return 0
     return run_ours(args, world, rank, local)

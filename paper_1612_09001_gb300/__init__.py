@@ -57,6 +57,32 @@ def _check_samples(t, name):
         raise ValueError(f"{name} must be contiguous")
 
 
+def _batch_pointers(xs, name):
+    """Device addresses (uint64) and lengths (int64) of a batch of sample
+    vectors given as a list of 1-D complex64 CUDA tensors, or as one contiguous
+    2-D tensor of equal-length problems (problems x samples; its rows are the
+    vectors).  Returns (addresses, lengths, device)."""
+    import numpy as np
+    import torch
+    if isinstance(xs, torch.Tensor):
+        _check_samples(xs, name)
+        if xs.dim() != 2 or xs.shape[0] < 1 or xs.shape[1] < 1:
+            raise ValueError(f"{name} must be a non-empty 2-D tensor (problems x samples) or a list of tensors")
+        cnt, n = xs.shape
+        addr = np.arange(cnt, dtype=np.uint64) * np.uint64(n * 8) + np.uint64(xs.data_ptr())
+        return addr, np.full(cnt, n, dtype=np.int64), xs.device
+    c64 = torch.complex64
+    addr, lens = [], []
+    for x in xs:   # one pass: the checks, the address and the length of each tensor
+        if not (isinstance(x, torch.Tensor) and x.dtype is c64 and x.is_cuda and x.is_contiguous()):
+            _check_samples(x, name)   # raises the specific error
+        addr.append(x.data_ptr())
+        lens.append(x.numel())
+    if not addr:
+        raise ValueError(f"{name} must not be empty")
+    return np.array(addr, dtype=np.uint64), np.array(lens, dtype=np.int64), xs[0].device
+
+
 class DPD:
     """One APH predistorter: orders P (main) and Q (conjugate), memory depth M."""
 
@@ -189,23 +215,22 @@ class DPD:
         return h, {"cond_est": stats[0], "rel_residual": stats[1]}
 
     def estimate_batched(self, us, ts, precision="tf32x3", refine_iters=2, stream=None, basis=None):
-        """Independent estimates for lists of (u, t); returns (count x K complex64 tensor, info list)."""
+        """Independent estimates of (u, t) pairs given as two lists of 1-D
+        tensors, or as two 2-D tensors of equal-length problems (problems x
+        samples); returns (count x K complex64 tensor, info list)."""
+        import numpy as np
         import torch
         if basis is not None:
             self.set_estimate_basis(basis)
-        if len(us) != len(ts) or not us:
-            raise ValueError("us and ts must be non-empty lists of the same length")
-        for u, t in zip(us, ts):
-            _check_samples(u, "u")
-            _check_samples(t, "t")
-        cnt = len(us)
-        up = (ctypes.c_void_p * cnt)(*[u.data_ptr() for u in us])
-        tp = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in ts])
-        ns = (ctypes.c_int64 * cnt)(*[u.numel() for u in us])
+        up, ns, dev = _batch_pointers(us, "u")
+        tp, nt, _ = _batch_pointers(ts, "t")
+        if len(up) != len(tp) or not np.array_equal(ns, nt):
+            raise ValueError("us and ts must hold the same number of problems, each t as long as its u")
+        cnt = len(up)
         info = (ctypes.c_int * cnt)()
-        h = torch.empty((cnt, self.K), dtype=torch.complex64, device=us[0].device)
-        rc = self._lib.dpd_estimate_batched(self._h, ctypes.cast(up, ctypes.c_void_p), ctypes.cast(tp, ctypes.c_void_p),
-                                            ctypes.cast(ns, ctypes.c_void_p), cnt, PRECISIONS[precision],
+        h = torch.empty((cnt, self.K), dtype=torch.complex64, device=dev)
+        rc = self._lib.dpd_estimate_batched(self._h, ctypes.c_void_p(up.ctypes.data), ctypes.c_void_p(tp.ctypes.data),
+                                            ctypes.c_void_p(ns.ctypes.data), cnt, PRECISIONS[precision],
                                             refine_iters, ctypes.c_void_p(h.data_ptr()), info, _stream_ptr(stream))
         if rc not in (0, 6):
             _lib.check("dpd_estimate_batched", rc)

@@ -353,11 +353,14 @@ dpd_status refine_batched(dpd_handle h, const std::vector<dpd::GramProblem> &pro
         w.bitems_cap = items.size();
     }
     for (int p = 0; p < count; ++p) adj[p].partials = w.bpart + (size_t)p * K;   // one row per problem
-    // The host vectors are copied before this function returns (synchronous copies).
-    if (cudaMemcpy(w.bstreams, st.data(), sizeof(dpd::BatchStream) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(w.bitems, items.data(), sizeof(dpd::BatchItem) * items.size(), cudaMemcpyHostToDevice) !=
+    // Stream-ordered uploads from pageable memory: the runtime stages the host
+    // data before each call returns (no device synchronisation), so the vectors
+    // may go out of scope and the host goes on enqueuing the launches.
+    if (cudaMemcpyAsync(w.bstreams, st.data(), sizeof(dpd::BatchStream) * count, cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
-        cudaMemcpy(w.badj, adj.data(), sizeof(dpd::AdjArgs) * count, cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpyAsync(w.bitems, items.data(), sizeof(dpd::BatchItem) * items.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(w.badj, adj.data(), sizeof(dpd::AdjArgs) * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return DPD_ERR_CUDA;
     dpd::BatchArgs ba;
     ba.streams = static_cast<const dpd::BatchStream *>(w.bstreams);
@@ -836,19 +839,23 @@ dpd_status dpd_estimate_batched(dpd_handle h, const void *const *u, const void *
     dpd_status st = reserve(h, count, cpp, nsamp);
     if (st != DPD_OK) return st;
     EstimateWorkspace &w = h->est;
-    if (cudaMemcpy(w.probs, probs.data(), sizeof(dpd::GramProblem) * count, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpyAsync(w.probs, probs.data(), sizeof(dpd::GramProblem) * count, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
         return DPD_ERR_CUDA;
     if (ortho(h) && (st = compute_basis(h, std::vector<int64_t>(n, n + count), s)) != DPD_OK) return st;
     if ((st = run_gram(h, count, cpp, precision, s)) != DPD_OK) return st;
     if (dpd::launch_chol(w.G, count, h->K, w.L, w.d, w.info, s) != cudaSuccess) return DPD_ERR_CUDA;
     w.use_inverse = false;
     if (dpd::launch_chol_solve(w.L, w.d, w.info, w.g, count, h->K, w.h64, 0, s) != cudaSuccess) return DPD_ERR_CUDA;
+    // The pivot status comes back here only for the refinement problem by
+    // problem, which skips problems that did not factor; refined together, the
+    // launches are queued behind the solve without a host round trip and the
+    // status is read at the end.
     std::vector<int> info((size_t)count);
-    if (cudaMemcpyAsync(info.data(), w.info, sizeof(int) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    if (!together && (cudaMemcpyAsync(info.data(), w.info, sizeof(int) * count, cudaMemcpyDeviceToHost, s) !=
+                          cudaSuccess ||
+                      cudaStreamSynchronize(s) != cudaSuccess))
         return DPD_ERR_CUDA;
-    bool any_bad = false;
-    for (int i = 0; i < count; ++i) any_bad |= info[i] != 0;
     if (together) {   // problems that did not factor keep unspecified coefficients
         if ((st = refine_batched(h, probs, nmax, refine_iters, s)) != DPD_OK) return st;
     } else {
@@ -860,7 +867,12 @@ dpd_status dpd_estimate_batched(dpd_handle h, const void *const *u, const void *
     const double2 *hm = monomial_h(h, 0, count, s, st);
     if (st != DPD_OK) return st;
     if (dpd::launch_h_to_f32(hm, count * h->K, static_cast<float2 *>(h_out), s) != cudaSuccess) return DPD_ERR_CUDA;
+    if (together &&
+        cudaMemcpyAsync(info.data(), w.info, sizeof(int) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return DPD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return DPD_ERR_CUDA;
+    bool any_bad = false;
+    for (int i = 0; i < count; ++i) any_bad |= info[i] != 0;
     if (info_out) std::copy(info.begin(), info.end(), info_out);
     return any_bad ? DPD_ERR_NOT_SPD : DPD_OK;
 }

@@ -215,8 +215,14 @@ __device__ __forceinline__ double rsqrt_newton(double x)
     return y;
 }
 
-// One CTA per problem: A = D G D in shared memory, factored in place (right
-// looking, lower triangle), written to L; d = diag(G)^{-1/2}.  On this GPU FP64
+// Offset of row i in a lower triangle packed by rows (row i holds columns
+// 0 .. i).  The batch kernels keep only that triangle in shared memory: 76 KB
+// at K = 97 instead of 150 KB for the full matrix, so that two CTAs share an SM
+// and a batch of more problems than SMs runs in one wave.
+__device__ __forceinline__ int tri_row(int i) { return i * (i + 1) / 2; }
+
+// One CTA per problem: A = D G D in shared memory (packed lower triangle),
+// factored in place (right looking), written to L; d = diag(G)^{-1/2}.  On this GPU FP64
 // runs at a small fraction of the FP32 rate (about two FMAs per clock per SM),
 // so the K^3/6 complex updates of one problem (K = 97: 0.6 M FP64 FMAs) and the
 // K sequential pivot steps bound the kernel: each complex update is four fused
@@ -228,7 +234,7 @@ __global__ void __launch_bounds__(256) chol_kernel(const double2 *__restrict__ G
                                                    double2 *__restrict__ Lall, double *__restrict__ dall,
                                                    int *__restrict__ info)
 {
-    extern __shared__ double2 A[];   // K x K
+    extern __shared__ double2 A[];   // lower triangle of K x K, packed by rows (tri_row)
     __shared__ double dsh[kMaxT * 12 + 1];
     __shared__ double rinv;
     __shared__ int bad;
@@ -247,17 +253,17 @@ __global__ void __launch_bounds__(256) chol_kernel(const double2 *__restrict__ G
         for (int k = tx; k <= i; k += 16) {
             const double2 v = G[(size_t)i * K + k];
             const double sc = dsh[i] * dsh[k];
-            A[(size_t)i * K + k] = make_double2(v.x * sc, v.y * sc);
+            A[tri_row(i) + k] = make_double2(v.x * sc, v.y * sc);
         }
     __syncthreads();
     for (int j = 0; j < K && !bad; ++j) {
         if (tid == 0) {
-            const double piv = A[(size_t)j * K + j].x;
+            const double piv = A[tri_row(j) + j].x;
             if (!(piv > 1e-30 && piv < 1e30)) {   // not positive definite (or numerically singular)
                 bad = j + 1;
             } else {
                 const double ri = rsqrt_newton(piv);
-                A[(size_t)j * K + j] = make_double2(piv * ri, 0.0);
+                A[tri_row(j) + j] = make_double2(piv * ri, 0.0);
                 rinv = ri;
             }
         }
@@ -265,8 +271,8 @@ __global__ void __launch_bounds__(256) chol_kernel(const double2 *__restrict__ G
         if (bad) break;
         const double ri = rinv;
         for (int i = j + 1 + tid; i < K; i += nt) {
-            const double2 v = A[(size_t)i * K + j];
-            A[(size_t)i * K + j] = make_double2(v.x * ri, v.y * ri);
+            const double2 v = A[tri_row(i) + j];
+            A[tri_row(i) + j] = make_double2(v.x * ri, v.y * ri);
         }
         __syncthreads();
         // A[i][k] -= L[i][j] conj(L[k][j]) over the m (m + 1) / 2 elements of the
@@ -285,19 +291,25 @@ __global__ void __launch_bounds__(256) chol_kernel(const double2 *__restrict__ G
                 while (r * (r + 1) / 2 > e) --r;
                 int c = e - r * (r + 1) / 2;
                 const int end = min(e + per, tot);
-                int i = j + 1 + r;
-                double2 a = A[(size_t)i * K + j];
+                int i = j + 1 + r, k = j + 1 + c;
+                int ib = tri_row(i), kb = tri_row(k);   // packed offsets of rows i and k
+                double2 a = A[ib + j];
                 for (; e < end; ++e) {
-                    const int k = j + 1 + c;
-                    const double2 b = A[(size_t)k * K + j];
-                    double2 &cc = A[(size_t)i * K + k];
+                    const double2 b = A[kb + j];
+                    double2 &cc = A[ib + k];
                     cc.x = fma(-a.x, b.x, fma(-a.y, b.y, cc.x));
                     cc.y = fma(-a.y, b.x, fma(a.x, b.y, cc.y));
                     if (++c > r) {   // next row of the triangle
                         c = 0;
                         ++r;
                         ++i;
-                        if (i < K) a = A[(size_t)i * K + j];
+                        ib += i;   // tri_row(i) = tri_row(i - 1) + i
+                        k = j + 1;
+                        kb = tri_row(k);
+                        if (i < K) a = A[ib + j];
+                    } else {
+                        ++k;
+                        kb += k;
                     }
                 }
             }
@@ -307,7 +319,7 @@ __global__ void __launch_bounds__(256) chol_kernel(const double2 *__restrict__ G
     double2 *L = Lall + (size_t)p * K * K;
     for (int e = tid; e < K * K; e += nt) {
         const int i = e / K, k = e % K;
-        L[e] = k <= i ? A[e] : make_double2(0.0, 0.0);
+        L[e] = k <= i ? A[tri_row(i) + k] : make_double2(0.0, 0.0);
     }
     for (int i = tid; i < K; i += nt) dall[(size_t)p * K + i] = dsh[i];
     if (tid == 0) info[p] = bad;
@@ -471,7 +483,7 @@ __global__ void __launch_bounds__(kCholClusterThreads) chol_cluster_kernel(const
 
 cudaError_t launch_chol(const double2 *G, int nprob, int K, double2 *L, double *d, int *info, cudaStream_t s)
 {
-    const size_t smem = sizeof(double2) * K * K;
+    const size_t smem = sizeof(double2) * (size_t)K * (K + 1) / 2;   // packed lower triangle
     if (nprob * kCholCluster <= 64 && K <= kCholMaxK) {
         // Few problems: a cluster of CTAs per problem (see chol_cluster_kernel).
         const size_t csmem = sizeof(double2) * (size_t)K * ((K + kCholCluster - 1) / kCholCluster);
@@ -521,7 +533,7 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restri
                                                          const double2 *__restrict__ rhs, int K,
                                                          double2 *__restrict__ h, int accumulate)
 {
-    extern __shared__ double2 Us[];   // K x K, strictly lower triangle used: U = L Lambda^{-1}
+    extern __shared__ double2 Us[];   // U = L Lambda^{-1}, lower triangle packed by rows (tri_row)
     __shared__ double inv[12 * kMaxT + 1];
     __shared__ double2 wv[12 * kMaxT + 1];
     const int p = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -536,11 +548,11 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restri
         wv[i] = make_double2(b[i].x * d[i], b[i].y * d[i]);
     }
     __syncthreads();
-    for (int e = tid; e < K * K; e += nt) {
-        const int i = e / K, k = e % K;
-        const double2 l = L[e];
-        Us[e] = k < i ? make_double2(l.x * inv[k], l.y * inv[k]) : make_double2(0.0, 0.0);
-    }
+    for (int i = warp; i < K; i += nt / 32)
+        for (int k = lane; k <= i; k += 32) {
+            const double2 l = L[(size_t)i * K + k];
+            Us[tri_row(i) + k] = k < i ? make_double2(l.x * inv[k], l.y * inv[k]) : make_double2(0.0, 0.0);
+        }
     __syncthreads();
 
     // forward: U y = D b
@@ -551,7 +563,7 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restri
             for (int i = 0; i < nb; ++i) {
                 const double2 vi = make_double2(__shfl_sync(0xffffffffu, v.x, i), __shfl_sync(0xffffffffu, v.y, i));
                 if (lane > i && lane < nb) {   // v -= U[b0+lane][b0+i] vi
-                    const double2 u = Us[(size_t)(b0 + lane) * K + b0 + i];
+                    const double2 u = Us[tri_row(b0 + lane) + b0 + i];
                     v.x = fma(-u.x, vi.x, fma(u.y, vi.y, v.x));
                     v.y = fma(-u.x, vi.y, fma(-u.y, vi.x, v.y));
                 }
@@ -564,7 +576,7 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restri
             double2 acc = make_double2(0.0, 0.0);
             if (r < K)
                 for (int c = sub; c < nb; c += 8) {
-                    const double2 u = Us[(size_t)r * K + b0 + c], v = wv[b0 + c];
+                    const double2 u = Us[tri_row(r) + b0 + c], v = wv[b0 + c];
                     acc.x = fma(u.x, v.x, fma(-u.y, v.y, acc.x));
                     acc.y = fma(u.x, v.y, fma(u.y, v.x, acc.y));
                 }
@@ -590,7 +602,7 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restri
             for (int i = nb - 1; i >= 0; --i) {
                 const double2 vi = make_double2(__shfl_sync(0xffffffffu, v.x, i), __shfl_sync(0xffffffffu, v.y, i));
                 if (lane < i) {   // v -= conj(U[b0+i][b0+lane]) vi
-                    const double2 u = Us[(size_t)(b0 + i) * K + b0 + lane];
+                    const double2 u = Us[tri_row(b0 + i) + b0 + lane];
                     v.x = fma(-u.x, vi.x, fma(-u.y, vi.y, v.x));
                     v.y = fma(-u.x, vi.y, fma(u.y, vi.x, v.y));
                 }
@@ -603,7 +615,7 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restri
             double2 acc = make_double2(0.0, 0.0);
             if (r < b0)
                 for (int c = sub; c < nb; c += 8) {
-                    const double2 u = Us[(size_t)(b0 + c) * K + r], v = wv[b0 + c];
+                    const double2 u = Us[tri_row(b0 + c) + r], v = wv[b0 + c];
                     acc.x = fma(u.x, v.x, fma(u.y, v.y, acc.x));
                     acc.y = fma(u.x, v.y, fma(-u.y, v.x, acc.y));
                 }
@@ -629,7 +641,7 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double2 *__restri
 cudaError_t launch_chol_solve(const double2 *L, const double *d, const int *info, const double2 *rhs, int nprob,
                               int K, double2 *h, int accumulate, cudaStream_t s)
 {
-    const size_t smem = sizeof(double2) * K * K;
+    const size_t smem = sizeof(double2) * (size_t)K * (K + 1) / 2;   // packed lower triangle
     static SmemAttr smem_rec;
     const cudaError_t e = ensure_smem(smem_rec, (const void *)chol_solve_kernel, smem);
     if (e != cudaSuccess) return e;

@@ -228,3 +228,26 @@ def test_estimate_residual_statistic_against_oracle(n, aligned):
     assert ref > 1e-3
     assert abs(st["rel_residual"] - ref) <= 1e-4 * ref, (st["rel_residual"], ref)
     f.close()
+
+
+def test_estimate_batched_accepts_a_2d_batch():
+    """Equal-length problems as two 2-D tensors (problems x samples) and as the
+    lists of their rows reach the library at the same device addresses: the
+    estimates agree bit for bit, each matches the FP64 oracle's LS solution
+    (Sec. 2.2), and a t shorter than its u is refused."""
+    P, Q, M, n = 5, 3, 4, 4000
+    probs = [_ls_problem(P, Q, M, n, 200 + i) for i in range(4)]
+    U = torch.stack([torch.from_numpy(u) for u, _, _ in probs]).cuda()
+    T = torch.stack([torch.from_numpy(t) for _, t, _ in probs]).cuda()
+    f = dpd.DPD(P, Q, M)
+    h2, info2 = f.estimate_batched(U, T, precision="tf32x3", refine_iters=2)
+    hl, infol = f.estimate_batched(list(U), list(T), precision="tf32x3", refine_iters=2)
+    assert info2 == infol == [0] * len(probs)
+    assert torch.equal(h2, hl)
+    for i, (u, t, _) in enumerate(probs):
+        ref = oracle.ls(u, t, P, Q, M)
+        e = np.linalg.norm(h2[i].cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref)
+        assert e <= 1e-4, (i, e)
+    with pytest.raises(ValueError):
+        f.estimate_batched([U[0]], [T[0][:-1]])
+    f.close()
