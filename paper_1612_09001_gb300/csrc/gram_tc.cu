@@ -597,9 +597,18 @@ __global__ void __launch_bounds__(256) gram_lag_assemble_kernel(const double *__
         }
     }
     __syncthreads();
-    // <x, y> for two signed distinct-column references
-    auto dot = [&](ColRef x, ColRef y) -> double {
-        if (x.sign == 0 || y.sign == 0) return 0.0;
+    // <x, y> for two signed distinct-column references, as the pair (lag sum,
+    // end products): <x, y> = c - t.  The entries of G and g add two such
+    // values; their lag sums are added in FP64 and their end products in FP32
+    // (at most 2 (T - 1) products of the last samples), so that each component
+    // costs one FP64 addition, one conversion and one FP64 subtraction (FP64 on
+    // this GPU is a small fraction of the FP32 rate).
+    struct Pair {
+        double c;
+        float t;
+    };
+    auto dot = [&](ColRef x, ColRef y) -> Pair {
+        if (x.sign == 0 || y.sign == 0) return {0.0, 0.f};
         int sa = src[x.d].x, ma = src[x.d].y, sb = src[y.d].x, mb = src[y.d].y;
         // (sa, ma): the larger tap; at equal taps the constant on the A side
         if (mb > ma || (mb == ma && sb == kLagSerOne)) {
@@ -610,26 +619,28 @@ __global__ void __launch_bounds__(256) gram_lag_assemble_kernel(const double *__
             mb = m0;
         }
         const int dl = ma - mb;
-        double v;
+        double c = 0.0;
+        float tl = 0.f;
         if ((int64_t)ma >= N) {
-            v = 0.0;   // column (sa, ma) is zero on every row
+            // column (sa, ma) is zero on every row
         } else if (sb == kLagSerOne) {
             // against the constant at tap 0: sum_{k < N - ma} x_sa(k) = C[one][sa][0] less the last ma samples
             if (sa == kLagSerOne) {
-                v = (double)N;
+                c = (double)N;
             } else {
-                float tl = 0.f;
                 for (int k = 0; k < ma; ++k) tl += xt[sa][kMaxT - 1 - k];
-                v = C[(kLagSerOne * kLagSigB + sa) * kMaxT] - (double)tl;
+                c = C[(kLagSerOne * kLagSigB + sa) * kMaxT];
             }
         } else {
             // samples N - ma .. N - 1 - dl: xt index k = sample - (N - 8)
-            float tl = 0.f;
             for (int k = kMaxT - ma; k <= kMaxT - 1 - dl; ++k) tl = fmaf(xt[sa][k], xt[sb][k + dl], tl);
-            v = C[(sa * kLagSigB + sb) * kMaxT + dl] - (double)tl;
+            c = C[(sa * kLagSigB + sb) * kMaxT + dl];
         }
-        return x.sign * y.sign > 0 ? v : -v;
+        return x.sign * y.sign > 0 ? Pair{c, tl} : Pair{-c, -tl};
     };
+    // x + y and x - y of two such values
+    auto sum = [](Pair x, Pair y) { return (x.c + y.c) - (double)(x.t + y.t); };
+    auto diff = [](Pair x, Pair y) { return (x.c - y.c) - (double)(x.t - y.t); };
     const int idx = blockIdx.x * blockDim.x + tid;
     const ColRef tre{2 * B * T + 1, 1}, tim{2 * B * T + 2, 1};
     if (idx < K * K) {
@@ -637,14 +648,14 @@ __global__ void __launch_bounds__(256) gram_lag_assemble_kernel(const double *__
         ColRef ar, ai, br, bi;
         psi_column_refs(a, K, Bp, B, T, ar, ai);
         psi_column_refs(b, K, Bp, B, T, br, bi);
-        G[(size_t)p * K * K + idx] = make_double2(dot(ar, br) + dot(ai, bi), dot(ar, bi) - dot(ai, br));
+        G[(size_t)p * K * K + idx] = make_double2(sum(dot(ar, br), dot(ai, bi)), diff(dot(ar, bi), dot(ai, br)));
     } else if (idx < K * K + K) {
         const int a = idx - K * K;
         ColRef ar, ai;
         psi_column_refs(a, K, Bp, B, T, ar, ai);
-        if (g) g[(size_t)p * K + a] = make_double2(dot(ar, tre) + dot(ai, tim), dot(ar, tim) - dot(ai, tre));
+        if (g) g[(size_t)p * K + a] = make_double2(sum(dot(ar, tre), dot(ai, tim)), diff(dot(ar, tim), dot(ai, tre)));
     } else if (idx == K * K + K) {
-        if (tt) tt[p] = dot(tre, tre) + dot(tim, tim);
+        if (tt) tt[p] = sum(dot(tre, tre), dot(tim, tim));
     }
 }
 
