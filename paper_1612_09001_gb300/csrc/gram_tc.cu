@@ -487,7 +487,7 @@ size_t gram_lag_smem(int fmt)
 }
 
 // ---- finishing: partial lag sums -> S
-// C[p][e] = sum over the problem's CTAs of the partial pairs, in FP64 and a fixed order.
+// C[p][e] = sum over the problem's CTAs of the partial pairs, in a fixed order (FP32 pairs, then FP64).
 __global__ void __launch_bounds__(256) gram_lag_reduce_kernel(const float2 *__restrict__ partials, int cpp,
                                                               double *__restrict__ C)
 {
@@ -496,21 +496,23 @@ __global__ void __launch_bounds__(256) gram_lag_reduce_kernel(const float2 *__re
     const int e = blockIdx.x * 32 + lane;
     double s = 0.0;
     if (e < kLagEntries) {
+        // The partials are FP32 (sum, error) pairs; they are added as pairs in
+        // FP32 (about 2^-48 relative) and each thread's total becomes FP64 once:
+        // FP64 additions and conversions per partial (a small fraction of the
+        // FP32 rate on this GPU) bound this kernel before.
         const float2 *base = partials + (size_t)p * cpp * kLagEntries + e;
-        auto val = [&](int k) {
-            const float2 v = base[(size_t)k * kLagEntries];
-            return (double)v.x + (double)v.y;
-        };
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // partials g, g + 8, g + 16, g + 24, g + 32, ...
+        auto val = [&](int k) { return base[(size_t)k * kLagEntries]; };
+        float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;   // partials g, g + 8, g + 16, g + 24, ...
         int k = g;
         for (; k + 24 < cpp; k += 32) {
-            s0 += val(k);
-            s1 += val(k + 8);
-            s2 += val(k + 16);
-            s3 += val(k + 24);
+            s0 = pair_add(s0, val(k));
+            s1 = pair_add(s1, val(k + 8));
+            s2 = pair_add(s2, val(k + 16));
+            s3 = pair_add(s3, val(k + 24));
         }
-        for (; k < cpp; k += 8) s0 += val(k);
-        s = (s0 + s1) + (s2 + s3);
+        for (; k < cpp; k += 8) s0 = pair_add(s0, val(k));
+        const float2 t = pair_add(pair_add(s0, s1), pair_add(s2, s3));
+        s = (double)t.x + (double)t.y;
     }
     grp[g][lane] = s;
     __syncthreads();
